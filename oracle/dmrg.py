@@ -1,0 +1,80 @@
+"""Two-site spin-adapted DMRG sweep for the oracle (plain dense algebra).
+
+Each micro-iteration follows Secs. 2.3, 2.4 and 3.4:
+  x = Eq. 25 from T[i] T[i+1]  ->  H_eff x = lambda x (Eq. 9) with H_eff = P^T H P,
+  its plain definition (P: reduced two-site basis -> determinants, H: Sec. 4.1)
+  ->  Eqs. 26-28 block SVD and truncation to D  ->  new T[i], T[i+1].
+A macro-iteration is a sweep to the right followed by a sweep to the left (Sec. 4.2);
+Solve reports the minimum energy over all micro-iterations (Sec. 4.3).
+The lowest eigenpair of the dense H_eff is taken from numpy.linalg.eigh.
+"""
+import numpy as np
+from .fci import FCISpace
+from .mps import TwoSiteProjector, tt_to_x, svd_truncate
+
+
+class Problem:
+    def __init__(self, h, V, irreps, N, two_S, I_G, ecore=0.0):
+        self.h, self.V = np.asarray(h, float), np.asarray(V, float)
+        self.irreps, self.N, self.two_S, self.I_G = list(irreps), N, two_S, I_G
+        self.ecore = ecore
+        self.L = len(irreps)
+        self.spaces, self.idx, self.H = [], [], []
+        for f in range(two_S + 1):
+            tm = 2 * f - two_S
+            na, nb = (N + tm) // 2, (N - tm) // 2
+            sp = FCISpace(self.L, na, nb, irreps, I_G)
+            idx = np.flatnonzero(sp.mask.ravel())
+            self.spaces.append(sp)
+            self.idx.append(idx)
+            self.H.append(sp.hamiltonian_matrix(self.h, self.V, idx, ecore))
+
+
+def effective_hamiltonian(prob, m, i):
+    """Dense H_eff for sites (i, i+1) and the projector used to build it."""
+    proj = TwoSiteProjector(m, i, prob.spaces)
+    H = np.zeros((proj.n, proj.n))
+    G = np.zeros((proj.n, proj.n))
+    for f, P in enumerate(proj.P):
+        Pr = P[prob.idx[f]]
+        H += Pr.T @ (prob.H[f] @ Pr)
+        G += Pr.T @ Pr
+    return 0.5 * (H + H.T), G, proj
+
+
+def matvec(prob, m, i, x):
+    H, _, proj = effective_hamiltonian(prob, m, i)
+    v = proj.flatten(x)
+    return proj.unflatten(H @ v)
+
+
+def micro_iteration(prob, m, i, D, direction, noise=0.0, noise_values=None, w_prev=0.0):
+    H, _, proj = effective_hamiltonian(prob, m, i)
+    w, U = np.linalg.eigh(H)
+    e = float(w[0])
+    v = U[:, 0]
+    x0 = proj.flatten(tt_to_x(m, i))
+    if np.dot(v, x0) < 0:
+        v = -v
+    if noise > 0.0 and noise_values is not None:
+        v = v + 0.5 * noise * w_prev * np.asarray(noise_values[:v.size])
+        v = v / np.linalg.norm(v)
+    w_disc, _, _ = svd_truncate(m, i, proj.unflatten(v), D, direction)
+    return e, w_disc
+
+
+def sweep(prob, m, D, n_macro, log=None):
+    """Right sweep then left sweep per macro-iteration; returns (min energy, list of
+    per-micro-iteration energies)."""
+    energies = []
+    L = m.L
+    for it in range(n_macro):
+        for i in range(0, L - 1):
+            e, wd = micro_iteration(prob, m, i, D, "right")
+            energies.append(e)
+        for i in range(L - 2, -1, -1):
+            e, wd = micro_iteration(prob, m, i, D, "left")
+            energies.append(e)
+        if log is not None:
+            log(it, energies[-1])
+    return min(energies), energies
