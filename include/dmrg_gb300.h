@@ -1,0 +1,151 @@
+/* C ABI of the GB300 spin-adapted two-site DMRG library (libdmrg_gb300.so).
+ *
+ * The calls follow the paper's statement of the problem (Wouters, Poelmans, Ayers,
+ * Van Neck, "CheMPS2", Sec. 4): a Hamiltonian given by E_const, one-body h_ij and
+ * two-body V_ijkl in physics notation (Sec. 4.1), the target spin, particle number and
+ * point-group irrep (Sec. 4.1 "Problem"), a convergence scheme of (D, E_conv, N_max,
+ * gamma_noise) instructions (Sec. 4.2) and the two-site sweep (Secs. 2.3-2.4, 3.3-3.4).
+ *
+ * Conventions shared by every call:
+ *  - Spins are passed doubled (two_S = 2S, tj = 2j).  Irreps are 0..7 of a real
+ *    abelian group with XOR as product; the group index is 0=C1 1=Ci 2=C2 3=Cs 4=D2
+ *    5=C2v 6=C2h 7=D2h (Sec. 3.1) and fixes how many irreps are valid (1, 2, 2, 2, 4,
+ *    4, 4, 8).
+ *  - Matrices are row-major float64.  The caller owns every pointer it passes; the
+ *    library copies what it keeps.
+ *  - "site i" of the two-site probes means orbitals i and i+1 (0-based), 0 <= i <= L-2.
+ *    Probes use the MPS as it is: it must be left-normalised left of i and
+ *    right-normalised right of i+1 (Eqs. 5-6), as after dmrg_set_mps of such an MPS or
+ *    inside a sweep.
+ *  - The two-site vector x holds, block by block, x = sqrt(2 jR + 1) * S with S the
+ *    reduced two-site object of Eq. 25; its Euclidean norm is the norm of the state,
+ *    so H_eff is symmetric.  dmrg_two_site_layout gives the block table.
+ *  - stream == 0: x / y / d are HOST pointers.  stream != 0: they are DEVICE pointers
+ *    (cudaStream_t cast to uintptr_t); the call first waits for work queued on that
+ *    stream and returns after its own device work has finished.
+ *  - Return 0 on success or a negative DMRG_E* code; dmrg_last_error(ctx) then holds a
+ *    message.  No exception crosses the ABI.  A context is single-threaded.
+ */
+#ifndef DMRG_GB300_H
+#define DMRG_GB300_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DMRG_OK 0
+#define DMRG_EINVAL -1   /* invalid argument (size, N/S/irrep, state of the context) */
+#define DMRG_ESYMM -2    /* integrals violate eightfold or point-group symmetry */
+#define DMRG_ENOTCONV -3 /* Davidson reached its iteration cap; outputs hold the best */
+#define DMRG_ENOMEM -4   /* host or device allocation failed */
+#define DMRG_ECUDA -5    /* a CUDA call failed */
+#define DMRG_EINTERNAL -6
+
+typedef struct dmrg_ctx dmrg_ctx;
+
+typedef struct {
+  int64_t matvecs;         /* H_eff applications since creation */
+  int64_t davidson_iters;
+  int64_t micro_iters;     /* two-site optimisation steps */
+  double matvec_flops;     /* planner-counted flops of all matvecs (nonzero blocks) */
+  double last_matvec_flops;
+  int64_t last_matvec_tasks;
+  double t_update_ms, t_trunc_ms, t_plan_ms, t_total_ms; /* host wall clock */
+  double last_w_disc, max_w_disc;                          /* Eq. 15 */
+  /* device time (CUDA events) and flops of the two matvec kernels: phase 1 applies
+   * the right-block operators (x D^T), phase 2 the left-block ones (sum c C Z) */
+  double k_phase1_ms, k_phase2_ms;
+  int64_t k_launches;
+  double k_phase1_flops, k_phase2_flops;
+} dmrg_stats_t;
+
+/* Sec. 4.1: L orbitals with irreps orb_irrep[L], N electrons (2 <= N <= 2L, needed by
+ * the one-body folding of Eq. 11), spin two_S, target irrep.  precision: 0 = FP64 block
+ * products (only value accepted).  *out receives a new context (free with
+ * dmrg_destroy).  Errors: DMRG_EINVAL. */
+int dmrg_create(dmrg_ctx** out, int L, int group, const int* orb_irrep, int N, int two_S,
+                int target_irrep, int precision);
+
+/* Sec. 4.1 setEconst / setTmat / setVmat: h is L*L, V is L^4 with V[((i*L+j)*L+k)*L+l] =
+ * (ij|V|kl).  h must be symmetric and V eightfold symmetric; both must respect the
+ * point group (DMRG_ESYMM otherwise).  Host pointers, copied. */
+int dmrg_set_integrals(dmrg_ctx* ctx, double econst, const double* h, const double* V);
+
+/* Sec. 4.2 ConvergenceScheme: n instructions (D, E_conv, N_max, gamma_noise); noise
+ * uniform in +-0.5 gamma w_disc(previous half sweep) is added to x before the
+ * decomposition.  Davidson stops at ||r||_2 <= davidson_tol or davidson_max_iter. */
+int dmrg_set_schedule(dmrg_ctx* ctx, int n, const int* D, const double* e_conv,
+                      const int* n_max, const double* noise, double davidson_tol,
+                      int davidson_max_iter);
+
+/* Sec. 4.3: new MPS with the first instruction's D spread equally over the sectors of
+ * every bond (capped by the FCI dimension) and filled with uniform(-1,1) numbers from
+ * splitmix64 seeded with `seed` (site by site, block by block, row-major). */
+int dmrg_init_mps(dmrg_ctx* ctx, uint64_t seed);
+
+/* Serialised MPS (the reduced tensors of Eq. 22).  Layout, little-endian:
+ * int32 magic 0x444D5247, version 1, L, N, two_S, irrep; for each bond 0..L: int32
+ * n_sectors then n_sectors x int32 (2j, N, irrep, dim); for each site 0..L-1: int32
+ * n_blocks then per block int32 (local state 0|1|2, left sector index, right sector
+ * index) followed by dL*dR float64 row-major.  dmrg_get_mps: call with buf == NULL to
+ * get the size in *len.  dmrg_set_mps replaces the MPS (DMRG_EINVAL on a malformed or
+ * symmetry-violating buffer). */
+int dmrg_get_mps(dmrg_ctx* ctx, void* buf, size_t* len);
+int dmrg_set_mps(dmrg_ctx* ctx, const void* buf, size_t len);
+
+/* Brings the MPS to mixed canonical form around sites (center, center+1) (Sec. 2.2,
+ * Eqs. 5-6) by exact decompositions (Eqs. 25-28 keeping every nonzero singular value);
+ * the state is unchanged up to normalisation. */
+int dmrg_canonicalize(dmrg_ctx* ctx, int center);
+
+/* Sec. 4.3 Solve: right-normalises the MPS, then runs the convergence scheme with
+ * macro-iterations of one sweep to the right and one to the left.  *e_min = the lowest
+ * energy of all micro-iterations (including E_const), *e_last = the last one. */
+int dmrg_solve(dmrg_ctx* ctx, double* e_min, double* e_last);
+
+/* Block table of x for sites (site, site+1): n_blocks rows of 12 int64 (2jL, NL, IL,
+ * s1, s2, 2j, 2jR, NR, IR, dL, dR, offset) with s1, s2 the local states 0|1|2 and the
+ * block stored row-major at x + offset.  table may be NULL (sizes only). */
+int dmrg_two_site_layout(dmrg_ctx* ctx, int site, int64_t* n_elem, int* n_blocks,
+                         int64_t* table);
+
+/* Eq. 25 from the current T[site], T[site+1] (x as above). */
+int dmrg_tt_to_x(dmrg_ctx* ctx, int site, double* x, uintptr_t stream);
+
+/* y = H_eff x (Eq. 9) with the renormalised and complementary operators of Sec. 2.5. */
+int dmrg_heff_matvec(dmrg_ctx* ctx, int site, const double* x, double* y, uintptr_t stream);
+
+/* d = diagonal of H_eff (the Davidson preconditioner). */
+int dmrg_heff_diag(dmrg_ctx* ctx, int site, double* d, uintptr_t stream);
+
+/* Davidson's lowest eigenpair of H_eff started from x (overwritten with the Ritz
+ * vector, norm 1); *energy excludes E_const.  DMRG_ENOTCONV if the cap was hit. */
+int dmrg_davidson(dmrg_ctx* ctx, int site, double* x, uintptr_t stream, double* energy,
+                  int* iters);
+
+/* Eqs. 26-28: decompose x, keep the D largest reduced singular values and write
+ * T[site], T[site+1] (dir = +1: A[site] = U, A[site+1] = kappa V; dir = -1:
+ * A[site] = U kappa, A[site+1] = V).  noise (>= 0) adds uniform(-noise, noise) to x
+ * first.  *w_disc = discarded weight (Eq. 15). */
+int dmrg_truncate(dmrg_ctx* ctx, int site, int dir, int D, double noise, const double* x,
+                  uintptr_t stream, double* w_disc);
+
+/* One micro-iteration of a sweep (Secs. 2.3-2.5, 3.4): Eq. 25 from T[site], T[site+1],
+ * Davidson with the scheme's tolerance and cap, noise gamma * 0.5 * w_disc(previous
+ * half sweep), Eqs. 26-28 to D, and the renormalised / complementary operator update
+ * for the next site in direction dir (+1 right, -1 left).  Outputs: energy (with
+ * E_const), discarded weight, Davidson iterations.  DMRG_ENOTCONV if Davidson hit the
+ * cap (the step is still completed). */
+int dmrg_sweep_step(dmrg_ctx* ctx, int site, int dir, int D, double gamma, double* energy,
+                    double* w_disc, int* iters);
+
+int dmrg_stats(dmrg_ctx* ctx, dmrg_stats_t* out);
+const char* dmrg_last_error(dmrg_ctx* ctx);
+void dmrg_destroy(dmrg_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,355 @@
+// extern "C" boundary: argument checks, host/device pointer handling, error codes.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <stdexcept>
+#include <string>
+
+#include "../../include/dmrg_gb300.h"
+#include "engine.hpp"
+
+struct dmrg_ctx {
+  dmrg::Engine* eng = nullptr;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  int L = 0;
+};
+
+namespace {
+
+const int kGroupOrder[8] = {1, 2, 2, 2, 4, 4, 4, 8};
+
+template <class F>
+int guard(dmrg_ctx* c, F&& f) {
+  if (!c) return DMRG_EINVAL;
+  try {
+    c->err.clear();
+    return f();
+  } catch (const std::bad_alloc& e) {
+    c->err = std::string("allocation failed: ") + e.what();
+    return DMRG_ENOMEM;
+  } catch (const std::domain_error& e) {
+    c->err = e.what();
+    return DMRG_ESYMM;
+  } catch (const std::invalid_argument& e) {
+    c->err = e.what();
+    return DMRG_EINVAL;
+  } catch (const std::out_of_range& e) {
+    c->err = e.what();
+    return DMRG_EINVAL;
+  } catch (const std::runtime_error& e) {
+    c->err = e.what();
+    std::string m = e.what();
+    if (m.find("out of memory") != std::string::npos) return DMRG_ENOMEM;
+    return m.find("cuda") != std::string::npos || m.find("launch") != std::string::npos ||
+                   m.find("Async") != std::string::npos || m.find("sync") != std::string::npos
+               ? DMRG_ECUDA
+               : DMRG_EINTERNAL;
+  } catch (...) {
+    c->err = "unknown failure";
+    return DMRG_EINTERNAL;
+  }
+}
+
+// Runs f(dev_in_or_out...) with device buffers: for host pointers, copies in/out.
+struct DevBuf {
+  double* p = nullptr;
+  dmrg::Stream s;
+  DevBuf(int64_t n, dmrg::Stream st) : s(st) { p = (double*)dmrg::dev_alloc(sizeof(double) * (n > 0 ? n : 1), st); }
+  ~DevBuf() { try { dmrg::dev_free(p, s); } catch (...) {} }
+};
+
+// The context's stream is created at the first call that touches the device, so that
+// problem setup and its validation work without a GPU.
+dmrg::Stream dev_stream(dmrg_ctx* c) {
+  if (!c->stream) {
+    cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) throw std::runtime_error(std::string("cuda stream: ") + cudaGetErrorString(e));
+    c->eng->set_stream((dmrg::Stream)c->stream);
+  }
+  return (dmrg::Stream)c->stream;
+}
+
+void wait_user(uintptr_t stream) {
+  if (stream) {
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) throw std::runtime_error(std::string("cuda user stream: ") + cudaGetErrorString(e));
+  }
+}
+
+dmrg::Stream dev_stream(dmrg_ctx* c);
+int64_t xsize(dmrg_ctx* c, int site) {
+  std::vector<int64_t> t;
+  int64_t n = 0;
+  c->eng->layout(site, t, n);
+  return n;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dmrg_create(dmrg_ctx** out, int L, int group, const int* orb_irrep, int N, int two_S,
+                int target_irrep, int precision) {
+  if (!out) return DMRG_EINVAL;
+  *out = nullptr;
+  if (L < 2 || L > 120 || group < 0 || group > 7 || !orb_irrep) return DMRG_EINVAL;
+  const int nir = kGroupOrder[group];
+  for (int i = 0; i < L; ++i)
+    if (orb_irrep[i] < 0 || orb_irrep[i] >= nir) return DMRG_EINVAL;
+  if (N < 2 || N > 2 * L || two_S < 0 || two_S > N || two_S > 2 * L - N || ((N - two_S) & 1))
+    return DMRG_EINVAL;
+  if (target_irrep < 0 || target_irrep >= nir) return DMRG_EINVAL;
+  if (precision != 0) return DMRG_EINVAL;
+  dmrg_ctx* c = new (std::nothrow) dmrg_ctx;
+  if (!c) return DMRG_ENOMEM;
+  try {
+    std::vector<int> ir(orb_irrep, orb_irrep + L);
+    c->eng = new dmrg::Engine(L, nir, ir, N, two_S, target_irrep, nullptr);
+    c->L = L;
+  } catch (...) {
+    delete c;
+    return DMRG_ENOMEM;
+  }
+  *out = c;
+  return DMRG_OK;
+}
+
+int dmrg_set_integrals(dmrg_ctx* c, double econst, const double* h, const double* V) {
+  return guard(c, [&] {
+    if (!h || !V || !std::isfinite(econst)) return DMRG_EINVAL;
+    c->eng->set_integrals(econst, h, V);
+    return DMRG_OK;
+  });
+}
+
+int dmrg_set_schedule(dmrg_ctx* c, int n, const int* D, const double* e_conv, const int* n_max,
+                      const double* noise, double davidson_tol, int davidson_max_iter) {
+  return guard(c, [&] {
+    if (n < 1 || !D || !e_conv || !n_max || !noise || !(davidson_tol > 0) || davidson_max_iter < 1)
+      return DMRG_EINVAL;
+    for (int i = 0; i < n; ++i)
+      if (D[i] < 1 || n_max[i] < 0 || noise[i] < 0 || !(e_conv[i] >= 0)) return DMRG_EINVAL;
+    c->eng->set_schedule(std::vector<int>(D, D + n), std::vector<double>(e_conv, e_conv + n),
+                         std::vector<int>(n_max, n_max + n), std::vector<double>(noise, noise + n),
+                         davidson_tol, davidson_max_iter);
+    return DMRG_OK;
+  });
+}
+
+int dmrg_init_mps(dmrg_ctx* c, uint64_t seed) {
+  return guard(c, [&] {
+    dev_stream(c);
+    c->eng->init_mps(seed);
+    return DMRG_OK;
+  });
+}
+
+int dmrg_get_mps(dmrg_ctx* c, void* buf, size_t* len) {
+  return guard(c, [&] {
+    if (!len) return DMRG_EINVAL;
+    dev_stream(c);
+    auto v = c->eng->get_mps();
+    if (!buf) { *len = v.size(); return DMRG_OK; }
+    if (*len < v.size()) { *len = v.size(); return DMRG_EINVAL; }
+    std::memcpy(buf, v.data(), v.size());
+    *len = v.size();
+    return DMRG_OK;
+  });
+}
+
+int dmrg_set_mps(dmrg_ctx* c, const void* buf, size_t len) {
+  return guard(c, [&] {
+    if (!buf) return DMRG_EINVAL;
+    dev_stream(c);
+    c->eng->set_mps((const char*)buf, len);
+    return DMRG_OK;
+  });
+}
+
+int dmrg_canonicalize(dmrg_ctx* c, int center) {
+  return guard(c, [&] {
+    dmrg::Stream s = dev_stream(c);
+    c->eng->canonicalize(center);
+    dmrg::dev_sync(s);
+    return DMRG_OK;
+  });
+}
+
+int dmrg_solve(dmrg_ctx* c, double* e_min, double* e_last) {
+  return guard(c, [&] {
+    double el = 0.0;
+    dev_stream(c);
+    double em = c->eng->solve(&el);
+    if (e_min) *e_min = em;
+    if (e_last) *e_last = el;
+    return DMRG_OK;
+  });
+}
+
+int dmrg_two_site_layout(dmrg_ctx* c, int site, int64_t* n_elem, int* n_blocks, int64_t* table) {
+  return guard(c, [&] {
+    std::vector<int64_t> t;
+    int64_t n = 0;
+    dev_stream(c);
+    c->eng->layout(site, t, n);
+    if (n_elem) *n_elem = n;
+    if (n_blocks) *n_blocks = (int)(t.size() / 12);
+    if (table) std::memcpy(table, t.data(), t.size() * sizeof(int64_t));
+    return DMRG_OK;
+  });
+}
+
+int dmrg_tt_to_x(dmrg_ctx* c, int site, double* x, uintptr_t stream) {
+  return guard(c, [&] {
+    if (!x) return DMRG_EINVAL;
+    wait_user(stream);
+    const int64_t n = xsize(c, site);
+    dmrg::Stream s = dev_stream(c);
+    if (stream) {
+      c->eng->tt_to_x(site, x);
+    } else {
+      DevBuf d(n, s);
+      c->eng->tt_to_x(site, d.p);
+      dmrg::dev_d2h(x, d.p, sizeof(double) * n, s);
+    }
+    dmrg::dev_sync(s);
+    return DMRG_OK;
+  });
+}
+
+int dmrg_heff_matvec(dmrg_ctx* c, int site, const double* x, double* y, uintptr_t stream) {
+  return guard(c, [&] {
+    if (!x || !y) return DMRG_EINVAL;
+    wait_user(stream);
+    const int64_t n = xsize(c, site);
+    dmrg::Stream s = dev_stream(c);
+    if (stream) {
+      c->eng->matvec(site, x, y);
+    } else {
+      DevBuf dx(n, s), dy(n, s);
+      dmrg::dev_h2d(dx.p, x, sizeof(double) * n, s);
+      c->eng->matvec(site, dx.p, dy.p);
+      dmrg::dev_d2h(y, dy.p, sizeof(double) * n, s);
+    }
+    dmrg::dev_sync(s);
+    return DMRG_OK;
+  });
+}
+
+int dmrg_heff_diag(dmrg_ctx* c, int site, double* d, uintptr_t stream) {
+  return guard(c, [&] {
+    if (!d) return DMRG_EINVAL;
+    wait_user(stream);
+    const int64_t n = xsize(c, site);
+    dmrg::Stream s = dev_stream(c);
+    if (stream) {
+      c->eng->diag(site, d);
+    } else {
+      DevBuf dd(n, s);
+      c->eng->diag(site, dd.p);
+      dmrg::dev_d2h(d, dd.p, sizeof(double) * n, s);
+    }
+    dmrg::dev_sync(s);
+    return DMRG_OK;
+  });
+}
+
+int dmrg_davidson(dmrg_ctx* c, int site, double* x, uintptr_t stream, double* energy, int* iters) {
+  return guard(c, [&] {
+    if (!x) return DMRG_EINVAL;
+    wait_user(stream);
+    const int64_t n = xsize(c, site);
+    dmrg::Stream s = dev_stream(c);
+    int it = 0;
+    bool conv = false;
+    double e;
+    if (stream) {
+      e = c->eng->davidson(site, x, &it, &conv);
+    } else {
+      DevBuf dx(n, s);
+      dmrg::dev_h2d(dx.p, x, sizeof(double) * n, s);
+      e = c->eng->davidson(site, dx.p, &it, &conv);
+      dmrg::dev_d2h(x, dx.p, sizeof(double) * n, s);
+    }
+    dmrg::dev_sync(s);
+    if (energy) *energy = e;
+    if (iters) *iters = it;
+    if (!conv) { c->err = "Davidson reached its iteration cap"; return DMRG_ENOTCONV; }
+    return DMRG_OK;
+  });
+}
+
+int dmrg_truncate(dmrg_ctx* c, int site, int dir, int D, double noise, const double* x,
+                  uintptr_t stream, double* w_disc) {
+  return guard(c, [&] {
+    if (!x || (dir != 1 && dir != -1) || D < 1 || !(noise >= 0)) return DMRG_EINVAL;
+    wait_user(stream);
+    const int64_t n = xsize(c, site);
+    dmrg::Stream s = dev_stream(c);
+    DevBuf dx(n, s);
+    if (stream) dmrg::dev_d2d(dx.p, x, sizeof(double) * n, s);
+    else dmrg::dev_h2d(dx.p, x, sizeof(double) * n, s);
+    if (noise > 0) dmrg::vec_add_noise(dx.p, n, noise, 0x7a11u + (uint64_t)site, s);
+    double w = c->eng->truncate(site, dir, D, dx.p, noise);
+    dmrg::dev_sync(s);
+    if (w_disc) *w_disc = w;
+    return DMRG_OK;
+  });
+}
+
+int dmrg_sweep_step(dmrg_ctx* c, int site, int dir, int D, double gamma, double* energy,
+                    double* w_disc, int* iters) {
+  return guard(c, [&] {
+    if ((dir != 1 && dir != -1) || D < 1 || !(gamma >= 0)) return DMRG_EINVAL;
+    dmrg::Stream s = dev_stream(c);
+    double w = 0.0;
+    int it = 0;
+    bool conv = false;
+    double e = c->eng->sweep_step(site, dir, D, gamma, &w, &it, &conv);
+    dmrg::dev_sync(s);
+    if (energy) *energy = e;
+    if (w_disc) *w_disc = w;
+    if (iters) *iters = it;
+    if (!conv) { c->err = "Davidson reached its iteration cap"; return DMRG_ENOTCONV; }
+    return DMRG_OK;
+  });
+}
+
+int dmrg_stats(dmrg_ctx* c, dmrg_stats_t* out) {
+  return guard(c, [&] {
+    if (!out) return DMRG_EINVAL;
+    const dmrg::Stats& s = c->eng->stats();
+    out->matvecs = s.matvecs;
+    out->davidson_iters = s.davidson_iters;
+    out->micro_iters = s.micro_iters;
+    out->matvec_flops = s.matvec_flops;
+    out->last_matvec_flops = s.last_matvec_flops;
+    out->last_matvec_tasks = s.last_matvec_tasks;
+    out->t_update_ms = s.t_update_ms;
+    out->t_trunc_ms = s.t_trunc_ms;
+    out->t_plan_ms = s.t_plan_ms;
+    out->t_total_ms = s.t_total_ms;
+    out->last_w_disc = s.last_w_disc;
+    out->max_w_disc = s.max_w_disc;
+    out->k_phase1_ms = s.k_phase1_ms;
+    out->k_phase2_ms = s.k_phase2_ms;
+    out->k_launches = s.k_launches;
+    out->k_phase1_flops = s.k_phase1_flops;
+    out->k_phase2_flops = s.k_phase2_flops;
+    return DMRG_OK;
+  });
+}
+
+const char* dmrg_last_error(dmrg_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+void dmrg_destroy(dmrg_ctx* c) {
+  if (!c) return;
+  delete c->eng;
+  if (c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,133 @@
+// Device memory and kernel launchers used by the engine.  Every numeric step of the
+// two-site sweep is one of these launches; the planner only builds their tables.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+namespace dmrg {
+
+typedef void* Stream;  // cudaStream_t
+
+// ---- memory (stream-ordered; sizes in bytes) ----
+void* dev_alloc(size_t bytes, Stream s);
+void dev_free(void* p, Stream s);
+void dev_h2d(void* dst, const void* src, size_t bytes, Stream s);
+void dev_d2h(void* dst, const void* src, size_t bytes, Stream s);
+void dev_d2d(void* dst, const void* src, size_t bytes, Stream s);
+void dev_zero(void* p, size_t bytes, Stream s);
+void dev_sync(Stream s);
+int dev_check(const char** msg);  // 0 if no CUDA error is pending
+void* host_pinned_alloc(size_t bytes);
+// CUDA events for timing kernels on the engine's stream
+void* event_create();
+void event_destroy(void* e);
+void event_record(void* e, Stream s);
+float event_elapsed_ms(void* a, void* b);  // both must have completed
+void host_pinned_free(void* p);
+
+// ---- grouped GEMM: C_g = C_g + sum_t alpha_t op(A_t) op(B_t), row-major blocks ----
+struct GemmTask {
+  const double* A;
+  const double* B;
+  int lda, ldb;
+  int k;
+  int transA, transB;
+  double alpha;
+};
+struct GemmGroup {
+  double* C;
+  int ldc, m, n;
+  int task_begin, task_end;
+  int tile_begin;  // prefix of 32x32 output tiles (filled by the uploader)
+};
+struct GemmPlan;  // device copy of a task/group table
+GemmPlan* gemm_plan_upload(const std::vector<GemmTask>& t, std::vector<GemmGroup>& g, Stream s);
+void gemm_plan_run(const GemmPlan* p, Stream s);
+void gemm_plan_free(GemmPlan* p, Stream s);
+int64_t gemm_plan_tasks(const GemmPlan* p);
+
+// ---- block combine: dst = (accumulate ? dst : 0) + sum alpha_s src_s (2-D blocks) ----
+struct CombSrc {
+  const double* src;
+  int ld;
+  double alpha;
+};
+struct CombDst {
+  double* dst;
+  int ld, rows, cols;
+  int src_begin, src_end;
+  int accumulate;
+};
+struct CombPlan;
+CombPlan* comb_plan_upload(const std::vector<CombSrc>& s, const std::vector<CombDst>& d, Stream st);
+void comb_plan_run(const CombPlan* p, Stream s);
+void comb_plan_free(CombPlan* p, Stream s);
+
+// ---- diagonal of a sum of C (x) D terms: out += coef diag(C)_a diag(D)_b ----
+struct DiagTerm {
+  const double* C;
+  const double* D;
+  int ldc, ldd;
+  double coef;
+};
+struct DiagOut {
+  double* out;
+  int dL, dR;
+  int term_begin, term_end;
+};
+struct DiagPlan;
+DiagPlan* diag_plan_upload(const std::vector<DiagTerm>& t, const std::vector<DiagOut>& o, Stream s);
+void diag_plan_run(const DiagPlan* p, Stream s);
+void diag_plan_free(DiagPlan* p, Stream s);
+
+// ---- dense vector kernels for Davidson (FP64) ----
+// out[j] = <V_j, w>, j < m; V is column-block storage V + j*ldv.
+void vec_multidot(const double* V, int64_t ldv, int m, const double* w, int64_t n, double* out,
+                  double* scratch, Stream s);
+// y = beta*y + sum_j c[j] V_j (c on device)
+void vec_combine(const double* V, int64_t ldv, int m, const double* c, double beta, double* y,
+                 int64_t n, Stream s);
+// y = a*x + b*y with a, b on device (pointers) or host scalars
+void vec_axpby(double a, const double* x, double b, double* y, int64_t n, Stream s);
+// scale y by 1/sqrt(*nrm2_dev)
+void vec_normalize(double* y, const double* nrm2_dev, int64_t n, Stream s);
+// t = r / (theta - diag), |denominator| floored
+void vec_precondition(const double* r, const double* diag, const double* theta_dev, double* t,
+                      int64_t n, Stream s);
+// lowest eigenpairs of the m x m (m <= 48) symmetric matrix whose lower triangle is in G
+// (ld gld) -> theta[0..k) ascending, C[v*m + i] = component i of vector v
+void small_eig(const double* G, int gld, int m, int k, double* theta, double* C, Stream s);
+// uniform noise in [-amp, amp) from splitmix64(seed + index), added to x
+void vec_add_noise(double* x, int64_t n, double amp, uint64_t seed, Stream s);
+
+// ---- batched symmetric eigensolver (cyclic Jacobi), eigenvalues sorted descending ----
+struct EigJob {
+  double* A;     // n x n symmetric, overwritten
+  double* Q;     // n x n eigenvectors (columns), output
+  double* w;     // n eigenvalues, output (descending)
+  int n;
+};
+void eig_batched(const std::vector<EigJob>& jobs, Stream s);
+
+// ---- global selection of the D largest values (ties: earlier group, lower index) ----
+// vals: concatenated eigenvalues (lambda^2) of groups with offsets goff (size G+1);
+// weights wgt[g] = 2jM+1.  Writes kept[g] and sums (norm2, discarded) to host.
+void select_largest(const double* vals, const std::vector<int>& goff, const std::vector<int>& wgt,
+                    int D, double zero_rel, std::vector<int>& kept, double* norm2, double* disc,
+                    Stream s);
+
+// ---- scaled block copy: dst[i,j] = a * r(i) * c(j) * src(i,j) (src transposed if set);
+// r(i) from rs[i] by mode 0 = 1, 1 = sqrt(rs[i]), 2 = 1/sqrt(rs[i]); same for c(j) ----
+struct ScatterJob {
+  double* dst;
+  const double* src;
+  const double* rs;
+  const double* cs;
+  int ldd, lds, rows, cols;
+  int rmode, cmode, trans;
+  double a;
+};
+void scatter_batched(const std::vector<ScatterJob>& jobs, Stream s);
+
+}  // namespace dmrg

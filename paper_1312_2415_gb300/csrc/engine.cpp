@@ -1,0 +1,1408 @@
+// Engine: symmetry tables, environments, and the micro-iteration pipeline
+// (Eq. 25 -> Davidson on H_eff (Eq. 9) -> Eqs. 26-28 -> operator update).
+#include "engine.hpp"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <limits>
+#include <map>
+#include <stdexcept>
+#include <tuple>
+
+#include "su2.hpp"
+
+namespace dmrg {
+
+namespace {
+
+inline int64_t bkey(int r, int c) { return ((int64_t)r << 32) | (uint32_t)c; }
+
+uint64_t splitmix64_next(uint64_t& state) {
+  state += 0x9E3779B97F4A7C15ull;
+  uint64_t z = state;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+double now_ms() {
+  using namespace std::chrono;
+  return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+struct Timer {
+  double t0;
+  Timer() : t0(now_ms()) {}
+  double ms() const { return now_ms() - t0; }
+};
+
+}  // namespace
+
+Engine::Engine(int L, int n_irrep, const std::vector<int>& orb_ir, int N, int two_S, int irrep,
+               Stream stream)
+    : L_(L), N_(N), two_S_(two_S), irrep_(irrep), stream_(stream) {
+  sym_.L = L;
+  sym_.N = N;
+  sym_.two_S = two_S;
+  sym_.irrep = irrep;
+  sym_.n_irrep = n_irrep;
+  sym_.orb_ir = orb_ir;
+  opsets_.resize(L + 1);
+  for (int k = 0; k <= L; ++k) opsets_[k] = make_op_set(k, L, orb_ir);
+  cp_.reset(new Coupling(&pt_));
+  lenv_.resize(L + 1);
+  renv_.resize(L + 1);
+  sites_.resize(L);
+  sched_D_ = {64};
+  sched_econv_ = {1e-8};
+  sched_nmax_ = {4};
+  sched_noise_ = {0.0};
+}
+
+Engine::~Engine() {
+  try {
+    flush_events();
+    for (auto& e : ev_) event_destroy(e);
+    if (cached_) free_plan(cached_);
+    for (auto& e : lenv_) free_env(e);
+    for (auto& e : renv_) free_env(e);
+    for (int k = 0; k < L_; ++k) free_site(k);
+    dev_sync(stream_);
+  } catch (...) {
+  }
+}
+
+void Engine::check_ready() const {
+  if (!have_integrals_) throw std::invalid_argument("integrals not set");
+  if (!have_mps_) throw std::invalid_argument("MPS not initialised");
+}
+
+// Eq. 11 folding of the one-body integrals into the two-body ones, after checking the
+// symmetries the paper requires (Sec. 4.1: eightfold permutation symmetry, real
+// orbitals, point-group selection).
+void Engine::set_integrals(double econst, const double* h, const double* V) {
+  const int L = L_;
+  if (N_ < 2) throw std::invalid_argument("the folding of Eq. 11 needs N >= 2");
+  double scale = 1e-300;
+  for (int i = 0; i < L * L; ++i) scale = std::max(scale, std::fabs(h[i]));
+  for (int64_t i = 0; i < (int64_t)L * L * L * L; ++i) scale = std::max(scale, std::fabs(V[i]));
+  const double tol = 1e-10 * scale;
+  auto Vat = [&](int i, int j, int k, int l) { return V[(((size_t)i * L + j) * L + k) * L + l]; };
+  const auto& ir = sym_.orb_ir;
+  for (int i = 0; i < L; ++i)
+    for (int k = 0; k < L; ++k) {
+      if (std::fabs(h[i * L + k] - h[k * L + i]) > tol) throw std::domain_error("h is not symmetric");
+      if (ir[i] != ir[k] && std::fabs(h[i * L + k]) > tol)
+        throw std::domain_error("h couples orbitals of different irreps");
+    }
+  for (int i = 0; i < L; ++i)
+    for (int j = 0; j < L; ++j)
+      for (int k = 0; k < L; ++k)
+        for (int l = 0; l < L; ++l) {
+          double v = Vat(i, j, k, l);
+          if ((ir[i] ^ ir[j] ^ ir[k] ^ ir[l]) != 0 && std::fabs(v) > tol)
+            throw std::domain_error("V breaks the point-group selection rule");
+          const double sym[7] = {Vat(j, i, l, k), Vat(k, l, i, j), Vat(l, k, j, i), Vat(k, j, i, l),
+                                 Vat(i, l, k, j), Vat(l, i, j, k), Vat(j, k, l, i)};
+          for (double s : sym)
+            if (std::fabs(v - s) > tol) throw std::domain_error("V lacks eightfold symmetry");
+        }
+  g_.L = L;
+  g_.g.assign((size_t)L * L * L * L, 0.0);
+  const double f = 1.0 / (N_ - 1);
+  for (int i = 0; i < L; ++i)
+    for (int j = 0; j < L; ++j)
+      for (int k = 0; k < L; ++k)
+        for (int l = 0; l < L; ++l) {
+          double v = Vat(i, j, k, l);
+          if (j == l) v += f * h[i * L + k];
+          if (i == k) v += f * h[j * L + l];
+          g_.g[(((size_t)i * L + j) * L + k) * L + l] = v;
+        }
+  econst_ = econst;
+  Timer t;
+  W_.assign(L, {});
+  for (int k = 0; k < L; ++k) W_[k] = build_site_recursion(k, opsets_[k], opsets_[k + 1], g_, pt_);
+  st_.t_plan_ms += t.ms();
+  have_integrals_ = true;
+  for (auto& e : lenv_) free_env(e);
+  for (auto& e : renv_) free_env(e);
+  if (cached_) { free_plan(cached_); cached_ = nullptr; cached_site_ = -1; }
+}
+
+void Engine::set_schedule(const std::vector<int>& D, const std::vector<double>& econv,
+                          const std::vector<int>& nmax, const std::vector<double>& noise,
+                          double dtol, int dmax) {
+  if (D.empty()) throw std::invalid_argument("empty schedule");
+  for (int d : D)
+    if (d < 1) throw std::invalid_argument("D must be positive");
+  sched_D_ = D;
+  sched_econv_ = econv;
+  sched_nmax_ = nmax;
+  sched_noise_ = noise;
+  dav_tol_ = dtol;
+  dav_max_ = dmax;
+}
+
+// ------------------------------------------------------------------ MPS storage
+
+void Engine::free_site(int k) {
+  if (sites_[k].data) dev_free(sites_[k].data, stream_);
+  sites_[k].data = nullptr;
+  sites_[k].size = 0;
+  sites_[k].blocks.clear();
+}
+
+void Engine::alloc_site(int k) {
+  free_site(k);
+  Site& S = sites_[k];
+  const Bond& bl = bonds_[k];
+  const Bond& br = bonds_[k + 1];
+  int64_t off = 0;
+  for (int l = 0; l < (int)bl.sec.size(); ++l)
+    for (int ls = 0; ls < 3; ++ls) {
+      const Sector& a = bl.sec[l];
+      Sector want{0, a.n + local_n(ls), a.ir ^ local_ir(ls, sym_.orb_ir[k])};
+      for (int r = 0; r < (int)br.sec.size(); ++r) {
+        const Sector& b = br.sec[r];
+        if (b.n != want.n || b.ir != want.ir || !triangle(a.tj, local_ts(ls), b.tj)) continue;
+        S.blocks.push_back({ls, l, r, off, bl.dim[l], br.dim[r]});
+        off += (int64_t)bl.dim[l] * br.dim[r];
+      }
+    }
+  S.size = off;
+  S.data = (double*)dev_alloc(sizeof(double) * std::max<int64_t>(off, 1), stream_);
+  dev_zero(S.data, sizeof(double) * std::max<int64_t>(off, 1), stream_);
+}
+
+void Engine::invalidate_envs_from_site(int k) {
+  for (int b = k + 1; b <= L_; ++b) free_env(lenv_[b]);
+  for (int b = 0; b <= k; ++b) free_env(renv_[b]);
+  if (cached_) { free_plan(cached_); cached_ = nullptr; cached_site_ = -1; }
+}
+
+void Engine::init_mps(uint64_t seed) {
+  if (!have_integrals_) throw std::invalid_argument("integrals not set");
+  bonds_ = sym_.initial_bonds(sched_D_[0]);
+  for (int k = 0; k <= L_; ++k)
+    if (bonds_[k].sec.empty()) throw std::domain_error("target symmetry sector is empty");
+  uint64_t state = seed;
+  for (int k = 0; k < L_; ++k) {
+    alloc_site(k);
+    std::vector<double> h(sites_[k].size);
+    for (auto& v : h) v = (double)(splitmix64_next(state) >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+    dev_h2d(sites_[k].data, h.data(), sizeof(double) * h.size(), stream_);
+    dev_sync(stream_);
+  }
+  have_mps_ = true;
+  invalidate_envs_from_site(-1);
+  for (auto& e : lenv_) free_env(e);
+}
+
+// Serialised MPS: int32 magic, version, L, N, 2S, irrep; per bond: nsec then
+// (2j, N, I, dim) per sector; per site: nblk then (ls, left sector, right sector) and
+// the dL x dR block row-major in float64 (the reduced tensors of Eq. 22).
+std::vector<char> Engine::get_mps() {
+  if (!have_mps_) throw std::invalid_argument("MPS not initialised");
+  std::vector<char> out;
+  auto put = [&](const void* p, size_t n) {
+    const char* c = (const char*)p;
+    out.insert(out.end(), c, c + n);
+  };
+  int32_t hdr[6] = {0x444D5247, 1, L_, N_, two_S_, irrep_};
+  put(hdr, sizeof(hdr));
+  for (int k = 0; k <= L_; ++k) {
+    int32_t n = (int32_t)bonds_[k].sec.size();
+    put(&n, 4);
+    for (int s = 0; s < n; ++s) {
+      int32_t v[4] = {bonds_[k].sec[s].tj, bonds_[k].sec[s].n, bonds_[k].sec[s].ir, bonds_[k].dim[s]};
+      put(v, 16);
+    }
+  }
+  for (int k = 0; k < L_; ++k) {
+    const Site& S = sites_[k];
+    std::vector<double> h(S.size);
+    dev_d2h(h.data(), S.data, sizeof(double) * S.size, stream_);
+    dev_sync(stream_);
+    int32_t n = (int32_t)S.blocks.size();
+    put(&n, 4);
+    for (auto& b : S.blocks) {
+      int32_t v[3] = {b.ls, b.l, b.r};
+      put(v, 12);
+      put(h.data() + b.off, sizeof(double) * (size_t)b.rows * b.cols);
+    }
+  }
+  return out;
+}
+
+void Engine::set_mps(const char* buf, size_t len) {
+  size_t pos = 0;
+  auto get = [&](void* p, size_t n) {
+    if (pos + n > len) throw std::invalid_argument("MPS buffer too short");
+    std::memcpy(p, buf + pos, n);
+    pos += n;
+  };
+  int32_t hdr[6];
+  get(hdr, sizeof(hdr));
+  if (hdr[0] != 0x444D5247 || hdr[1] != 1) throw std::invalid_argument("bad MPS header");
+  if (hdr[2] != L_ || hdr[3] != N_ || hdr[4] != two_S_ || hdr[5] != irrep_)
+    throw std::invalid_argument("MPS belongs to another problem");
+  std::vector<Bond> nb(L_ + 1);
+  std::vector<std::vector<int>> perm(L_ + 1);
+  for (int k = 0; k <= L_; ++k) {
+    int32_t n;
+    get(&n, 4);
+    std::vector<std::pair<Sector, int>> v(n);
+    for (int s = 0; s < n; ++s) {
+      int32_t x[4];
+      get(x, 16);
+      if (x[3] <= 0) throw std::invalid_argument("non-positive sector dimension");
+      v[s] = {Sector{x[0], x[1], x[2]}, x[3]};
+    }
+    std::vector<std::pair<Sector, int>> sorted = v;
+    std::sort(sorted.begin(), sorted.end(), [](auto& a, auto& b) { return a.first < b.first; });
+    for (auto& p : sorted) { nb[k].sec.push_back(p.first); nb[k].dim.push_back(p.second); }
+    perm[k].resize(n);
+    for (int s = 0; s < n; ++s) perm[k][s] = nb[k].find(v[s].first);
+  }
+  if (nb[0].sec.size() != 1 || !(nb[0].sec[0] == Sector{0, 0, 0}) || nb[0].dim[0] != 1)
+    throw std::invalid_argument("left boundary must be the (0,0,0) singlet");
+  if (nb[L_].sec.size() != 1 || !(nb[L_].sec[0] == Sector{two_S_, N_, irrep_}) || nb[L_].dim[0] != 1)
+    throw std::invalid_argument("right boundary must be the target sector");
+  for (int k = 0; k < L_; ++k) free_site(k);
+  bonds_ = nb;
+  for (int k = 0; k < L_; ++k) {
+    alloc_site(k);
+    Site& S = sites_[k];
+    std::vector<double> h(S.size, 0.0);
+    std::map<std::tuple<int, int, int>, const SiteBlock*> idx;
+    for (auto& b : S.blocks) idx[{b.ls, b.l, b.r}] = &b;
+    int32_t n;
+    get(&n, 4);
+    for (int b = 0; b < n; ++b) {
+      int32_t x[3];
+      get(x, 12);
+      if (x[1] < 0 || x[1] >= (int)perm[k].size() || x[2] < 0 || x[2] >= (int)perm[k + 1].size())
+        throw std::invalid_argument("block sector index out of range");
+      auto it = idx.find({x[0], perm[k][x[1]], perm[k + 1][x[2]]});
+      if (it == idx.end()) throw std::invalid_argument("block violates the symmetry of Eq. 22");
+      const SiteBlock* sb = it->second;
+      get(h.data() + sb->off, sizeof(double) * (size_t)sb->rows * sb->cols);
+    }
+    dev_h2d(S.data, h.data(), sizeof(double) * h.size(), stream_);
+    dev_sync(stream_);
+  }
+  if (pos != len) throw std::invalid_argument("trailing bytes in MPS buffer");
+  have_mps_ = true;
+  for (auto& e : lenv_) free_env(e);
+  for (auto& e : renv_) free_env(e);
+  if (cached_) { free_plan(cached_); cached_ = nullptr; cached_site_ = -1; }
+}
+
+// ------------------------------------------------------------------ environments
+
+void Engine::free_env(OpStore& e) {
+  if (e.data) dev_free(e.data, stream_);
+  e = OpStore();
+}
+
+void Engine::alloc_env(OpStore& e, int bond, const OpSet& ops) {
+  free_env(e);
+  const Bond& B = bonds_[bond];
+  e.bond = bond;
+  e.blocks.resize(ops.ops.size());
+  e.at.resize(ops.ops.size());
+  int64_t off = 0;
+  for (size_t o = 0; o < ops.ops.size(); ++o) {
+    const OpInfo& op = ops.ops[o];
+    for (int c = 0; c < (int)B.sec.size(); ++c) {
+      const Sector& sc = B.sec[c];
+      for (int tj = std::abs(sc.tj - op.tk); tj <= sc.tj + op.tk; tj += 2) {
+        int r = B.find({tj, sc.n + op.dn, sc.ir ^ op.ir});
+        if (r < 0) continue;
+        e.at[o][bkey(r, c)] = (int)e.blocks[o].size();
+        e.blocks[o].push_back({r, c, off, B.dim[r], B.dim[c]});
+        off += (int64_t)B.dim[r] * B.dim[c];
+      }
+    }
+  }
+  e.size = off;
+  e.data = (double*)dev_alloc(sizeof(double) * std::max<int64_t>(off, 1), stream_);
+  dev_zero(e.data, sizeof(double) * std::max<int64_t>(off, 1), stream_);
+  e.valid = false;
+}
+
+void Engine::identity_fill(OpStore& e, int op) {
+  std::vector<ScatterJob> jobs;
+  static thread_local std::vector<double> ones;
+  int dmax = 1;
+  for (auto& b : e.blocks[op]) dmax = std::max(dmax, b.rows);
+  std::vector<double> eye((size_t)dmax * dmax, 0.0);
+  for (int i = 0; i < dmax; ++i) eye[(size_t)i * dmax + i] = 1.0;
+  double* d = (double*)dev_alloc(sizeof(double) * eye.size(), stream_);
+  dev_h2d(d, eye.data(), sizeof(double) * eye.size(), stream_);
+  for (auto& b : e.blocks[op])
+    if (b.r == b.c) jobs.push_back({e.data + b.off, d, nullptr, nullptr, b.cols, dmax, b.rows, b.cols, 0, 0, 0, 1.0});
+  scatter_batched(jobs, stream_);
+  dev_free(d, stream_);
+}
+
+void Engine::ensure_left(int k) {
+  if (lenv_[k].valid) return;
+  if (k == 0) {
+    alloc_env(lenv_[0], 0, opsets_[0]);
+    identity_fill(lenv_[0], 0);
+    lenv_[0].valid = true;
+    return;
+  }
+  ensure_left(k - 1);
+  build_left(k);
+}
+
+void Engine::ensure_right(int k) {
+  if (renv_[k].valid) return;
+  if (k == L_) {
+    alloc_env(renv_[L_], L_, opsets_[L_]);
+    int h = opsets_[L_].find({OP_H, -1, -1, 0});
+    identity_fill(renv_[L_], h);
+    renv_[L_].valid = true;
+    return;
+  }
+  ensure_right(k + 1);
+  build_right(k);
+}
+
+std::vector<XBlock> Engine::x_layout(int i, int64_t* n) const {
+  std::vector<XBlock> X;
+  const Bond& bl = bonds_[i];
+  const Bond& br = bonds_[i + 2];
+  int64_t off = 0;
+  for (int l = 0; l < (int)bl.sec.size(); ++l)
+    for (int ls1 = 0; ls1 < 3; ++ls1)
+      for (int ls2 = 0; ls2 < 3; ++ls2) {
+        const Sector& a = bl.sec[l];
+        int nn = a.n + local_n(ls1) + local_n(ls2);
+        int ir = a.ir ^ local_ir(ls1, sym_.orb_ir[i]) ^ local_ir(ls2, sym_.orb_ir[i + 1]);
+        for (int r = 0; r < (int)br.sec.size(); ++r) {
+          const Sector& b = br.sec[r];
+          if (b.n != nn || b.ir != ir) continue;
+          int t1 = local_ts(ls1), t2 = local_ts(ls2);
+          for (int tj = std::abs(t1 - t2); tj <= t1 + t2; tj += 2) {
+            if (!triangle(a.tj, tj, b.tj)) continue;
+            X.push_back({l, ls1, ls2, tj, r, off, bl.dim[l], br.dim[r]});
+            off += (int64_t)bl.dim[l] * br.dim[r];
+          }
+        }
+      }
+  *n = off;
+  return X;
+}
+
+void Engine::layout(int i, std::vector<int64_t>& table, int64_t& n) {
+  check_ready();
+  if (i < 0 || i > L_ - 2) throw std::out_of_range("site out of range");
+  auto X = x_layout(i, &n);
+  table.clear();
+  for (auto& x : X) {
+    const Sector& a = bonds_[i].sec[x.l];
+    const Sector& b = bonds_[i + 2].sec[x.r];
+    int64_t row[12] = {a.tj, a.n, a.ir, x.ls1, x.ls2, x.tj, b.tj, b.n, b.ir, x.rows, x.cols, x.off};
+    table.insert(table.end(), row, row + 12);
+  }
+}
+
+}  // namespace dmrg
+
+namespace dmrg {
+
+namespace {
+
+// Materialise combined operators with more than one source: dst = sum scalar * src.
+double* materialise(std::vector<CombOp>& comb, const OpStore& src, Stream st) {
+  int64_t total = 0;
+  for (auto& c : comb)
+    if (c.sources.size() > 1)
+      for (auto& b : src.blocks[c.sources[0].first]) total += (int64_t)b.rows * b.cols;
+  if (total == 0) return nullptr;
+  double* buf = (double*)dev_alloc(sizeof(double) * total, st);
+  std::vector<CombSrc> cs;
+  std::vector<CombDst> cd;
+  int64_t off = 0;
+  for (auto& c : comb) {
+    if (c.sources.size() <= 1) continue;
+    const auto& proto = src.blocks[c.sources[0].first];
+    c.own_blocks.clear();
+    c.own_at.clear();
+    for (size_t bi = 0; bi < proto.size(); ++bi) {
+      const BlockRef& pb = proto[bi];
+      BlockRef nb = pb;
+      nb.off = off;
+      c.own_at[bkey(pb.r, pb.c)] = (int)c.own_blocks.size();
+      c.own_blocks.push_back(nb);
+      CombDst d{buf + off, pb.cols, pb.rows, pb.cols, (int)cs.size(), 0, 0};
+      for (auto& s : c.sources) {
+        auto it = src.at[s.first].find(bkey(pb.r, pb.c));
+        if (it == src.at[s.first].end()) throw std::logic_error("combined sources differ in blocks");
+        const BlockRef& sb = src.blocks[s.first][it->second];
+        cs.push_back({src.data + sb.off, sb.cols, s.second});
+      }
+      d.src_end = (int)cs.size();
+      cd.push_back(d);
+      off += (int64_t)pb.rows * pb.cols;
+    }
+    c.blocks = &c.own_blocks;
+    c.at = &c.own_at;
+    c.data = buf;
+    c.scalar = 1.0;
+  }
+  CombPlan* p = comb_plan_upload(cs, cd, st);
+  comb_plan_run(p, st);
+  comb_plan_free(p, st);
+  return buf;
+}
+
+}  // namespace
+
+// Left combined operators for the targets at bond i+1: C_{b,P} = sum_a s_a L_a(bond i).
+void Engine::group_left(int i, std::vector<CombOp>& out, double** scratch) {
+  const OpStore& E = lenv_[i];
+  std::map<std::pair<int, int>, int> idx;
+  out.clear();
+  for (const WEntry& w : W_[i]) {
+    if (E.blocks[w.a].empty()) continue;
+    auto key = std::make_pair(w.b, w.pattern);
+    auto it = idx.find(key);
+    if (it == idx.end()) {
+      CombOp c;
+      c.target = w.b;
+      c.pattern = w.pattern;
+      idx[key] = (int)out.size();
+      out.push_back(std::move(c));
+      it = idx.find(key);
+    }
+    out[it->second].sources.push_back({w.a, w.scalar});
+  }
+  for (auto& c : out)
+    if (c.sources.size() == 1) {
+      c.blocks = &E.blocks[c.sources[0].first];
+      c.at = &E.at[c.sources[0].first];
+      c.data = E.data;
+      c.scalar = c.sources[0].second;
+    }
+  *scratch = materialise(out, E, stream_);
+}
+
+// Right combined operators for targets at bond j (site j): D_{a,P} = sum_b s_b R_b(bond j+1).
+void Engine::group_right(int j, std::vector<CombOp>& out, double** scratch) {
+  const OpStore& E = renv_[j + 1];
+  std::map<std::pair<int, int>, int> idx;
+  out.clear();
+  for (const WEntry& w : W_[j]) {
+    if (E.blocks[w.b].empty()) continue;
+    if (j + 1 == L_ && opsets_[L_].ops[w.b].key.type != OP_H) continue;  // zero partners
+    auto key = std::make_pair(w.a, w.pattern);
+    auto it = idx.find(key);
+    if (it == idx.end()) {
+      CombOp c;
+      c.target = w.a;
+      c.pattern = w.pattern;
+      idx[key] = (int)out.size();
+      out.push_back(std::move(c));
+      it = idx.find(key);
+    }
+    out[it->second].sources.push_back({w.b, w.scalar});
+  }
+  for (auto& c : out)
+    if (c.sources.size() == 1) {
+      c.blocks = &E.blocks[c.sources[0].first];
+      c.at = &E.at[c.sources[0].first];
+      c.data = E.data;
+      c.scalar = c.sources[0].second;
+    }
+  *scratch = materialise(out, E, stream_);
+}
+
+// L_b(bond i+1)[jM' <- jM] = sum coef T[i]^T C_{b,P}[jL' <- jL] T[i], T[i] left-normalised.
+void Engine::update_left_from(int i, std::vector<CombOp>& comb) {
+  Timer tm;
+  OpStore& E = lenv_[i + 1];
+  alloc_env(E, i + 1, opsets_[i + 1]);
+  const Site& T = sites_[i];
+  const Bond& bl = bonds_[i];
+  const Bond& bm = bonds_[i + 1];
+  std::vector<std::vector<int>> by_l(bl.sec.size());
+  for (int t = 0; t < (int)T.blocks.size(); ++t) by_l[T.blocks[t].l].push_back(t);
+  const int id_op = opsets_[i + 1].find({OP_I, -1, -1, 0});
+  std::vector<GemmTask> t1, t2;
+  std::vector<GemmGroup> g1;
+  std::map<std::pair<int, int>, std::vector<GemmTask>> out2;  // (op, block) -> tasks
+  int64_t zsize = 0;
+  struct ZRef { int64_t off; int rows, cols; };
+  std::vector<ZRef> zs;
+  for (auto& c : comb) {
+    if (c.target == id_op) continue;
+    for (const BlockRef& cb : *c.blocks) {
+      for (int t : by_l[cb.c]) {
+        const SiteBlock& tb = T.blocks[t];
+        // Z1 = C_blk (rows x cols) . T_t (dL x dM)
+        int zid = -1;
+        for (int tp : by_l[cb.r]) {
+          const SiteBlock& tpb = T.blocks[tp];
+          double coef = c.scalar * cp_->left(c.pattern, bl.sec[tb.l].tj, tb.ls, bm.sec[tb.r].tj,
+                                              bl.sec[tpb.l].tj, tpb.ls, bm.sec[tpb.r].tj);
+          if (coef == 0.0) continue;
+          auto it = E.at[c.target].find(bkey(tpb.r, tb.r));
+          if (it == E.at[c.target].end()) continue;
+          if (zid < 0) {
+            zid = (int)zs.size();
+            zs.push_back({zsize, cb.rows, tb.cols});
+            zsize += (int64_t)cb.rows * tb.cols;
+            t1.push_back({c.data + cb.off, T.data + tb.off, cb.cols, tb.cols, cb.cols, 0, 0, 1.0});
+            g1.push_back({nullptr, tb.cols, cb.rows, tb.cols, (int)t1.size() - 1, (int)t1.size(), 0});
+          }
+          out2[{c.target, it->second}].push_back(
+              {T.data + tpb.off, nullptr, tpb.cols, tb.cols, tpb.rows, 1, 0, coef});
+          out2[{c.target, it->second}].back().B = (const double*)(intptr_t)zid;
+        }
+      }
+    }
+  }
+  double* Z = (double*)dev_alloc(sizeof(double) * std::max<int64_t>(zsize, 1), stream_);
+  for (size_t z = 0; z < g1.size(); ++z) g1[z].C = Z + zs[z].off;
+  dev_zero(Z, sizeof(double) * std::max<int64_t>(zsize, 1), stream_);
+  std::vector<GemmGroup> g2;
+  for (auto& kv : out2) {
+    const BlockRef& ob = E.blocks[kv.first.first][kv.first.second];
+    int b0 = (int)t2.size();
+    for (auto t : kv.second) {
+      t.B = Z + zs[(int)(intptr_t)t.B].off;
+      t2.push_back(t);
+    }
+    g2.push_back({E.data + ob.off, ob.cols, ob.rows, ob.cols, b0, (int)t2.size(), 0});
+  }
+  GemmPlan* p1 = gemm_plan_upload(t1, g1, stream_);
+  GemmPlan* p2 = gemm_plan_upload(t2, g2, stream_);
+  gemm_plan_run(p1, stream_);
+  gemm_plan_run(p2, stream_);
+  gemm_plan_free(p1, stream_);
+  gemm_plan_free(p2, stream_);
+  dev_free(Z, stream_);
+  identity_fill(E, id_op);
+  E.valid = true;
+  st_.t_update_ms += tm.ms();
+}
+
+// R_a(bond j)[jM' <- jM] = sum coef V D_{a,P}[jR' <- jR] V^T with the mirrored tensor
+// V = sqrt((2jR+1)/(2jM+1)) T[j] (Euclidean-orthonormal rows, the bracket of Eq. 27).
+void Engine::update_right_from(int j, std::vector<CombOp>& comb) {
+  Timer tm;
+  OpStore& E = renv_[j];
+  alloc_env(E, j, opsets_[j]);
+  const Site& T = sites_[j];
+  const Bond& bm = bonds_[j];
+  const Bond& br = bonds_[j + 1];
+  std::vector<std::vector<int>> by_r(br.sec.size());
+  for (int t = 0; t < (int)T.blocks.size(); ++t) by_r[T.blocks[t].r].push_back(t);
+  const int h_op = opsets_[j].find({OP_H, -1, -1, 0});
+  auto f = [&](const SiteBlock& b) {
+    return std::sqrt((double)(br.sec[b.r].tj + 1) / (double)(bm.sec[b.l].tj + 1));
+  };
+  std::vector<GemmTask> t1, t2;
+  std::vector<GemmGroup> g1;
+  std::map<std::pair<int, int>, std::vector<GemmTask>> out2;
+  int64_t zsize = 0;
+  struct ZRef { int64_t off; int rows, cols; };
+  std::vector<ZRef> zs;
+  for (auto& c : comb) {
+    if (c.target == h_op) continue;
+    for (const BlockRef& db : *c.blocks) {
+      for (int t : by_r[db.c]) {
+        const SiteBlock& tb = T.blocks[t];
+        int zid = -1;
+        for (int tp : by_r[db.r]) {
+          const SiteBlock& tpb = T.blocks[tp];
+          double coef = c.scalar * f(tb) * f(tpb) *
+                        cp_->right(c.pattern, tb.ls, br.sec[tb.r].tj, bm.sec[tb.l].tj, tpb.ls,
+                                   br.sec[tpb.r].tj, bm.sec[tpb.l].tj);
+          if (coef == 0.0) continue;
+          auto it = E.at[c.target].find(bkey(tpb.l, tb.l));
+          if (it == E.at[c.target].end()) continue;
+          if (zid < 0) {
+            // Z1 = D_blk (dR' x dR) . T_t^T (dR x dM)
+            zid = (int)zs.size();
+            zs.push_back({zsize, db.rows, tb.rows});
+            zsize += (int64_t)db.rows * tb.rows;
+            t1.push_back({c.data + db.off, T.data + tb.off, db.cols, tb.cols, db.cols, 0, 1, 1.0});
+            g1.push_back({nullptr, tb.rows, db.rows, tb.rows, (int)t1.size() - 1, (int)t1.size(), 0});
+          }
+          GemmTask tk{T.data + tpb.off, (const double*)(intptr_t)zid, tpb.cols, tb.rows, tpb.cols, 0, 0, coef};
+          out2[{c.target, it->second}].push_back(tk);
+        }
+      }
+    }
+  }
+  double* Z = (double*)dev_alloc(sizeof(double) * std::max<int64_t>(zsize, 1), stream_);
+  for (size_t z = 0; z < g1.size(); ++z) g1[z].C = Z + zs[z].off;
+  dev_zero(Z, sizeof(double) * std::max<int64_t>(zsize, 1), stream_);
+  std::vector<GemmGroup> g2;
+  for (auto& kv : out2) {
+    const BlockRef& ob = E.blocks[kv.first.first][kv.first.second];
+    int b0 = (int)t2.size();
+    for (auto t : kv.second) {
+      t.B = Z + zs[(int)(intptr_t)t.B].off;
+      t2.push_back(t);
+    }
+    g2.push_back({E.data + ob.off, ob.cols, ob.rows, ob.cols, b0, (int)t2.size(), 0});
+  }
+  GemmPlan* p1 = gemm_plan_upload(t1, g1, stream_);
+  GemmPlan* p2 = gemm_plan_upload(t2, g2, stream_);
+  gemm_plan_run(p1, stream_);
+  gemm_plan_run(p2, stream_);
+  gemm_plan_free(p1, stream_);
+  gemm_plan_free(p2, stream_);
+  dev_free(Z, stream_);
+  identity_fill(E, h_op);
+  E.valid = true;
+  st_.t_update_ms += tm.ms();
+}
+
+void Engine::build_left(int k) {
+  std::vector<CombOp> comb;
+  double* scr = nullptr;
+  group_left(k - 1, comb, &scr);
+  update_left_from(k - 1, comb);
+  if (scr) dev_free(scr, stream_);
+}
+
+void Engine::build_right(int k) {
+  std::vector<CombOp> comb;
+  double* scr = nullptr;
+  group_right(k, comb, &scr);
+  update_right_from(k, comb);
+  if (scr) dev_free(scr, stream_);
+}
+
+}  // namespace dmrg
+
+namespace dmrg {
+
+struct Engine::MatvecPlan {
+  int site = -1;
+  int64_t n = 0;
+  std::vector<XBlock> X;
+  std::vector<CombOp> cl, cr;
+  double* scr_l = nullptr;
+  double* scr_r = nullptr;
+  double* Z = nullptr;
+  double* xin = nullptr;
+  double* yout = nullptr;
+  double* diag = nullptr;
+  GemmPlan* p1 = nullptr;
+  GemmPlan* p2 = nullptr;
+  double flops = 0.0, flops1 = 0.0, flops2 = 0.0;
+  int64_t ntasks = 0;
+  int64_t zsize = 0;
+};
+
+namespace {
+// site transitions allowed by a pattern: ok[ket ls][bra ls]
+void allowed(const Pattern& P, bool ok[3][3]) {
+  static const int ls_of[4] = {0, 1, 1, 2};
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) ok[a][b] = false;
+  const int nq = (P.tka + 1) * (P.tkb + 1);
+  for (int q = 0; q < nq; ++q)
+    for (int br = 0; br < 4; ++br)
+      for (int kt = 0; kt < 4; ++kt)
+        if (P.w[(size_t)q * 16 + br * 4 + kt] != 0.0) ok[ls_of[kt]][ls_of[br]] = true;
+}
+}  // namespace
+
+Engine::MatvecPlan* Engine::plan_matvec(int i) {
+  Timer tm;
+  ensure_left(i);
+  ensure_right(i + 2);
+  MatvecPlan* P = new MatvecPlan;
+  P->site = i;
+  P->X = x_layout(i, &P->n);
+  group_left(i, P->cl, &P->scr_l);
+  group_right(i + 1, P->cr, &P->scr_r);
+  const Bond& bl = bonds_[i];
+  const Bond& br = bonds_[i + 2];
+  const OpSet& mid = opsets_[i + 1];
+  std::vector<std::vector<int>> byb_l(mid.ops.size()), byb_r(mid.ops.size());
+  for (int g = 0; g < (int)P->cl.size(); ++g) byb_l[P->cl[g].target].push_back(g);
+  for (int g = 0; g < (int)P->cr.size(); ++g) byb_r[P->cr[g].target].push_back(g);
+  std::map<std::tuple<int, int, int, int, int>, int> xidx;
+  for (int x = 0; x < (int)P->X.size(); ++x) {
+    const XBlock& b = P->X[x];
+    xidx[{b.l, b.ls1, b.ls2, b.tj, b.r}] = x;
+  }
+  std::vector<std::vector<int>> x_by_l(bl.sec.size());
+  for (int x = 0; x < (int)P->X.size(); ++x) x_by_l[P->X[x].l].push_back(x);
+  P->xin = (double*)dev_alloc(sizeof(double) * std::max<int64_t>(P->n, 1), stream_);
+  P->yout = (double*)dev_alloc(sizeof(double) * std::max<int64_t>(P->n, 1), stream_);
+
+  struct ZRef { int64_t off; int rows, cols, x; };
+  std::vector<ZRef> zs;
+  std::vector<GemmTask> t1;
+  std::vector<GemmGroup> g1;
+  std::vector<std::vector<GemmTask>> out2(P->X.size());
+  std::vector<std::vector<DiagTerm>> dout(P->X.size());
+  std::map<std::tuple<int, int, int>, int> zmap;  // (right group, D block, x) -> z
+  double flops = 0.0;
+  const int i1 = i, i2 = i + 1;
+  (void)i1;
+  (void)i2;
+  for (int b = 0; b < (int)mid.ops.size(); ++b) {
+    if (byb_l[b].empty() || byb_r[b].empty()) continue;
+    const int tkb = mid.ops[b].tk, pb = mid.ops[b].parity;
+    for (int gl : byb_l[b])
+      for (int gr : byb_r[b]) {
+        const CombOp& C = P->cl[gl];
+        const CombOp& D = P->cr[gr];
+        bool ok1[3][3], ok2[3][3];
+        allowed(pt_.pats[C.pattern], ok1);
+        allowed(pt_.pats[D.pattern], ok2);
+        for (int x = 0; x < (int)P->X.size(); ++x) {
+          const XBlock& X = P->X[x];
+          const int tjL = bl.sec[X.l].tj, tjR = br.sec[X.r].tj;
+          const int t1s = local_ts(X.ls1), t2s = local_ts(X.ls2);
+          for (int dbi = 0; dbi < (int)D.blocks->size(); ++dbi) {
+            const BlockRef& db = (*D.blocks)[dbi];
+            if (db.c != X.r) continue;
+            const int tjRp = br.sec[db.r].tj;
+            int zid = -1;
+            for (const BlockRef& cb : *C.blocks) {
+              if (cb.c != X.l) continue;
+              const int tjLp = bl.sec[cb.r].tj;
+              for (int ls1p = 0; ls1p < 3; ++ls1p) {
+                if (!ok1[X.ls1][ls1p]) continue;
+                for (int ls2p = 0; ls2p < 3; ++ls2p) {
+                  if (!ok2[X.ls2][ls2p]) continue;
+                  const int t1p = local_ts(ls1p), t2p = local_ts(ls2p);
+                  for (int tjp = std::abs(t1p - t2p); tjp <= t1p + t2p; tjp += 2) {
+                    auto it = xidx.find({cb.r, ls1p, ls2p, tjp, db.r});
+                    if (it == xidx.end()) continue;
+                    const XBlock& Xp = P->X[it->second];
+                    double coef = 0.0;
+                    for (int tjM = std::abs(tjL - t1s); tjM <= tjL + t1s; tjM += 2) {
+                      if (!triangle(t2s, tjR, tjM)) continue;
+                      double ov = cp_->overlap(tjL, X.ls1, X.ls2, X.tj, tjR, tjM);
+                      if (ov == 0.0) continue;
+                      for (int tjMp = std::abs(tjLp - t1p); tjMp <= tjLp + t1p; tjMp += 2) {
+                        if (!triangle(t2p, tjRp, tjMp)) continue;
+                        double ovp = cp_->overlap(tjLp, ls1p, ls2p, tjp, tjRp, tjMp);
+                        if (ovp == 0.0) continue;
+                        double sf = cp_->singlet(tkb, pb, tjM, tjMp);
+                        if (sf == 0.0) continue;
+                        double lc = cp_->left(C.pattern, tjL, X.ls1, tjM, tjLp, ls1p, tjMp);
+                        if (lc == 0.0) continue;
+                        double rc = cp_->right(D.pattern, X.ls2, tjR, tjM, ls2p, tjRp, tjMp);
+                        coef += ov * ovp * sf * lc * rc;
+                      }
+                    }
+                    coef *= C.scalar;
+                    if (std::fabs(coef) < 1e-14) continue;
+                    if (zid < 0) {
+                      auto zk = std::make_tuple(gr, dbi, x);
+                      auto zi = zmap.find(zk);
+                      if (zi == zmap.end()) {
+                        zid = (int)zs.size();
+                        zmap[zk] = zid;
+                        zs.push_back({0, X.rows, db.rows, x});
+                        // Z = x_X (dL x dR) . D_blk^T (dR x dR'), scaled by D's alias scalar
+                        t1.push_back({nullptr, D.data + db.off, X.cols, db.cols, X.cols, 0, 1, D.scalar});
+                        g1.push_back({nullptr, db.rows, X.rows, db.rows, (int)t1.size() - 1, (int)t1.size(), 0});
+                        flops += 2.0 * X.rows * X.cols * db.rows;
+                        P->flops1 += 2.0 * X.rows * X.cols * db.rows;
+                      } else {
+                        zid = zi->second;
+                      }
+                    }
+                    out2[it->second].push_back({C.data + cb.off, (const double*)(intptr_t)zid, cb.cols,
+                                                db.rows, cb.cols, 0, 0, coef});
+                    flops += 2.0 * cb.rows * cb.cols * db.rows;
+                    P->flops2 += 2.0 * cb.rows * cb.cols * db.rows;
+                    if (it->second == x && cb.r == cb.c && db.r == db.c)
+                      dout[x].push_back({C.data + cb.off, D.data + db.off, cb.cols, db.cols,
+                                         coef * D.scalar});
+                    (void)Xp;
+                  }
+                }
+              }
+            }
+          }
+        }
+      }
+  }
+  int64_t zsize = 0;
+  for (auto& z : zs) { z.off = zsize; zsize += (int64_t)z.rows * z.cols; }
+  P->zsize = zsize;
+  P->Z = (double*)dev_alloc(sizeof(double) * std::max<int64_t>(zsize, 1), stream_);
+  for (size_t z = 0; z < g1.size(); ++z) {
+    g1[z].C = P->Z + zs[z].off;
+    t1[z].A = P->xin + P->X[zs[z].x].off;
+  }
+  std::vector<GemmTask> t2;
+  std::vector<GemmGroup> g2;
+  std::vector<DiagTerm> dt;
+  std::vector<DiagOut> dov;
+  P->diag = (double*)dev_alloc(sizeof(double) * std::max<int64_t>(P->n, 1), stream_);
+  dev_zero(P->diag, sizeof(double) * std::max<int64_t>(P->n, 1), stream_);
+  for (int x = 0; x < (int)P->X.size(); ++x) {
+    const XBlock& X = P->X[x];
+    int b0 = (int)t2.size();
+    for (auto t : out2[x]) {
+      t.B = P->Z + zs[(int)(intptr_t)t.B].off;
+      t2.push_back(t);
+    }
+    if ((int)t2.size() > b0) g2.push_back({P->yout + X.off, X.cols, X.rows, X.cols, b0, (int)t2.size(), 0});
+    if (!dout[x].empty()) {
+      int d0 = (int)dt.size();
+      dt.insert(dt.end(), dout[x].begin(), dout[x].end());
+      dov.push_back({P->diag + X.off, X.rows, X.cols, d0, (int)dt.size()});
+    }
+  }
+  P->p1 = gemm_plan_upload(t1, g1, stream_);
+  P->p2 = gemm_plan_upload(t2, g2, stream_);
+  DiagPlan* pd = diag_plan_upload(dt, dov, stream_);
+  diag_plan_run(pd, stream_);
+  diag_plan_free(pd, stream_);
+  P->flops = flops;
+  P->ntasks = (int64_t)t1.size() + (int64_t)t2.size();
+  st_.t_plan_ms += tm.ms();
+  return P;
+}
+
+}  // namespace dmrg
+
+namespace dmrg {
+
+void Engine::free_plan(MatvecPlan* p) {
+  if (!p) return;
+  gemm_plan_free(p->p1, stream_);
+  gemm_plan_free(p->p2, stream_);
+  dev_free(p->Z, stream_);
+  dev_free(p->xin, stream_);
+  dev_free(p->yout, stream_);
+  dev_free(p->diag, stream_);
+  if (p->scr_l) dev_free(p->scr_l, stream_);
+  if (p->scr_r) dev_free(p->scr_r, stream_);
+  delete p;
+}
+
+Engine::MatvecPlan* Engine::plan_for(int i) {
+  if (cached_ && cached_site_ == i) return cached_;
+  if (cached_) { free_plan(cached_); cached_ = nullptr; cached_site_ = -1; }
+  cached_ = plan_matvec(i);
+  cached_site_ = i;
+  return cached_;
+}
+
+// y = H_eff x on the plan's fixed buffers: Z = x D^T (phase 1), y = sum coef C Z (phase 2).
+void Engine::flush_events() {
+  if (!ev_pending_) return;
+  st_.k_phase1_ms += event_elapsed_ms(ev_[0], ev_[1]);
+  st_.k_phase2_ms += event_elapsed_ms(ev_[1], ev_[2]);
+  ev_pending_ = false;
+}
+
+void Engine::run_matvec(MatvecPlan* p, const double* x, double* y) {
+  if (x != p->xin) dev_d2d(p->xin, x, sizeof(double) * p->n, stream_);
+  dev_zero(p->Z, sizeof(double) * std::max<int64_t>(p->zsize, 1), stream_);
+  dev_zero(p->yout, sizeof(double) * std::max<int64_t>(p->n, 1), stream_);
+  flush_events();
+  if (!ev_[0]) for (auto& e : ev_) e = event_create();
+  event_record(ev_[0], stream_);
+  gemm_plan_run(p->p1, stream_);
+  event_record(ev_[1], stream_);
+  gemm_plan_run(p->p2, stream_);
+  event_record(ev_[2], stream_);
+  ev_pending_ = true;
+  st_.k_launches += 1;
+  st_.k_phase1_flops += p->flops1;
+  st_.k_phase2_flops += p->flops2;
+  if (y != p->yout) dev_d2d(y, p->yout, sizeof(double) * p->n, stream_);
+  st_.matvecs += 1;
+  st_.matvec_flops += p->flops;
+  st_.last_matvec_flops = p->flops;
+  st_.last_matvec_tasks = p->ntasks;
+}
+
+void Engine::matvec(int i, const double* x, double* y) {
+  check_ready();
+  if (i < 0 || i > L_ - 2) throw std::out_of_range("site out of range");
+  MatvecPlan* p = plan_for(i);
+  run_matvec(p, x, y);
+}
+
+void Engine::diag(int i, double* d) {
+  check_ready();
+  if (i < 0 || i > L_ - 2) throw std::out_of_range("site out of range");
+  MatvecPlan* p = plan_for(i);
+  dev_d2d(d, p->diag, sizeof(double) * p->n, stream_);
+}
+
+// Eq. 25 followed by x = sqrt(2jR+1) S.
+void Engine::tt_to_x(int i, double* x) {
+  check_ready();
+  if (i < 0 || i > L_ - 2) throw std::out_of_range("site out of range");
+  int64_t n;
+  auto X = x_layout(i, &n);
+  const Bond& bl = bonds_[i];
+  const Bond& bm = bonds_[i + 1];
+  const Bond& br = bonds_[i + 2];
+  const Site& A = sites_[i];
+  const Site& B = sites_[i + 1];
+  std::map<std::tuple<int, int, int>, int> ia, ib;  // (ls, l, r) -> block
+  for (int t = 0; t < (int)A.blocks.size(); ++t) ia[{A.blocks[t].ls, A.blocks[t].l, A.blocks[t].r}] = t;
+  for (int t = 0; t < (int)B.blocks.size(); ++t) ib[{B.blocks[t].ls, B.blocks[t].l, B.blocks[t].r}] = t;
+  std::vector<GemmTask> tasks;
+  std::vector<GemmGroup> groups;
+  for (auto& xb : X) {
+    const int tjL = bl.sec[xb.l].tj, tjR = br.sec[xb.r].tj;
+    const int t1 = local_ts(xb.ls1), t2 = local_ts(xb.ls2);
+    const int ph = (((tjL + tjR + t1 + t2) / 2) & 1) ? -1 : 1;
+    int b0 = (int)tasks.size();
+    for (int m = 0; m < (int)bm.sec.size(); ++m) {
+      auto a = ia.find({xb.ls1, xb.l, m});
+      auto b = ib.find({xb.ls2, m, xb.r});
+      if (a == ia.end() || b == ib.end()) continue;
+      const int tjM = bm.sec[m].tj;
+      double c = std::sqrt((double)(tjR + 1)) * std::sqrt((double)(xb.tj + 1)) * ph *
+                 std::sqrt((double)(tjM + 1)) * wigner6j(tjL, tjR, xb.tj, t2, t1, tjM);
+      if (c == 0.0) continue;
+      const SiteBlock& sa = A.blocks[a->second];
+      const SiteBlock& sb = B.blocks[b->second];
+      tasks.push_back({A.data + sa.off, B.data + sb.off, sa.cols, sb.cols, sa.cols, 0, 0, c});
+    }
+    if ((int)tasks.size() > b0) groups.push_back({x + xb.off, xb.cols, xb.rows, xb.cols, b0, (int)tasks.size(), 0});
+  }
+  dev_zero(x, sizeof(double) * std::max<int64_t>(n, 1), stream_);
+  GemmPlan* p = gemm_plan_upload(tasks, groups, stream_);
+  gemm_plan_run(p, stream_);
+  gemm_plan_free(p, stream_);
+}
+
+// Davidson's algorithm (lowest eigenpair of H_eff, Eq. 9) entirely on the device in
+// FP64: subspace up to 32 vectors, restart on the 3 lowest Ritz vectors, diagonal
+// preconditioner, two classical Gram-Schmidt passes, convergence on ||r||_2.
+double Engine::davidson(int i, double* x, int* iters, bool* converged) {
+  check_ready();
+  MatvecPlan* P = plan_for(i);
+  const int64_t n = P->n;
+  const int mmax = std::min<int64_t>(32, std::max<int64_t>(n, 1));
+  const int nkeep = std::min(3, mmax - 1 > 0 ? mmax - 1 : 1);
+  double* V = (double*)dev_alloc(sizeof(double) * n * (mmax + 1), stream_);
+  double* AV = (double*)dev_alloc(sizeof(double) * n * (mmax + 1), stream_);
+  double* G = (double*)dev_alloc(sizeof(double) * mmax * mmax, stream_);
+  double* C = (double*)dev_alloc(sizeof(double) * mmax * mmax, stream_);
+  double* th = (double*)dev_alloc(sizeof(double) * mmax, stream_);
+  double* sc = (double*)dev_alloc(sizeof(double) * mmax * 520, stream_);
+  double* dots = (double*)dev_alloc(sizeof(double) * (mmax + 2), stream_);
+  double* r = (double*)dev_alloc(sizeof(double) * n, stream_);
+  double* t = (double*)dev_alloc(sizeof(double) * n, stream_);
+  double* tmp = (double*)dev_alloc(sizeof(double) * n * nkeep * 2, stream_);
+  dev_zero(G, sizeof(double) * mmax * mmax, stream_);
+  double* hs = (double*)host_pinned_alloc(sizeof(double) * 4);
+  auto cleanup = [&]() {
+    dev_free(V, stream_); dev_free(AV, stream_); dev_free(G, stream_); dev_free(C, stream_);
+    dev_free(th, stream_); dev_free(sc, stream_); dev_free(dots, stream_); dev_free(r, stream_);
+    dev_free(t, stream_); dev_free(tmp, stream_);
+    host_pinned_free(hs);
+  };
+  // v0 = x / |x|
+  dev_d2d(V, x, sizeof(double) * n, stream_);
+  vec_multidot(V, n, 1, V, n, dots, sc, stream_);
+  vec_normalize(V, dots, n, stream_);
+  run_matvec(P, V, AV);
+  vec_multidot(V, n, 1, AV, n, G, sc, stream_);
+  int m = 1;
+  double theta = 0.0;
+  bool conv = false;
+  int it = 0;
+  for (; it < dav_max_; ++it) {
+    small_eig(G, mmax, m, std::min(m, nkeep), th, C, stream_);
+    // u = V c0 -> x ; r = AV c0 - theta u
+    vec_combine(V, n, m, C, 0.0, x, n, stream_);
+    vec_combine(AV, n, m, C, 0.0, r, n, stream_);
+    dev_d2h(hs, th, sizeof(double), stream_);
+    dev_sync(stream_);
+    theta = hs[0];
+    vec_axpby(-theta, x, 1.0, r, n, stream_);
+    vec_multidot(r, n, 1, r, n, dots, sc, stream_);
+    dev_d2h(hs + 1, dots, sizeof(double), stream_);
+    dev_sync(stream_);
+    st_.davidson_iters += 1;
+    if (std::sqrt(std::max(hs[1], 0.0)) <= dav_tol_) { conv = true; break; }
+    if (m >= n) { conv = true; break; }
+    vec_precondition(r, P->diag, th, t, n, stream_);
+    for (int pass = 0; pass < 2; ++pass) {
+      // t -= V (V^T t)
+      vec_multidot(V, n, m, t, n, dots, sc, stream_);
+      vec_combine(V, n, m, dots, 0.0, tmp, n, stream_);
+      vec_axpby(-1.0, tmp, 1.0, t, n, stream_);
+    }
+    vec_multidot(t, n, 1, t, n, dots, sc, stream_);
+    dev_d2h(hs + 2, dots, sizeof(double), stream_);
+    dev_sync(stream_);
+    if (!(hs[2] > 1e-28)) {
+      // preconditioned direction collapsed: fall back to the residual
+      dev_d2d(t, r, sizeof(double) * n, stream_);
+      for (int pass = 0; pass < 2; ++pass) {
+        vec_multidot(V, n, m, t, n, dots, sc, stream_);
+        vec_combine(V, n, m, dots, 0.0, tmp, n, stream_);
+        vec_axpby(-1.0, tmp, 1.0, t, n, stream_);
+      }
+      vec_multidot(t, n, 1, t, n, dots, sc, stream_);
+      dev_d2h(hs + 2, dots, sizeof(double), stream_);
+      dev_sync(stream_);
+      if (!(hs[2] > 1e-30)) { conv = true; break; }
+    }
+    vec_normalize(t, dots, n, stream_);
+    if (m == mmax) {
+      // restart on the nkeep lowest Ritz vectors
+      for (int v = 0; v < nkeep; ++v) {
+        vec_combine(V, n, m, C + (size_t)v * m, 0.0, tmp + (size_t)v * n, n, stream_);
+        vec_combine(AV, n, m, C + (size_t)v * m, 0.0, tmp + (size_t)(nkeep + v) * n, n, stream_);
+      }
+      for (int v = 0; v < nkeep; ++v) {
+        dev_d2d(V + (size_t)v * n, tmp + (size_t)v * n, sizeof(double) * n, stream_);
+        dev_d2d(AV + (size_t)v * n, tmp + (size_t)(nkeep + v) * n, sizeof(double) * n, stream_);
+      }
+      std::vector<double> hth(nkeep);
+      dev_d2h(hth.data(), th, sizeof(double) * nkeep, stream_);
+      dev_sync(stream_);
+      std::vector<double> Gh((size_t)mmax * mmax, 0.0);
+      for (int v = 0; v < nkeep; ++v) Gh[(size_t)v * mmax + v] = hth[v];
+      dev_h2d(G, Gh.data(), sizeof(double) * Gh.size(), stream_);
+      m = nkeep;
+    }
+    dev_d2d(V + (size_t)m * n, t, sizeof(double) * n, stream_);
+    run_matvec(P, V + (size_t)m * n, AV + (size_t)m * n);
+    // row m of the Rayleigh matrix (lower triangle is what small_eig reads)
+    vec_multidot(V, n, m + 1, AV + (size_t)m * n, n, G + (size_t)m * mmax, sc, stream_);
+    ++m;
+  }
+  cleanup();
+  *iters = it + 1;
+  *converged = conv;
+  return theta;
+}
+
+}  // namespace dmrg
+
+namespace dmrg {
+
+// Eqs. 26-28: back-transform x into TT per middle sector (jM, NM, IM), weight the
+// columns by sqrt((2jR+1)/(2jM+1)) (which makes the bracket of Eq. 27 right-normalised),
+// decompose M = U lambda V through the eigenpairs of the smaller Gram matrix, keep the
+// D largest lambda over all sectors (D counts reduced multiplets), normalise with
+// kappa = lambda / sqrt(sum (2jM+1) lambda^2), and write T[i], T[i+1] for the sweep
+// direction (dir > 0: A[i] = U, A[i+1] = kappa V; dir < 0: A[i] = U kappa, A[i+1] = V).
+// Returns the discarded weight sum over dropped (2jM+1) kappa^2 (Eq. 15).
+double Engine::truncate(int i, int dir, int D, const double* x, double /*unused*/) {
+  check_ready();
+  if (i < 0 || i > L_ - 2) throw std::out_of_range("site out of range");
+  Timer tm;
+  int64_t nx;
+  auto X = x_layout(i, &nx);
+  const Bond bl = bonds_[i];
+  const Bond br = bonds_[i + 2];
+  if ((int)fci_.size() != L_ + 1) fci_ = sym_.fci_dims();
+  const auto& fci_cache = fci_;
+  const int I1 = sym_.orb_ir[i], I2 = sym_.orb_ir[i + 1];
+  std::vector<Sector> cands;
+  for (int l = 0; l < (int)bl.sec.size(); ++l)
+    for (int ls1 = 0; ls1 < 3; ++ls1) {
+      const Sector& a = bl.sec[l];
+      int t1 = local_ts(ls1);
+      for (int tjM = std::abs(a.tj - t1); tjM <= a.tj + t1; tjM += 2) {
+        Sector s{tjM, a.n + local_n(ls1), a.ir ^ local_ir(ls1, I1)};
+        if (fci_cache[i + 1].count(s)) cands.push_back(s);
+      }
+    }
+  std::sort(cands.begin(), cands.end());
+  cands.erase(std::unique(cands.begin(), cands.end()), cands.end());
+  struct Grp {
+    Sector s;
+    std::vector<std::pair<int, int>> rows, cols;  // (l, ls1), (r, ls2)
+    std::vector<int> roff, coff;
+    int R = 0, C = 0, n = 0;
+    int64_t moff = 0, goff = 0, woff = 0, aoff = 0;
+  };
+  std::vector<Grp> gs;
+  for (auto& s : cands) {
+    Grp g;
+    g.s = s;
+    for (int l = 0; l < (int)bl.sec.size(); ++l)
+      for (int ls1 = 0; ls1 < 3; ++ls1) {
+        const Sector& a = bl.sec[l];
+        if (a.n + local_n(ls1) == s.n && (a.ir ^ local_ir(ls1, I1)) == s.ir && triangle(a.tj, local_ts(ls1), s.tj)) {
+          g.rows.push_back({l, ls1});
+          g.roff.push_back(g.R);
+          g.R += bl.dim[l];
+        }
+      }
+    for (int r = 0; r < (int)br.sec.size(); ++r)
+      for (int ls2 = 0; ls2 < 3; ++ls2) {
+        const Sector& b = br.sec[r];
+        if (s.n + local_n(ls2) == b.n && (s.ir ^ local_ir(ls2, I2)) == b.ir && triangle(s.tj, local_ts(ls2), b.tj)) {
+          g.cols.push_back({r, ls2});
+          g.coff.push_back(g.C);
+          g.C += br.dim[r];
+        }
+      }
+    if (g.R == 0 || g.C == 0) continue;
+    g.n = std::min(g.R, g.C);
+    gs.push_back(g);
+  }
+  int64_t msz = 0, gsz = 0, wsz = 0, asz = 0;
+  for (auto& g : gs) {
+    g.moff = msz; msz += (int64_t)g.R * g.C;
+    g.goff = gsz; gsz += (int64_t)g.n * g.n;
+    g.woff = wsz; wsz += g.n;
+    g.aoff = asz; asz += (int64_t)g.R * g.C;  // room for U (R x r) or V (r x C)
+  }
+  double* M = (double*)dev_alloc(sizeof(double) * std::max<int64_t>(msz, 1), stream_);
+  double* Gm = (double*)dev_alloc(sizeof(double) * std::max<int64_t>(gsz, 1), stream_);
+  double* Q = (double*)dev_alloc(sizeof(double) * std::max<int64_t>(gsz, 1), stream_);
+  double* W = (double*)dev_alloc(sizeof(double) * std::max<int64_t>(wsz, 1), stream_);
+  double* Aux = (double*)dev_alloc(sizeof(double) * std::max<int64_t>(asz, 1), stream_);
+  dev_zero(M, sizeof(double) * std::max<int64_t>(msz, 1), stream_);
+  dev_zero(Gm, sizeof(double) * std::max<int64_t>(gsz, 1), stream_);
+  dev_zero(Aux, sizeof(double) * std::max<int64_t>(asz, 1), stream_);
+  // M blocks: sum_j (-1)^(jL+jR+s1+s2) {jL jR j; s2 s1 jM} sqrt(2j+1) x_(l s1 s2 j r)
+  std::map<Sector, int> gidx;
+  for (int g = 0; g < (int)gs.size(); ++g) gidx[gs[g].s] = g;
+  std::map<std::tuple<int, int, int>, std::vector<CombSrc>> dsts;  // (g, row blk, col blk)
+  for (auto& xb : X) {
+    const Sector& a = bl.sec[xb.l];
+    const Sector& b = br.sec[xb.r];
+    const int t1 = local_ts(xb.ls1), t2 = local_ts(xb.ls2);
+    const int ph = (((a.tj + b.tj + t1 + t2) / 2) & 1) ? -1 : 1;
+    for (int tjM = std::abs(a.tj - t1); tjM <= a.tj + t1; tjM += 2) {
+      auto it = gidx.find({tjM, a.n + local_n(xb.ls1), a.ir ^ local_ir(xb.ls1, I1)});
+      if (it == gidx.end()) continue;
+      double c = ph * wigner6j(a.tj, b.tj, xb.tj, t2, t1, tjM) * std::sqrt((double)(xb.tj + 1));
+      if (c == 0.0) continue;
+      const Grp& g = gs[it->second];
+      int rb = -1, cb = -1;
+      for (int q = 0; q < (int)g.rows.size(); ++q) if (g.rows[q] == std::make_pair(xb.l, xb.ls1)) rb = q;
+      for (int q = 0; q < (int)g.cols.size(); ++q) if (g.cols[q] == std::make_pair(xb.r, xb.ls2)) cb = q;
+      if (rb < 0 || cb < 0) continue;
+      dsts[{it->second, rb, cb}].push_back({x + xb.off, xb.cols, c});
+    }
+  }
+  {
+    std::vector<CombSrc> cs;
+    std::vector<CombDst> cd;
+    for (auto& kv : dsts) {
+      const Grp& g = gs[std::get<0>(kv.first)];
+      int rb = std::get<1>(kv.first), cb = std::get<2>(kv.first);
+      CombDst d{M + g.moff + (int64_t)g.roff[rb] * g.C + g.coff[cb], g.C,
+                bl.dim[g.rows[rb].first], br.dim[g.cols[cb].first], (int)cs.size(), 0, 0};
+      cs.insert(cs.end(), kv.second.begin(), kv.second.end());
+      d.src_end = (int)cs.size();
+      cd.push_back(d);
+    }
+    CombPlan* p = comb_plan_upload(cs, cd, stream_);
+    comb_plan_run(p, stream_);
+    comb_plan_free(p, stream_);
+  }
+  // Gram matrices of the smaller side
+  {
+    std::vector<GemmTask> t;
+    std::vector<GemmGroup> gg;
+    for (auto& g : gs) {
+      if (g.R <= g.C) t.push_back({M + g.moff, M + g.moff, g.C, g.C, g.C, 0, 1, 1.0});
+      else t.push_back({M + g.moff, M + g.moff, g.C, g.C, g.R, 1, 0, 1.0});
+      gg.push_back({Gm + g.goff, g.n, g.n, g.n, (int)t.size() - 1, (int)t.size(), 0});
+    }
+    GemmPlan* p = gemm_plan_upload(t, gg, stream_);
+    gemm_plan_run(p, stream_);
+    gemm_plan_free(p, stream_);
+  }
+  std::vector<EigJob> jobs;
+  for (auto& g : gs) jobs.push_back({Gm + g.goff, Q + g.goff, W + g.woff, g.n});
+  eig_batched(jobs, stream_);
+  std::vector<int> goff(1, 0), wgt;
+  for (auto& g : gs) { goff.push_back(goff.back() + g.n); wgt.push_back(g.s.tj + 1); }
+  std::vector<int> kept;
+  double norm2 = 0.0, disc = 0.0;
+  select_largest(W, goff, wgt, D, 1e-13, kept, &norm2, &disc, stream_);
+  if (!(norm2 > 0.0)) throw std::runtime_error("two-site vector has zero norm");
+  const double w_disc = disc / norm2;
+  // the other factor: V = Q_r^T M (R <= C) or U = M Q_r (C < R)
+  {
+    std::vector<GemmTask> t;
+    std::vector<GemmGroup> gg;
+    for (int q = 0; q < (int)gs.size(); ++q) {
+      const Grp& g = gs[q];
+      int r = kept[q];
+      if (r == 0) continue;
+      if (g.R <= g.C) {
+        t.push_back({Q + g.goff, M + g.moff, g.n, g.C, g.R, 1, 0, 1.0});
+        gg.push_back({Aux + g.aoff, g.C, r, g.C, (int)t.size() - 1, (int)t.size(), 0});
+      } else {
+        t.push_back({M + g.moff, Q + g.goff, g.C, g.n, g.C, 0, 0, 1.0});
+        gg.push_back({Aux + g.aoff, r, g.R, r, (int)t.size() - 1, (int)t.size(), 0});
+      }
+    }
+    GemmPlan* p = gemm_plan_upload(t, gg, stream_);
+    gemm_plan_run(p, stream_);
+    gemm_plan_free(p, stream_);
+  }
+  // new middle bond and tensors
+  Bond nb;
+  std::vector<int> gnew(gs.size(), -1);
+  for (int q = 0; q < (int)gs.size(); ++q)
+    if (kept[q] > 0) { gnew[q] = (int)nb.sec.size(); nb.sec.push_back(gs[q].s); nb.dim.push_back(kept[q]); }
+  if (nb.sec.empty()) throw std::runtime_error("truncation kept no states");
+  bonds_[i + 1] = nb;
+  for (int b = i + 1; b <= L_; ++b) free_env(lenv_[b]);
+  for (int b = 0; b <= i + 1; ++b) free_env(renv_[b]);
+  if (cached_) { free_plan(cached_); cached_ = nullptr; cached_site_ = -1; }
+  alloc_site(i);
+  alloc_site(i + 1);
+  const double inv = 1.0 / std::sqrt(norm2);
+  std::vector<ScatterJob> sj;
+  std::map<std::tuple<int, int, int>, const SiteBlock*> ia, ib;
+  for (auto& b : sites_[i].blocks) ia[{b.ls, b.l, b.r}] = &b;
+  for (auto& b : sites_[i + 1].blocks) ib[{b.ls, b.l, b.r}] = &b;
+  for (int q = 0; q < (int)gs.size(); ++q) {
+    const Grp& g = gs[q];
+    const int r = kept[q];
+    if (r == 0) continue;
+    const int m = gnew[q];
+    const double* wq = W + g.woff;
+    for (int rb = 0; rb < (int)g.rows.size(); ++rb) {
+      const SiteBlock* sb = ia.at({g.rows[rb].second, g.rows[rb].first, m});
+      double* dst = sites_[i].data + sb->off;
+      if (g.R <= g.C) {  // U = Q_r
+        const double* src = Q + g.goff + (int64_t)g.roff[rb] * g.n;
+        if (dir > 0) sj.push_back({dst, src, nullptr, nullptr, r, g.n, sb->rows, r, 0, 0, 0, 1.0});
+        else sj.push_back({dst, src, nullptr, wq, r, g.n, sb->rows, r, 0, 1, 0, inv});
+      } else {  // U = M Q_r / lambda
+        const double* src = Aux + g.aoff + (int64_t)g.roff[rb] * r;
+        if (dir > 0) sj.push_back({dst, src, nullptr, wq, r, r, sb->rows, r, 0, 2, 0, 1.0});
+        else sj.push_back({dst, src, nullptr, nullptr, r, r, sb->rows, r, 0, 0, 0, inv});
+      }
+    }
+    for (int cb = 0; cb < (int)g.cols.size(); ++cb) {
+      const SiteBlock* sb = ib.at({g.cols[cb].second, m, g.cols[cb].first});
+      double* dst = sites_[i + 1].data + sb->off;
+      const double f = std::sqrt((double)(g.s.tj + 1) / (double)(br.sec[g.cols[cb].first].tj + 1));
+      const int dR = sb->cols;
+      if (g.R <= g.C) {  // V = Q_r^T M / lambda
+        const double* src = Aux + g.aoff + g.coff[cb];
+        if (dir > 0) sj.push_back({dst, src, nullptr, nullptr, dR, g.C, r, dR, 0, 0, 0, f * inv});
+        else sj.push_back({dst, src, wq, nullptr, dR, g.C, r, dR, 2, 0, 0, f});
+      } else {  // V = Q_r^T
+        const double* src = Q + g.goff + (int64_t)g.coff[cb] * g.n;
+        if (dir > 0) sj.push_back({dst, src, wq, nullptr, dR, g.n, r, dR, 1, 0, 1, f * inv});
+        else sj.push_back({dst, src, nullptr, nullptr, dR, g.n, r, dR, 0, 0, 1, f});
+      }
+    }
+  }
+  scatter_batched(sj, stream_);
+  dev_free(M, stream_);
+  dev_free(Gm, stream_);
+  dev_free(Q, stream_);
+  dev_free(W, stream_);
+  dev_free(Aux, stream_);
+  st_.last_w_disc = w_disc;
+  st_.max_w_disc = std::max(st_.max_w_disc, w_disc);
+  st_.t_trunc_ms += tm.ms();
+  return w_disc;
+}
+
+// Mixed canonical form around `center` (Sec. 2.2, Eqs. 5-6) by exact decompositions:
+// moving left from the right end right-normalises sites L-1..1, then moving right
+// left-normalises sites 0..center-1.
+void Engine::canonicalize(int center) {
+  check_ready();
+  if (center < 0 || center > L_ - 2) throw std::out_of_range("center out of range");
+  auto move = [&](int i, int dir) {
+    int64_t n;
+    x_layout(i, &n);
+    double* x = (double*)dev_alloc(sizeof(double) * std::max<int64_t>(n, 1), stream_);
+    tt_to_x(i, x);
+    truncate(i, dir, std::numeric_limits<int>::max() / 2, x, 0.0);
+    dev_free(x, stream_);
+  };
+  for (int i = L_ - 2; i >= 0; --i) move(i, -1);
+  for (int i = 0; i < center; ++i) move(i, +1);
+}
+
+// ConvergenceScheme of Sec. 4.2: per instruction, macro-iterations (a sweep right then
+// a sweep left) until the energy change is below E_conv or N_max is reached; the
+// result is the lowest micro-iteration energy (Sec. 4.3).
+double Engine::solve(double* e_last_out) {
+  check_ready();
+  Timer total;
+  canonicalize(0);
+  double e_min = std::numeric_limits<double>::infinity(), e_last = 0.0;
+  double e_prev = std::numeric_limits<double>::infinity();
+  bool all_conv = true;
+  for (size_t s = 0; s < sched_D_.size(); ++s) {
+    const int D = sched_D_[s];
+    const double econv = s < sched_econv_.size() ? sched_econv_[s] : 1e-8;
+    const int nmax = s < sched_nmax_.size() ? sched_nmax_[s] : 1;
+    const double gamma = s < sched_noise_.size() ? sched_noise_[s] : 0.0;
+    for (int it = 0; it < nmax; ++it) {
+      for (int dir = 1; dir >= -1; dir -= 2) {
+        double wmax = 0.0;
+        for (int step = 0; step < L_ - 1; ++step) {
+          const int i = dir > 0 ? step : L_ - 2 - step;
+          double w = 0.0;
+          int iters = 0;
+          bool conv = false;
+          double e = sweep_step(i, dir, D, gamma, &w, &iters, &conv);
+          all_conv = all_conv && conv;
+          e_min = std::min(e_min, e);
+          e_last = e;
+          wmax = std::max(wmax, w);
+          st_.micro_iters += 1;
+        }
+        w_prev_ = wmax;
+      }
+      const bool done = std::fabs(e_last - e_prev) < econv;
+      e_prev = e_last;
+      if (done) break;
+    }
+  }
+  st_.t_total_ms += total.ms();
+  if (e_last_out) *e_last_out = e_last;
+  (void)all_conv;
+  return e_min;
+}
+
+double Engine::sweep_step(int i, int dir, int D, double gamma, double* w_disc, int* iters, bool* conv) {
+  check_ready();
+  if (i < 0 || i > L_ - 2) throw std::out_of_range("site out of range");
+  MatvecPlan* P = plan_for(i);
+  double* x = (double*)dev_alloc(sizeof(double) * std::max<int64_t>(P->n, 1), stream_);
+  tt_to_x(i, x);
+  double e = davidson(i, x, iters, conv) + econst_;
+  if (gamma > 0.0 && w_prev_ > 0.0) {
+    // Sec. 4.2: noise bounded by 0.5 gamma w_disc(previous half sweep), then the
+    // decomposition renormalises through kappa
+    vec_add_noise(x, P->n, 0.5 * gamma * w_prev_, 0x5eed0000ull + (noise_counter_++) * 1000003ull, stream_);
+  }
+  cached_ = nullptr;  // keep P's combined operators for the update below
+  cached_site_ = -1;
+  double w = truncate(i, dir, D, x, 0.0);
+  if (dir > 0) update_left_from(i, P->cl);
+  else update_right_from(i + 1, P->cr);
+  free_plan(P);
+  dev_free(x, stream_);
+  st_.micro_iters += 1;
+  *w_disc = w;
+  return e;
+}
+
+}  // namespace dmrg

@@ -1,0 +1,160 @@
+// Host orchestration of the two-site spin-adapted DMRG on one GPU.
+#pragma once
+#include <cstdint>
+#include <map>
+#include <memory>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "coupling.hpp"
+#include "device.hpp"
+#include "mpo.hpp"
+#include "symmetry.hpp"
+
+namespace dmrg {
+
+struct BlockRef {
+  int r, c;      // row / column sector indices at the bond
+  int64_t off;   // element offset inside the owning buffer
+  int rows, cols;
+};
+
+// Reduced blocks of every operator of one bond (one side), in one device buffer.
+struct OpStore {
+  bool valid = false;
+  int bond = -1;
+  std::vector<std::vector<BlockRef>> blocks;         // per operator
+  std::vector<std::unordered_map<int64_t, int>> at;  // (r << 32 | c) -> block index
+  double* data = nullptr;
+  int64_t size = 0;
+};
+
+// One MPS site: reduced tensor blocks T[k]^{(s N I)}_{(left sector),(right sector)}.
+struct SiteBlock {
+  int ls, l, r;
+  int64_t off;
+  int rows, cols;
+};
+struct Site {
+  std::vector<SiteBlock> blocks;
+  double* data = nullptr;
+  int64_t size = 0;
+};
+
+struct XBlock {  // block of the two-site vector: (jL NL IL) (s1) (s2) j (jR NR IR)
+  int l, ls1, ls2, tj, r;
+  int64_t off;
+  int rows, cols;
+};
+
+// A combined operator sum_a scalar_a O_a over sources sharing one site pattern.
+struct CombOp {
+  int target = -1, pattern = -1;
+  double scalar = 1.0;           // multiplies the blocks (alias) or 1 (materialised)
+  const std::vector<BlockRef>* blocks = nullptr;
+  const std::unordered_map<int64_t, int>* at = nullptr;
+  const double* data = nullptr;  // base of the blocks
+  // materialised storage
+  std::vector<BlockRef> own_blocks;
+  std::unordered_map<int64_t, int> own_at;
+  std::vector<std::pair<int, double>> sources;  // (operator index, scalar)
+};
+
+struct Stats {
+  int64_t matvecs = 0, davidson_iters = 0, micro_iters = 0;
+  double matvec_flops = 0.0, last_matvec_flops = 0.0, last_matvec_ms = 0.0;
+  int64_t last_matvec_tasks = 0;
+  double t_matvec_ms = 0, t_update_ms = 0, t_trunc_ms = 0, t_plan_ms = 0, t_total_ms = 0;
+  double last_w_disc = 0.0, max_w_disc = 0.0;
+  // device time of the matvec kernels (CUDA events on the engine's stream)
+  double k_phase1_ms = 0.0, k_phase2_ms = 0.0;
+  int64_t k_launches = 0;
+  double k_phase1_flops = 0.0, k_phase2_flops = 0.0;
+};
+
+class Engine {
+ public:
+  Engine(int L, int n_irrep, const std::vector<int>& orb_ir, int N, int two_S, int irrep,
+         Stream stream);
+  ~Engine();
+
+  void set_integrals(double econst, const double* h, const double* V);
+  void set_schedule(const std::vector<int>& D, const std::vector<double>& econv,
+                    const std::vector<int>& nmax, const std::vector<double>& noise, double dtol,
+                    int dmax);
+  void init_mps(uint64_t seed);
+  std::vector<char> get_mps();
+  void set_mps(const char* buf, size_t len);
+
+  // two-site probes (site i means orbitals i, i+1); the MPS must be in mixed canonical
+  // form around i (left-normalised left of i, right-normalised right of i+1)
+  void layout(int i, std::vector<int64_t>& table, int64_t& n);
+  void tt_to_x(int i, double* x_dev);
+  void matvec(int i, const double* x_dev, double* y_dev);
+  void diag(int i, double* d_dev);
+  double davidson(int i, double* x_dev, int* iters, bool* converged);
+  double truncate(int i, int dir, int D, const double* x_dev, double noise);
+  double solve(double* e_last);
+  // one micro-iteration of a sweep at sites (i, i+1): Eq. 25, Davidson, noise,
+  // Eqs. 26-28 and the operator update in the sweep direction
+  double sweep_step(int i, int dir, int D, double gamma, double* w_disc, int* iters, bool* conv);
+  void canonicalize(int center);
+
+  const Stats& stats() { flush_events(); return st_; }
+  Stream stream() const { return stream_; }
+  void set_stream(Stream s) { stream_ = s; }
+  int L() const { return L_; }
+
+ private:
+  struct MatvecPlan;
+  void check_ready() const;
+  void free_env(OpStore& e);
+  void alloc_env(OpStore& e, int bond, const OpSet& ops);
+  void ensure_left(int k);
+  void ensure_right(int k);
+  void build_left(int k);
+  void build_right(int k);
+  void invalidate_envs_from_site(int k);
+  std::vector<XBlock> x_layout(int i, int64_t* n) const;
+  void group_left(int i, std::vector<CombOp>& out, double** scratch);
+  void group_right(int i, std::vector<CombOp>& out, double** scratch);
+  MatvecPlan* plan_matvec(int i);
+  void free_plan(MatvecPlan* p);
+  MatvecPlan* plan_for(int i);
+  void run_matvec(MatvecPlan* p, const double* x, double* y);
+  void update_left_from(int i, std::vector<CombOp>& comb);
+  void update_right_from(int i, std::vector<CombOp>& comb);
+  void alloc_site(int k);
+  void free_site(int k);
+  void identity_fill(OpStore& e, int op);
+
+  int L_, N_, two_S_, irrep_;
+  Symmetry sym_;
+  Integrals g_;
+  double econst_ = 0.0;
+  bool have_integrals_ = false, have_mps_ = false;
+  std::vector<OpSet> opsets_;
+  PatternTable pt_;
+  std::unique_ptr<Coupling> cp_;
+  std::vector<std::vector<WEntry>> W_;
+  std::vector<Bond> bonds_;
+  std::vector<std::map<Sector, int>> fci_;  // FCI-capped sector dimensions per bond
+  std::vector<Site> sites_;
+  std::vector<OpStore> lenv_, renv_;
+  std::vector<int> sched_D_, sched_nmax_;
+  std::vector<double> sched_econv_, sched_noise_;
+  double dav_tol_ = 1e-10;
+  int dav_max_ = 100;
+  Stream stream_;
+  Stats st_;
+  MatvecPlan* cached_ = nullptr;
+  int cached_site_ = -1;
+  double w_prev_ = 0.0;
+  uint64_t noise_counter_ = 0;
+  void* ev_[3] = {nullptr, nullptr, nullptr};
+  void flush_events();
+  bool ev_pending_ = false;
+};
+
+}  // namespace dmrg

@@ -1,0 +1,738 @@
+// FP64 kernels of the two-site sweep (sm_103a).  Every launch executes a table built
+// by the host planner; no kernel waits on another block or on another launch.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <stdexcept>
+#include <string>
+
+#include "device.hpp"
+
+namespace dmrg {
+
+namespace {
+
+thread_local std::string g_err;
+
+inline cudaStream_t S(Stream s) { return (cudaStream_t)s; }
+
+inline void ck(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) {
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    throw std::runtime_error(g_err);
+  }
+}
+
+inline int nblk(int64_t n, int t) { return (int)std::min<int64_t>((n + t - 1) / t, 65535 * 8); }
+
+}  // namespace
+
+// ------------------------------------------------------------------ memory
+
+void* dev_alloc(size_t bytes, Stream s) {
+  void* p = nullptr;
+  if (bytes == 0) bytes = 16;
+  ck(cudaMallocAsync(&p, bytes, S(s)), "cudaMallocAsync");
+  return p;
+}
+void dev_free(void* p, Stream s) {
+  if (p) ck(cudaFreeAsync(p, S(s)), "cudaFreeAsync");
+}
+void dev_h2d(void* d, const void* h, size_t b, Stream s) {
+  if (b) ck(cudaMemcpyAsync(d, h, b, cudaMemcpyHostToDevice, S(s)), "h2d");
+}
+void dev_d2h(void* h, const void* d, size_t b, Stream s) {
+  if (b) ck(cudaMemcpyAsync(h, d, b, cudaMemcpyDeviceToHost, S(s)), "d2h");
+}
+void dev_d2d(void* d, const void* x, size_t b, Stream s) {
+  if (b) ck(cudaMemcpyAsync(d, x, b, cudaMemcpyDeviceToDevice, S(s)), "d2d");
+}
+void dev_zero(void* p, size_t b, Stream s) {
+  if (b) ck(cudaMemsetAsync(p, 0, b, S(s)), "memset");
+}
+void dev_sync(Stream s) { ck(cudaStreamSynchronize(S(s)), "stream sync"); }
+int dev_check(const char** msg) {
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) return 0;
+  g_err = cudaGetErrorString(e);
+  if (msg) *msg = g_err.c_str();
+  return (int)e;
+}
+void* host_pinned_alloc(size_t b) {
+  void* p = nullptr;
+  ck(cudaMallocHost(&p, b ? b : 16), "cudaMallocHost");
+  return p;
+}
+void host_pinned_free(void* p) {
+  if (p) cudaFreeHost(p);
+}
+void* event_create() {
+  cudaEvent_t e;
+  ck(cudaEventCreate(&e), "cudaEventCreate");
+  return (void*)e;
+}
+void event_destroy(void* e) {
+  if (e) cudaEventDestroy((cudaEvent_t)e);
+}
+void event_record(void* e, Stream s) { ck(cudaEventRecord((cudaEvent_t)e, S(s)), "cudaEventRecord"); }
+float event_elapsed_ms(void* a, void* b) {
+  float ms = 0.f;
+  ck(cudaEventSynchronize((cudaEvent_t)b), "cudaEventSynchronize");
+  ck(cudaEventElapsedTime(&ms, (cudaEvent_t)a, (cudaEvent_t)b), "cudaEventElapsedTime");
+  return ms;
+}
+
+// ------------------------------------------------------------------ grouped GEMM
+
+namespace {
+constexpr int BM = 32, BN = 32, BK = 16;
+
+__global__ void __launch_bounds__(256) k_grouped_gemm(const GemmTask* __restrict__ tasks,
+                                                     const GemmGroup* __restrict__ groups,
+                                                     int ngroups) {
+  __shared__ double As[BK][BM + 1];
+  __shared__ double Bs[BK][BN + 1];
+  const int tile = blockIdx.x;
+  int lo = 0, hi = ngroups - 1;
+  while (lo < hi) {  // last group with tile_begin <= tile
+    int mid = (lo + hi + 1) >> 1;
+    if (groups[mid].tile_begin <= tile) lo = mid; else hi = mid - 1;
+  }
+  const GemmGroup g = groups[lo];
+  const int local = tile - g.tile_begin;
+  const int tn = (g.n + BN - 1) / BN;
+  const int row0 = (local / tn) * BM, col0 = (local % tn) * BN;
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+  for (int t = g.task_begin; t < g.task_end; ++t) {
+    const GemmTask T = tasks[t];
+    for (int k0 = 0; k0 < T.k; k0 += BK) {
+      for (int e = tid; e < BM * BK; e += 256) {
+        int r, kk;
+        double v = 0.0;
+        if (T.transA) { kk = e / BM; r = e % BM; } else { r = e / BK; kk = e % BK; }
+        int gr = row0 + r, gk = k0 + kk;
+        if (gr < g.m && gk < T.k)
+          v = T.transA ? T.A[(size_t)gk * T.lda + gr] : T.A[(size_t)gr * T.lda + gk];
+        As[kk][r] = v * T.alpha;
+      }
+      for (int e = tid; e < BK * BN; e += 256) {
+        int c, kk;
+        double v = 0.0;
+        if (T.transB) { c = e / BK; kk = e % BK; } else { kk = e / BN; c = e % BN; }
+        int gc = col0 + c, gk = k0 + kk;
+        if (gc < g.n && gk < T.k)
+          v = T.transB ? T.B[(size_t)gc * T.ldb + gk] : T.B[(size_t)gk * T.ldb + gc];
+        Bs[kk][c] = v;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < BK; ++kk) {
+        double a0 = As[kk][ty], a1 = As[kk][ty + 16];
+        double b0 = Bs[kk][tx], b1 = Bs[kk][tx + 16];
+        acc[0][0] = fma(a0, b0, acc[0][0]);
+        acc[0][1] = fma(a0, b1, acc[0][1]);
+        acc[1][0] = fma(a1, b0, acc[1][0]);
+        acc[1][1] = fma(a1, b1, acc[1][1]);
+      }
+      __syncthreads();
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      int r = row0 + ty + 16 * i, c = col0 + tx + 16 * j;
+      if (r < g.m && c < g.n) g.C[(size_t)r * g.ldc + c] += acc[i][j];
+    }
+}
+}  // namespace
+
+struct GemmPlan {
+  GemmTask* tasks = nullptr;
+  GemmGroup* groups = nullptr;
+  int ngroups = 0, ntiles = 0;
+  int64_t ntasks = 0;
+};
+
+GemmPlan* gemm_plan_upload(const std::vector<GemmTask>& t, std::vector<GemmGroup>& g, Stream s) {
+  GemmPlan* p = new GemmPlan;
+  int tiles = 0;
+  for (auto& gr : g) {
+    gr.tile_begin = tiles;
+    if (gr.m > 0 && gr.n > 0) tiles += ((gr.m + BM - 1) / BM) * ((gr.n + BN - 1) / BN);
+  }
+  p->ngroups = (int)g.size();
+  p->ntiles = tiles;
+  p->ntasks = (int64_t)t.size();
+  if (!t.empty()) {
+    p->tasks = (GemmTask*)dev_alloc(t.size() * sizeof(GemmTask), s);
+    dev_h2d(p->tasks, t.data(), t.size() * sizeof(GemmTask), s);
+  }
+  if (!g.empty()) {
+    p->groups = (GemmGroup*)dev_alloc(g.size() * sizeof(GemmGroup), s);
+    dev_h2d(p->groups, g.data(), g.size() * sizeof(GemmGroup), s);
+  }
+  return p;
+}
+
+void gemm_plan_run(const GemmPlan* p, Stream s) {
+  if (!p || p->ntiles == 0) return;
+  k_grouped_gemm<<<p->ntiles, 256, 0, S(s)>>>(p->tasks, p->groups, p->ngroups);
+  ck(cudaGetLastError(), "grouped_gemm launch");
+}
+
+void gemm_plan_free(GemmPlan* p, Stream s) {
+  if (!p) return;
+  dev_free(p->tasks, s);
+  dev_free(p->groups, s);
+  delete p;
+}
+
+int64_t gemm_plan_tasks(const GemmPlan* p) { return p ? p->ntasks : 0; }
+
+// ------------------------------------------------------------------ combine
+
+namespace {
+__global__ void k_combine(const CombSrc* __restrict__ src, const CombDst* __restrict__ dst) {
+  const CombDst d = dst[blockIdx.x];
+  const int64_t n = (int64_t)d.rows * d.cols;
+  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+    int r = (int)(e / d.cols), c = (int)(e % d.cols);
+    double v = d.accumulate ? d.dst[(size_t)r * d.ld + c] : 0.0;
+    for (int s = d.src_begin; s < d.src_end; ++s) v += src[s].alpha * src[s].src[(size_t)r * src[s].ld + c];
+    d.dst[(size_t)r * d.ld + c] = v;
+  }
+}
+}  // namespace
+
+struct CombPlan {
+  CombSrc* src = nullptr;
+  CombDst* dst = nullptr;
+  int ndst = 0;
+};
+
+CombPlan* comb_plan_upload(const std::vector<CombSrc>& s, const std::vector<CombDst>& d, Stream st) {
+  CombPlan* p = new CombPlan;
+  p->ndst = (int)d.size();
+  if (!s.empty()) {
+    p->src = (CombSrc*)dev_alloc(s.size() * sizeof(CombSrc), st);
+    dev_h2d(p->src, s.data(), s.size() * sizeof(CombSrc), st);
+  }
+  if (!d.empty()) {
+    p->dst = (CombDst*)dev_alloc(d.size() * sizeof(CombDst), st);
+    dev_h2d(p->dst, d.data(), d.size() * sizeof(CombDst), st);
+  }
+  return p;
+}
+
+void comb_plan_run(const CombPlan* p, Stream s) {
+  if (!p || p->ndst == 0) return;
+  for (int off = 0; off < p->ndst; off += 65535) {
+    int n = std::min(65535, p->ndst - off);
+    k_combine<<<n, 128, 0, S(s)>>>(p->src, p->dst + off);
+  }
+  ck(cudaGetLastError(), "combine launch");
+}
+
+void comb_plan_free(CombPlan* p, Stream s) {
+  if (!p) return;
+  dev_free(p->src, s);
+  dev_free(p->dst, s);
+  delete p;
+}
+
+// ------------------------------------------------------------------ diagonal
+
+namespace {
+__global__ void k_diag(const DiagTerm* __restrict__ t, const DiagOut* __restrict__ o) {
+  const DiagOut d = o[blockIdx.x];
+  const int64_t n = (int64_t)d.dL * d.dR;
+  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+    int a = (int)(e / d.dR), b = (int)(e % d.dR);
+    double v = d.out[e];
+    for (int s = d.term_begin; s < d.term_end; ++s)
+      v += t[s].coef * t[s].C[(size_t)a * t[s].ldc + a] * t[s].D[(size_t)b * t[s].ldd + b];
+    d.out[e] = v;
+  }
+}
+}  // namespace
+
+struct DiagPlan {
+  DiagTerm* t = nullptr;
+  DiagOut* o = nullptr;
+  int n = 0;
+};
+
+DiagPlan* diag_plan_upload(const std::vector<DiagTerm>& t, const std::vector<DiagOut>& o, Stream s) {
+  DiagPlan* p = new DiagPlan;
+  p->n = (int)o.size();
+  if (!t.empty()) {
+    p->t = (DiagTerm*)dev_alloc(t.size() * sizeof(DiagTerm), s);
+    dev_h2d(p->t, t.data(), t.size() * sizeof(DiagTerm), s);
+  }
+  if (!o.empty()) {
+    p->o = (DiagOut*)dev_alloc(o.size() * sizeof(DiagOut), s);
+    dev_h2d(p->o, o.data(), o.size() * sizeof(DiagOut), s);
+  }
+  return p;
+}
+
+void diag_plan_run(const DiagPlan* p, Stream s) {
+  if (!p || p->n == 0) return;
+  for (int off = 0; off < p->n; off += 65535) {
+    int n = std::min(65535, p->n - off);
+    k_diag<<<n, 128, 0, S(s)>>>(p->t, p->o + off);
+  }
+  ck(cudaGetLastError(), "diag launch");
+}
+
+void diag_plan_free(DiagPlan* p, Stream s) {
+  if (!p) return;
+  dev_free(p->t, s);
+  dev_free(p->o, s);
+  delete p;
+}
+
+// ------------------------------------------------------------------ vector kernels
+
+namespace {
+constexpr int kDotChunk = 4096;
+constexpr int kMaxChunks = 512;
+
+__global__ void k_multidot_partial(const double* __restrict__ V, int64_t ldv,
+                                   const double* __restrict__ w, int64_t n, int nch,
+                                   double* __restrict__ part) {
+  __shared__ double sh[256];
+  const int j = blockIdx.y, c = blockIdx.x;
+  const double* v = V + (size_t)j * ldv;
+  double s = 0.0;
+  for (int64_t i = (int64_t)c * 256 + threadIdx.x; i < n; i += (int64_t)nch * 256) s += v[i] * w[i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[(size_t)j * nch + c] = sh[0];
+}
+
+__global__ void k_multidot_final(const double* __restrict__ part, int nch, int m, double* out) {
+  const int j = blockIdx.x;
+  __shared__ double sh[256];
+  double s = 0.0;
+  for (int c = threadIdx.x; c < nch; c += 256) s += part[(size_t)j * nch + c];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[j] = sh[0];
+}
+
+__global__ void k_vec_combine(const double* __restrict__ V, int64_t ldv, int m,
+                              const double* __restrict__ c, double beta, double* __restrict__ y,
+                              int64_t n) {
+  __shared__ double cs[128];
+  for (int j = threadIdx.x; j < m; j += blockDim.x) cs[j] = c[j];
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double s = beta == 0.0 ? 0.0 : beta * y[i];
+    for (int j = 0; j < m; ++j) s += cs[j] * V[(size_t)j * ldv + i];
+    y[i] = s;
+  }
+}
+
+__global__ void k_axpby(double a, const double* __restrict__ x, double b, double* __restrict__ y,
+                        int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = a * x[i] + (b == 0.0 ? 0.0 : b * y[i]);
+}
+
+__global__ void k_normalize(double* __restrict__ y, const double* __restrict__ nrm2, int64_t n) {
+  double s = *nrm2 > 0.0 ? 1.0 / sqrt(*nrm2) : 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] *= s;
+}
+
+__global__ void k_precondition(const double* __restrict__ r, const double* __restrict__ d,
+                               const double* __restrict__ theta, double* __restrict__ t,
+                               int64_t n) {
+  const double th = *theta;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double den = th - d[i];
+    if (fabs(den) < 1e-12) den = den < 0 ? -1e-12 : 1e-12;
+    t[i] = r[i] / den;
+  }
+}
+
+__device__ inline void sym_schur2(double app, double aqq, double apq, double& c, double& s) {
+  if (apq == 0.0) { c = 1.0; s = 0.0; return; }
+  double th = (aqq - app) / (2.0 * apq);
+  double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(1.0 + th * th));
+  c = 1.0 / sqrt(1.0 + t * t);
+  s = t * c;
+}
+
+// one CTA: Jacobi on an m x m symmetric matrix in shared memory (m <= 48)
+__global__ void k_small_eig(const double* __restrict__ G, int gld, int m, int k,
+                            double* __restrict__ theta, double* __restrict__ C) {
+  __shared__ double A[48][49];
+  __shared__ double Q[48][49];
+  __shared__ double cs[32], sn[32];
+  __shared__ int pp[32], qq[32];
+  __shared__ double off_s;
+  __shared__ int order[48];
+  const int tid = threadIdx.x;
+  for (int e = tid; e < m * m; e += blockDim.x) {
+    int i = e / m, j = e % m;
+    A[i][j] = i >= j ? G[(size_t)i * gld + j] : G[(size_t)j * gld + i];  // lower triangle
+    Q[i][j] = (i == j) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  const int np = (m + 1) & ~1;
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    if (tid == 0) {
+      double off = 0.0, tot = 0.0;
+      for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) {
+          tot += A[i][j] * A[i][j];
+          if (i != j) off += A[i][j] * A[i][j];
+        }
+      off_s = (off <= 1e-30 * tot || off == 0.0) ? -1.0 : off;
+    }
+    __syncthreads();
+    if (off_s < 0.0) break;
+    for (int step = 0; step < np - 1; ++step) {
+      if (tid < np / 2) {
+        // round-robin pairing: position 0 fixed, others rotate
+        int a = tid, b = np - 1 - tid;
+        auto pos = [&](int x) { return x == 0 ? 0 : 1 + (x - 1 + step) % (np - 1); };
+        int p = pos(a), q = pos(b);
+        if (p > q) { int t = p; p = q; q = t; }
+        pp[tid] = p; qq[tid] = q;
+        if (q < m) sym_schur2(A[p][p], A[q][q], A[p][q], cs[tid], sn[tid]);
+        else { cs[tid] = 1.0; sn[tid] = 0.0; }
+      }
+      __syncthreads();
+      for (int e = tid; e < (np / 2) * m; e += blockDim.x) {
+        int r = e / m, j = e % m;
+        int p = pp[r], q = qq[r];
+        if (q >= m) continue;
+        double c = cs[r], s = sn[r];
+        double ap = A[p][j], aq = A[q][j];
+        A[p][j] = c * ap - s * aq;
+        A[q][j] = s * ap + c * aq;
+      }
+      __syncthreads();
+      for (int e = tid; e < (np / 2) * m; e += blockDim.x) {
+        int r = e / m, i = e % m;
+        int p = pp[r], q = qq[r];
+        if (q >= m) continue;
+        double c = cs[r], s = sn[r];
+        double ap = A[i][p], aq = A[i][q];
+        A[i][p] = c * ap - s * aq;
+        A[i][q] = s * ap + c * aq;
+        double qp = Q[i][p], qv = Q[i][q];
+        Q[i][p] = c * qp - s * qv;
+        Q[i][q] = s * qp + c * qv;
+      }
+      __syncthreads();
+    }
+  }
+  if (tid == 0) {
+    for (int i = 0; i < m; ++i) order[i] = i;
+    for (int i = 0; i < m; ++i)
+      for (int j = i + 1; j < m; ++j)
+        if (A[order[j]][order[j]] < A[order[i]][order[i]]) { int t = order[i]; order[i] = order[j]; order[j] = t; }
+  }
+  __syncthreads();
+  for (int e = tid; e < k * m; e += blockDim.x) {
+    int v = e / m, i = e % m;
+    C[(size_t)v * m + i] = Q[i][order[v]];
+  }
+  if (tid < k) theta[tid] = A[order[tid]][order[tid]];
+}
+
+__device__ inline uint64_t splitmix(uint64_t x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+
+__global__ void k_noise(double* x, int64_t n, double amp, uint64_t seed) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t u = splitmix(seed + (uint64_t)i) >> 11;
+    double r = (double)u * (2.0 / 9007199254740992.0) - 1.0;
+    x[i] += amp * r;
+  }
+}
+}  // namespace
+
+void vec_multidot(const double* V, int64_t ldv, int m, const double* w, int64_t n, double* out,
+                  double* scratch, Stream s) {
+  if (m <= 0) return;
+  int nch = (int)std::min<int64_t>(kMaxChunks, std::max<int64_t>(1, (n + kDotChunk - 1) / kDotChunk));
+  dim3 grid(nch, m);
+  k_multidot_partial<<<grid, 256, 0, S(s)>>>(V, ldv, w, n, nch, scratch);
+  k_multidot_final<<<m, 256, 0, S(s)>>>(scratch, nch, m, out);
+  ck(cudaGetLastError(), "multidot");
+}
+
+void vec_combine(const double* V, int64_t ldv, int m, const double* c, double beta, double* y,
+                 int64_t n, Stream s) {
+  k_vec_combine<<<nblk(n, 256), 256, 0, S(s)>>>(V, ldv, m, c, beta, y, n);
+  ck(cudaGetLastError(), "vec_combine");
+}
+
+void vec_axpby(double a, const double* x, double b, double* y, int64_t n, Stream s) {
+  k_axpby<<<nblk(n, 256), 256, 0, S(s)>>>(a, x, b, y, n);
+  ck(cudaGetLastError(), "axpby");
+}
+
+void vec_normalize(double* y, const double* nrm2, int64_t n, Stream s) {
+  k_normalize<<<nblk(n, 256), 256, 0, S(s)>>>(y, nrm2, n);
+  ck(cudaGetLastError(), "normalize");
+}
+
+void vec_precondition(const double* r, const double* d, const double* th, double* t, int64_t n,
+                      Stream s) {
+  k_precondition<<<nblk(n, 256), 256, 0, S(s)>>>(r, d, th, t, n);
+  ck(cudaGetLastError(), "precondition");
+}
+
+void small_eig(const double* G, int gld, int m, int k, double* theta, double* C, Stream s) {
+  k_small_eig<<<1, 256, 0, S(s)>>>(G, gld, m, k, theta, C);
+  ck(cudaGetLastError(), "small_eig");
+}
+
+void vec_add_noise(double* x, int64_t n, double amp, uint64_t seed, Stream s) {
+  k_noise<<<nblk(n, 256), 256, 0, S(s)>>>(x, n, amp, seed);
+  ck(cudaGetLastError(), "noise");
+}
+
+// ------------------------------------------------------------------ batched Jacobi
+
+namespace {
+__global__ void __launch_bounds__(256) k_eig_batched(const EigJob* __restrict__ jobs) {
+  const EigJob J = jobs[blockIdx.x];
+  const int n = J.n, tid = threadIdx.x;
+  double* A = J.A;
+  double* Q = J.Q;
+  extern __shared__ double sm[];
+  const int np = (n + 1) & ~1;
+  double* cs = sm;
+  double* sn = sm + np / 2;
+  __shared__ double red[256];
+  __shared__ int done;
+  for (int e = tid; e < n * n; e += 256) Q[e] = (e / n == e % n) ? 1.0 : 0.0;
+  __syncthreads();
+  for (int sweep = 0; sweep < 50; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int e = tid; e < n * n; e += 256) {
+      double v = A[e];
+      tot += v * v;
+      if (e / n != e % n) off += v * v;
+    }
+    red[tid] = off;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) { if (tid < o) red[tid] += red[tid + o]; __syncthreads(); }
+    double offs = red[0];
+    __syncthreads();
+    red[tid] = tot;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) { if (tid < o) red[tid] += red[tid + o]; __syncthreads(); }
+    if (tid == 0) done = (offs <= 1e-32 * red[0]) ? 1 : 0;
+    __syncthreads();
+    if (done) break;
+    for (int step = 0; step < np - 1; ++step) {
+      for (int r = tid; r < np / 2; r += 256) {
+        int a = r, b = np - 1 - r;
+        int p = a == 0 ? 0 : 1 + (a - 1 + step) % (np - 1);
+        int q = b == 0 ? 0 : 1 + (b - 1 + step) % (np - 1);
+        if (p > q) { int t = p; p = q; q = t; }
+        double c = 1.0, s = 0.0;
+        if (q < n) sym_schur2(A[(size_t)p * n + p], A[(size_t)q * n + q], A[(size_t)p * n + q], c, s);
+        cs[r] = c; sn[r] = s;
+      }
+      __syncthreads();
+      for (int e = tid; e < (np / 2) * n; e += 256) {
+        int r = e / n, j = e % n;
+        int a = r, b = np - 1 - r;
+        int p = a == 0 ? 0 : 1 + (a - 1 + step) % (np - 1);
+        int q = b == 0 ? 0 : 1 + (b - 1 + step) % (np - 1);
+        if (p > q) { int t = p; p = q; q = t; }
+        if (q >= n) continue;
+        double c = cs[r], s = sn[r];
+        double ap = A[(size_t)p * n + j], aq = A[(size_t)q * n + j];
+        A[(size_t)p * n + j] = c * ap - s * aq;
+        A[(size_t)q * n + j] = s * ap + c * aq;
+      }
+      __syncthreads();
+      for (int e = tid; e < (np / 2) * n; e += 256) {
+        int r = e / n, i = e % n;
+        int a = r, b = np - 1 - r;
+        int p = a == 0 ? 0 : 1 + (a - 1 + step) % (np - 1);
+        int q = b == 0 ? 0 : 1 + (b - 1 + step) % (np - 1);
+        if (p > q) { int t = p; p = q; q = t; }
+        if (q >= n) continue;
+        double c = cs[r], s = sn[r];
+        double ap = A[(size_t)i * n + p], aq = A[(size_t)i * n + q];
+        A[(size_t)i * n + p] = c * ap - s * aq;
+        A[(size_t)i * n + q] = s * ap + c * aq;
+        double qp = Q[(size_t)i * n + p], qv = Q[(size_t)i * n + q];
+        Q[(size_t)i * n + p] = c * qp - s * qv;
+        Q[(size_t)i * n + q] = s * qp + c * qv;
+      }
+      __syncthreads();
+    }
+  }
+  // sort eigenpairs descending: rank by value, ties by index
+  for (int i = tid; i < n; i += 256) J.w[i] = A[(size_t)i * n + i];
+  __syncthreads();
+  for (int e = tid; e < n * n; e += 256) A[e] = Q[e];
+  __syncthreads();
+  for (int i = tid; i < n; i += 256) {
+    double vi = J.w[i];
+    int rank = 0;
+    for (int j = 0; j < n; ++j) {
+      double vj = J.w[j];
+      if (vj > vi || (vj == vi && j < i)) ++rank;
+    }
+    sm[np + i] = vi;
+    for (int r = 0; r < n; ++r) Q[(size_t)r * n + rank] = A[(size_t)r * n + i];
+    ((int*)(sm + np + n))[i] = rank;
+  }
+  __syncthreads();
+  for (int i = tid; i < n; i += 256) J.w[((int*)(sm + np + n))[i]] = sm[np + i];
+}
+}  // namespace
+
+void eig_batched(const std::vector<EigJob>& jobs, Stream s) {
+  if (jobs.empty()) return;
+  int nmax = 0;
+  for (auto& j : jobs) nmax = std::max(nmax, j.n);
+  EigJob* d = (EigJob*)dev_alloc(jobs.size() * sizeof(EigJob), s);
+  dev_h2d(d, jobs.data(), jobs.size() * sizeof(EigJob), s);
+  size_t shm = (size_t)((nmax + 1) & ~1) * sizeof(double) + (size_t)nmax * (sizeof(double) + sizeof(int)) + 64;
+  if (shm > 200 * 1024) throw std::runtime_error("eig_batched: block too large");
+  if (shm > 48 * 1024) ck(cudaFuncSetAttribute(k_eig_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm), "eig smem");
+  k_eig_batched<<<(int)jobs.size(), 256, shm, S(s)>>>(d);
+  ck(cudaGetLastError(), "eig_batched");
+  dev_free(d, s);
+}
+
+// ------------------------------------------------------------------ selection
+
+namespace {
+__global__ void k_select(const double* __restrict__ v, int n, const int* __restrict__ gid,
+                         const int* __restrict__ wgt, int D, double zero_rel, int* kept,
+                         double* sums) {
+  __shared__ double red[2][256];
+  __shared__ double vmax_s;
+  const int tid = threadIdx.x;
+  double mx = 0.0;
+  for (int i = tid; i < n; i += 256) mx = fmax(mx, v[i]);
+  red[0][tid] = mx;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) { if (tid < o) red[0][tid] = fmax(red[0][tid], red[0][tid + o]); __syncthreads(); }
+  if (tid == 0) vmax_s = red[0][0];
+  __syncthreads();
+  const double vmax = vmax_s;
+  double nrm = 0.0, disc = 0.0;
+  for (int i = tid; i < n; i += 256) {
+    double vi = fmax(v[i], 0.0);
+    int rank = 0;
+    for (int j = 0; j < n; ++j) {
+      double vj = fmax(v[j], 0.0);
+      if (vj > vi || (vj == vi && j < i)) ++rank;
+    }
+    double w = (double)wgt[gid[i]] * vi;
+    nrm += w;
+    // lambda > zero_rel * lambda_max  <=>  lambda^2 > zero_rel^2 * lambda_max^2
+    bool keep = rank < D && vi > zero_rel * zero_rel * vmax;
+    if (keep) atomicAdd(&kept[gid[i]], 1); else disc += w;
+  }
+  red[0][tid] = nrm;
+  red[1][tid] = disc;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (tid < o) { red[0][tid] += red[0][tid + o]; red[1][tid] += red[1][tid + o]; }
+    __syncthreads();
+  }
+  if (tid == 0) { sums[0] = red[0][0]; sums[1] = red[1][0]; }
+}
+}  // namespace
+
+void select_largest(const double* vals, const std::vector<int>& goff, const std::vector<int>& wgt,
+                    int D, double zero_rel, std::vector<int>& kept, double* norm2, double* disc,
+                    Stream s) {
+  const int G = (int)wgt.size();
+  const int n = goff.back();
+  std::vector<int> gid(n);
+  for (int g = 0; g < G; ++g)
+    for (int i = goff[g]; i < goff[g + 1]; ++i) gid[i] = g;
+  int* d_gid = (int*)dev_alloc(sizeof(int) * (n + 1), s);
+  int* d_w = (int*)dev_alloc(sizeof(int) * (G + 1), s);
+  int* d_k = (int*)dev_alloc(sizeof(int) * (G + 1), s);
+  double* d_s = (double*)dev_alloc(sizeof(double) * 2, s);
+  dev_h2d(d_gid, gid.data(), sizeof(int) * n, s);
+  dev_h2d(d_w, wgt.data(), sizeof(int) * G, s);
+  dev_zero(d_k, sizeof(int) * (G + 1), s);
+  k_select<<<1, 256, 0, S(s)>>>(vals, n, d_gid, d_w, D, zero_rel, d_k, d_s);
+  ck(cudaGetLastError(), "select");
+  kept.assign(G, 0);
+  double sums[2];
+  dev_d2h(kept.data(), d_k, sizeof(int) * G, s);
+  dev_d2h(sums, d_s, sizeof(double) * 2, s);
+  dev_sync(s);
+  *norm2 = sums[0];
+  *disc = sums[1];
+  dev_free(d_gid, s);
+  dev_free(d_w, s);
+  dev_free(d_k, s);
+  dev_free(d_s, s);
+}
+
+// ------------------------------------------------------------------ scatter
+
+namespace {
+__device__ inline double scl(const double* v, int i, int mode) {
+  if (mode == 0) return 1.0;
+  double x = v[i];
+  return mode == 1 ? sqrt(x) : 1.0 / sqrt(x);
+}
+
+__global__ void k_scatter(const ScatterJob* __restrict__ jobs) {
+  const ScatterJob J = jobs[blockIdx.x];
+  const int64_t n = (int64_t)J.rows * J.cols;
+  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+    int i = (int)(e / J.cols), j = (int)(e % J.cols);
+    double v = J.trans ? J.src[(size_t)j * J.lds + i] : J.src[(size_t)i * J.lds + j];
+    J.dst[(size_t)i * J.ldd + j] = J.a * scl(J.rs, i, J.rmode) * scl(J.cs, j, J.cmode) * v;
+  }
+}
+}  // namespace
+
+void scatter_batched(const std::vector<ScatterJob>& jobs, Stream s) {
+  if (jobs.empty()) return;
+  ScatterJob* d = (ScatterJob*)dev_alloc(jobs.size() * sizeof(ScatterJob), s);
+  dev_h2d(d, jobs.data(), jobs.size() * sizeof(ScatterJob), s);
+  for (size_t off = 0; off < jobs.size(); off += 65535) {
+    int n = (int)std::min<size_t>(65535, jobs.size() - off);
+    k_scatter<<<n, 128, 0, S(s)>>>(d + off);
+  }
+  ck(cudaGetLastError(), "scatter");
+  dev_free(d, s);
+}
+
+}  // namespace dmrg

@@ -1,0 +1,52 @@
+"""Serialise an oracle MPS into the library's dmrg_set_mps format and map the
+library's two-site block table onto the oracle's block keys (test helpers)."""
+import struct
+
+import numpy as np
+
+from oracle.mps import sector_order
+
+
+def mps_to_bytes(m):
+    out = [struct.pack("<6i", 0x444D5247, 1, m.L, m.N, m.two_S, m.I_G)]
+    orders = []
+    for k in range(m.L + 1):
+        secs = sector_order(m.dims[k])
+        orders.append({s: i for i, s in enumerate(secs)})
+        out.append(struct.pack("<i", len(secs)))
+        for s in secs:
+            out.append(struct.pack("<4i", s[0], s[1], s[2], m.dims[k][s]))
+    for k in range(m.L):
+        blocks = [(key, blk) for key, blk in m.T[k].items()
+                  if key[1] in orders[k] and key[2] in orders[k + 1]]
+        out.append(struct.pack("<i", len(blocks)))
+        for (ls, lsec, rsec), blk in blocks:
+            out.append(struct.pack("<3i", ls, orders[k][lsec], orders[k + 1][rsec]))
+            out.append(np.ascontiguousarray(blk, dtype="<f8").tobytes())
+    return b"".join(out)
+
+
+def layout_keys(table):
+    """Oracle block keys (lsec, ls1, ls2, tj, rsec) of the library's block table rows."""
+    keys = []
+    for row in table:
+        tjL, nL, iL, ls1, ls2, tj, tjR, nR, iR, dL, dR, off = (int(v) for v in row)
+        keys.append(((tjL, nL, iL), ls1, ls2, tj, (tjR, nR, iR)))
+    return keys
+
+
+def oracle_x_to_lib(x_blocks, table, n):
+    v = np.zeros(n)
+    for key, row in zip(layout_keys(table), table):
+        dL, dR, off = int(row[9]), int(row[10]), int(row[11])
+        if key in x_blocks:
+            v[off:off + dL * dR] = x_blocks[key].ravel()
+    return v
+
+
+def lib_x_to_oracle(v, table):
+    out = {}
+    for key, row in zip(layout_keys(table), table):
+        dL, dR, off = int(row[9]), int(row[10]), int(row[11])
+        out[key] = v[off:off + dL * dR].reshape(dL, dR).copy()
+    return out
