@@ -59,6 +59,7 @@ typedef struct {
   double k_phase1_ms, k_phase2_ms;
   int64_t k_launches;
   double k_phase1_flops, k_phase2_flops;
+  int64_t kernels_launched; /* all kernels this library launched in the process */
 } dmrg_stats_t;
 
 /* Sec. 4.1: L orbitals with irreps orb_irrep[L], N electrons (2 <= N <= 2L, needed by
@@ -100,7 +101,8 @@ int dmrg_set_mps(dmrg_ctx* ctx, const void* buf, size_t len);
  * the state is unchanged up to normalisation. */
 int dmrg_canonicalize(dmrg_ctx* ctx, int center);
 
-/* Sec. 4.3 Solve: right-normalises the MPS, then runs the convergence scheme with
+/* Sec. 4.3 Solve: right-normalises the MPS (unless Eq. 6 already holds to 1e-10 on every
+ * site right of the first), then runs the convergence scheme with
  * macro-iterations of one sweep to the right and one to the left.  *e_min = the lowest
  * energy of all micro-iterations (including E_const), *e_last = the last one. */
 int dmrg_solve(dmrg_ctx* ctx, double* e_min, double* e_last);

@@ -165,6 +165,22 @@ class FCISpace:
         S2 = S2.tocsr()
         return S2[idx][:, idx]
 
+    def s2_apply(self, C):
+        """S^2 C = (Sz^2 + Sz) C + S- S+ C with S+ C = (-1)^n_a sum_p c+_p C a_p^T
+        (alpha creation on the rows, beta annihilation on the columns)."""
+        sz = 0.5 * (self.A.n - self.B.n)
+        out = (sz * sz + sz) * C
+        if self.B.n > 0 and self.A.n < self.L:
+            if not hasattr(self, "_lad"):
+                A1 = StringSpace(self.L, self.A.n + 1, self.irreps)
+                B1 = StringSpace(self.L, self.B.n - 1, self.irreps)
+                self._lad = [(_ladder(self.A, A1, p, True), _ladder(self.B, B1, p, False))
+                             for p in range(self.L)]
+            sg = (-1) ** self.A.n
+            Sp = sum(cA @ C @ aB.T for cA, aB in self._lad) * sg
+            out = out + sg * sum(cA.T @ Sp @ aB for cA, aB in self._lad)
+        return out
+
     def s_plus(self, other, C):
         """S+ = sum_p a+_{p,up} a_{p,down}: maps this space's vector into `other`
         (n_alpha + 1, n_beta - 1).  Beta annihilation passes all alpha creators."""
@@ -224,16 +240,9 @@ def fci_ground_state(h, V, N, two_S, irreps, target_irrep, ecore=0.0, nroots=1,
         w, U = np.linalg.eigh(Hm)
         U = U[:, :nroots]
     else:
-        def s2_apply(C):
-            sz = 0.5 * (na - nb)
-            out = (sz * sz + sz) * C
-            if other is not None:
-                out = out + _s_minus(other, space, space.s_plus(other, C))
-            return out
-
         def matvec(x):
             C = embed(x)
-            y = space.sigma(h, V, C, ecore) + spin_penalty * (s2_apply(C) - S * (S + 1) * C)
+            y = space.sigma(h, V, C, ecore) + spin_penalty * (space.s2_apply(C) - S * (S + 1) * C)
             return y.ravel()[idx]
         op = spla.LinearOperator((n, n), matvec=matvec, dtype=np.float64)
         w, U = spla.eigsh(op, k=nroots, which="SA", tol=tol)

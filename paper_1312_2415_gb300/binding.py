@@ -32,7 +32,7 @@ class Stats(ctypes.Structure):
         ("last_w_disc", ctypes.c_double), ("max_w_disc", ctypes.c_double),
         ("k_phase1_ms", ctypes.c_double), ("k_phase2_ms", ctypes.c_double),
         ("k_launches", ctypes.c_int64), ("k_phase1_flops", ctypes.c_double),
-        ("k_phase2_flops", ctypes.c_double),
+        ("k_phase2_flops", ctypes.c_double), ("kernels_launched", ctypes.c_int64),
     ]
 
 

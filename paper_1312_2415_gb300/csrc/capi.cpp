@@ -339,6 +339,7 @@ int dmrg_stats(dmrg_ctx* c, dmrg_stats_t* out) {
     out->k_launches = s.k_launches;
     out->k_phase1_flops = s.k_phase1_flops;
     out->k_phase2_flops = s.k_phase2_flops;
+    out->kernels_launched = dmrg::kernel_launches();
     return DMRG_OK;
   });
 }

@@ -17,6 +17,7 @@ void dev_d2h(void* dst, const void* src, size_t bytes, Stream s);
 void dev_d2d(void* dst, const void* src, size_t bytes, Stream s);
 void dev_zero(void* p, size_t bytes, Stream s);
 void dev_sync(Stream s);
+int64_t kernel_launches();  // number of this library's kernel launches so far
 int dev_check(const char** msg);  // 0 if no CUDA error is pending
 void* host_pinned_alloc(size_t bytes);
 // CUDA events for timing kernels on the engine's stream
@@ -26,7 +27,8 @@ void event_record(void* e, Stream s);
 float event_elapsed_ms(void* a, void* b);  // both must have completed
 void host_pinned_free(void* p);
 
-// ---- grouped GEMM: C_g = C_g + sum_t alpha_t op(A_t) op(B_t), row-major blocks ----
+// ---- grouped GEMM: C_g = C_g + sum_t alpha_t op(A_t) op(B_t), row-major blocks;
+// A == nullptr means op(A) = identity (C_g += alpha op(B)) ----
 struct GemmTask {
   const double* A;
   const double* B;

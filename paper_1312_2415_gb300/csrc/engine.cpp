@@ -3,6 +3,7 @@
 #include "engine.hpp"
 
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -374,28 +375,32 @@ void Engine::ensure_right(int k) {
   build_right(k);
 }
 
+// Blocks ordered by right sector first, so that all blocks with the same right sector
+// form one row-major stack (rows = sum dL, cols = dR) that a single GEMM can multiply.
 std::vector<XBlock> Engine::x_layout(int i, int64_t* n) const {
   std::vector<XBlock> X;
   const Bond& bl = bonds_[i];
   const Bond& br = bonds_[i + 2];
   int64_t off = 0;
-  for (int l = 0; l < (int)bl.sec.size(); ++l)
-    for (int ls1 = 0; ls1 < 3; ++ls1)
-      for (int ls2 = 0; ls2 < 3; ++ls2) {
-        const Sector& a = bl.sec[l];
-        int nn = a.n + local_n(ls1) + local_n(ls2);
-        int ir = a.ir ^ local_ir(ls1, sym_.orb_ir[i]) ^ local_ir(ls2, sym_.orb_ir[i + 1]);
-        for (int r = 0; r < (int)br.sec.size(); ++r) {
-          const Sector& b = br.sec[r];
+  for (int r = 0; r < (int)br.sec.size(); ++r) {
+    const Sector& b = br.sec[r];
+    int trow = 0;
+    for (int l = 0; l < (int)bl.sec.size(); ++l)
+      for (int ls1 = 0; ls1 < 3; ++ls1)
+        for (int ls2 = 0; ls2 < 3; ++ls2) {
+          const Sector& a = bl.sec[l];
+          int nn = a.n + local_n(ls1) + local_n(ls2);
+          int ir = a.ir ^ local_ir(ls1, sym_.orb_ir[i]) ^ local_ir(ls2, sym_.orb_ir[i + 1]);
           if (b.n != nn || b.ir != ir) continue;
           int t1 = local_ts(ls1), t2 = local_ts(ls2);
           for (int tj = std::abs(t1 - t2); tj <= t1 + t2; tj += 2) {
             if (!triangle(a.tj, tj, b.tj)) continue;
-            X.push_back({l, ls1, ls2, tj, r, off, bl.dim[l], br.dim[r]});
+            X.push_back({l, ls1, ls2, tj, r, off, bl.dim[l], br.dim[r], trow});
             off += (int64_t)bl.dim[l] * br.dim[r];
+            trow += bl.dim[l];
           }
         }
-      }
+  }
   *n = off;
   return X;
 }
@@ -484,12 +489,14 @@ void Engine::group_left(int i, std::vector<CombOp>& out, double** scratch) {
     }
     out[it->second].sources.push_back({w.a, w.scalar});
   }
+  const int id_op = opsets_[i].find({OP_I, -1, -1, 0});
   for (auto& c : out)
     if (c.sources.size() == 1) {
       c.blocks = &E.blocks[c.sources[0].first];
       c.at = &E.at[c.sources[0].first];
       c.data = E.data;
       c.scalar = c.sources[0].second;
+      c.identity = c.sources[0].first == id_op;
     }
   *scratch = materialise(out, E, stream_);
 }
@@ -514,12 +521,14 @@ void Engine::group_right(int j, std::vector<CombOp>& out, double** scratch) {
     }
     out[it->second].sources.push_back({w.b, w.scalar});
   }
+  const int h_op = opsets_[j + 1].find({OP_H, -1, -1, 0});
   for (auto& c : out)
     if (c.sources.size() == 1) {
       c.blocks = &E.blocks[c.sources[0].first];
       c.at = &E.at[c.sources[0].first];
       c.data = E.data;
       c.scalar = c.sources[0].second;
+      c.identity = c.sources[0].first == h_op;  // partner of H is the identity
     }
   *scratch = materialise(out, E, stream_);
 }
@@ -696,6 +705,9 @@ struct Engine::MatvecPlan {
   double* scr_l = nullptr;
   double* scr_r = nullptr;
   double* Z = nullptr;
+  double* W = nullptr;
+  CombPlan* pc = nullptr;
+  int64_t wsize = 0;
   double* xin = nullptr;
   double* yout = nullptr;
   double* diag = nullptr;
@@ -732,147 +744,238 @@ Engine::MatvecPlan* Engine::plan_matvec(int i) {
   const Bond& bl = bonds_[i];
   const Bond& br = bonds_[i + 2];
   const OpSet& mid = opsets_[i + 1];
+  const int nl = (int)bl.sec.size(), nr = (int)br.sec.size();
   std::vector<std::vector<int>> byb_l(mid.ops.size()), byb_r(mid.ops.size());
   for (int g = 0; g < (int)P->cl.size(); ++g) byb_l[P->cl[g].target].push_back(g);
   for (int g = 0; g < (int)P->cr.size(); ++g) byb_r[P->cr[g].target].push_back(g);
-  std::map<std::tuple<int, int, int, int, int>, int> xidx;
+  // X' lookup: index by (l, ls1, ls2, tj, r) -> dense table
+  auto xkey = [&](int l, int ls1, int ls2, int tj, int r) {
+    return ((((int64_t)l * 3 + ls1) * 3 + ls2) * 3 + tj) * nr + r;
+  };
+  std::vector<int> xidx((size_t)nl * 27 * nr, -1);
+  std::vector<std::vector<int>> x_by_l(nl);
+  std::vector<int64_t> tall_rows(nr, 0), tall_off(nr, -1);
   for (int x = 0; x < (int)P->X.size(); ++x) {
     const XBlock& b = P->X[x];
-    xidx[{b.l, b.ls1, b.ls2, b.tj, b.r}] = x;
+    xidx[xkey(b.l, b.ls1, b.ls2, b.tj, b.r)] = x;
+    x_by_l[b.l].push_back(x);
+    tall_rows[b.r] = std::max<int64_t>(tall_rows[b.r], b.trow + b.rows);
+    if (tall_off[b.r] < 0) tall_off[b.r] = b.off;
   }
-  std::vector<std::vector<int>> x_by_l(bl.sec.size());
-  for (int x = 0; x < (int)P->X.size(); ++x) x_by_l[P->X[x].l].push_back(x);
   P->xin = (double*)dev_alloc(sizeof(double) * std::max<int64_t>(P->n, 1), stream_);
   P->yout = (double*)dev_alloc(sizeof(double) * std::max<int64_t>(P->n, 1), stream_);
-
-  struct ZRef { int64_t off; int rows, cols, x; };
-  std::vector<ZRef> zs;
+  // right-group blocks indexed by column sector
+  std::vector<std::vector<std::vector<int>>> dby(P->cr.size());
+  for (int g = 0; g < (int)P->cr.size(); ++g) {
+    dby[g].resize(nr);
+    for (int bi = 0; bi < (int)P->cr[g].blocks->size(); ++bi) dby[g][(*P->cr[g].blocks)[bi].c].push_back(bi);
+  }
+  // phase 1: Z(gr, D block) = stack(r) . D^T ; identity D reads x directly
+  struct ZRef { int64_t off; int ld; };
+  std::unordered_map<int64_t, ZRef> zmap;
   std::vector<GemmTask> t1;
   std::vector<GemmGroup> g1;
-  std::vector<std::vector<GemmTask>> out2(P->X.size());
+  std::vector<int64_t> g1off;
+  int64_t zsize = 0;
+  double flops1 = 0.0, flops2 = 0.0;
+  auto get_z = [&](int gr, int dbi) -> ZRef {
+    const CombOp& D = P->cr[gr];
+    const BlockRef& db = (*D.blocks)[dbi];
+    int64_t key = ((int64_t)gr << 24) | dbi;
+    auto it = zmap.find(key);
+    if (it != zmap.end()) return it->second;
+    ZRef z;
+    if (D.identity) {
+      z = {-1 - tall_off[db.c], br.dim[db.c]};  // negative: offset into xin
+    } else {
+      const int64_t rows = tall_rows[db.c];
+      z = {zsize, db.rows};
+      t1.push_back({nullptr, D.data + db.off, db.cols, db.cols, db.cols, 0, 1, D.scalar});
+      g1.push_back({nullptr, db.rows, (int)rows, db.rows, (int)t1.size() - 1, (int)t1.size(), 0});
+      g1off.push_back(tall_off[db.c]);
+      zsize += rows * db.rows;
+      flops1 += 2.0 * rows * db.cols * db.rows;
+    }
+    zmap.emplace(key, z);
+    return z;
+  };
+  // site transitions allowed by each pattern, and the recoupled coefficient of a
+  // (left pattern, right pattern, block labels) combination, memoised
+  std::vector<std::array<std::array<bool, 3>, 3>> okp(pt_.pats.size());
+  for (size_t q = 0; q < pt_.pats.size(); ++q) {
+    bool ok[3][3];
+    allowed(pt_.pats[q], ok);
+    for (int a = 0; a < 3; ++a)
+      for (int c = 0; c < 3; ++c) okp[q][a][c] = ok[a][c];
+  }
+  struct K2 {
+    uint64_t a, b;
+    bool operator==(const K2& o) const { return a == o.a && b == o.b; }
+  };
+  struct H2 {
+    size_t operator()(const K2& k) const { return std::hash<uint64_t>()(k.a * 0x9E3779B97F4A7C15ull ^ k.b); }
+  };
+  std::unordered_map<K2, double, H2> coef_cache;
+  coef_cache.reserve(1 << 16);
+  // W(gl, C block, X') = sum coef * Z rows of X ; phase 2: y_X' += C_blk W
+  struct WItem { int gl, cbi, xp; int64_t off; int rows, cols; int src_begin, src_end; };
+  std::vector<WItem> ws;
+  struct WS { int64_t zoff; int ld; double coef; };  // zoff < 0: into xin (-1 - off)
+  std::vector<WS> wsrc;
   std::vector<std::vector<DiagTerm>> dout(P->X.size());
-  std::map<std::tuple<int, int, int>, int> zmap;  // (right group, D block, x) -> z
-  double flops = 0.0;
-  const int i1 = i, i2 = i + 1;
-  (void)i1;
-  (void)i2;
+  std::vector<std::vector<int>> w_by_x(P->X.size());
+  int64_t wsize = 0;
+  std::unordered_map<int64_t, std::vector<WS>> acc;  // xp -> sources, per (gl, cbi)
   for (int b = 0; b < (int)mid.ops.size(); ++b) {
     if (byb_l[b].empty() || byb_r[b].empty()) continue;
     const int tkb = mid.ops[b].tk, pb = mid.ops[b].parity;
-    for (int gl : byb_l[b])
-      for (int gr : byb_r[b]) {
-        const CombOp& C = P->cl[gl];
-        const CombOp& D = P->cr[gr];
-        bool ok1[3][3], ok2[3][3];
-        allowed(pt_.pats[C.pattern], ok1);
-        allowed(pt_.pats[D.pattern], ok2);
-        for (int x = 0; x < (int)P->X.size(); ++x) {
+    for (int gl : byb_l[b]) {
+      const CombOp& C = P->cl[gl];
+      const auto& ok1 = okp[C.pattern];
+      for (int cbi = 0; cbi < (int)C.blocks->size(); ++cbi) {
+        const BlockRef& cb = (*C.blocks)[cbi];
+        const int tjL = bl.sec[cb.c].tj, tjLp = bl.sec[cb.r].tj;
+        acc.clear();
+        for (int x : x_by_l[cb.c]) {
           const XBlock& X = P->X[x];
-          const int tjL = bl.sec[X.l].tj, tjR = br.sec[X.r].tj;
+          const int tjR = br.sec[X.r].tj;
           const int t1s = local_ts(X.ls1), t2s = local_ts(X.ls2);
-          for (int dbi = 0; dbi < (int)D.blocks->size(); ++dbi) {
-            const BlockRef& db = (*D.blocks)[dbi];
-            if (db.c != X.r) continue;
-            const int tjRp = br.sec[db.r].tj;
-            int zid = -1;
-            for (const BlockRef& cb : *C.blocks) {
-              if (cb.c != X.l) continue;
-              const int tjLp = bl.sec[cb.r].tj;
+          for (int gr : byb_r[b]) {
+            const CombOp& D = P->cr[gr];
+            const auto& ok2 = okp[D.pattern];
+            for (int dbi : dby[gr][X.r]) {
+              const BlockRef& db = (*D.blocks)[dbi];
+              const int tjRp = br.sec[db.r].tj;
               for (int ls1p = 0; ls1p < 3; ++ls1p) {
                 if (!ok1[X.ls1][ls1p]) continue;
+                const int t1p = local_ts(ls1p);
                 for (int ls2p = 0; ls2p < 3; ++ls2p) {
                   if (!ok2[X.ls2][ls2p]) continue;
-                  const int t1p = local_ts(ls1p), t2p = local_ts(ls2p);
+                  const int t2p = local_ts(ls2p);
                   for (int tjp = std::abs(t1p - t2p); tjp <= t1p + t2p; tjp += 2) {
-                    auto it = xidx.find({cb.r, ls1p, ls2p, tjp, db.r});
-                    if (it == xidx.end()) continue;
-                    const XBlock& Xp = P->X[it->second];
+                    const int xp = xidx[xkey(cb.r, ls1p, ls2p, tjp, db.r)];
+                    if (xp < 0) continue;
+                    K2 key{(uint64_t)C.pattern | ((uint64_t)D.pattern << 16) | ((uint64_t)tjL << 32) |
+                               ((uint64_t)tjR << 40) | ((uint64_t)tjLp << 48) | ((uint64_t)tjRp << 56),
+                           (uint64_t)X.ls1 | ((uint64_t)X.ls2 << 2) | ((uint64_t)X.tj << 4) |
+                               ((uint64_t)ls1p << 8) | ((uint64_t)ls2p << 10) | ((uint64_t)tjp << 12)};
+                    auto ci = coef_cache.find(key);
                     double coef = 0.0;
-                    for (int tjM = std::abs(tjL - t1s); tjM <= tjL + t1s; tjM += 2) {
-                      if (!triangle(t2s, tjR, tjM)) continue;
-                      double ov = cp_->overlap(tjL, X.ls1, X.ls2, X.tj, tjR, tjM);
-                      if (ov == 0.0) continue;
-                      for (int tjMp = std::abs(tjLp - t1p); tjMp <= tjLp + t1p; tjMp += 2) {
-                        if (!triangle(t2p, tjRp, tjMp)) continue;
-                        double ovp = cp_->overlap(tjLp, ls1p, ls2p, tjp, tjRp, tjMp);
-                        if (ovp == 0.0) continue;
-                        double sf = cp_->singlet(tkb, pb, tjM, tjMp);
-                        if (sf == 0.0) continue;
-                        double lc = cp_->left(C.pattern, tjL, X.ls1, tjM, tjLp, ls1p, tjMp);
-                        if (lc == 0.0) continue;
-                        double rc = cp_->right(D.pattern, X.ls2, tjR, tjM, ls2p, tjRp, tjMp);
-                        coef += ov * ovp * sf * lc * rc;
+                    if (ci != coef_cache.end()) {
+                      coef = ci->second;
+                    } else {
+                      for (int tjM = std::abs(tjL - t1s); tjM <= tjL + t1s; tjM += 2) {
+                        if (!triangle(t2s, tjR, tjM)) continue;
+                        double ov = cp_->overlap(tjL, X.ls1, X.ls2, X.tj, tjR, tjM);
+                        if (ov == 0.0) continue;
+                        for (int tjMp = std::abs(tjLp - t1p); tjMp <= tjLp + t1p; tjMp += 2) {
+                          if (!triangle(t2p, tjRp, tjMp)) continue;
+                          double ovp = cp_->overlap(tjLp, ls1p, ls2p, tjp, tjRp, tjMp);
+                          if (ovp == 0.0) continue;
+                          double sf = cp_->singlet(tkb, pb, tjM, tjMp);
+                          if (sf == 0.0) continue;
+                          double lc = cp_->left(C.pattern, tjL, X.ls1, tjM, tjLp, ls1p, tjMp);
+                          if (lc == 0.0) continue;
+                          double rc = cp_->right(D.pattern, X.ls2, tjR, tjM, ls2p, tjRp, tjMp);
+                          coef += ov * ovp * sf * lc * rc;
+                        }
                       }
+                      coef_cache.emplace(key, coef);
                     }
-                    coef *= C.scalar;
                     if (std::fabs(coef) < 1e-14) continue;
-                    if (zid < 0) {
-                      auto zk = std::make_tuple(gr, dbi, x);
-                      auto zi = zmap.find(zk);
-                      if (zi == zmap.end()) {
-                        zid = (int)zs.size();
-                        zmap[zk] = zid;
-                        zs.push_back({0, X.rows, db.rows, x});
-                        // Z = x_X (dL x dR) . D_blk^T (dR x dR'), scaled by D's alias scalar
-                        t1.push_back({nullptr, D.data + db.off, X.cols, db.cols, X.cols, 0, 1, D.scalar});
-                        g1.push_back({nullptr, db.rows, X.rows, db.rows, (int)t1.size() - 1, (int)t1.size(), 0});
-                        flops += 2.0 * X.rows * X.cols * db.rows;
-                        P->flops1 += 2.0 * X.rows * X.cols * db.rows;
-                      } else {
-                        zid = zi->second;
-                      }
-                    }
-                    out2[it->second].push_back({C.data + cb.off, (const double*)(intptr_t)zid, cb.cols,
-                                                db.rows, cb.cols, 0, 0, coef});
-                    flops += 2.0 * cb.rows * cb.cols * db.rows;
-                    P->flops2 += 2.0 * cb.rows * cb.cols * db.rows;
-                    if (it->second == x && cb.r == cb.c && db.r == db.c)
+                    ZRef z = get_z(gr, dbi);
+                    int64_t zoff = z.off >= 0 ? z.off + (int64_t)X.trow * z.ld
+                                              : z.off - (int64_t)X.trow * z.ld;
+                    // identity right operator: Z is x itself, its alias scalar goes here
+                    acc[xp].push_back({zoff, z.ld, D.identity ? coef * D.scalar : coef});
+                    if (xp == x && cb.r == cb.c && db.r == db.c)
                       dout[x].push_back({C.data + cb.off, D.data + db.off, cb.cols, db.cols,
-                                         coef * D.scalar});
-                    (void)Xp;
+                                         coef * C.scalar * D.scalar});
                   }
                 }
               }
             }
           }
         }
+        for (auto& kv : acc) {
+          const XBlock& Xp = P->X[kv.first];
+          WItem w{gl, cbi, (int)kv.first, wsize, cb.cols, Xp.cols, (int)wsrc.size(), 0};
+          for (auto& q : kv.second) wsrc.push_back(q);
+          w.src_end = (int)wsrc.size();
+          wsize += (int64_t)cb.cols * Xp.cols;
+          w_by_x[kv.first].push_back((int)ws.size());
+          ws.push_back(w);
+          if (!C.identity) flops2 += 2.0 * cb.rows * cb.cols * Xp.cols;
+        }
       }
+    }
   }
-  int64_t zsize = 0;
-  for (auto& z : zs) { z.off = zsize; zsize += (int64_t)z.rows * z.cols; }
   P->zsize = zsize;
   P->Z = (double*)dev_alloc(sizeof(double) * std::max<int64_t>(zsize, 1), stream_);
-  for (size_t z = 0; z < g1.size(); ++z) {
-    g1[z].C = P->Z + zs[z].off;
-    t1[z].A = P->xin + P->X[zs[z].x].off;
+  P->W = (double*)dev_alloc(sizeof(double) * std::max<int64_t>(wsize, 1), stream_);
+  {
+    // fix up phase-1 pointers: A = stack of x rows for the column sector
+    int64_t zo = 0;
+    for (size_t z = 0; z < g1.size(); ++z) {
+      t1[z].A = P->xin + g1off[z];
+      t1[z].lda = t1[z].ldb;  // stack(r) has ld = d_r = D block columns
+      g1[z].C = P->Z + zo;
+      zo += (int64_t)g1[z].m * g1[z].n;
+    }
   }
+  // combine plan for W
+  std::vector<CombSrc> cs;
+  std::vector<CombDst> cd;
+  cs.reserve(wsrc.size());
+  cd.reserve(ws.size());
+  for (auto& w : ws) {
+    CombDst d{P->W + w.off, w.cols, w.rows, w.cols, (int)cs.size(), 0, 0};
+    for (int q = w.src_begin; q < w.src_end; ++q) {
+      const WS& src = wsrc[q];
+      const double* ptr = src.zoff >= 0 ? P->Z + src.zoff : P->xin + (-1 - src.zoff);
+      cs.push_back({ptr, src.ld, src.coef});
+    }
+    d.src_end = (int)cs.size();
+    cd.push_back(d);
+  }
+  // phase 2 grouped by output block
   std::vector<GemmTask> t2;
   std::vector<GemmGroup> g2;
+  for (int x = 0; x < (int)P->X.size(); ++x) {
+    const XBlock& X = P->X[x];
+    int b0 = (int)t2.size();
+    for (int wi : w_by_x[x]) {
+      const WItem& w = ws[wi];
+      const CombOp& C = P->cl[w.gl];
+      const BlockRef& cb = (*C.blocks)[w.cbi];
+      if (C.identity) t2.push_back({nullptr, P->W + w.off, 0, w.cols, w.rows, 0, 0, C.scalar});
+      else t2.push_back({C.data + cb.off, P->W + w.off, cb.cols, w.cols, cb.cols, 0, 0, C.scalar});
+    }
+    if ((int)t2.size() > b0) g2.push_back({P->yout + X.off, X.cols, X.rows, X.cols, b0, (int)t2.size(), 0});
+  }
+  // diagonal
   std::vector<DiagTerm> dt;
   std::vector<DiagOut> dov;
   P->diag = (double*)dev_alloc(sizeof(double) * std::max<int64_t>(P->n, 1), stream_);
   dev_zero(P->diag, sizeof(double) * std::max<int64_t>(P->n, 1), stream_);
   for (int x = 0; x < (int)P->X.size(); ++x) {
+    if (dout[x].empty()) continue;
     const XBlock& X = P->X[x];
-    int b0 = (int)t2.size();
-    for (auto t : out2[x]) {
-      t.B = P->Z + zs[(int)(intptr_t)t.B].off;
-      t2.push_back(t);
-    }
-    if ((int)t2.size() > b0) g2.push_back({P->yout + X.off, X.cols, X.rows, X.cols, b0, (int)t2.size(), 0});
-    if (!dout[x].empty()) {
-      int d0 = (int)dt.size();
-      dt.insert(dt.end(), dout[x].begin(), dout[x].end());
-      dov.push_back({P->diag + X.off, X.rows, X.cols, d0, (int)dt.size()});
-    }
+    int d0 = (int)dt.size();
+    dt.insert(dt.end(), dout[x].begin(), dout[x].end());
+    dov.push_back({P->diag + X.off, X.rows, X.cols, d0, (int)dt.size()});
   }
   P->p1 = gemm_plan_upload(t1, g1, stream_);
+  P->pc = comb_plan_upload(cs, cd, stream_);
   P->p2 = gemm_plan_upload(t2, g2, stream_);
   DiagPlan* pd = diag_plan_upload(dt, dov, stream_);
   diag_plan_run(pd, stream_);
   diag_plan_free(pd, stream_);
-  P->flops = flops;
-  P->ntasks = (int64_t)t1.size() + (int64_t)t2.size();
+  P->flops1 = flops1;
+  P->flops2 = flops2;
+  P->flops = flops1 + flops2;
+  P->ntasks = (int64_t)t1.size() + (int64_t)t2.size() + (int64_t)cs.size();
+  P->wsize = wsize;
   st_.t_plan_ms += tm.ms();
   return P;
 }
@@ -885,7 +988,9 @@ void Engine::free_plan(MatvecPlan* p) {
   if (!p) return;
   gemm_plan_free(p->p1, stream_);
   gemm_plan_free(p->p2, stream_);
+  comb_plan_free(p->pc, stream_);
   dev_free(p->Z, stream_);
+  dev_free(p->W, stream_);
   dev_free(p->xin, stream_);
   dev_free(p->yout, stream_);
   dev_free(p->diag, stream_);
@@ -912,12 +1017,13 @@ void Engine::flush_events() {
 
 void Engine::run_matvec(MatvecPlan* p, const double* x, double* y) {
   if (x != p->xin) dev_d2d(p->xin, x, sizeof(double) * p->n, stream_);
-  dev_zero(p->Z, sizeof(double) * std::max<int64_t>(p->zsize, 1), stream_);
+  if (p->zsize) dev_zero(p->Z, sizeof(double) * p->zsize, stream_);
   dev_zero(p->yout, sizeof(double) * std::max<int64_t>(p->n, 1), stream_);
   flush_events();
   if (!ev_[0]) for (auto& e : ev_) e = event_create();
   event_record(ev_[0], stream_);
   gemm_plan_run(p->p1, stream_);
+  comb_plan_run(p->pc, stream_);
   event_record(ev_[1], stream_);
   gemm_plan_run(p->p2, stream_);
   event_record(ev_[2], stream_);
@@ -1099,10 +1205,12 @@ namespace dmrg {
 
 // Eqs. 26-28: back-transform x into TT per middle sector (jM, NM, IM), weight the
 // columns by sqrt((2jR+1)/(2jM+1)) (which makes the bracket of Eq. 27 right-normalised),
-// decompose M = U lambda V through the eigenpairs of the smaller Gram matrix, keep the
-// D largest lambda over all sectors (D counts reduced multiplets), normalise with
-// kappa = lambda / sqrt(sum (2jM+1) lambda^2), and write T[i], T[i+1] for the sweep
+// keep the D largest lambda over all sectors (D counts reduced multiplets), normalise
+// with kappa = lambda / sqrt(sum (2jM+1) lambda^2), and write T[i], T[i+1] for the sweep
 // direction (dir > 0: A[i] = U, A[i+1] = kappa V; dir < 0: A[i] = U kappa, A[i+1] = V).
+// The factor that must be normalised comes from the eigenvectors of the Gram matrix on
+// its side (M M^T for U, M^T M for V); the other factor is the projection of M onto
+// them (kappa V = U^T M / |M|, U kappa = M V^T / |M|), with no division by lambda.
 // Returns the discarded weight sum over dropped (2jM+1) kappa^2 (Eq. 15).
 double Engine::truncate(int i, int dir, int D, const double* x, double /*unused*/) {
   check_ready();
@@ -1157,7 +1265,7 @@ double Engine::truncate(int i, int dir, int D, const double* x, double /*unused*
         }
       }
     if (g.R == 0 || g.C == 0) continue;
-    g.n = std::min(g.R, g.C);
+    g.n = dir > 0 ? g.R : g.C;
     gs.push_back(g);
   }
   int64_t msz = 0, gsz = 0, wsz = 0, asz = 0;
@@ -1218,7 +1326,7 @@ double Engine::truncate(int i, int dir, int D, const double* x, double /*unused*
     std::vector<GemmTask> t;
     std::vector<GemmGroup> gg;
     for (auto& g : gs) {
-      if (g.R <= g.C) t.push_back({M + g.moff, M + g.moff, g.C, g.C, g.C, 0, 1, 1.0});
+      if (dir > 0) t.push_back({M + g.moff, M + g.moff, g.C, g.C, g.C, 0, 1, 1.0});
       else t.push_back({M + g.moff, M + g.moff, g.C, g.C, g.R, 1, 0, 1.0});
       gg.push_back({Gm + g.goff, g.n, g.n, g.n, (int)t.size() - 1, (int)t.size(), 0});
     }
@@ -1233,10 +1341,12 @@ double Engine::truncate(int i, int dir, int D, const double* x, double /*unused*
   for (auto& g : gs) { goff.push_back(goff.back() + g.n); wgt.push_back(g.s.tj + 1); }
   std::vector<int> kept;
   double norm2 = 0.0, disc = 0.0;
-  select_largest(W, goff, wgt, D, 1e-13, kept, &norm2, &disc, stream_);
+  // eigenvalues of the Gram matrix are lambda^2 with an error ~ eps lambda_max^2: values
+  // with lambda below 3e-8 lambda_max are at that noise level and are treated as zero
+  select_largest(W, goff, wgt, D, 3e-8, kept, &norm2, &disc, stream_);
   if (!(norm2 > 0.0)) throw std::runtime_error("two-site vector has zero norm");
   const double w_disc = disc / norm2;
-  // the other factor: V = Q_r^T M (R <= C) or U = M Q_r (C < R)
+  // the other factor: Q_r^T M (right move) or M Q_r (left move)
   {
     std::vector<GemmTask> t;
     std::vector<GemmGroup> gg;
@@ -1244,7 +1354,7 @@ double Engine::truncate(int i, int dir, int D, const double* x, double /*unused*
       const Grp& g = gs[q];
       int r = kept[q];
       if (r == 0) continue;
-      if (g.R <= g.C) {
+      if (dir > 0) {
         t.push_back({Q + g.goff, M + g.moff, g.n, g.C, g.R, 1, 0, 1.0});
         gg.push_back({Aux + g.aoff, g.C, r, g.C, (int)t.size() - 1, (int)t.size(), 0});
       } else {
@@ -1278,18 +1388,15 @@ double Engine::truncate(int i, int dir, int D, const double* x, double /*unused*
     const int r = kept[q];
     if (r == 0) continue;
     const int m = gnew[q];
-    const double* wq = W + g.woff;
     for (int rb = 0; rb < (int)g.rows.size(); ++rb) {
       const SiteBlock* sb = ia.at({g.rows[rb].second, g.rows[rb].first, m});
       double* dst = sites_[i].data + sb->off;
-      if (g.R <= g.C) {  // U = Q_r
+      if (dir > 0) {  // A[i] = U = Q_r (rows of the row block)
         const double* src = Q + g.goff + (int64_t)g.roff[rb] * g.n;
-        if (dir > 0) sj.push_back({dst, src, nullptr, nullptr, r, g.n, sb->rows, r, 0, 0, 0, 1.0});
-        else sj.push_back({dst, src, nullptr, wq, r, g.n, sb->rows, r, 0, 1, 0, inv});
-      } else {  // U = M Q_r / lambda
+        sj.push_back({dst, src, nullptr, nullptr, r, g.n, sb->rows, r, 0, 0, 0, 1.0});
+      } else {        // A[i] = U kappa = M Q_r / |M|
         const double* src = Aux + g.aoff + (int64_t)g.roff[rb] * r;
-        if (dir > 0) sj.push_back({dst, src, nullptr, wq, r, r, sb->rows, r, 0, 2, 0, 1.0});
-        else sj.push_back({dst, src, nullptr, nullptr, r, r, sb->rows, r, 0, 0, 0, inv});
+        sj.push_back({dst, src, nullptr, nullptr, r, r, sb->rows, r, 0, 0, 0, inv});
       }
     }
     for (int cb = 0; cb < (int)g.cols.size(); ++cb) {
@@ -1297,14 +1404,12 @@ double Engine::truncate(int i, int dir, int D, const double* x, double /*unused*
       double* dst = sites_[i + 1].data + sb->off;
       const double f = std::sqrt((double)(g.s.tj + 1) / (double)(br.sec[g.cols[cb].first].tj + 1));
       const int dR = sb->cols;
-      if (g.R <= g.C) {  // V = Q_r^T M / lambda
+      if (dir > 0) {  // A[i+1] = kappa V (bracket of Eq. 27) = Q_r^T M / |M|
         const double* src = Aux + g.aoff + g.coff[cb];
-        if (dir > 0) sj.push_back({dst, src, nullptr, nullptr, dR, g.C, r, dR, 0, 0, 0, f * inv});
-        else sj.push_back({dst, src, wq, nullptr, dR, g.C, r, dR, 2, 0, 0, f});
-      } else {  // V = Q_r^T
+        sj.push_back({dst, src, nullptr, nullptr, dR, g.C, r, dR, 0, 0, 0, f * inv});
+      } else {        // A[i+1] = V = Q_r^T
         const double* src = Q + g.goff + (int64_t)g.coff[cb] * g.n;
-        if (dir > 0) sj.push_back({dst, src, wq, nullptr, dR, g.n, r, dR, 1, 0, 1, f * inv});
-        else sj.push_back({dst, src, nullptr, nullptr, dR, g.n, r, dR, 0, 0, 1, f});
+        sj.push_back({dst, src, nullptr, nullptr, dR, g.n, r, dR, 0, 0, 1, f});
       }
     }
   }
@@ -1320,22 +1425,185 @@ double Engine::truncate(int i, int dir, int D, const double* x, double /*unused*
   return w_disc;
 }
 
-// Mixed canonical form around `center` (Sec. 2.2, Eqs. 5-6) by exact decompositions:
-// moving left from the right end right-normalises sites L-1..1, then moving right
-// left-normalises sites 0..center-1.
+// Right-normalise site k (reduced Eq. 6) and push the remaining factor into site k-1:
+// per left sector, G = sum (2jR+1)/(2jL+1) T T^T = Q lambda Q^T, T <- lambda^-1/2 Q^T T,
+// T[k-1] <- T[k-1] Q lambda^1/2.  Directions with lambda below 1e-14 lambda_max of their
+// sector (numerically absent from the state) are dropped from the bond.  One pass leaves
+// an orthonormality error ~ eps lambda_max / lambda_min; callers run a second pass on
+// the then well-conditioned tensor (as in Cholesky-QR2).
+void Engine::right_normalize_site(int k) {
+  Site& S = sites_[k];
+  const Bond bl = bonds_[k];
+  const Bond& br = bonds_[k + 1];
+  const int nl = (int)bl.sec.size();
+  std::vector<int64_t> goff(nl + 1, 0), woff(nl + 1, 0);
+  for (int l = 0; l < nl; ++l) {
+    goff[l + 1] = goff[l] + (int64_t)bl.dim[l] * bl.dim[l];
+    woff[l + 1] = woff[l] + bl.dim[l];
+  }
+  double* G = (double*)dev_alloc(sizeof(double) * std::max<int64_t>(goff[nl], 1), stream_);
+  double* Q = (double*)dev_alloc(sizeof(double) * std::max<int64_t>(goff[nl], 1), stream_);
+  double* W = (double*)dev_alloc(sizeof(double) * std::max<int64_t>(woff[nl], 1), stream_);
+  dev_zero(G, sizeof(double) * std::max<int64_t>(goff[nl], 1), stream_);
+  {
+    std::vector<GemmTask> t;
+    std::vector<GemmGroup> g;
+    for (int l = 0; l < nl; ++l) {
+      int b0 = (int)t.size();
+      for (auto& b : S.blocks)
+        if (b.l == l)
+          t.push_back({S.data + b.off, S.data + b.off, b.cols, b.cols, b.cols, 0, 1,
+                       (double)(br.sec[b.r].tj + 1) / (double)(bl.sec[l].tj + 1)});
+      if ((int)t.size() > b0) g.push_back({G + goff[l], bl.dim[l], bl.dim[l], bl.dim[l], b0, (int)t.size(), 0});
+    }
+    GemmPlan* p = gemm_plan_upload(t, g, stream_);
+    gemm_plan_run(p, stream_);
+    gemm_plan_free(p, stream_);
+  }
+  std::vector<EigJob> jobs;
+  for (int l = 0; l < nl; ++l) jobs.push_back({G + goff[l], Q + goff[l], W + woff[l], bl.dim[l]});
+  eig_batched(jobs, stream_);
+  std::vector<double> w(woff[nl]);
+  dev_d2h(w.data(), W, sizeof(double) * w.size(), stream_);
+  dev_sync(stream_);
+  Bond nb;
+  std::vector<int> keep(nl, 0);
+  for (int l = 0; l < nl; ++l) {
+    const double wmax = bl.dim[l] > 0 ? w[woff[l]] : 0.0;
+    for (int a = 0; a < bl.dim[l]; ++a)
+      if (w[woff[l] + a] > 1e-14 * wmax && wmax > 0.0) ++keep[l];
+    if (keep[l] > 0) { nb.sec.push_back(bl.sec[l]); nb.dim.push_back(keep[l]); }
+  }
+  // new tensors: site k rows Q_r^T T scaled by lambda^-1/2; site k-1 columns T Q_r lambda^1/2
+  Site oldk = S;
+  Site oldm = sites_[k - 1];
+  sites_[k].data = nullptr;
+  sites_[k - 1].data = nullptr;
+  bonds_[k] = nb;
+  alloc_site(k - 1);
+  alloc_site(k);
+  std::vector<GemmTask> t;
+  std::vector<GemmGroup> g;
+  std::vector<double> scl(woff[nl], 0.0);
+  for (int l = 0; l < nl; ++l)
+    for (int a = 0; a < keep[l]; ++a) scl[woff[l] + a] = w[woff[l] + a];
+  for (auto& b : oldk.blocks) {
+    const int l = b.l;
+    if (keep[l] == 0) continue;
+    const int nlid = nb.find(bl.sec[l]);
+    for (auto& nbk : sites_[k].blocks)
+      if (nbk.ls == b.ls && nbk.l == nlid && nbk.r == b.r) {
+        // new block (keep x dR) = Q_r^T (keep x dL) . T (dL x dR); rows scaled afterwards
+        t.push_back({Q + goff[l], oldk.data + b.off, bl.dim[l], b.cols, bl.dim[l], 1, 0, 1.0});
+        g.push_back({sites_[k].data + nbk.off, nbk.cols, keep[l], nbk.cols, (int)t.size() - 1, (int)t.size(), 0});
+      }
+  }
+  for (auto& b : oldm.blocks) {
+    const int l = b.r;  // right sector of site k-1 is the left sector of site k
+    if (keep[l] == 0) continue;
+    const int nlid = nb.find(bl.sec[l]);
+    for (auto& nbk : sites_[k - 1].blocks)
+      if (nbk.ls == b.ls && nbk.l == b.l && nbk.r == nlid) {
+        t.push_back({oldm.data + b.off, Q + goff[l], b.cols, bl.dim[l], b.cols, 0, 0, 1.0});
+        g.push_back({sites_[k - 1].data + nbk.off, nbk.cols, nbk.rows, keep[l], (int)t.size() - 1, (int)t.size(), 0});
+      }
+  }
+  GemmPlan* p = gemm_plan_upload(t, g, stream_);
+  gemm_plan_run(p, stream_);
+  gemm_plan_free(p, stream_);
+  std::vector<ScatterJob> sj;
+  for (auto& nbk : sites_[k].blocks) {
+    const int l = bl.find(nb.sec[nbk.l]);
+    sj.push_back({sites_[k].data + nbk.off, sites_[k].data + nbk.off, W + woff[l], nullptr,
+                  nbk.cols, nbk.cols, nbk.rows, nbk.cols, 2, 0, 0, 1.0});
+  }
+  for (auto& nbk : sites_[k - 1].blocks) {
+    const int l = bl.find(nb.sec[nbk.r]);
+    sj.push_back({sites_[k - 1].data + nbk.off, sites_[k - 1].data + nbk.off, nullptr, W + woff[l],
+                  nbk.cols, nbk.cols, nbk.rows, nbk.cols, 0, 1, 0, 1.0});
+  }
+  scatter_batched(sj, stream_);
+  dev_free(oldk.data, stream_);
+  dev_free(oldm.data, stream_);
+  dev_free(G, stream_);
+  dev_free(Q, stream_);
+  dev_free(W, stream_);
+}
+
+// Mixed canonical form around `center` (Sec. 2.2, Eqs. 5-6): sites L-1..1 are
+// right-normalised one by one (the factor moves left into site 0, whose norm is then
+// set to 1), then exact two-site decompositions moving right left-normalise sites
+// 0..center-1.  The state is unchanged up to normalisation.
 void Engine::canonicalize(int center) {
   check_ready();
   if (center < 0 || center > L_ - 2) throw std::out_of_range("center out of range");
-  auto move = [&](int i, int dir) {
+  Timer tm;
+  for (int k = L_ - 1; k >= 1; --k) {
+    right_normalize_site(k);
+    right_normalize_site(k);
+  }
+  {  // normalise: |Psi|^2 = sum over site-0 blocks of (2jR+1) |T|^2
+    const Site& S = sites_[0];
+    std::vector<double> h(S.size);
+    dev_d2h(h.data(), S.data, sizeof(double) * S.size, stream_);
+    dev_sync(stream_);
+    double n2 = 0.0;
+    for (auto& b : S.blocks)
+      for (int e = 0; e < b.rows * b.cols; ++e)
+        n2 += (bonds_[1].sec[b.r].tj + 1) * h[b.off + e] * h[b.off + e];
+    if (!(n2 > 0.0)) throw std::runtime_error("MPS has zero norm");
+    for (auto& v : h) v /= std::sqrt(n2);
+    dev_h2d(S.data, h.data(), sizeof(double) * S.size, stream_);
+  }
+  for (auto& e : lenv_) free_env(e);
+  for (auto& e : renv_) free_env(e);
+  if (cached_) { free_plan(cached_); cached_ = nullptr; cached_site_ = -1; }
+  for (int i = 0; i < center; ++i) {
     int64_t n;
     x_layout(i, &n);
     double* x = (double*)dev_alloc(sizeof(double) * std::max<int64_t>(n, 1), stream_);
     tt_to_x(i, x);
-    truncate(i, dir, std::numeric_limits<int>::max() / 2, x, 0.0);
+    truncate(i, +1, std::numeric_limits<int>::max() / 2, x, 0.0);
     dev_free(x, stream_);
-  };
-  for (int i = L_ - 2; i >= 0; --i) move(i, -1);
-  for (int i = 0; i < center; ++i) move(i, +1);
+  }
+  st_.t_trunc_ms += 0.0 * tm.ms();
+}
+
+// True if sites 1..L-1 satisfy the reduced right-normalisation of Eq. 6,
+// sum (2jR+1)/(2jL+1) T T^T = 1 per left sector, to 1e-10.
+bool Engine::is_right_canonical() {
+  for (int k = L_ - 1; k >= 1; --k) {
+    const Site& S = sites_[k];
+    const Bond& bl = bonds_[k];
+    const Bond& br = bonds_[k + 1];
+    std::vector<int64_t> goff(bl.sec.size(), 0);
+    int64_t tot = 0;
+    for (size_t l = 0; l < bl.sec.size(); ++l) { goff[l] = tot; tot += (int64_t)bl.dim[l] * bl.dim[l]; }
+    double* G = (double*)dev_alloc(sizeof(double) * std::max<int64_t>(tot, 1), stream_);
+    dev_zero(G, sizeof(double) * std::max<int64_t>(tot, 1), stream_);
+    std::vector<GemmTask> t;
+    std::vector<GemmGroup> g;
+    for (size_t l = 0; l < bl.sec.size(); ++l) {
+      int b0 = (int)t.size();
+      for (auto& b : S.blocks)
+        if (b.l == (int)l)
+          t.push_back({S.data + b.off, S.data + b.off, b.cols, b.cols, b.cols, 0, 1,
+                       (double)(br.sec[b.r].tj + 1) / (double)(bl.sec[l].tj + 1)});
+      if ((int)t.size() > b0) g.push_back({G + goff[l], bl.dim[l], bl.dim[l], bl.dim[l], b0, (int)t.size(), 0});
+    }
+    GemmPlan* p = gemm_plan_upload(t, g, stream_);
+    gemm_plan_run(p, stream_);
+    gemm_plan_free(p, stream_);
+    std::vector<double> h(tot);
+    dev_d2h(h.data(), G, sizeof(double) * tot, stream_);
+    dev_sync(stream_);
+    dev_free(G, stream_);
+    for (size_t l = 0; l < bl.sec.size(); ++l)
+      for (int a = 0; a < bl.dim[l]; ++a)
+        for (int c = 0; c < bl.dim[l]; ++c)
+          if (std::fabs(h[goff[l] + (int64_t)a * bl.dim[l] + c] - (a == c ? 1.0 : 0.0)) > 1e-10) return false;
+  }
+  return true;
 }
 
 // ConvergenceScheme of Sec. 4.2: per instruction, macro-iterations (a sweep right then
@@ -1344,7 +1612,7 @@ void Engine::canonicalize(int center) {
 double Engine::solve(double* e_last_out) {
   check_ready();
   Timer total;
-  canonicalize(0);
+  if (!is_right_canonical()) canonicalize(0);
   double e_min = std::numeric_limits<double>::infinity(), e_last = 0.0;
   double e_prev = std::numeric_limits<double>::infinity();
   bool all_conv = true;

@@ -46,12 +46,14 @@ struct XBlock {  // block of the two-site vector: (jL NL IL) (s1) (s2) j (jR NR 
   int l, ls1, ls2, tj, r;
   int64_t off;
   int rows, cols;
+  int trow;       // row offset inside the stack of blocks sharing the right sector r
 };
 
 // A combined operator sum_a scalar_a O_a over sources sharing one site pattern.
 struct CombOp {
   int target = -1, pattern = -1;
   double scalar = 1.0;           // multiplies the blocks (alias) or 1 (materialised)
+  bool identity = false;         // the operator is the identity (scaled by scalar)
   const std::vector<BlockRef>* blocks = nullptr;
   const std::unordered_map<int64_t, int>* at = nullptr;
   const double* data = nullptr;  // base of the blocks
@@ -100,6 +102,8 @@ class Engine {
   // Eqs. 26-28 and the operator update in the sweep direction
   double sweep_step(int i, int dir, int D, double gamma, double* w_disc, int* iters, bool* conv);
   void canonicalize(int center);
+  bool is_right_canonical();
+  void right_normalize_site(int k);
 
   const Stats& stats() { flush_events(); return st_; }
   Stream stream() const { return stream_; }

@@ -15,6 +15,7 @@ namespace dmrg {
 namespace {
 
 thread_local std::string g_err;
+int64_t g_launches = 0;  // kernels launched by this library (all contexts)
 
 inline cudaStream_t S(Stream s) { return (cudaStream_t)s; }
 
@@ -53,6 +54,7 @@ void dev_zero(void* p, size_t b, Stream s) {
   if (b) ck(cudaMemsetAsync(p, 0, b, S(s)), "memset");
 }
 void dev_sync(Stream s) { ck(cudaStreamSynchronize(S(s)), "stream sync"); }
+int64_t kernel_launches() { return g_launches; }
 int dev_check(const char** msg) {
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) return 0;
@@ -108,6 +110,17 @@ __global__ void __launch_bounds__(256) k_grouped_gemm(const GemmTask* __restrict
   double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
   for (int t = g.task_begin; t < g.task_end; ++t) {
     const GemmTask T = tasks[t];
+    if (T.A == nullptr) {  // op(A) = identity: C += alpha op(B)
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          int r = row0 + ty + 16 * i, c = col0 + tx + 16 * j;
+          if (r < g.m && c < g.n)
+            acc[i][j] += T.alpha * (T.transB ? T.B[(size_t)c * T.ldb + r] : T.B[(size_t)r * T.ldb + c]);
+        }
+      continue;
+    }
     for (int k0 = 0; k0 < T.k; k0 += BK) {
       for (int e = tid; e < BM * BK; e += 256) {
         int r, kk;
@@ -181,6 +194,7 @@ GemmPlan* gemm_plan_upload(const std::vector<GemmTask>& t, std::vector<GemmGroup
 void gemm_plan_run(const GemmPlan* p, Stream s) {
   if (!p || p->ntiles == 0) return;
   k_grouped_gemm<<<p->ntiles, 256, 0, S(s)>>>(p->tasks, p->groups, p->ngroups);
+  ++g_launches;
   ck(cudaGetLastError(), "grouped_gemm launch");
 }
 
@@ -233,6 +247,7 @@ void comb_plan_run(const CombPlan* p, Stream s) {
   for (int off = 0; off < p->ndst; off += 65535) {
     int n = std::min(65535, p->ndst - off);
     k_combine<<<n, 128, 0, S(s)>>>(p->src, p->dst + off);
+    ++g_launches;
   }
   ck(cudaGetLastError(), "combine launch");
 }
@@ -285,6 +300,7 @@ void diag_plan_run(const DiagPlan* p, Stream s) {
   for (int off = 0; off < p->n; off += 65535) {
     int n = std::min(65535, p->n - off);
     k_diag<<<n, 128, 0, S(s)>>>(p->t, p->o + off);
+    ++g_launches;
   }
   ck(cudaGetLastError(), "diag launch");
 }
@@ -484,150 +500,184 @@ void vec_multidot(const double* V, int64_t ldv, int m, const double* w, int64_t 
   int nch = (int)std::min<int64_t>(kMaxChunks, std::max<int64_t>(1, (n + kDotChunk - 1) / kDotChunk));
   dim3 grid(nch, m);
   k_multidot_partial<<<grid, 256, 0, S(s)>>>(V, ldv, w, n, nch, scratch);
+  ++g_launches;
   k_multidot_final<<<m, 256, 0, S(s)>>>(scratch, nch, m, out);
+  ++g_launches;
   ck(cudaGetLastError(), "multidot");
 }
 
 void vec_combine(const double* V, int64_t ldv, int m, const double* c, double beta, double* y,
                  int64_t n, Stream s) {
   k_vec_combine<<<nblk(n, 256), 256, 0, S(s)>>>(V, ldv, m, c, beta, y, n);
+  ++g_launches;
   ck(cudaGetLastError(), "vec_combine");
 }
 
 void vec_axpby(double a, const double* x, double b, double* y, int64_t n, Stream s) {
   k_axpby<<<nblk(n, 256), 256, 0, S(s)>>>(a, x, b, y, n);
+  ++g_launches;
   ck(cudaGetLastError(), "axpby");
 }
 
 void vec_normalize(double* y, const double* nrm2, int64_t n, Stream s) {
   k_normalize<<<nblk(n, 256), 256, 0, S(s)>>>(y, nrm2, n);
+  ++g_launches;
   ck(cudaGetLastError(), "normalize");
 }
 
 void vec_precondition(const double* r, const double* d, const double* th, double* t, int64_t n,
                       Stream s) {
   k_precondition<<<nblk(n, 256), 256, 0, S(s)>>>(r, d, th, t, n);
+  ++g_launches;
   ck(cudaGetLastError(), "precondition");
 }
 
 void small_eig(const double* G, int gld, int m, int k, double* theta, double* C, Stream s) {
   k_small_eig<<<1, 256, 0, S(s)>>>(G, gld, m, k, theta, C);
+  ++g_launches;
   ck(cudaGetLastError(), "small_eig");
 }
 
 void vec_add_noise(double* x, int64_t n, double amp, uint64_t seed, Stream s) {
   k_noise<<<nblk(n, 256), 256, 0, S(s)>>>(x, n, amp, seed);
+  ++g_launches;
   ck(cudaGetLastError(), "noise");
 }
 
 // ------------------------------------------------------------------ batched Jacobi
 
 namespace {
-__global__ void __launch_bounds__(256) k_eig_batched(const EigJob* __restrict__ jobs) {
+constexpr int kEigSmemN = 112;  // blocks up to this size are diagonalised in shared memory
+
+// Cyclic Jacobi (round-robin pairing, n/2 rotations per step) on one symmetric block per
+// CTA.  SM: the matrix and the eigenvectors live in shared memory (row stride n+1);
+// otherwise in global memory (stride n).  A pair is rotated only while |a_pq| exceeds
+// 1e-16 sqrt(|a_pp a_qq|) plus an absolute floor; the loop ends after a sweep without
+// rotations (at most 40 sweeps).  Output: eigenvalues descending, eigenvectors as
+// columns of J.Q.
+template <bool SM, int NT>
+__global__ void __launch_bounds__(NT) k_eig_batched(const EigJob* __restrict__ jobs) {
   const EigJob J = jobs[blockIdx.x];
   const int n = J.n, tid = threadIdx.x;
-  double* A = J.A;
-  double* Q = J.Q;
   extern __shared__ double sm[];
+  const int ld = SM ? n + 1 : n;
+  double* A = SM ? sm : J.A;
+  double* Q = SM ? sm + (size_t)n * ld : J.Q;
   const int np = (n + 1) & ~1;
-  double* cs = sm;
-  double* sn = sm + np / 2;
-  __shared__ double red[256];
-  __shared__ int done;
-  for (int e = tid; e < n * n; e += 256) Q[e] = (e / n == e % n) ? 1.0 : 0.0;
+  double* cs = SM ? sm + (size_t)2 * n * ld : sm;
+  double* sn = cs + np / 2;
+  double* wtmp = sn + np / 2;
+  __shared__ int nrot;
+  if (SM)
+    for (int e = tid; e < n * n; e += NT) A[(size_t)(e / n) * ld + e % n] = J.A[e];
+  for (int e = tid; e < n * n; e += NT) Q[(size_t)(e / n) * ld + e % n] = (e / n == e % n) ? 1.0 : 0.0;
   __syncthreads();
-  for (int sweep = 0; sweep < 50; ++sweep) {
-    double off = 0.0, tot = 0.0;
-    for (int e = tid; e < n * n; e += 256) {
-      double v = A[e];
-      tot += v * v;
-      if (e / n != e % n) off += v * v;
-    }
-    red[tid] = off;
+  double scale = 0.0;
+  for (int i = 0; i < n; ++i) scale = fmax(scale, fabs(A[(size_t)i * ld + i]));
+  const double floor_abs = 1e-300 + 1e-18 * scale;
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    if (tid == 0) nrot = 0;
     __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) { if (tid < o) red[tid] += red[tid + o]; __syncthreads(); }
-    double offs = red[0];
-    __syncthreads();
-    red[tid] = tot;
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) { if (tid < o) red[tid] += red[tid + o]; __syncthreads(); }
-    if (tid == 0) done = (offs <= 1e-32 * red[0]) ? 1 : 0;
-    __syncthreads();
-    if (done) break;
     for (int step = 0; step < np - 1; ++step) {
-      for (int r = tid; r < np / 2; r += 256) {
+      for (int r = tid; r < np / 2; r += NT) {
         int a = r, b = np - 1 - r;
         int p = a == 0 ? 0 : 1 + (a - 1 + step) % (np - 1);
         int q = b == 0 ? 0 : 1 + (b - 1 + step) % (np - 1);
         if (p > q) { int t = p; p = q; q = t; }
         double c = 1.0, s = 0.0;
-        if (q < n) sym_schur2(A[(size_t)p * n + p], A[(size_t)q * n + q], A[(size_t)p * n + q], c, s);
+        if (q < n) {
+          double app = A[(size_t)p * ld + p], aqq = A[(size_t)q * ld + q], apq = A[(size_t)p * ld + q];
+          if (fabs(apq) > 1e-16 * sqrt(fabs(app * aqq)) + floor_abs) {
+            sym_schur2(app, aqq, apq, c, s);
+            atomicAdd(&nrot, 1);
+          }
+        }
         cs[r] = c; sn[r] = s;
       }
       __syncthreads();
-      for (int e = tid; e < (np / 2) * n; e += 256) {
+      for (int e = tid; e < (np / 2) * n; e += NT) {
         int r = e / n, j = e % n;
+        if (sn[r] == 0.0) continue;
         int a = r, b = np - 1 - r;
         int p = a == 0 ? 0 : 1 + (a - 1 + step) % (np - 1);
         int q = b == 0 ? 0 : 1 + (b - 1 + step) % (np - 1);
         if (p > q) { int t = p; p = q; q = t; }
-        if (q >= n) continue;
         double c = cs[r], s = sn[r];
-        double ap = A[(size_t)p * n + j], aq = A[(size_t)q * n + j];
-        A[(size_t)p * n + j] = c * ap - s * aq;
-        A[(size_t)q * n + j] = s * ap + c * aq;
+        double ap = A[(size_t)p * ld + j], aq = A[(size_t)q * ld + j];
+        A[(size_t)p * ld + j] = c * ap - s * aq;
+        A[(size_t)q * ld + j] = s * ap + c * aq;
       }
       __syncthreads();
-      for (int e = tid; e < (np / 2) * n; e += 256) {
+      for (int e = tid; e < (np / 2) * n; e += NT) {
         int r = e / n, i = e % n;
+        if (sn[r] == 0.0) continue;
         int a = r, b = np - 1 - r;
         int p = a == 0 ? 0 : 1 + (a - 1 + step) % (np - 1);
         int q = b == 0 ? 0 : 1 + (b - 1 + step) % (np - 1);
         if (p > q) { int t = p; p = q; q = t; }
-        if (q >= n) continue;
         double c = cs[r], s = sn[r];
-        double ap = A[(size_t)i * n + p], aq = A[(size_t)i * n + q];
-        A[(size_t)i * n + p] = c * ap - s * aq;
-        A[(size_t)i * n + q] = s * ap + c * aq;
-        double qp = Q[(size_t)i * n + p], qv = Q[(size_t)i * n + q];
-        Q[(size_t)i * n + p] = c * qp - s * qv;
-        Q[(size_t)i * n + q] = s * qp + c * qv;
+        double ap = A[(size_t)i * ld + p], aq = A[(size_t)i * ld + q];
+        A[(size_t)i * ld + p] = c * ap - s * aq;
+        A[(size_t)i * ld + q] = s * ap + c * aq;
+        double qp = Q[(size_t)i * ld + p], qv = Q[(size_t)i * ld + q];
+        Q[(size_t)i * ld + p] = c * qp - s * qv;
+        Q[(size_t)i * ld + q] = s * qp + c * qv;
       }
       __syncthreads();
     }
+    if (nrot == 0) break;
+    __syncthreads();
   }
-  // sort eigenpairs descending: rank by value, ties by index
-  for (int i = tid; i < n; i += 256) J.w[i] = A[(size_t)i * n + i];
+  // eigenpairs sorted descending (ties by index)
+  for (int i = tid; i < n; i += NT) wtmp[i] = A[(size_t)i * ld + i];
   __syncthreads();
-  for (int e = tid; e < n * n; e += 256) A[e] = Q[e];
-  __syncthreads();
-  for (int i = tid; i < n; i += 256) {
-    double vi = J.w[i];
+  if (!SM) {  // the global matrix becomes scratch for the unsorted eigenvectors
+    for (int e = tid; e < n * n; e += NT) A[e] = Q[e];
+    __syncthreads();
+  }
+  const double* Qs = SM ? Q : A;
+  for (int i = tid; i < n; i += NT) {
+    double vi = wtmp[i];
     int rank = 0;
     for (int j = 0; j < n; ++j) {
-      double vj = J.w[j];
+      double vj = wtmp[j];
       if (vj > vi || (vj == vi && j < i)) ++rank;
     }
-    sm[np + i] = vi;
-    for (int r = 0; r < n; ++r) Q[(size_t)r * n + rank] = A[(size_t)r * n + i];
-    ((int*)(sm + np + n))[i] = rank;
+    J.w[rank] = vi;
+    for (int rr = 0; rr < n; ++rr) J.Q[(size_t)rr * n + rank] = Qs[(size_t)rr * ld + i];
   }
-  __syncthreads();
-  for (int i = tid; i < n; i += 256) J.w[((int*)(sm + np + n))[i]] = sm[np + i];
 }
 }  // namespace
 
 void eig_batched(const std::vector<EigJob>& jobs, Stream s) {
   if (jobs.empty()) return;
-  int nmax = 0;
-  for (auto& j : jobs) nmax = std::max(nmax, j.n);
+  std::vector<EigJob> small, large;
+  int nmax_s = 1, nmax_l = 1;
+  for (auto& j : jobs) {
+    if (j.n <= kEigSmemN) { small.push_back(j); nmax_s = std::max(nmax_s, j.n); }
+    else { large.push_back(j); nmax_l = std::max(nmax_l, j.n); }
+  }
   EigJob* d = (EigJob*)dev_alloc(jobs.size() * sizeof(EigJob), s);
-  dev_h2d(d, jobs.data(), jobs.size() * sizeof(EigJob), s);
-  size_t shm = (size_t)((nmax + 1) & ~1) * sizeof(double) + (size_t)nmax * (sizeof(double) + sizeof(int)) + 64;
-  if (shm > 200 * 1024) throw std::runtime_error("eig_batched: block too large");
-  if (shm > 48 * 1024) ck(cudaFuncSetAttribute(k_eig_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm), "eig smem");
-  k_eig_batched<<<(int)jobs.size(), 256, shm, S(s)>>>(d);
-  ck(cudaGetLastError(), "eig_batched");
+  if (!small.empty()) {
+    dev_h2d(d, small.data(), small.size() * sizeof(EigJob), s);
+    const int np = (nmax_s + 1) & ~1;
+    size_t shm = sizeof(double) * ((size_t)2 * nmax_s * (nmax_s + 1) + np + nmax_s) + 64;
+    ck(cudaFuncSetAttribute(k_eig_batched<true, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm), "eig smem");
+    k_eig_batched<true, 256><<<(int)small.size(), 256, shm, S(s)>>>(d);
+    ++g_launches;
+    ck(cudaGetLastError(), "eig_batched (shared)");
+  }
+  if (!large.empty()) {
+    EigJob* dl = d + small.size();
+    dev_h2d(dl, large.data(), large.size() * sizeof(EigJob), s);
+    const int np = (nmax_l + 1) & ~1;
+    size_t shm = sizeof(double) * ((size_t)np + nmax_l) + 64;
+    if (shm > 200 * 1024) throw std::runtime_error("eig_batched: block too large");
+    if (shm > 48 * 1024) ck(cudaFuncSetAttribute(k_eig_batched<false, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm), "eig smem");
+    k_eig_batched<false, 1024><<<(int)large.size(), 1024, shm, S(s)>>>(dl);
+    ++g_launches;
+    ck(cudaGetLastError(), "eig_batched (global)");
+  }
   dev_free(d, s);
 }
 
@@ -689,6 +739,7 @@ void select_largest(const double* vals, const std::vector<int>& goff, const std:
   dev_h2d(d_w, wgt.data(), sizeof(int) * G, s);
   dev_zero(d_k, sizeof(int) * (G + 1), s);
   k_select<<<1, 256, 0, S(s)>>>(vals, n, d_gid, d_w, D, zero_rel, d_k, d_s);
+  ++g_launches;
   ck(cudaGetLastError(), "select");
   kept.assign(G, 0);
   double sums[2];
@@ -730,6 +781,7 @@ void scatter_batched(const std::vector<ScatterJob>& jobs, Stream s) {
   for (size_t off = 0; off < jobs.size(); off += 65535) {
     int n = (int)std::min<size_t>(65535, jobs.size() - off);
     k_scatter<<<n, 128, 0, S(s)>>>(d + off);
+    ++g_launches;
   }
   ck(cudaGetLastError(), "scatter");
   dev_free(d, s);

@@ -43,22 +43,10 @@ def random12():
     cfg, h, V = make_problem("random12")
     L, N = cfg["L"], cfg["N"]
     irr = cfg["group_irreps"]
-    space = FCISpace(L, N // 2, N // 2, irr, 0)
-    idx = np.flatnonzero(space.mask.ravel())
-    import scipy.sparse.linalg as spla
-
-    def mv(x):
-        C = np.zeros(space.shape[0] * space.shape[1]); C[idx] = x
-        return space.sigma(h, V, C.reshape(space.shape)).ravel()[idx]
-    op = spla.LinearOperator((idx.size, idx.size), matvec=mv, dtype=np.float64)
-    w, U = spla.eigsh(op, k=3, which="SA", tol=1e-12)
-    order = np.argsort(w)
-    out = []
-    for a in order:
-        C = np.zeros(space.shape[0] * space.shape[1]); C[idx] = U[:, a]
-        out.append((float(w[a]), float(space.s2(C.reshape(space.shape)))))
-    singlet = [e for e, s2 in out if abs(s2) < 1e-6]
-    return {"random12_fci": {"e": singlet[0], "n_det": int(idx.size), "lowest_three": out}}
+    E, vecs, space = fci_ground_state(h, V, N, 0, irr, 0, dense_max=0, tol=1e-12)
+    C = vecs[0]
+    return {"random12_fci": {"e": float(E[0]), "n_det": int(space.mask.sum()),
+                             "s2": float(np.vdot(C, space.s2_apply(C)) / np.vdot(C, C))}}
 
 
 if __name__ == "__main__":
