@@ -1530,10 +1530,102 @@ void Engine::right_normalize_site(int k) {
   dev_free(W, stream_);
 }
 
+// Left-normalise site k (reduced Eq. 5, sum T^T T = 1 per right sector) and push the
+// remaining factor into site k+1: G = sum T^T T = Q lambda Q^T, T <- T Q lambda^-1/2,
+// T[k+1] <- lambda^1/2 Q^T T[k+1]; same threshold and second-pass rule as above.
+void Engine::left_normalize_site(int k) {
+  Site& S = sites_[k];
+  const Bond br = bonds_[k + 1];
+  const int nr = (int)br.sec.size();
+  std::vector<int64_t> goff(nr + 1, 0), woff(nr + 1, 0);
+  for (int r = 0; r < nr; ++r) {
+    goff[r + 1] = goff[r] + (int64_t)br.dim[r] * br.dim[r];
+    woff[r + 1] = woff[r] + br.dim[r];
+  }
+  double* G = (double*)dev_alloc(sizeof(double) * std::max<int64_t>(goff[nr], 1), stream_);
+  double* Q = (double*)dev_alloc(sizeof(double) * std::max<int64_t>(goff[nr], 1), stream_);
+  double* W = (double*)dev_alloc(sizeof(double) * std::max<int64_t>(woff[nr], 1), stream_);
+  dev_zero(G, sizeof(double) * std::max<int64_t>(goff[nr], 1), stream_);
+  {
+    std::vector<GemmTask> t;
+    std::vector<GemmGroup> g;
+    for (int r = 0; r < nr; ++r) {
+      int b0 = (int)t.size();
+      for (auto& b : S.blocks)
+        if (b.r == r) t.push_back({S.data + b.off, S.data + b.off, b.cols, b.cols, b.rows, 1, 0, 1.0});
+      if ((int)t.size() > b0) g.push_back({G + goff[r], br.dim[r], br.dim[r], br.dim[r], b0, (int)t.size(), 0});
+    }
+    GemmPlan* p = gemm_plan_upload(t, g, stream_);
+    gemm_plan_run(p, stream_);
+    gemm_plan_free(p, stream_);
+  }
+  std::vector<EigJob> jobs;
+  for (int r = 0; r < nr; ++r) jobs.push_back({G + goff[r], Q + goff[r], W + woff[r], br.dim[r]});
+  eig_batched(jobs, stream_);
+  std::vector<double> w(woff[nr]);
+  dev_d2h(w.data(), W, sizeof(double) * w.size(), stream_);
+  dev_sync(stream_);
+  Bond nb;
+  std::vector<int> keep(nr, 0);
+  for (int r = 0; r < nr; ++r) {
+    const double wmax = br.dim[r] > 0 ? w[woff[r]] : 0.0;
+    for (int a = 0; a < br.dim[r]; ++a)
+      if (w[woff[r] + a] > 1e-14 * wmax && wmax > 0.0) ++keep[r];
+    if (keep[r] > 0) { nb.sec.push_back(br.sec[r]); nb.dim.push_back(keep[r]); }
+  }
+  Site oldk = S;
+  Site oldn = sites_[k + 1];
+  sites_[k].data = nullptr;
+  sites_[k + 1].data = nullptr;
+  bonds_[k + 1] = nb;
+  alloc_site(k);
+  alloc_site(k + 1);
+  std::vector<GemmTask> t;
+  std::vector<GemmGroup> g;
+  for (auto& b : oldk.blocks) {  // new block (dL x keep) = T (dL x dR) . Q_r (dR x keep)
+    if (keep[b.r] == 0) continue;
+    const int nrid = nb.find(br.sec[b.r]);
+    for (auto& nbk : sites_[k].blocks)
+      if (nbk.ls == b.ls && nbk.l == b.l && nbk.r == nrid) {
+        t.push_back({oldk.data + b.off, Q + goff[b.r], b.cols, br.dim[b.r], b.cols, 0, 0, 1.0});
+        g.push_back({sites_[k].data + nbk.off, nbk.cols, nbk.rows, keep[b.r], (int)t.size() - 1, (int)t.size(), 0});
+      }
+  }
+  for (auto& b : oldn.blocks) {  // new block (keep x dR') = Q_r^T (keep x dL') . T
+    if (keep[b.l] == 0) continue;
+    const int nlid = nb.find(br.sec[b.l]);
+    for (auto& nbk : sites_[k + 1].blocks)
+      if (nbk.ls == b.ls && nbk.l == nlid && nbk.r == b.r) {
+        t.push_back({Q + goff[b.l], oldn.data + b.off, br.dim[b.l], b.cols, br.dim[b.l], 1, 0, 1.0});
+        g.push_back({sites_[k + 1].data + nbk.off, nbk.cols, keep[b.l], nbk.cols, (int)t.size() - 1, (int)t.size(), 0});
+      }
+  }
+  GemmPlan* p = gemm_plan_upload(t, g, stream_);
+  gemm_plan_run(p, stream_);
+  gemm_plan_free(p, stream_);
+  std::vector<ScatterJob> sj;
+  for (auto& nbk : sites_[k].blocks) {
+    const int r = br.find(nb.sec[nbk.r]);
+    sj.push_back({sites_[k].data + nbk.off, sites_[k].data + nbk.off, nullptr, W + woff[r],
+                  nbk.cols, nbk.cols, nbk.rows, nbk.cols, 0, 2, 0, 1.0});
+  }
+  for (auto& nbk : sites_[k + 1].blocks) {
+    const int r = br.find(nb.sec[nbk.l]);
+    sj.push_back({sites_[k + 1].data + nbk.off, sites_[k + 1].data + nbk.off, W + woff[r], nullptr,
+                  nbk.cols, nbk.cols, nbk.rows, nbk.cols, 1, 0, 0, 1.0});
+  }
+  scatter_batched(sj, stream_);
+  dev_free(oldk.data, stream_);
+  dev_free(oldn.data, stream_);
+  dev_free(G, stream_);
+  dev_free(Q, stream_);
+  dev_free(W, stream_);
+}
+
 // Mixed canonical form around `center` (Sec. 2.2, Eqs. 5-6): sites L-1..1 are
 // right-normalised one by one (the factor moves left into site 0, whose norm is then
-// set to 1), then exact two-site decompositions moving right left-normalise sites
-// 0..center-1.  The state is unchanged up to normalisation.
+// set to 1), then sites 0..center-1 are left-normalised one by one (the factor moves
+// right into the centre).  The state is unchanged up to normalisation.
 void Engine::canonicalize(int center) {
   check_ready();
   if (center < 0 || center > L_ - 2) throw std::out_of_range("center out of range");
@@ -1559,14 +1651,10 @@ void Engine::canonicalize(int center) {
   for (auto& e : renv_) free_env(e);
   if (cached_) { free_plan(cached_); cached_ = nullptr; cached_site_ = -1; }
   for (int i = 0; i < center; ++i) {
-    int64_t n;
-    x_layout(i, &n);
-    double* x = (double*)dev_alloc(sizeof(double) * std::max<int64_t>(n, 1), stream_);
-    tt_to_x(i, x);
-    truncate(i, +1, std::numeric_limits<int>::max() / 2, x, 0.0);
-    dev_free(x, stream_);
+    left_normalize_site(i);
+    left_normalize_site(i);
   }
-  st_.t_trunc_ms += 0.0 * tm.ms();
+  (void)tm;
 }
 
 // True if sites 1..L-1 satisfy the reduced right-normalisation of Eq. 6,

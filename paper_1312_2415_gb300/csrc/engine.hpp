@@ -104,6 +104,7 @@ class Engine {
   void canonicalize(int center);
   bool is_right_canonical();
   void right_normalize_site(int k);
+  void left_normalize_site(int k);
 
   const Stats& stats() { flush_events(); return st_; }
   Stream stream() const { return stream_; }
