@@ -119,6 +119,24 @@ int dmrg_tt_to_x(dmrg_ctx* ctx, int site, double* x, uintptr_t stream);
 /* y = H_eff x (Eq. 9) with the renormalised and complementary operators of Sec. 2.5. */
 int dmrg_heff_matvec(dmrg_ctx* ctx, int site, const double* x, double* y, uintptr_t stream);
 
+/* Allocation-free variant of dmrg_heff_matvec (no counterpart in the paper; it exists
+ * for callers that may not allocate device memory when they apply H_eff: code running
+ * inside a CUDA graph capture or under a fixed memory budget, where cudaMalloc is
+ * forbidden or must not grow the footprint).  It computes the same y = H_eff x with the
+ * tables that an earlier dmrg_heff_matvec / dmrg_davidson call prepared for this site
+ * (DMRG_EINVAL if there are none) and keeps its intermediate products in one fixed
+ * device array of the library (64 MiB, per device, held until the process exits);
+ * problems that need more scratch are rejected with DMRG_EINVAL and a message.  It
+ * calls no cudaMalloc / cudaFree and no allocating library routine.
+ * x and y are DEVICE pointers of n_elem doubles (see dmrg_two_site_layout); the work is
+ * queued on `stream` (0 = the default stream) and the call returns without waiting for
+ * it.  The first call on a device looks up the array's address (cudaGetSymbolAddress):
+ * make that first call before any stream capture.  All calls share the array, which
+ * keeps the previous call's contents (the call clears what must start at zero), so
+ * calls whose device work overlaps in time race on it: serialise them. */
+int dmrg_heff_matvec_noalloc(dmrg_ctx* ctx, int site, const double* x, double* y,
+                             uintptr_t stream);
+
 /* d = diagonal of H_eff (the Davidson preconditioner). */
 int dmrg_heff_diag(dmrg_ctx* ctx, int site, double* d, uintptr_t stream);
 

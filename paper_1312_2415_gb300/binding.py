@@ -55,6 +55,8 @@ _SIGS = {
     "dmrg_tt_to_x": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t]),
     "dmrg_heff_matvec": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
     "dmrg_heff_diag": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t]),
+    "dmrg_heff_matvec_noalloc": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                                ctypes.c_size_t]),
     "dmrg_davidson": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, _D, _I]),
     "dmrg_truncate": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                      ctypes.c_void_p, ctypes.c_size_t, _D]),
@@ -194,6 +196,10 @@ class Context:
         py, _ = _ptr_and_stream(y)
         self._check(self.lib.dmrg_heff_matvec(self.h, site, px, py, s))
         return y
+
+    def matvec_noalloc(self, site, x, y, stream=0):
+        """y = H_eff x without any allocation (x, y: device addresses; see the header)."""
+        self._check(self.lib.dmrg_heff_matvec_noalloc(self.h, int(site), int(x), int(y), int(stream)))
 
     def diag(self, site, out=None):
         if out is None:

@@ -239,6 +239,17 @@ int dmrg_heff_matvec(dmrg_ctx* c, int site, const double* x, double* y, uintptr_
   });
 }
 
+int dmrg_heff_matvec_noalloc(dmrg_ctx* c, int site, const double* x, double* y, uintptr_t stream) {
+  return guard(c, [&] {
+    if (!x || !y || !c->stream) return DMRG_EINVAL;
+    // the prepared tables were written on the context's stream
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) throw std::runtime_error(std::string("cuda stream: ") + cudaGetErrorString(e));
+    c->eng->matvec_noalloc(site, x, y, (dmrg::Stream)stream);
+    return DMRG_OK;
+  });
+}
+
 int dmrg_heff_diag(dmrg_ctx* c, int site, double* d, uintptr_t stream) {
   return guard(c, [&] {
     if (!d) return DMRG_EINVAL;

@@ -132,4 +132,12 @@ struct ScatterJob {
 };
 void scatter_batched(const std::vector<ScatterJob>& jobs, Stream s);
 
+// ---- allocation-free matvec: runs prepared matvec tables with the scratch in a
+// fixed device array (capacity in doubles) and x / y redirected to caller buffers ----
+int64_t noalloc_scratch_capacity();
+void noalloc_matvec_run(const GemmPlan* p1, const CombPlan* pc, const GemmPlan* p2,
+                        const double* xin, const double* yout, int64_t n, const double* Z,
+                        int64_t zsize, const double* W, int64_t wsize, const double* x,
+                        double* y, Stream s);
+
 }  // namespace dmrg

@@ -1045,6 +1045,16 @@ void Engine::matvec(int i, const double* x, double* y) {
   run_matvec(p, x, y);
 }
 
+void Engine::matvec_noalloc(int i, const double* x, double* y, Stream s) {
+  if (!cached_ || cached_site_ != i)
+    throw std::invalid_argument(
+        "no prepared matvec for this site: call dmrg_heff_matvec (or dmrg_davidson) at this site "
+        "first, outside the region where allocation is not allowed");
+  MatvecPlan* p = cached_;
+  noalloc_matvec_run(p->p1, p->pc, p->p2, p->xin, p->yout, p->n, p->Z, p->zsize, p->W, p->wsize,
+                     x, y, s);
+}
+
 void Engine::diag(int i, double* d) {
   check_ready();
   if (i < 0 || i > L_ - 2) throw std::out_of_range("site out of range");

@@ -95,6 +95,9 @@ class Engine {
   void tt_to_x(int i, double* x_dev);
   void matvec(int i, const double* x_dev, double* y_dev);
   void diag(int i, double* d_dev);
+  // y = H_eff x with the prepared tables of site i and the library's fixed scratch array;
+  // allocates nothing (throws invalid_argument if no table is prepared for i)
+  void matvec_noalloc(int i, const double* x_dev, double* y_dev, Stream s);
   double davidson(int i, double* x_dev, int* iters, bool* converged);
   double truncate(int i, int dir, int D, const double* x_dev, double noise);
   double solve(double* e_last);

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <mutex>
 #include <stdexcept>
 #include <string>
 
@@ -785,6 +786,180 @@ void scatter_batched(const std::vector<ScatterJob>& jobs, Stream s) {
   }
   ck(cudaGetLastError(), "scatter");
   dev_free(d, s);
+}
+
+// ------------------------------------------------------------------ allocation-free matvec
+//
+// For callers that cannot allocate device memory at the time of the call (inside a
+// region where cudaMalloc is not allowed, or on a budget that forbids growth): the
+// matvec's scratch (the right-operator products Z and the weighted sums W) is placed in
+// this fixed array instead of the context's own buffers.  The array exists once per
+// device that loads the library and stays allocated until the process exits.
+
+namespace {
+
+constexpr int64_t kNoAllocScratchDoubles = (int64_t)8 << 20;  // 64 MiB
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
+
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[64] = {nullptr};  // device address of the array, per device ordinal
+
+struct Remap {
+  const char* lo[4];
+  const char* hi[4];
+  char* to[4];
+};
+
+__device__ __forceinline__ const double* remap_ptr(const double* p, const Remap& m) {
+  const char* c = (const char*)p;
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    if (c >= m.lo[k] && c < m.hi[k]) return (const double*)(m.to[k] + (c - m.lo[k]));
+  return p;
+}
+
+// k_grouped_gemm with every operand / output address passed through the remap
+__global__ void __launch_bounds__(256) k_grouped_gemm_ra(const GemmTask* __restrict__ tasks,
+                                                        const GemmGroup* __restrict__ groups,
+                                                        int ngroups, Remap rm) {
+  __shared__ double As[BK][BM + 1];
+  __shared__ double Bs[BK][BN + 1];
+  const int tile = blockIdx.x;
+  int lo = 0, hi = ngroups - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (groups[mid].tile_begin <= tile) lo = mid; else hi = mid - 1;
+  }
+  const GemmGroup g = groups[lo];
+  double* Cp = (double*)remap_ptr(g.C, rm);
+  const int local = tile - g.tile_begin;
+  const int tn = (g.n + BN - 1) / BN;
+  const int row0 = (local / tn) * BM, col0 = (local % tn) * BN;
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+  for (int t = g.task_begin; t < g.task_end; ++t) {
+    const GemmTask T = tasks[t];
+    const double* Bp = remap_ptr(T.B, rm);
+    if (T.A == nullptr) {
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          int r = row0 + ty + 16 * i, c = col0 + tx + 16 * j;
+          if (r < g.m && c < g.n)
+            acc[i][j] += T.alpha * (T.transB ? Bp[(size_t)c * T.ldb + r] : Bp[(size_t)r * T.ldb + c]);
+        }
+      continue;
+    }
+    const double* Ap = remap_ptr(T.A, rm);
+    for (int k0 = 0; k0 < T.k; k0 += BK) {
+      for (int e = tid; e < BM * BK; e += 256) {
+        int r, kk;
+        double v = 0.0;
+        if (T.transA) { kk = e / BM; r = e % BM; } else { r = e / BK; kk = e % BK; }
+        int gr = row0 + r, gk = k0 + kk;
+        if (gr < g.m && gk < T.k)
+          v = T.transA ? Ap[(size_t)gk * T.lda + gr] : Ap[(size_t)gr * T.lda + gk];
+        As[kk][r] = v * T.alpha;
+      }
+      for (int e = tid; e < BK * BN; e += 256) {
+        int c, kk;
+        double v = 0.0;
+        if (T.transB) { c = e / BK; kk = e % BK; } else { kk = e / BN; c = e % BN; }
+        int gc = col0 + c, gk = k0 + kk;
+        if (gc < g.n && gk < T.k)
+          v = T.transB ? Bp[(size_t)gc * T.ldb + gk] : Bp[(size_t)gk * T.ldb + gc];
+        Bs[kk][c] = v;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < BK; ++kk) {
+        double a0 = As[kk][ty], a1 = As[kk][ty + 16];
+        double b0 = Bs[kk][tx], b1 = Bs[kk][tx + 16];
+        acc[0][0] = fma(a0, b0, acc[0][0]);
+        acc[0][1] = fma(a0, b1, acc[0][1]);
+        acc[1][0] = fma(a1, b0, acc[1][0]);
+        acc[1][1] = fma(a1, b1, acc[1][1]);
+      }
+      __syncthreads();
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      int r = row0 + ty + 16 * i, c = col0 + tx + 16 * j;
+      if (r < g.m && c < g.n) Cp[(size_t)r * g.ldc + c] += acc[i][j];
+    }
+}
+
+// k_combine with remapped addresses
+__global__ void k_combine_ra(const CombSrc* __restrict__ src, const CombDst* __restrict__ dst, Remap rm) {
+  const CombDst d = dst[blockIdx.x];
+  double* dp = (double*)remap_ptr(d.dst, rm);
+  const int64_t n = (int64_t)d.rows * d.cols;
+  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+    int r = (int)(e / d.cols), c = (int)(e % d.cols);
+    double v = d.accumulate ? dp[(size_t)r * d.ld + c] : 0.0;
+    for (int s = d.src_begin; s < d.src_end; ++s)
+      v += src[s].alpha * remap_ptr(src[s].src, rm)[(size_t)r * src[s].ld + c];
+    dp[(size_t)r * d.ld + c] = v;
+  }
+}
+
+// Device address of the static array on the current device (looked up once per device).
+double* noalloc_scratch(int* err) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= 64) { *err = 1; return nullptr; }
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    double* p = nullptr;
+    e = cudaGetSymbolAddress((void**)&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) { *err = 2; return nullptr; }
+    g_noalloc_ptr[dev] = p;
+  }
+  *err = 0;
+  return g_noalloc_ptr[dev];
+}
+
+}  // namespace
+
+int64_t noalloc_scratch_capacity() { return kNoAllocScratchDoubles; }
+
+void noalloc_matvec_run(const GemmPlan* p1, const CombPlan* pc, const GemmPlan* p2,
+                        const double* xin, const double* yout, int64_t n, const double* Z,
+                        int64_t zsize, const double* Wb, int64_t wsize, const double* x,
+                        double* y, Stream s) {
+  if (zsize + wsize > kNoAllocScratchDoubles)
+    throw std::invalid_argument("scratch needed exceeds the 64 MiB static maximum of the allocation-free matvec");
+  int err = 0;
+  double* scratch = noalloc_scratch(&err);
+  if (!scratch) throw std::runtime_error("cuda: cudaGetSymbolAddress of the static scratch failed");
+  Remap rm;
+  rm.lo[0] = (const char*)xin;  rm.hi[0] = (const char*)(xin + n);     rm.to[0] = (char*)x;
+  rm.lo[1] = (const char*)yout; rm.hi[1] = (const char*)(yout + n);    rm.to[1] = (char*)y;
+  rm.lo[2] = (const char*)Z;    rm.hi[2] = (const char*)(Z + zsize);   rm.to[2] = (char*)scratch;
+  rm.lo[3] = (const char*)Wb;   rm.hi[3] = (const char*)(Wb + wsize);  rm.to[3] = (char*)(scratch + zsize);
+  // phase 1 accumulates into Z and phase 2 into y: both start at zero; W is overwritten
+  if (zsize) ck(cudaMemsetAsync(scratch, 0, sizeof(double) * zsize, S(s)), "memset scratch");
+  if (n) ck(cudaMemsetAsync(y, 0, sizeof(double) * n, S(s)), "memset y");
+  if (p1 && p1->ntiles) {
+    k_grouped_gemm_ra<<<p1->ntiles, 256, 0, S(s)>>>(p1->tasks, p1->groups, p1->ngroups, rm);
+    ++g_launches;
+  }
+  if (pc && pc->ndst) {
+    for (int off = 0; off < pc->ndst; off += 65535) {
+      int nb = std::min(65535, pc->ndst - off);
+      k_combine_ra<<<nb, 128, 0, S(s)>>>(pc->src, pc->dst + off, rm);
+      ++g_launches;
+    }
+  }
+  if (p2 && p2->ntiles) {
+    k_grouped_gemm_ra<<<p2->ntiles, 256, 0, S(s)>>>(p2->tasks, p2->groups, p2->ngroups, rm);
+    ++g_launches;
+  }
+  ck(cudaGetLastError(), "allocation-free matvec launch");
 }
 
 }  // namespace dmrg
