@@ -60,12 +60,18 @@ typedef struct {
   int64_t k_launches;
   double k_phase1_flops, k_phase2_flops;
   int64_t kernels_launched; /* all kernels this library launched in the process */
+  /* matvecs done on the tensor cores (precision 1), their flops and device time */
+  int64_t tc_matvecs;
+  double tc_flops, tc_phase1_ms, tc_phase2_ms;
 } dmrg_stats_t;
 
 /* Sec. 4.1: L orbitals with irreps orb_irrep[L], N electrons (2 <= N <= 2L, needed by
  * the one-body folding of Eq. 11), spin two_S, target irrep.  precision: 0 = FP64 block
- * products (only value accepted).  *out receives a new context (free with
- * dmrg_destroy).  Errors: DMRG_EINVAL. */
+ * products; 1 = block products on the tensor cores in TF32 with each operand split into
+ * two TF32 parts (three products, FP32 accumulation), used inside Davidson, which then
+ * finishes with FP64 iterations from that vector so that energies are FP64 Rayleigh
+ * quotients.  *out receives a new context (free with dmrg_destroy).  Errors:
+ * DMRG_EINVAL. */
 int dmrg_create(dmrg_ctx** out, int L, int group, const int* orb_irrep, int N, int two_S,
                 int target_irrep, int precision);
 
@@ -80,6 +86,11 @@ int dmrg_set_integrals(dmrg_ctx* ctx, double econst, const double* h, const doub
 int dmrg_set_schedule(dmrg_ctx* ctx, int n, const int* D, const double* e_conv,
                       const int* n_max, const double* noise, double davidson_tol,
                       int davidson_max_iter);
+
+/* Switch the precision mode (0 or 1, as in dmrg_create) of an existing context.
+ * fp64_iters caps the FP64 Davidson iterations that finish each mixed-precision solve
+ * (0 = until the Davidson tolerance or the Davidson cap). */
+int dmrg_set_precision(dmrg_ctx* ctx, int precision, int fp64_iters);
 
 /* Sec. 4.3: new MPS with the first instruction's D spread equally over the sectors of
  * every bond (capped by the FCI dimension) and filled with uniform(-1,1) numbers from

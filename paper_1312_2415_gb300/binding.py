@@ -33,6 +33,8 @@ class Stats(ctypes.Structure):
         ("k_phase1_ms", ctypes.c_double), ("k_phase2_ms", ctypes.c_double),
         ("k_launches", ctypes.c_int64), ("k_phase1_flops", ctypes.c_double),
         ("k_phase2_flops", ctypes.c_double), ("kernels_launched", ctypes.c_int64),
+        ("tc_matvecs", ctypes.c_int64), ("tc_flops", ctypes.c_double),
+        ("tc_phase1_ms", ctypes.c_double), ("tc_phase2_ms", ctypes.c_double),
     ]
 
 
@@ -47,6 +49,7 @@ _SIGS = {
     "dmrg_set_integrals": (ctypes.c_int, [_P, ctypes.c_double, _D, _D]),
     "dmrg_set_schedule": (ctypes.c_int, [_P, ctypes.c_int, _I, _D, _I, _D, ctypes.c_double, ctypes.c_int]),
     "dmrg_init_mps": (ctypes.c_int, [_P, ctypes.c_uint64]),
+    "dmrg_set_precision": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
     "dmrg_get_mps": (ctypes.c_int, [_P, ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
     "dmrg_set_mps": (ctypes.c_int, [_P, ctypes.c_void_p, ctypes.c_size_t]),
     "dmrg_solve": (ctypes.c_int, [_P, _D, _D]),
@@ -152,6 +155,9 @@ class Context:
         Za = np.ascontiguousarray(noise, dtype=np.float64)
         self._check(self.lib.dmrg_set_schedule(self.h, n, Da, _dptr(Ea), Na, _dptr(Za),
                                                float(davidson_tol), int(davidson_max_iter)))
+
+    def set_precision(self, precision, fp64_iters=0):
+        self._check(self.lib.dmrg_set_precision(self.h, int(precision), int(fp64_iters)))
 
     def init_mps(self, seed):
         self._check(self.lib.dmrg_init_mps(self.h, int(seed)))

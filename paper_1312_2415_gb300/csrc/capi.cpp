@@ -102,12 +102,13 @@ int dmrg_create(dmrg_ctx** out, int L, int group, const int* orb_irrep, int N, i
   if (N < 2 || N > 2 * L || two_S < 0 || two_S > N || two_S > 2 * L - N || ((N - two_S) & 1))
     return DMRG_EINVAL;
   if (target_irrep < 0 || target_irrep >= nir) return DMRG_EINVAL;
-  if (precision != 0) return DMRG_EINVAL;
+  if (precision != 0 && precision != 1) return DMRG_EINVAL;
   dmrg_ctx* c = new (std::nothrow) dmrg_ctx;
   if (!c) return DMRG_ENOMEM;
   try {
     std::vector<int> ir(orb_irrep, orb_irrep + L);
     c->eng = new dmrg::Engine(L, nir, ir, N, two_S, target_irrep, nullptr);
+    c->eng->set_precision(precision, 0);
     c->L = L;
   } catch (...) {
     delete c;
@@ -135,6 +136,14 @@ int dmrg_set_schedule(dmrg_ctx* c, int n, const int* D, const double* e_conv, co
     c->eng->set_schedule(std::vector<int>(D, D + n), std::vector<double>(e_conv, e_conv + n),
                          std::vector<int>(n_max, n_max + n), std::vector<double>(noise, noise + n),
                          davidson_tol, davidson_max_iter);
+    return DMRG_OK;
+  });
+}
+
+int dmrg_set_precision(dmrg_ctx* c, int precision, int fp64_iters) {
+  return guard(c, [&] {
+    if ((precision != 0 && precision != 1) || fp64_iters < 0) return DMRG_EINVAL;
+    c->eng->set_precision(precision, fp64_iters);
     return DMRG_OK;
   });
 }
@@ -351,6 +360,10 @@ int dmrg_stats(dmrg_ctx* c, dmrg_stats_t* out) {
     out->k_phase1_flops = s.k_phase1_flops;
     out->k_phase2_flops = s.k_phase2_flops;
     out->kernels_launched = dmrg::kernel_launches();
+    out->tc_matvecs = s.tc_matvecs;
+    out->tc_flops = s.tc_flops;
+    out->tc_phase1_ms = s.tc_phase1_ms;
+    out->tc_phase2_ms = s.tc_phase2_ms;
     return DMRG_OK;
   });
 }

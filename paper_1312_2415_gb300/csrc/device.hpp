@@ -41,11 +41,16 @@ struct GemmGroup {
   double* C;
   int ldc, m, n;
   int task_begin, task_end;
-  int tile_begin;  // prefix of 32x32 output tiles (filled by the uploader)
+  int tile_begin;     // prefix of 32x32 output tiles (filled by the uploader)
+  int tile_begin_tc;  // prefix of 128x64 tensor-core tiles (filled by the uploader)
 };
 struct GemmPlan;  // device copy of a task/group table
 GemmPlan* gemm_plan_upload(const std::vector<GemmTask>& t, std::vector<GemmGroup>& g, Stream s);
 void gemm_plan_run(const GemmPlan* p, Stream s);
+// the same products on the tensor cores (split TF32, FP32 accumulation); returns after
+// queueing; tc_error_flag() reports a timed-out tensor-core wait (0 = none)
+void gemm_plan_run_tc(const GemmPlan* p, Stream s);
+int tc_error_flag(Stream s);
 void gemm_plan_free(GemmPlan* p, Stream s);
 int64_t gemm_plan_tasks(const GemmPlan* p);
 

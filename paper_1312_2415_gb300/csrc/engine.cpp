@@ -1010,27 +1010,34 @@ Engine::MatvecPlan* Engine::plan_for(int i) {
 // y = H_eff x on the plan's fixed buffers: Z = x D^T (phase 1), y = sum coef C Z (phase 2).
 void Engine::flush_events() {
   if (!ev_pending_) return;
-  st_.k_phase1_ms += event_elapsed_ms(ev_[0], ev_[1]);
-  st_.k_phase2_ms += event_elapsed_ms(ev_[1], ev_[2]);
+  const double a = event_elapsed_ms(ev_[0], ev_[1]), b = event_elapsed_ms(ev_[1], ev_[2]);
+  if (ev_tc_) { st_.tc_phase1_ms += a; st_.tc_phase2_ms += b; }
+  else { st_.k_phase1_ms += a; st_.k_phase2_ms += b; }
   ev_pending_ = false;
 }
 
-void Engine::run_matvec(MatvecPlan* p, const double* x, double* y) {
+void Engine::run_matvec(MatvecPlan* p, const double* x, double* y, bool tc) {
   if (x != p->xin) dev_d2d(p->xin, x, sizeof(double) * p->n, stream_);
   if (p->zsize) dev_zero(p->Z, sizeof(double) * p->zsize, stream_);
   dev_zero(p->yout, sizeof(double) * std::max<int64_t>(p->n, 1), stream_);
   flush_events();
   if (!ev_[0]) for (auto& e : ev_) e = event_create();
   event_record(ev_[0], stream_);
-  gemm_plan_run(p->p1, stream_);
+  if (tc) gemm_plan_run_tc(p->p1, stream_); else gemm_plan_run(p->p1, stream_);
   comb_plan_run(p->pc, stream_);
   event_record(ev_[1], stream_);
-  gemm_plan_run(p->p2, stream_);
+  if (tc) gemm_plan_run_tc(p->p2, stream_); else gemm_plan_run(p->p2, stream_);
   event_record(ev_[2], stream_);
   ev_pending_ = true;
-  st_.k_launches += 1;
-  st_.k_phase1_flops += p->flops1;
-  st_.k_phase2_flops += p->flops2;
+  ev_tc_ = tc;
+  if (tc) {
+    st_.tc_matvecs += 1;
+    st_.tc_flops += p->flops;
+  } else {
+    st_.k_launches += 1;
+    st_.k_phase1_flops += p->flops1;
+    st_.k_phase2_flops += p->flops2;
+  }
   if (y != p->yout) dev_d2d(y, p->yout, sizeof(double) * p->n, stream_);
   st_.matvecs += 1;
   st_.matvec_flops += p->flops;
@@ -1042,7 +1049,8 @@ void Engine::matvec(int i, const double* x, double* y) {
   check_ready();
   if (i < 0 || i > L_ - 2) throw std::out_of_range("site out of range");
   MatvecPlan* p = plan_for(i);
-  run_matvec(p, x, y);
+  run_matvec(p, x, y, precision_ == 1);
+  if (precision_ == 1 && tc_error_flag(stream_)) throw std::runtime_error("cuda: tensor-core wait timed out");
 }
 
 void Engine::matvec_noalloc(int i, const double* x, double* y, Stream s) {
@@ -1109,6 +1117,21 @@ void Engine::tt_to_x(int i, double* x) {
 double Engine::davidson(int i, double* x, int* iters, bool* converged) {
   check_ready();
   MatvecPlan* P = plan_for(i);
+  if (precision_ != 1) return davidson_core(P, x, dav_tol_, dav_max_, false, iters, converged);
+  // mixed precision: Davidson on the tensor-core matvec down to its accuracy, then FP64
+  // Davidson iterations from that vector (the residual and Rayleigh quotient in FP64)
+  int it1 = 0, it2 = 0;
+  bool c1 = false, c2 = false;
+  davidson_core(P, x, std::max(dav_tol_, 1e-6), dav_max_, true, &it1, &c1);
+  if (tc_error_flag(stream_)) throw std::runtime_error("cuda: tensor-core wait timed out");
+  double e = davidson_core(P, x, dav_tol_, refine_iters_ > 0 ? refine_iters_ : dav_max_, false, &it2, &c2);
+  *iters = it1 + it2;
+  *converged = c2;
+  return e;
+}
+
+double Engine::davidson_core(MatvecPlan* P, double* x, double tol, int maxit, bool tc, int* iters,
+                             bool* converged) {
   const int64_t n = P->n;
   const int mmax = std::min<int64_t>(32, std::max<int64_t>(n, 1));
   const int nkeep = std::min(3, mmax - 1 > 0 ? mmax - 1 : 1);
@@ -1134,13 +1157,13 @@ double Engine::davidson(int i, double* x, int* iters, bool* converged) {
   dev_d2d(V, x, sizeof(double) * n, stream_);
   vec_multidot(V, n, 1, V, n, dots, sc, stream_);
   vec_normalize(V, dots, n, stream_);
-  run_matvec(P, V, AV);
+  run_matvec(P, V, AV, tc);
   vec_multidot(V, n, 1, AV, n, G, sc, stream_);
   int m = 1;
   double theta = 0.0;
   bool conv = false;
   int it = 0;
-  for (; it < dav_max_; ++it) {
+  for (; it < maxit; ++it) {
     small_eig(G, mmax, m, std::min(m, nkeep), th, C, stream_);
     // u = V c0 -> x ; r = AV c0 - theta u
     vec_combine(V, n, m, C, 0.0, x, n, stream_);
@@ -1153,7 +1176,7 @@ double Engine::davidson(int i, double* x, int* iters, bool* converged) {
     dev_d2h(hs + 1, dots, sizeof(double), stream_);
     dev_sync(stream_);
     st_.davidson_iters += 1;
-    if (std::sqrt(std::max(hs[1], 0.0)) <= dav_tol_) { conv = true; break; }
+    if (std::sqrt(std::max(hs[1], 0.0)) <= tol) { conv = true; break; }
     if (m >= n) { conv = true; break; }
     vec_precondition(r, P->diag, th, t, n, stream_);
     for (int pass = 0; pass < 2; ++pass) {
@@ -1198,7 +1221,7 @@ double Engine::davidson(int i, double* x, int* iters, bool* converged) {
       m = nkeep;
     }
     dev_d2d(V + (size_t)m * n, t, sizeof(double) * n, stream_);
-    run_matvec(P, V + (size_t)m * n, AV + (size_t)m * n);
+    run_matvec(P, V + (size_t)m * n, AV + (size_t)m * n, tc);
     // row m of the Rayleigh matrix (lower triangle is what small_eig reads)
     vec_multidot(V, n, m + 1, AV + (size_t)m * n, n, G + (size_t)m * mmax, sc, stream_);
     ++m;

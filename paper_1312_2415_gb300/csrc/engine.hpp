@@ -73,6 +73,9 @@ struct Stats {
   double k_phase1_ms = 0.0, k_phase2_ms = 0.0;
   int64_t k_launches = 0;
   double k_phase1_flops = 0.0, k_phase2_flops = 0.0;
+  // tensor-core (mixed precision) matvecs
+  int64_t tc_matvecs = 0;
+  double tc_flops = 0.0, tc_phase1_ms = 0.0, tc_phase2_ms = 0.0;
 };
 
 class Engine {
@@ -112,6 +115,10 @@ class Engine {
   const Stats& stats() { flush_events(); return st_; }
   Stream stream() const { return stream_; }
   void set_stream(Stream s) { stream_ = s; }
+  // 0: FP64 block products; 1: split-TF32 tensor-core products (FP32 accumulation) in
+  // Davidson, finished by FP64 Davidson iterations from the mixed-precision vector
+  void set_precision(int p, int refine_iters) { precision_ = p; refine_iters_ = refine_iters; }
+  int precision() const { return precision_; }
   int L() const { return L_; }
 
  private:
@@ -130,7 +137,9 @@ class Engine {
   MatvecPlan* plan_matvec(int i);
   void free_plan(MatvecPlan* p);
   MatvecPlan* plan_for(int i);
-  void run_matvec(MatvecPlan* p, const double* x, double* y);
+  void run_matvec(MatvecPlan* p, const double* x, double* y, bool tc = false);
+  double davidson_core(MatvecPlan* P, double* x, double tol, int maxit, bool tc, int* iters,
+                       bool* converged);
   void update_left_from(int i, std::vector<CombOp>& comb);
   void update_right_from(int i, std::vector<CombOp>& comb);
   void alloc_site(int k);
@@ -163,6 +172,9 @@ class Engine {
   void* ev_[3] = {nullptr, nullptr, nullptr};
   void flush_events();
   bool ev_pending_ = false;
+  bool ev_tc_ = false;
+  int precision_ = 0;
+  int refine_iters_ = 0;  // FP64 finishing iterations in mixed mode (0: up to the cap)
 };
 
 }  // namespace dmrg

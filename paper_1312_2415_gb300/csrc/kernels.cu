@@ -10,6 +10,7 @@
 #include <string>
 
 #include "device.hpp"
+#include "plans.hpp"
 
 namespace dmrg {
 
@@ -164,22 +165,20 @@ __global__ void __launch_bounds__(256) k_grouped_gemm(const GemmTask* __restrict
 }
 }  // namespace
 
-struct GemmPlan {
-  GemmTask* tasks = nullptr;
-  GemmGroup* groups = nullptr;
-  int ngroups = 0, ntiles = 0;
-  int64_t ntasks = 0;
-};
-
 GemmPlan* gemm_plan_upload(const std::vector<GemmTask>& t, std::vector<GemmGroup>& g, Stream s) {
   GemmPlan* p = new GemmPlan;
-  int tiles = 0;
+  int tiles = 0, tiles_tc = 0;
   for (auto& gr : g) {
     gr.tile_begin = tiles;
-    if (gr.m > 0 && gr.n > 0) tiles += ((gr.m + BM - 1) / BM) * ((gr.n + BN - 1) / BN);
+    gr.tile_begin_tc = tiles_tc;
+    if (gr.m > 0 && gr.n > 0) {
+      tiles += ((gr.m + BM - 1) / BM) * ((gr.n + BN - 1) / BN);
+      tiles_tc += ((gr.m + 127) / 128) * ((gr.n + 63) / 64);
+    }
   }
   p->ngroups = (int)g.size();
   p->ntiles = tiles;
+  p->ntiles_tc = tiles_tc;
   p->ntasks = (int64_t)t.size();
   if (!t.empty()) {
     p->tasks = (GemmTask*)dev_alloc(t.size() * sizeof(GemmTask), s);
@@ -222,12 +221,6 @@ __global__ void k_combine(const CombSrc* __restrict__ src, const CombDst* __rest
   }
 }
 }  // namespace
-
-struct CombPlan {
-  CombSrc* src = nullptr;
-  CombDst* dst = nullptr;
-  int ndst = 0;
-};
 
 CombPlan* comb_plan_upload(const std::vector<CombSrc>& s, const std::vector<CombDst>& d, Stream st) {
   CombPlan* p = new CombPlan;
@@ -275,12 +268,6 @@ __global__ void k_diag(const DiagTerm* __restrict__ t, const DiagOut* __restrict
   }
 }
 }  // namespace
-
-struct DiagPlan {
-  DiagTerm* t = nullptr;
-  DiagOut* o = nullptr;
-  int n = 0;
-};
 
 DiagPlan* diag_plan_upload(const std::vector<DiagTerm>& t, const std::vector<DiagOut>& o, Stream s) {
   DiagPlan* p = new DiagPlan;
@@ -685,42 +672,56 @@ void eig_batched(const std::vector<EigJob>& jobs, Stream s) {
 // ------------------------------------------------------------------ selection
 
 namespace {
-__global__ void k_select(const double* __restrict__ v, int n, const int* __restrict__ gid,
-                         const int* __restrict__ wgt, int D, double zero_rel, int* kept,
-                         double* sums) {
-  __shared__ double red[2][256];
-  __shared__ double vmax_s;
-  const int tid = threadIdx.x;
-  double mx = 0.0;
-  for (int i = tid; i < n; i += 256) mx = fmax(mx, v[i]);
-  red[0][tid] = mx;
-  __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) { if (tid < o) red[0][tid] = fmax(red[0][tid], red[0][tid + o]); __syncthreads(); }
-  if (tid == 0) vmax_s = red[0][0];
-  __syncthreads();
-  const double vmax = vmax_s;
-  double nrm = 0.0, disc = 0.0;
-  for (int i = tid; i < n; i += 256) {
-    double vi = fmax(v[i], 0.0);
-    int rank = 0;
-    for (int j = 0; j < n; ++j) {
-      double vj = fmax(v[j], 0.0);
-      if (vj > vi || (vj == vi && j < i)) ++rank;
+// rank of every value (descending, ties by position) over all n values: one thread per
+// value, many CTAs; keep[i] = rank < D and above the zero threshold
+__global__ void k_select_rank(const double* __restrict__ v, int n, const double* __restrict__ vmax,
+                              int D, double zero_rel, int* __restrict__ keep) {
+  __shared__ double tile[1024];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const double vi = i < n ? fmax(v[i], 0.0) : 0.0;
+  int rank = 0;
+  for (int j0 = 0; j0 < n; j0 += 1024) {
+    for (int t = threadIdx.x; t < 1024; t += blockDim.x) tile[t] = (j0 + t < n) ? fmax(v[j0 + t], 0.0) : -1.0;
+    __syncthreads();
+    const int jn = min(1024, n - j0);
+    for (int t = 0; t < jn; ++t) {
+      const double vj = tile[t];
+      rank += (vj > vi || (vj == vi && j0 + t < i)) ? 1 : 0;
     }
-    double w = (double)wgt[gid[i]] * vi;
-    nrm += w;
-    // lambda > zero_rel * lambda_max  <=>  lambda^2 > zero_rel^2 * lambda_max^2
-    bool keep = rank < D && vi > zero_rel * zero_rel * vmax;
-    if (keep) atomicAdd(&kept[gid[i]], 1); else disc += w;
-  }
-  red[0][tid] = nrm;
-  red[1][tid] = disc;
-  __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
-    if (tid < o) { red[0][tid] += red[0][tid + o]; red[1][tid] += red[1][tid + o]; }
     __syncthreads();
   }
-  if (tid == 0) { sums[0] = red[0][0]; sums[1] = red[1][0]; }
+  if (i < n) keep[i] = (rank < D && vi > zero_rel * zero_rel * (*vmax)) ? 1 : 0;
+}
+
+__global__ void k_select_max(const double* __restrict__ v, int n, double* __restrict__ vmax) {
+  __shared__ double red[256];
+  double mx = 0.0;
+  for (int i = threadIdx.x; i < n; i += 256) mx = fmax(mx, v[i]);
+  red[threadIdx.x] = mx;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) { if (threadIdx.x < o) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + o]); __syncthreads(); }
+  if (threadIdx.x == 0) *vmax = red[0];
+}
+
+// per-group kept counts and the weighted sums (norm^2, discarded) in a fixed order
+__global__ void k_select_sums(const double* __restrict__ v, int n, const int* __restrict__ gid,
+                              const int* __restrict__ wgt, const int* __restrict__ keep, int* kept,
+                              double* sums) {
+  __shared__ double red[2][256];
+  double nrm = 0.0, disc = 0.0;
+  for (int i = threadIdx.x; i < n; i += 256) {
+    const double w = (double)wgt[gid[i]] * fmax(v[i], 0.0);
+    nrm += w;
+    if (keep[i]) atomicAdd(&kept[gid[i]], 1); else disc += w;
+  }
+  red[0][threadIdx.x] = nrm;
+  red[1][threadIdx.x] = disc;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) { red[0][threadIdx.x] += red[0][threadIdx.x + o]; red[1][threadIdx.x] += red[1][threadIdx.x + o]; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) { sums[0] = red[0][0]; sums[1] = red[1][0]; }
 }
 }  // namespace
 
@@ -735,11 +736,18 @@ void select_largest(const double* vals, const std::vector<int>& goff, const std:
   int* d_gid = (int*)dev_alloc(sizeof(int) * (n + 1), s);
   int* d_w = (int*)dev_alloc(sizeof(int) * (G + 1), s);
   int* d_k = (int*)dev_alloc(sizeof(int) * (G + 1), s);
-  double* d_s = (double*)dev_alloc(sizeof(double) * 2, s);
+  int* d_keep = (int*)dev_alloc(sizeof(int) * (n + 1), s);
+  double* d_s = (double*)dev_alloc(sizeof(double) * 3, s);
   dev_h2d(d_gid, gid.data(), sizeof(int) * n, s);
   dev_h2d(d_w, wgt.data(), sizeof(int) * G, s);
   dev_zero(d_k, sizeof(int) * (G + 1), s);
-  k_select<<<1, 256, 0, S(s)>>>(vals, n, d_gid, d_w, D, zero_rel, d_k, d_s);
+  k_select_max<<<1, 256, 0, S(s)>>>(vals, n, d_s + 2);
+  ++g_launches;
+  if (n > 0) {
+    k_select_rank<<<(n + 255) / 256, 256, 0, S(s)>>>(vals, n, d_s + 2, D, zero_rel, d_keep);
+    ++g_launches;
+  }
+  k_select_sums<<<1, 256, 0, S(s)>>>(vals, n, d_gid, d_w, d_keep, d_k, d_s);
   ++g_launches;
   ck(cudaGetLastError(), "select");
   kept.assign(G, 0);
@@ -752,6 +760,7 @@ void select_largest(const double* vals, const std::vector<int>& goff, const std:
   dev_free(d_gid, s);
   dev_free(d_w, s);
   dev_free(d_k, s);
+  dev_free(d_keep, s);
   dev_free(d_s, s);
 }
 
