@@ -42,15 +42,10 @@ struct GemmGroup {
   int ldc, m, n;
   int task_begin, task_end;
   int tile_begin;     // prefix of 32x32 output tiles (filled by the uploader)
-  int tile_begin_tc;  // prefix of 128x64 tensor-core tiles (filled by the uploader)
 };
 struct GemmPlan;  // device copy of a task/group table
 GemmPlan* gemm_plan_upload(const std::vector<GemmTask>& t, std::vector<GemmGroup>& g, Stream s);
 void gemm_plan_run(const GemmPlan* p, Stream s);
-// the same products on the tensor cores (split TF32, FP32 accumulation); returns after
-// queueing; tc_error_flag() reports a timed-out tensor-core wait (0 = none)
-void gemm_plan_run_tc(const GemmPlan* p, Stream s);
-int tc_error_flag(Stream s);
 void gemm_plan_free(GemmPlan* p, Stream s);
 int64_t gemm_plan_tasks(const GemmPlan* p);
 
@@ -136,6 +131,56 @@ struct ScatterJob {
   double a;
 };
 void scatter_batched(const std::vector<ScatterJob>& jobs, Stream s);
+
+// ---- mixed-precision matvec: FP32 data, split-TF32 products on the tensor cores with
+// FP32 accumulation (kernels_tc.cu).  Phase 1 writes Zt = (stack_c D^T)^T column-major for
+// every right-operator block D (several blocks side by side in one MMA tile, the stack
+// tile reused); phase 2 forms W^T = sum coef Zt while staging and accumulates
+// y += C W over a task list (y FP64, added with atomics).  Every FP32 matrix here has a
+// row stride that is a multiple of 4 and a 16-byte aligned first row, with zeros in the
+// padding, so that rows are read as float4. ----
+struct Tc1Entry {   // one right-operator block, or a piece of at most 128 of its rows
+  const float* D;   // first row of the piece: ncols rows of K elements, row stride ldd
+  float* zt;        // first column of its Zt: ncols columns of the stack's rows, stride ldz
+  int ldd, ldz, ncols;
+  int start;        // first column of the piece inside its pack (multiple of 8)
+  float alpha;      // scalar of the operator
+};
+struct Tc1Pack { int e_begin, e_end, n; };  // n = padded columns of the pack (<= 128)
+struct Tc1Unit {
+  const float* A;   // stack rows row0 .. row0 + rows - 1 (rows <= 128), row stride lda
+  int lda, rows, K, row0;
+  int p_begin, p_end;
+};
+struct Tc2Src { const float* z; int ldz; float coef; };  // W^T(j, k) += coef z[j ldz + k]
+struct Tc2Task {
+  const float* C;   // left-operator block (m x K, row stride ldc); nullptr = identity
+  int ldc, K;
+  float alpha;
+  int s_begin, s_end;
+};
+struct Tc2Unit {
+  double* y;        // output block (row stride ldy); tile rows row0 .., columns col0 ..
+  int ldy, m, n, row0, col0;
+  int t_begin, t_end;
+};
+// one x block (rows x cols at src in the FP64 vector) and its places in the FP32 stack
+// (row-major, stride ld) and in the transposed stack (column-major, stride ldt)
+struct TcXBlock { int64_t src, dst, dstt; int rows, cols, ld, ldt; };
+// one FP64 block converted to FP32 with row stride ld (a multiple of 4)
+struct TcMirror { const double* src; float* dst; int rows, cols, ld; };
+struct TcPlan;
+TcPlan* tc_plan_upload(const std::vector<Tc1Entry>& e, const std::vector<Tc1Pack>& p,
+                       const std::vector<Tc1Unit>& u1, const std::vector<Tc2Src>& s,
+                       const std::vector<Tc2Task>& t, const std::vector<Tc2Unit>& u2,
+                       const std::vector<TcXBlock>& xb, float* x32, float* x32t, int64_t n,
+                       Stream st);
+// y = H x: x (FP64) -> the FP32 stacks, phase 1, phase 2 (y zeroed first); ev (3 events or
+// nullptr) are recorded before phase 1, between the phases and after
+void tc_plan_run(const TcPlan* p, const double* x, double* y, void* const* ev, Stream s);
+void tc_plan_free(TcPlan* p, Stream s);
+int tc_error_flag(Stream s);  // 1 if a tensor-core kernel timed out on a wait
+void tc_mirror(const std::vector<TcMirror>& m, Stream s);  // blocks -> FP32, padding untouched
 
 // ---- allocation-free matvec: runs prepared matvec tables with the scratch in a
 // fixed device array (capacity in doubles) and x / y redirected to caller buffers ----

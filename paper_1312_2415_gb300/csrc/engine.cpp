@@ -425,11 +425,12 @@ namespace dmrg {
 namespace {
 
 // Materialise combined operators with more than one source: dst = sum scalar * src.
-double* materialise(std::vector<CombOp>& comb, const OpStore& src, Stream st) {
+double* materialise(std::vector<CombOp>& comb, const OpStore& src, Stream st, int64_t* size) {
   int64_t total = 0;
   for (auto& c : comb)
     if (c.sources.size() > 1)
       for (auto& b : src.blocks[c.sources[0].first]) total += (int64_t)b.rows * b.cols;
+  *size = total;
   if (total == 0) return nullptr;
   double* buf = (double*)dev_alloc(sizeof(double) * total, st);
   std::vector<CombSrc> cs;
@@ -471,7 +472,7 @@ double* materialise(std::vector<CombOp>& comb, const OpStore& src, Stream st) {
 }  // namespace
 
 // Left combined operators for the targets at bond i+1: C_{b,P} = sum_a s_a L_a(bond i).
-void Engine::group_left(int i, std::vector<CombOp>& out, double** scratch) {
+void Engine::group_left(int i, std::vector<CombOp>& out, double** scratch, int64_t* scratch_n) {
   const OpStore& E = lenv_[i];
   std::map<std::pair<int, int>, int> idx;
   out.clear();
@@ -498,11 +499,11 @@ void Engine::group_left(int i, std::vector<CombOp>& out, double** scratch) {
       c.scalar = c.sources[0].second;
       c.identity = c.sources[0].first == id_op;
     }
-  *scratch = materialise(out, E, stream_);
+  *scratch = materialise(out, E, stream_, scratch_n);
 }
 
 // Right combined operators for targets at bond j (site j): D_{a,P} = sum_b s_b R_b(bond j+1).
-void Engine::group_right(int j, std::vector<CombOp>& out, double** scratch) {
+void Engine::group_right(int j, std::vector<CombOp>& out, double** scratch, int64_t* scratch_n) {
   const OpStore& E = renv_[j + 1];
   std::map<std::pair<int, int>, int> idx;
   out.clear();
@@ -530,7 +531,7 @@ void Engine::group_right(int j, std::vector<CombOp>& out, double** scratch) {
       c.scalar = c.sources[0].second;
       c.identity = c.sources[0].first == h_op;  // partner of H is the identity
     }
-  *scratch = materialise(out, E, stream_);
+  *scratch = materialise(out, E, stream_, scratch_n);
 }
 
 // L_b(bond i+1)[jM' <- jM] = sum coef T[i]^T C_{b,P}[jL' <- jL] T[i], T[i] left-normalised.
@@ -680,7 +681,8 @@ void Engine::update_right_from(int j, std::vector<CombOp>& comb) {
 void Engine::build_left(int k) {
   std::vector<CombOp> comb;
   double* scr = nullptr;
-  group_left(k - 1, comb, &scr);
+  int64_t scr_n = 0;
+  group_left(k - 1, comb, &scr, &scr_n);
   update_left_from(k - 1, comb);
   if (scr) dev_free(scr, stream_);
 }
@@ -688,7 +690,8 @@ void Engine::build_left(int k) {
 void Engine::build_right(int k) {
   std::vector<CombOp> comb;
   double* scr = nullptr;
-  group_right(k, comb, &scr);
+  int64_t scr_n = 0;
+  group_right(k, comb, &scr, &scr_n);
   update_right_from(k, comb);
   if (scr) dev_free(scr, stream_);
 }
@@ -704,6 +707,7 @@ struct Engine::MatvecPlan {
   std::vector<CombOp> cl, cr;
   double* scr_l = nullptr;
   double* scr_r = nullptr;
+  int64_t scr_l_n = 0, scr_r_n = 0;
   double* Z = nullptr;
   double* W = nullptr;
   CombPlan* pc = nullptr;
@@ -716,6 +720,19 @@ struct Engine::MatvecPlan {
   double flops = 0.0, flops1 = 0.0, flops2 = 0.0;
   int64_t ntasks = 0;
   int64_t zsize = 0;
+  // host tables kept for the mixed-precision plan (built on first use, then released)
+  struct ZGroup { const double* D; int n, K; double alpha; int c; int64_t off; };
+  struct WSrc { int zg, xb; double coef; };  // source x block xb; zg < 0: D is the identity
+  struct WItem { int gl, cbi, rows, cols, src_begin, src_end; };
+  std::vector<ZGroup> zg;
+  std::vector<WSrc> wsrc;
+  std::vector<WItem> witems;
+  std::vector<std::vector<int>> w_by_x;
+  std::vector<int64_t> tall_off, tall_rows;
+  std::vector<int> sec_dim;
+  TcPlan* tc = nullptr;
+  float* tc_zt = nullptr;
+  float* tc_mem[3] = {nullptr, nullptr, nullptr};  // x32, x32t, operator mirrors
 };
 
 namespace {
@@ -739,8 +756,8 @@ Engine::MatvecPlan* Engine::plan_matvec(int i) {
   MatvecPlan* P = new MatvecPlan;
   P->site = i;
   P->X = x_layout(i, &P->n);
-  group_left(i, P->cl, &P->scr_l);
-  group_right(i + 1, P->cr, &P->scr_r);
+  group_left(i, P->cl, &P->scr_l, &P->scr_l_n);
+  group_right(i + 1, P->cr, &P->scr_r, &P->scr_r_n);
   const Bond& bl = bonds_[i];
   const Bond& br = bonds_[i + 2];
   const OpSet& mid = opsets_[i + 1];
@@ -771,7 +788,7 @@ Engine::MatvecPlan* Engine::plan_matvec(int i) {
     for (int bi = 0; bi < (int)P->cr[g].blocks->size(); ++bi) dby[g][(*P->cr[g].blocks)[bi].c].push_back(bi);
   }
   // phase 1: Z(gr, D block) = stack(r) . D^T ; identity D reads x directly
-  struct ZRef { int64_t off; int ld; };
+  struct ZRef { int64_t off; int ld; int zg; };
   std::unordered_map<int64_t, ZRef> zmap;
   std::vector<GemmTask> t1;
   std::vector<GemmGroup> g1;
@@ -786,10 +803,11 @@ Engine::MatvecPlan* Engine::plan_matvec(int i) {
     if (it != zmap.end()) return it->second;
     ZRef z;
     if (D.identity) {
-      z = {-1 - tall_off[db.c], br.dim[db.c]};  // negative: offset into xin
+      z = {-1 - tall_off[db.c], br.dim[db.c], -1 - db.c};  // negative: offset into xin
     } else {
       const int64_t rows = tall_rows[db.c];
-      z = {zsize, db.rows};
+      z = {zsize, db.rows, (int)g1.size()};
+      P->zg.push_back({D.data + db.off, db.rows, db.cols, D.scalar, db.c, zsize});
       t1.push_back({nullptr, D.data + db.off, db.cols, db.cols, db.cols, 0, 1, D.scalar});
       g1.push_back({nullptr, db.rows, (int)rows, db.rows, (int)t1.size() - 1, (int)t1.size(), 0});
       g1off.push_back(tall_off[db.c]);
@@ -820,7 +838,7 @@ Engine::MatvecPlan* Engine::plan_matvec(int i) {
   // W(gl, C block, X') = sum coef * Z rows of X ; phase 2: y_X' += C_blk W
   struct WItem { int gl, cbi, xp; int64_t off; int rows, cols; int src_begin, src_end; };
   std::vector<WItem> ws;
-  struct WS { int64_t zoff; int ld; double coef; };  // zoff < 0: into xin (-1 - off)
+  struct WS { int64_t zoff; int ld; double coef; int zg, xb; };  // zoff < 0: into xin (-1 - off)
   std::vector<WS> wsrc;
   std::vector<std::vector<DiagTerm>> dout(P->X.size());
   std::vector<std::vector<int>> w_by_x(P->X.size());
@@ -887,7 +905,7 @@ Engine::MatvecPlan* Engine::plan_matvec(int i) {
                     int64_t zoff = z.off >= 0 ? z.off + (int64_t)X.trow * z.ld
                                               : z.off - (int64_t)X.trow * z.ld;
                     // identity right operator: Z is x itself, its alias scalar goes here
-                    acc[xp].push_back({zoff, z.ld, D.identity ? coef * D.scalar : coef});
+                    acc[xp].push_back({zoff, z.ld, D.identity ? coef * D.scalar : coef, z.zg, x});
                     if (xp == x && cb.r == cb.c && db.r == db.c)
                       dout[x].push_back({C.data + cb.off, D.data + db.off, cb.cols, db.cols,
                                          coef * C.scalar * D.scalar});
@@ -900,8 +918,12 @@ Engine::MatvecPlan* Engine::plan_matvec(int i) {
         for (auto& kv : acc) {
           const XBlock& Xp = P->X[kv.first];
           WItem w{gl, cbi, (int)kv.first, wsize, cb.cols, Xp.cols, (int)wsrc.size(), 0};
-          for (auto& q : kv.second) wsrc.push_back(q);
+          for (auto& q : kv.second) {
+            wsrc.push_back(q);
+            P->wsrc.push_back({q.zg, q.xb, q.coef});
+          }
           w.src_end = (int)wsrc.size();
+          P->witems.push_back({gl, cbi, w.rows, w.cols, w.src_begin, w.src_end});
           wsize += (int64_t)cb.cols * Xp.cols;
           w_by_x[kv.first].push_back((int)ws.size());
           ws.push_back(w);
@@ -965,6 +987,10 @@ Engine::MatvecPlan* Engine::plan_matvec(int i) {
     dt.insert(dt.end(), dout[x].begin(), dout[x].end());
     dov.push_back({P->diag + X.off, X.rows, X.cols, d0, (int)dt.size()});
   }
+  P->w_by_x = std::move(w_by_x);
+  P->tall_off = std::move(tall_off);
+  P->tall_rows = std::move(tall_rows);
+  P->sec_dim = br.dim;
   P->p1 = gemm_plan_upload(t1, g1, stream_);
   P->pc = comb_plan_upload(cs, cd, stream_);
   P->p2 = gemm_plan_upload(t2, g2, stream_);
@@ -986,6 +1012,10 @@ namespace dmrg {
 
 void Engine::free_plan(MatvecPlan* p) {
   if (!p) return;
+  tc_plan_free(p->tc, stream_);
+  for (float* m : p->tc_mem)
+    if (m) dev_free(m, stream_);
+  if (p->tc_zt) dev_free(p->tc_zt, stream_);
   gemm_plan_free(p->p1, stream_);
   gemm_plan_free(p->p2, stream_);
   comb_plan_free(p->pc, stream_);
@@ -1016,28 +1046,186 @@ void Engine::flush_events() {
   ev_pending_ = false;
 }
 
+// Tables of the mixed-precision matvec (kernels_tc.cu) from the planner's host tables.
+// FP32 layouts: every operator block the matvec reads is mirrored with its row stride
+// rounded up to 4; the stack of right sector c keeps its x blocks at row offsets rounded
+// up to 4 (zero rows between them) with row stride d_c rounded up to 4, and its
+// transpose and every Zt use the padded stack height as stride, so that all rows start
+// on 16 bytes.  Phase 1 runs packs of right-operator blocks per right sector and 128-row
+// stack tile, phase 2 runs task lists per output tile.
+void Engine::build_tc(MatvecPlan* P) {
+  Timer tm;
+  auto r4 = [](int64_t v) { return (v + 3) & ~(int64_t)3; };
+  // padded stacks
+  const int nr = (int)P->sec_dim.size();
+  std::vector<int64_t> rpad(nr, 0), xoff(nr, 0), xtoff(nr, 0);
+  std::vector<int64_t> trow_pad(P->X.size(), 0);
+  for (int x = 0; x < (int)P->X.size(); ++x) {  // blocks of a stack are in row order
+    const XBlock& X = P->X[x];
+    trow_pad[x] = rpad[X.r];
+    rpad[X.r] += r4(X.rows);
+  }
+  int64_t nx = 0, nxt = 0;
+  for (int c = 0; c < nr; ++c) {
+    xoff[c] = nx;
+    xtoff[c] = nxt;
+    nx += rpad[c] * r4(P->sec_dim[c]);
+    nxt += rpad[c] * P->sec_dim[c];
+    nxt = r4(nxt);
+  }
+  float* x32 = (float*)dev_alloc(sizeof(float) * std::max<int64_t>(nx, 4), stream_);
+  P->tc_mem[0] = x32;
+  float* x32t = (float*)dev_alloc(sizeof(float) * std::max<int64_t>(nxt, 4), stream_);
+  P->tc_mem[1] = x32t;
+  dev_zero(x32, sizeof(float) * std::max<int64_t>(nx, 4), stream_);
+  dev_zero(x32t, sizeof(float) * std::max<int64_t>(nxt, 4), stream_);
+  std::vector<TcXBlock> xbt;
+  xbt.reserve(P->X.size());
+  for (int x = 0; x < (int)P->X.size(); ++x) {
+    const XBlock& X = P->X[x];
+    const int ld = (int)r4(P->sec_dim[X.r]);
+    xbt.push_back({X.off, xoff[X.r] + trow_pad[x] * ld, xtoff[X.r] + trow_pad[x], X.rows, X.cols, ld,
+                   (int)rpad[X.r]});
+  }
+  // operator mirrors: every block phase 1 or phase 2 reads
+  std::unordered_map<const double*, int64_t> moff;
+  std::vector<TcMirror> mir;
+  int64_t nm = 0;
+  auto want = [&](const double* p, int rows, int cols) {
+    if (moff.emplace(p, nm).second) {
+      mir.push_back({p, nullptr, rows, cols, (int)r4(cols)});
+      nm += (int64_t)rows * r4(cols);
+    }
+  };
+  for (const auto& Zg : P->zg) want(Zg.D, Zg.n, Zg.K);
+  for (const auto& w : P->witems) {
+    const CombOp& C = P->cl[w.gl];
+    if (C.identity) continue;
+    const BlockRef& cb = (*C.blocks)[w.cbi];
+    want(C.data + cb.off, cb.rows, cb.cols);
+  }
+  float* m32 = (float*)dev_alloc(sizeof(float) * std::max<int64_t>(nm, 4), stream_);
+  P->tc_mem[2] = m32;
+  dev_zero(m32, sizeof(float) * std::max<int64_t>(nm, 4), stream_);
+  for (auto& m : mir) m.dst = m32 + moff[m.src];
+  tc_mirror(mir, stream_);
+  auto f32 = [&](const double* p) -> const float* { return m32 + moff.at(p); };
+  // Zt: one column-major block per phase-1 group, stride = padded stack height
+  std::vector<int64_t> zoff(P->zg.size());
+  int64_t nz = 0;
+  for (size_t g = 0; g < P->zg.size(); ++g) {
+    zoff[g] = nz;
+    nz += r4((int64_t)P->zg[g].n * rpad[P->zg[g].c]);
+  }
+  float* zt = (float*)dev_alloc(sizeof(float) * std::max<int64_t>(nz, 4), stream_);
+  P->tc_zt = zt;
+  // phase 1
+  std::vector<std::vector<int>> byc(nr);
+  for (int g = 0; g < (int)P->zg.size(); ++g) byc[P->zg[g].c].push_back(g);
+  std::vector<Tc1Entry> ents;
+  std::vector<Tc1Pack> packs;
+  std::vector<Tc1Unit> u1;
+  constexpr int kPacksPerUnit = 8;
+  for (int c = 0; c < nr; ++c) {
+    if (byc[c].empty()) continue;
+    const int M = (int)rpad[c], K = P->sec_dim[c], lda = (int)r4(K);
+    const int p0 = (int)packs.size();
+    Tc1Pack cur{(int)ents.size(), (int)ents.size(), 0};
+    for (int g : byc[c]) {
+      const auto& Zg = P->zg[g];
+      const float* D32 = f32(Zg.D);
+      for (int n0 = 0; n0 < Zg.n; n0 += 128) {
+        const int nc = std::min(128, Zg.n - n0), pad = (nc + 7) & ~7;
+        if (cur.n + pad > 128 || cur.e_end - cur.e_begin == 16) {
+          packs.push_back(cur);
+          cur = {(int)ents.size(), (int)ents.size(), 0};
+        }
+        ents.push_back({D32 + (int64_t)n0 * lda, zt + zoff[g] + (int64_t)n0 * M, lda, M, nc, cur.n, (float)Zg.alpha});
+        cur.n += pad;
+        cur.e_end = (int)ents.size();
+      }
+    }
+    if (cur.e_end > cur.e_begin) packs.push_back(cur);
+    const int p1 = (int)packs.size();
+    for (int row0 = 0; row0 < M; row0 += 128)
+      for (int pb = p0; pb < p1; pb += kPacksPerUnit)
+        u1.push_back({x32 + xoff[c] + (int64_t)row0 * lda, lda, std::min(128, M - row0), K, row0, pb,
+                      std::min(p1, pb + kPacksPerUnit)});
+  }
+  // phase 2
+  std::vector<Tc2Src> srcs;
+  std::vector<Tc2Task> tasks;
+  std::vector<Tc2Unit> u2;
+  srcs.reserve(P->wsrc.size());
+  tasks.reserve(P->witems.size());
+  constexpr int kTasksPerUnit = 48;
+  for (int x = 0; x < (int)P->X.size(); ++x) {
+    const XBlock& X = P->X[x];
+    const int t0 = (int)tasks.size();
+    for (int wi : P->w_by_x[x]) {
+      const auto& w = P->witems[wi];
+      const CombOp& C = P->cl[w.gl];
+      const BlockRef& cb = (*C.blocks)[w.cbi];
+      Tc2Task t{C.identity ? nullptr : f32(C.data + cb.off), (int)r4(cb.cols), w.rows, (float)C.scalar,
+                (int)srcs.size(), 0};
+      for (int q = w.src_begin; q < w.src_end; ++q) {
+        const auto& src = P->wsrc[q];
+        const int c = P->X[src.xb].r;
+        if (src.zg >= 0) srcs.push_back({zt + zoff[src.zg] + trow_pad[src.xb], (int)rpad[c], (float)src.coef});
+        else srcs.push_back({x32t + xtoff[c] + trow_pad[src.xb], (int)rpad[c], (float)src.coef});
+      }
+      t.s_end = (int)srcs.size();
+      tasks.push_back(t);
+    }
+    const int t1 = (int)tasks.size();
+    if (t1 == t0) continue;
+    for (int row0 = 0; row0 < X.rows; row0 += 128)
+      for (int col0 = 0; col0 < X.cols; col0 += 64)
+        for (int tb = t0; tb < t1; tb += kTasksPerUnit)
+          u2.push_back({P->yout + X.off, X.cols, X.rows, X.cols, row0, col0, tb, std::min(t1, tb + kTasksPerUnit)});
+  }
+  P->tc = tc_plan_upload(ents, packs, u1, srcs, tasks, u2, xbt, x32, x32t, P->n, stream_);
+  // the host tables are not needed any more
+  std::vector<MatvecPlan::ZGroup>().swap(P->zg);
+  std::vector<MatvecPlan::WSrc>().swap(P->wsrc);
+  std::vector<MatvecPlan::WItem>().swap(P->witems);
+  std::vector<std::vector<int>>().swap(P->w_by_x);
+  st_.t_plan_ms += tm.ms();
+}
+
 void Engine::run_matvec(MatvecPlan* p, const double* x, double* y, bool tc) {
+  if (tc) {
+    flush_events();
+    if (!ev_[0]) for (auto& e : ev_) e = event_create();
+    if (!p->tc) build_tc(p);
+    tc_plan_run(p->tc, x, p->yout, ev_, stream_);
+    ev_pending_ = true;
+    ev_tc_ = true;
+    if (y != p->yout) dev_d2d(y, p->yout, sizeof(double) * p->n, stream_);
+    st_.tc_matvecs += 1;
+    st_.tc_flops += p->flops;
+    st_.matvecs += 1;
+    st_.matvec_flops += p->flops;
+    st_.last_matvec_flops = p->flops;
+    st_.last_matvec_tasks = p->ntasks;
+    return;
+  }
   if (x != p->xin) dev_d2d(p->xin, x, sizeof(double) * p->n, stream_);
   if (p->zsize) dev_zero(p->Z, sizeof(double) * p->zsize, stream_);
   dev_zero(p->yout, sizeof(double) * std::max<int64_t>(p->n, 1), stream_);
   flush_events();
   if (!ev_[0]) for (auto& e : ev_) e = event_create();
   event_record(ev_[0], stream_);
-  if (tc) gemm_plan_run_tc(p->p1, stream_); else gemm_plan_run(p->p1, stream_);
+  gemm_plan_run(p->p1, stream_);
   comb_plan_run(p->pc, stream_);
   event_record(ev_[1], stream_);
-  if (tc) gemm_plan_run_tc(p->p2, stream_); else gemm_plan_run(p->p2, stream_);
+  gemm_plan_run(p->p2, stream_);
   event_record(ev_[2], stream_);
   ev_pending_ = true;
-  ev_tc_ = tc;
-  if (tc) {
-    st_.tc_matvecs += 1;
-    st_.tc_flops += p->flops;
-  } else {
-    st_.k_launches += 1;
-    st_.k_phase1_flops += p->flops1;
-    st_.k_phase2_flops += p->flops2;
-  }
+  ev_tc_ = false;
+  st_.k_launches += 1;
+  st_.k_phase1_flops += p->flops1;
+  st_.k_phase2_flops += p->flops2;
   if (y != p->yout) dev_d2d(y, p->yout, sizeof(double) * p->n, stream_);
   st_.matvecs += 1;
   st_.matvec_flops += p->flops;
@@ -1178,6 +1366,7 @@ double Engine::davidson_core(MatvecPlan* P, double* x, double tol, int maxit, bo
     st_.davidson_iters += 1;
     if (std::sqrt(std::max(hs[1], 0.0)) <= tol) { conv = true; break; }
     if (m >= n) { conv = true; break; }
+    if (it + 1 >= maxit) break;  // no use expanding the subspace on the last iteration
     vec_precondition(r, P->diag, th, t, n, stream_);
     for (int pass = 0; pass < 2; ++pass) {
       // t -= V (V^T t)

@@ -132,8 +132,9 @@ class Engine {
   void build_right(int k);
   void invalidate_envs_from_site(int k);
   std::vector<XBlock> x_layout(int i, int64_t* n) const;
-  void group_left(int i, std::vector<CombOp>& out, double** scratch);
-  void group_right(int i, std::vector<CombOp>& out, double** scratch);
+  void group_left(int i, std::vector<CombOp>& out, double** scratch, int64_t* scratch_n);
+  void group_right(int i, std::vector<CombOp>& out, double** scratch, int64_t* scratch_n);
+  void build_tc(MatvecPlan* p);
   MatvecPlan* plan_matvec(int i);
   void free_plan(MatvecPlan* p);
   MatvecPlan* plan_for(int i);

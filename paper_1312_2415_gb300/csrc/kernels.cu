@@ -57,6 +57,7 @@ void dev_zero(void* p, size_t b, Stream s) {
 }
 void dev_sync(Stream s) { ck(cudaStreamSynchronize(S(s)), "stream sync"); }
 int64_t kernel_launches() { return g_launches; }
+void note_launches(int64_t k) { g_launches += k; }
 int dev_check(const char** msg) {
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) return 0;
@@ -167,18 +168,13 @@ __global__ void __launch_bounds__(256) k_grouped_gemm(const GemmTask* __restrict
 
 GemmPlan* gemm_plan_upload(const std::vector<GemmTask>& t, std::vector<GemmGroup>& g, Stream s) {
   GemmPlan* p = new GemmPlan;
-  int tiles = 0, tiles_tc = 0;
+  int tiles = 0;
   for (auto& gr : g) {
     gr.tile_begin = tiles;
-    gr.tile_begin_tc = tiles_tc;
-    if (gr.m > 0 && gr.n > 0) {
-      tiles += ((gr.m + BM - 1) / BM) * ((gr.n + BN - 1) / BN);
-      tiles_tc += ((gr.m + 127) / 128) * ((gr.n + 63) / 64);
-    }
+    if (gr.m > 0 && gr.n > 0) tiles += ((gr.m + BM - 1) / BM) * ((gr.n + BN - 1) / BN);
   }
   p->ngroups = (int)g.size();
   p->ntiles = tiles;
-  p->ntiles_tc = tiles_tc;
   p->ntasks = (int64_t)t.size();
   if (!t.empty()) {
     p->tasks = (GemmTask*)dev_alloc(t.size() * sizeof(GemmTask), s);

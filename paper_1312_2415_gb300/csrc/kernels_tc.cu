@@ -1,21 +1,32 @@
-// Tensor-core (tcgen05, sm_103a) grouped block GEMM for the mixed-precision matvec.
+// Mixed-precision H_eff matvec on the 5th-generation tensor cores (tcgen05, sm_103a).
 //
-// C_g += sum_t alpha_t op(A_t) op(B_t) as in k_grouped_gemm, with every product done on
-// the 5th-generation tensor cores in TF32 with FP32 accumulation, each operand split
-// into a TF32 head and a TF32 tail (a = a_hi + a_lo) and the three leading products
-// a_hi b_hi + a_hi b_lo + a_lo b_hi accumulated (about 2^-21 relative per product).
-// One CTA (4 warps) owns a 128 x 64 tile of one output block (the MMA N is the block's
-// width rounded up to 16, at most 64); its FP32 accumulator lives in tensor memory for
-// the whole task list of the block and is added to the FP64 output once.  Two staging
-// buffers alternate, so the next K chunk is staged while the tensor core consumes the
-// previous one.  Operands are read from FP64 global memory (the coefficient alpha
-// is applied while staging), rounded / split, and written to shared memory in the
-// canonical K-major layout without swizzle: 8-row x 16-byte core matrices, core
-// matrices adjacent in K 128 bytes apart (LBO), adjacent in M/N 1024 bytes apart (SBO)
-// for a 32-wide K chunk.  The operand blocks are small and irregular (reduced symmetry
-// blocks of tens to a few hundred rows), so they are staged by the threads rather than
-// by TMA tensor maps.  Every wait on the MMA-completion barrier is bounded; on timeout
-// the CTA records an error, frees its tensor memory and returns.
+// Data are FP32 (operators mirrored once per two-site problem, x converted per matvec);
+// every block product runs on the tensor cores in TF32 with each operand split into a
+// TF32 head and tail (v = hi + lo) and the three leading products hi*hi + hi*lo + lo*hi
+// accumulated in FP32 in tensor memory (about 2^-21 relative per product, the accuracy
+// of FP32 data).  Operands are staged by the threads into shared memory in the canonical
+// K-major layout without swizzle: core matrices of 8 rows x 16 bytes, 128 bytes apart
+// along K (LBO) and 1024 bytes apart along M/N (SBO) for a 32-column K chunk.  A thread
+// moves one core-matrix row at a time: a float4 from global memory (every FP32 matrix
+// has 16-byte aligned rows padded with zeros), split into two float4 stores.  The
+// blocks are small and irregular (reduced symmetry blocks of a few to a few hundred
+// rows) and are gathered and split while staging, so tensor maps do not apply.
+//
+// Phase 1 (k_tc_phase1): for a right sector c the x blocks with that sector form a stack
+// (rows = sum of their left dimensions, columns = d_c).  Every right-operator block D
+// with column sector c gives Z = stack D^T, written transposed (Zt, column-major) so
+// that phase 2 reads it K-contiguously.  A CTA keeps a 128-row tile of the stack in
+// shared memory and runs through packs of operator blocks placed side by side in the
+// MMA's N dimension (up to 128 columns); two accumulators in tensor memory alternate so
+// that the epilogue of one pack overlaps the products of the next.
+//
+// Phase 2 (k_tc_phase2): for an output block of y and a run of its tasks, each task
+// stages a left-operator block C (or the identity) as A and W^T = sum coef Zt (the
+// complementary-operator sums) as B, and accumulates C W in tensor memory; the tile is
+// added to y (FP64) with atomics, since a block's tasks may be split over several CTAs.
+//
+// Every wait on an MMA-completion barrier is bounded; on timeout the CTA records an
+// error, stops issuing work, frees its tensor memory and returns.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -29,10 +40,9 @@ namespace dmrg {
 
 namespace {
 
-constexpr int TM = 128, TN = 64, TK = 32;
-constexpr int kThreads = 128;
-constexpr uint32_t kTmemCols = 64;
-constexpr long long kSpinLimit = 1ll << 22;  // a few seconds at most
+constexpr int kThreads = 256;               // 8 warps: all stage, warps w and w+4 share TMEM lanes
+constexpr long long kSpinLimit = 1ll << 22; // polls of an mbarrier before giving up (seconds)
+constexpr int kTileF = 128 * 32;            // floats of a 128-row x 32-column operand tile
 
 __device__ int g_tc_error = 0;
 
@@ -46,20 +56,21 @@ __device__ __forceinline__ float tf32_round(float x) {
   return __uint_as_float(r);
 }
 
-// byte offset of element (row, k) inside a K-major no-swizzle tile with TK columns
-__device__ __forceinline__ uint32_t kmajor_off(int row, int k) {
-  return (uint32_t)((row >> 3) * 1024 + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4);
+// float index of element (row, k) in a K-major no-swizzle tile with 32 columns
+__device__ __forceinline__ int kmo(int row, int k) {
+  return (row >> 3) * 256 + (k >> 2) * 32 + (row & 7) * 4 + (k & 3);
 }
 
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
-  // start address >> 4 | LBO (128 B) >> 4 << 16 | SBO (1024 B) >> 4 << 32 | version 1 << 46
+  // start >> 4 | LBO (128 B) >> 4 << 16 | SBO (1024 B) >> 4 << 32 | descriptor version 1 << 46
   return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)(128 >> 4) << 16) |
          ((uint64_t)(1024 >> 4) << 32) | ((uint64_t)1 << 46);
 }
 
-// instruction descriptor: D f32, A/B tf32, both K-major, N = TN, M = TM
-constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TN >> 3) << 17) |
-                            ((uint32_t)(TM >> 4) << 24);
+// instruction descriptor: D f32, A and B tf32, both K-major, M = 128, N = n (multiple of 16)
+__device__ __forceinline__ uint32_t idesc_tf32(int n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
 
 __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc,
                                          uint32_t acc) {
@@ -69,195 +80,685 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, 
       "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
-__device__ __forceinline__ void mma_commit(uint32_t mbar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+// the three split products of one 32-column K chunk (kpad / 8 steps of K = 8)
+__device__ __forceinline__ void mma_chunk(uint32_t tmem, const float* Ah, const float* Al,
+                                          const float* Bh, const float* Bl, int kpad, uint32_t idesc,
+                                          bool first) {
+  const uint32_t ah = smem_u32(Ah), al = smem_u32(Al), bh = smem_u32(Bh), bl = smem_u32(Bl);
+  for (int st = 0; st < kpad / 8; ++st) {
+    const uint32_t ko = st * 256;  // 8 columns = two core matrices along K
+    mma_tf32(tmem, smem_desc(ah + ko), smem_desc(bh + ko), idesc, (first && st == 0) ? 0u : 1u);
+    mma_tf32(tmem, smem_desc(ah + ko), smem_desc(bl + ko), idesc, 1u);
+    mma_tf32(tmem, smem_desc(al + ko), smem_desc(bh + ko), idesc, 1u);
+  }
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(mbar))
                : "memory");
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
+  const uint32_t a = smem_u32(mbar);
   for (long long it = 0; it < kSpinLimit; ++it) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
         "selp.b32 %0, 1, 0, p;\n\t}\n"
         : "=r"(done)
-        : "r"(mbar), "r"(parity)
+        : "r"(a), "r"(parity)
         : "memory");
     if (done) return true;
   }
   return false;
 }
 
-// Stage alpha * op(X)[r0 + r][k0 + k] for r < vrows, k < kpad into hi / lo tiles (the
-// other rows of the tile stay zero from the initial clear; columns in [kvalid, kpad) are
-// written as zeros).  op = identity if trans == 0, transpose otherwise; X == nullptr
-// stands for the identity matrix.  Threads walk core matrices (8 rows x 4 columns =
-// 128 contiguous bytes) so that consecutive threads write consecutive words.
-__device__ __forceinline__ void stage(float* hi, float* lo, int vrows, int kvalid, int kpad,
-                                      const double* X, int ld, int trans, int r0, int k0,
-                                      double alpha) {
-  const int nkb = kpad >> 2;                 // 4-column groups
-  const int ncm = ((vrows + 7) >> 3) * nkb;  // core matrices touched
-  for (int e = threadIdx.x; e < ncm * 32; e += kThreads) {
-    const int q = e & 31, cm = e >> 5;
-    const int r = (cm / nkb) * 8 + (q >> 2), k = (cm % nkb) * 4 + (q & 3);
-    if (r >= vrows) continue;
-    double v = 0.0;
-    if (k < kvalid) {
-      const int gr = r0 + r, gk = k0 + k;
-      if (X == nullptr) v = (gr == gk) ? alpha : 0.0;
-      else v = alpha * (trans ? X[(size_t)gk * ld + gr] : X[(size_t)gr * ld + gk]);
+__device__ __forceinline__ void mbar_init(uint64_t* mbar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t cols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+               "r"(cols));
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+}
+
+__device__ __forceinline__ void tmem_free(uint32_t tmem, uint32_t cols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(cols));
+}
+
+// 16 consecutive accumulator columns of this warp's 32 lanes
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ float4 ldg4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+
+__device__ __forceinline__ void put_split4(float* hi, float* lo, int off, float4 v) {
+  float4 h, l;
+  h.x = tf32_round(v.x);
+  h.y = tf32_round(v.y);
+  h.z = tf32_round(v.z);
+  h.w = tf32_round(v.w);
+  l.x = tf32_round(v.x - h.x);
+  l.y = tf32_round(v.y - h.y);
+  l.z = tf32_round(v.z - h.z);
+  l.w = tf32_round(v.w - h.w);
+  *reinterpret_cast<float4*>(hi + off) = h;
+  *reinterpret_cast<float4*>(lo + off) = l;
+}
+
+__device__ __forceinline__ float4 fma4(float a, float4 x, float4 y) {
+  return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
+}
+
+// Work item e of a tile with nrows rows: 64 items per 8-row group, item = (row group,
+// 4-column group kb, row r7); 32 consecutive items fill 512 consecutive bytes of the tile.
+struct Item { int r, kb; };
+__device__ __forceinline__ Item item(int e) { return {(e >> 6) * 8 + (e & 7), (e >> 3) & 7}; }
+
+// Stage rows [0, nrows) of a 32-column chunk into hi / lo tiles from row-major FP32 data:
+// tile(row_base + r, k) = a X[r ld + k0 + k] for the first kval4 groups of 4 columns,
+// zero for the following groups up to nkg (kpad / 4).  Columns past K inside the last
+// group read the zero padding of X.  Threads t0, t0 + nthr, ... of the caller.
+__device__ __forceinline__ void stage4(float* hi, float* lo, int row_base, int nrows, int nkg, int kval4,
+                                       const float* __restrict__ X, int ld, int k0, float a, int t0,
+                                       int nthr) {
+  const int ne = ((nrows + 7) >> 3) * 64;
+  for (int e = t0; e < ne; e += nthr) {
+    const Item it = item(e);
+    if (it.r >= nrows || it.kb >= nkg) continue;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (it.kb < kval4) {
+      v = ldg4(X + (size_t)it.r * ld + k0 + it.kb * 4);
+      v.x *= a;
+      v.y *= a;
+      v.z *= a;
+      v.w *= a;
     }
-    const float h = tf32_round((float)v);
-    const float l = tf32_round((float)(v - (double)h));
-    const uint32_t off = kmajor_off(r, k) >> 2;
-    hi[off] = h;
-    lo[off] = l;
+    put_split4(hi, lo, kmo(row_base + it.r, it.kb * 4), v);
   }
 }
 
-constexpr int kStageFloats = 2 * TM * TK + 2 * TN * TK;  // A hi, A lo, B hi, B lo
+// A = alpha * identity rows row0 .. row0 + nrows - 1 of a K x K identity, columns k0 ..
+__device__ __forceinline__ void stage4_identity(float* hi, float* lo, int nrows, int nkg, int kvalid, int row0,
+                                                int k0, float alpha, int t0, int nthr) {
+  const int ne = ((nrows + 7) >> 3) * 64;
+  for (int e = t0; e < ne; e += nthr) {
+    const Item it = item(e);
+    if (it.r >= nrows || it.kb >= nkg) continue;
+    const int d = row0 + it.r - k0 - it.kb * 4;  // column of the diagonal inside the group
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (d >= 0 && d < 4 && k0 + it.kb * 4 + d < k0 + kvalid) (&v.x)[d] = alpha;
+    put_split4(hi, lo, kmo(it.r, it.kb * 4), v);
+  }
+}
 
-__global__ void __launch_bounds__(kThreads, 1) k_grouped_gemm_tc(const GemmTask* __restrict__ tasks,
-                                                                const GemmGroup* __restrict__ groups,
-                                                                int ngroups) {
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
-  float* buf[2] = {(float*)smem_raw, (float*)smem_raw + kStageFloats};
-  __shared__ __align__(8) uint64_t mbar[2];
+// B = W^T rows col0 .. col0 + nrows - 1: sum over sources of coef * z[(col0 + j) ldz + k0 + k]
+__device__ __forceinline__ void stage4_wsum(float* hi, float* lo, int nrows, int nkg, int kval4,
+                                            const Tc2Src* __restrict__ srcs, int s_begin, int s_end, int col0,
+                                            int k0, int t0, int nthr) {
+  const int ne = ((nrows + 7) >> 3) * 64;
+  for (int e0 = 0; e0 < ne; e0 += 4 * nthr) {
+    float4 acc[4];
+    Item it[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int e = e0 + t0 + i * nthr;
+      it[i] = item(e);
+      if (e >= ne) it[i].r = 1 << 20;
+      acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    for (int si = s_begin; si < s_end; ++si) {
+      const Tc2Src S = srcs[si];
+      const float* zb = S.z + (size_t)col0 * S.ldz + k0;
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (it[i].r < nrows && it[i].kb < kval4) acc[i] = fma4(S.coef, ldg4(zb + (size_t)it[i].r * S.ldz + it[i].kb * 4), acc[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (it[i].r < nrows && it[i].kb < nkg) put_split4(hi, lo, kmo(it[i].r, it[i].kb * 4), acc[i]);
+  }
+}
+
+// ------------------------------------------------------------------ phase 1
+
+constexpr int kMaxPackEntries = 16;  // pack columns are padded per entry to multiples of 8
+
+// shared-memory floats: one-chunk units keep the stack tile (hi, lo) and two B buffers;
+// multi-chunk units double-buffer A and B together
+template <bool kOne>
+constexpr int p1_smem_floats() { return kOne ? 6 * kTileF : 8 * kTileF; }
+
+template <bool kOne>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_tc_phase1(const Tc1Unit* __restrict__ units, const Tc1Pack* __restrict__ packs,
+                const Tc1Entry* __restrict__ ents) {
+  extern __shared__ unsigned char smem_dyn[];
+  float* sm = (float*)(((uintptr_t)smem_dyn + 127) & ~(uintptr_t)127);
+  __shared__ __align__(8) uint64_t mbar_buf[2];
+  __shared__ __align__(8) uint64_t mbar_acc[2];
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
+  __shared__ Tc1Entry pent[2][kMaxPackEntries];
+  __shared__ signed char pgrp[2][16];  // entry of each 8-column group, -1 = none
+  __shared__ int pn[2];
 
-  const int tile = blockIdx.x;
-  int lo_g = 0, hi_g = ngroups - 1;
-  while (lo_g < hi_g) {
-    int mid = (lo_g + hi_g + 1) >> 1;
-    if (groups[mid].tile_begin_tc <= tile) lo_g = mid; else hi_g = mid - 1;
-  }
-  const GemmGroup g = groups[lo_g];
-  const int local = tile - g.tile_begin_tc;
-  const int tn = (g.n + TN - 1) / TN;
-  const int row0 = (local / tn) * TM, col0 = (local % tn) * TN;
-  const int vrows_a = min(TM, g.m - row0), vrows_b = min(TN, g.n - col0);
-  const int nmma = min(TN, (vrows_b + 15) & ~15);  // MMA N: multiple of 16, at most 64
-  const uint32_t idesc = (kIdesc & ~(0x3Fu << 17)) | ((uint32_t)(nmma >> 3) << 17);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                 "r"(kTmemCols));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-  if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])));
+  const Tc1Unit u = units[blockIdx.x];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 0) tmem_alloc(&tmem_slot, 256);
+  if (tid == 0) {
+    mbar_init(&mbar_buf[0]);
+    mbar_init(&mbar_buf[1]);
+    mbar_init(&mbar_acc[0]);
+    mbar_init(&mbar_acc[1]);
     asm volatile("fence.mbarrier_init.release.cluster;");
     abort_flag = 0;
   }
-  for (int e = threadIdx.x; e < 2 * kStageFloats; e += kThreads) ((float*)smem_raw)[e] = 0.0f;
+  const int nch = (u.K + 31) >> 5;
+  if (kOne) {
+    const int kpad = (u.K + 7) & ~7;
+    stage4(sm, sm + kTileF, 0, u.rows, kpad >> 2, (u.K + 3) >> 2, u.A, u.lda, 0, 1.0f, tid, kThreads);
+  }
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_slot;
-  uint32_t phase[2] = {0, 0};
-  bool pending[2] = {false, false};
-  uint32_t accumulate = 0;
-  int chunk = 0;
+  uint32_t ph_buf[2] = {0, 0}, ph_acc[2] = {0, 0};
 
-  for (int t = g.task_begin; t < g.task_end && !abort_flag; ++t) {
-    const GemmTask T = tasks[t];
-    // op(A) is m x k, op(B) is k x n; the tensor core reads B as n x k (K-major), i.e.
-    // op(B)^T: rows n, columns k  ->  stage B with the opposite transpose flag
-    const int K = T.A ? T.k : g.m;
-    for (int k0 = 0; k0 < K && !abort_flag; k0 += TK, ++chunk) {
-      const int b = chunk & 1;
-      if (pending[b]) {  // the tensor core must be done with this buffer
-        if (!mbar_wait(smem_u32(&mbar[b]), phase[b])) { atomicExch(&g_tc_error, 1); abort_flag = 1; }
-        phase[b] ^= 1;
-        pending[b] = false;
-        __syncthreads();
-        if (abort_flag) break;
+  // epilogue of pack slot a: accumulator columns -> Zt (column-major, coalesced along rows)
+  auto epilogue = [&](int a) {
+    if (tid == 0 && !mbar_wait(&mbar_acc[a], ph_acc[a])) {
+      atomicExch(&g_tc_error, 1);
+      abort_flag = 1;
+    }
+    ph_acc[a] ^= 1;
+    __syncthreads();
+    if (abort_flag) return;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const int q = warp & 3, h = warp >> 2;
+    const int r = q * 32 + lane;
+    const int n16 = (pn[a] + 15) & ~15;
+    for (int c0 = h * 16; c0 < n16; c0 += 32) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * 128 + c0), v);
+#pragma unroll
+      for (int g8 = 0; g8 < 2; ++g8) {
+        const int e = pgrp[a][(c0 >> 3) + g8];
+        if (e < 0 || r >= u.rows) continue;
+        const Tc1Entry& E = pent[a][e];
+        const int j0 = c0 + 8 * g8 - E.start, nc = E.ncols, ldz = E.ldz;
+        float* zp = E.zt + (size_t)j0 * ldz + u.row0 + r;
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          if (j0 + j < nc) zp[(size_t)j * ldz] = v[8 * g8 + j];
       }
-      const int kvalid = min(TK, K - k0);
-      const int kpad = (kvalid + 7) & ~7;
-      float* Ahi = buf[b];
-      float* Alo = Ahi + TM * TK;
-      float* Bhi = Alo + TM * TK;
-      float* Blo = Bhi + TN * TK;
-      stage(Ahi, Alo, vrows_a, kvalid, kpad, T.A, T.lda, T.transA, row0, k0, T.alpha);
-      stage(Bhi, Blo, vrows_b, kvalid, kpad, T.B, T.ldb, !T.transB, col0, k0, 1.0);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+  };
+
+  int s = 0;
+  const int npk = u.p_end - u.p_begin;
+  for (int pi = 0; pi < npk && !abort_flag; ++pi) {
+    const Tc1Pack P = packs[u.p_begin + pi];
+    const int slot = pi & 1;
+    const int nent = P.e_end - P.e_begin;
+    if (tid < nent) pent[slot][tid] = ents[P.e_begin + tid];
+    if (tid == 0) pn[slot] = P.n;
+    for (int ch = 0; ch < nch; ++ch, ++s) {
+      const int b = s & 1;
+      if (s >= 2) {
+        if (tid == 0 && !mbar_wait(&mbar_buf[b], ph_buf[b])) {
+          atomicExch(&g_tc_error, 1);
+          abort_flag = 1;
+        }
+        ph_buf[b] ^= 1;
+      }
+      __syncthreads();
+      if (abort_flag) break;
+      if (ch == 0 && tid < 16) {
+        int g = -1;
+        for (int e = 0; e < nent; ++e) {
+          const int st = pent[slot][e].start, en = st + ((pent[slot][e].ncols + 7) & ~7);
+          if (tid * 8 >= st && tid * 8 < en) g = e;
+        }
+        pgrp[slot][tid] = (signed char)g;
+      }
+      const int k0 = ch * 32, kvalid = min(32, u.K - k0), kpad = (kvalid + 7) & ~7;
+      const int nkg = kpad >> 2, kval4 = (kvalid + 3) >> 2;
+      float* Ah = kOne ? sm : sm + b * 4 * kTileF;
+      float* Al = Ah + kTileF;
+      float* Bh = kOne ? sm + (2 + 2 * b) * kTileF : Ah + 2 * kTileF;
+      float* Bl = Bh + kTileF;
+      if (!kOne) stage4(Ah, Al, 0, u.rows, nkg, kval4, u.A, u.lda, k0, 1.0f, tid, kThreads);
+      for (int e = 0; e < nent; ++e) {
+        const Tc1Entry& E = pent[slot][e];
+        stage4(Bh, Bl, E.start, E.ncols, nkg, kval4, E.D, E.ldd, k0, E.alpha, tid, kThreads);
+      }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();
-      if (threadIdx.x == 0) {
+      if (tid == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;");
-        const uint32_t a_hi = smem_u32(Ahi), a_lo = smem_u32(Alo);
-        const uint32_t b_hi = smem_u32(Bhi), b_lo = smem_u32(Blo);
-        for (int st = 0; st < kpad / 8; ++st) {  // K = 8 per instruction
-          const uint32_t ko = st * 256;
-          mma_tf32(tmem, smem_desc(a_hi + ko), smem_desc(b_hi + ko), idesc, accumulate);
-          accumulate = 1;
-          mma_tf32(tmem, smem_desc(a_hi + ko), smem_desc(b_lo + ko), idesc, 1);
-          mma_tf32(tmem, smem_desc(a_lo + ko), smem_desc(b_hi + ko), idesc, 1);
-        }
-        mma_commit(smem_u32(&mbar[b]));
+        mma_chunk(tmem + (uint32_t)(slot * 128), Ah, Al, Bh, Bl, kpad, idesc_tf32((P.n + 15) & ~15), ch == 0);
+        mma_commit(&mbar_buf[b]);
+        if (ch == nch - 1) mma_commit(&mbar_acc[slot]);
       }
-      pending[b] = true;
-      accumulate = 1;
     }
+    if (abort_flag) break;
+    if (pi >= 1) epilogue((pi - 1) & 1);
   }
-  for (int b = 0; b < 2; ++b)
-    if (pending[b] && !abort_flag) {
-      if (!mbar_wait(smem_u32(&mbar[b]), phase[b])) { atomicExch(&g_tc_error, 1); abort_flag = 1; }
-    }
+  if (!abort_flag && npk > 0) epilogue((npk - 1) & 1);
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) tmem_free(tmem, 256);
+}
+
+// ------------------------------------------------------------------ phase 2
+
+// Output tiles of more than 32 rows: all 8 warps stage each step, double-buffered.
+constexpr int kP2BufF = 3 * kTileF;  // A hi, A lo (128 rows), B hi, B lo (64 rows)
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_tc_phase2(const Tc2Unit* __restrict__ units, const Tc2Task* __restrict__ tasks,
+                const Tc2Src* __restrict__ srcs) {
+  extern __shared__ unsigned char smem_dyn[];
+  float* sm = (float*)(((uintptr_t)smem_dyn + 127) & ~(uintptr_t)127);
+  __shared__ __align__(8) uint64_t mbar_buf[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+
+  const Tc2Unit u = units[blockIdx.x];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int mv = min(128, u.m - u.row0), nv = min(64, u.n - u.col0);
+  const int n16 = (nv + 15) & ~15;
+  if (warp == 0) tmem_alloc(&tmem_slot, 64);
+  if (tid == 0) {
+    mbar_init(&mbar_buf[0]);
+    mbar_init(&mbar_buf[1]);
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    abort_flag = 0;
+  }
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
-  if (!abort_flag && accumulate) {
-    // epilogue: warp w reads TMEM lanes 32w..32w+31 (= rows), 16 columns at a time
-    const int r = row0 + warp * 32 + lane;
-#pragma unroll 1
-    for (int c0 = 0; c0 < nmma; c0 += 16) {
-      uint32_t v[16];
-      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-          : "r"(taddr));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (r < g.m) {
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int c = col0 + c0 + j;
-          if (c < g.n) g.C[(size_t)r * g.ldc + c] += (double)__uint_as_float(v[j]);
+  const uint32_t tmem = tmem_slot;
+  const uint32_t idesc = idesc_tf32(n16);
+  uint32_t ph_buf[2] = {0, 0};
+  int s = 0;
+  for (int t = u.t_begin; t < u.t_end && !abort_flag; ++t) {
+    const Tc2Task T = tasks[t];
+    const int nch = (T.K + 31) >> 5;
+    for (int ch = 0; ch < nch; ++ch, ++s) {
+      const int b = s & 1;
+      if (s >= 2) {
+        if (tid == 0 && !mbar_wait(&mbar_buf[b], ph_buf[b])) {
+          atomicExch(&g_tc_error, 1);
+          abort_flag = 1;
         }
+        ph_buf[b] ^= 1;
+      }
+      __syncthreads();
+      if (abort_flag) break;
+      const int k0 = ch * 32, kvalid = min(32, T.K - k0), kpad = (kvalid + 7) & ~7;
+      const int nkg = kpad >> 2, kval4 = (kvalid + 3) >> 2;
+      float* Ah = sm + b * kP2BufF;
+      float* Al = Ah + kTileF;
+      float* Bh = Al + kTileF;
+      float* Bl = Bh + kTileF / 2;
+      if (T.C) stage4(Ah, Al, 0, mv, nkg, kval4, T.C + (size_t)u.row0 * T.ldc, T.ldc, k0, T.alpha, tid, kThreads);
+      else stage4_identity(Ah, Al, mv, nkg, kvalid, u.row0, k0, T.alpha, tid, kThreads);
+      stage4_wsum(Bh, Bl, nv, nkg, kval4, srcs, T.s_begin, T.s_end, u.col0, k0, tid, kThreads);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      if (tid == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        mma_chunk(tmem, Ah, Al, Bh, Bl, kpad, idesc, s == 0);
+        mma_commit(&mbar_buf[b]);
+      }
+    }
+  }
+  // the last commit covers every product of the unit
+  if (s > 0 && !abort_flag) {
+    const int b = (s - 1) & 1;
+    if (tid == 0 && !mbar_wait(&mbar_buf[b], ph_buf[b])) {
+      atomicExch(&g_tc_error, 1);
+      abort_flag = 1;
+    }
+  }
+  __syncthreads();
+  if (s > 0 && !abort_flag) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const int q = warp & 3, h = warp >> 2;
+    const int r = q * 32 + lane;
+    for (int c0 = h * 16; c0 < n16; c0 += 32) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+      if (r < mv) {
+        double* yr = u.y + (size_t)(u.row0 + r) * u.ldy + u.col0;
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          if (c0 + j < nv) atomicAdd(yr + c0 + j, (double)v[j]);
       }
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  if (warp == 0) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+  if (warp == 0) tmem_free(tmem, 64);
+}
+
+// Phase 2 for output tiles of at most 32 rows (the common case of small symmetry
+// blocks), as a warp-specialised pipeline: four producer groups of two warps each own
+// one shared-memory stage and fill it for every fourth step (a step is one 32-column K
+// chunk of one task); one thread issues the MMAs of the steps in order and releases
+// each stage with tcgen05.commit.  A stage holds A = 32 rows of C (hi, lo) and B = 64
+// rows of W^T (hi, lo); the MMA still reads 128 rows of A, and rows 32..127 fall on the
+// rest of the same stage: they only produce accumulator rows that are never read.
+constexpr int kGroups = 4, kGroupThreads = 64;
+constexpr int kP2sThreads = kGroups * kGroupThreads + 32;
+constexpr int kSA = 32 * 32, kSB = 64 * 32;   // floats of an A (32-row) / B (64-row) tile
+constexpr int kP2sStageF = 2 * kSA + 2 * kSB;  // 24 KB: the 16 KB A footprint stays inside
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
+  uint64_t state;
+  asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(state) : "r"(smem_u32(mbar)) : "memory");
+  (void)state;
+}
+
+__device__ __forceinline__ void mbar_init_n(uint64_t* mbar, int n) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(n));
+}
+
+// bounded wait that also gives up once another thread has flagged an abort
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* mbar, uint32_t parity, volatile int* abort_flag) {
+  const uint32_t a = smem_u32(mbar);
+  for (long long it = 0; it < kSpinLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((it & 1023) == 1023 && *abort_flag) return false;
+  }
+  atomicExch(&g_tc_error, 1);
+  *abort_flag = 1;
+  return false;
+}
+
+__global__ void __launch_bounds__(kP2sThreads, 2)
+    k_tc_phase2s(const Tc2Unit* __restrict__ units, const Tc2Task* __restrict__ tasks,
+                 const Tc2Src* __restrict__ srcs) {
+  extern __shared__ unsigned char smem_dyn[];
+  float* sm = (float*)(((uintptr_t)smem_dyn + 127) & ~(uintptr_t)127);
+  __shared__ __align__(8) uint64_t full[kGroups];
+  __shared__ __align__(8) uint64_t empty[kGroups];
+  __shared__ __align__(8) uint64_t done;
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int abort_flag;
+
+  const Tc2Unit u = units[blockIdx.x];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int mv = u.m - u.row0, nv = min(64, u.n - u.col0);  // mv <= 32 by construction
+  const int n16 = (nv + 15) & ~15;
+  if (warp == kGroups * 2) tmem_alloc(&tmem_slot, 64);
+  if (tid == 0) {
+    for (int g = 0; g < kGroups; ++g) {
+      mbar_init_n(&full[g], kGroupThreads);
+      mbar_init_n(&empty[g], 1);
+    }
+    mbar_init_n(&done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    abort_flag = 0;
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_slot;
+
+  if (warp < kGroups * 2) {
+    // ---- producers: group g fills stage g for steps s = g, g + 4, ...
+    const int g = warp >> 1, gt = tid & (kGroupThreads - 1);
+    float* Ah = sm + g * kP2sStageF;
+    float* Al = Ah + kSA;
+    float* Bh = Al + kSA;
+    float* Bl = Bh + kSB;
+    int s = 0;
+    for (int t = u.t_begin; t < u.t_end && !abort_flag; ++t) {
+      const Tc2Task T = tasks[t];
+      const int nch = (T.K + 31) >> 5;
+      for (int ch = 0; ch < nch; ++ch, ++s) {
+        if ((s & (kGroups - 1)) != g) continue;
+        const int k = s / kGroups;  // fill number of this stage
+        if (k > 0 && !mbar_wait_or_abort(&empty[g], (k - 1) & 1, &abort_flag)) break;
+        const int k0 = ch * 32, kvalid = min(32, T.K - k0), kpad = (kvalid + 7) & ~7;
+        const int nkg = kpad >> 2, kval4 = (kvalid + 3) >> 2;
+        if (T.C) stage4(Ah, Al, 0, mv, nkg, kval4, T.C + (size_t)u.row0 * T.ldc, T.ldc, k0, T.alpha, gt, kGroupThreads);
+        else stage4_identity(Ah, Al, mv, nkg, kvalid, u.row0, k0, T.alpha, gt, kGroupThreads);
+        stage4_wsum(Bh, Bl, nv, nkg, kval4, srcs, T.s_begin, T.s_end, u.col0, k0, gt, kGroupThreads);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(&full[g]);
+      }
+    }
+  } else if (lane == 0) {
+    // ---- MMA issue: steps in order
+    const uint32_t idesc = idesc_tf32(n16);
+    int s = 0;
+    for (int t = u.t_begin; t < u.t_end && !abort_flag; ++t) {
+      const int K = tasks[t].K;
+      const int nch = (K + 31) >> 5;
+      for (int ch = 0; ch < nch; ++ch, ++s) {
+        const int g = s & (kGroups - 1);
+        if (!mbar_wait_or_abort(&full[g], (s / kGroups) & 1, &abort_flag)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const int kvalid = min(32, K - ch * 32), kpad = (kvalid + 7) & ~7;
+        float* Ah = sm + g * kP2sStageF;
+        mma_chunk(tmem, Ah, Ah + kSA, Ah + 2 * kSA, Ah + 2 * kSA + kSB, kpad, idesc, s == 0);
+        mma_commit(&empty[g]);
+      }
+      if (abort_flag) break;
+    }
+    if (!abort_flag) mma_commit(&done);
+  }
+  __syncthreads();
+  if (tid == 0 && !abort_flag) mbar_wait_or_abort(&done, 0, &abort_flag);
+  __syncthreads();
+  if (!abort_flag && (warp == 0 || warp == 4)) {
+    // accumulator rows 0..31 sit in TMEM lanes 0..31 (warps 0 and 4 reach them)
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const int h = warp >> 2;
+    for (int c0 = h * 16; c0 < n16; c0 += 32) {
+      float v[16];
+      tmem_ld16(tmem + (uint32_t)c0, v);
+      if (lane < mv) {
+        double* yr = u.y + (size_t)(u.row0 + lane) * u.ldy + u.col0;
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          if (c0 + j < nv) atomicAdd(yr + c0 + j, (double)v[j]);
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == kGroups * 2) tmem_free(tmem, 64);
+}
+
+// ------------------------------------------------------------------ conversions
+
+// x (FP64) -> x32 (row-major stacks) and x32t (column-major stacks), one CTA per x block
+__global__ void k_x_prep(const double* __restrict__ x, float* __restrict__ x32, float* __restrict__ x32t,
+                         const TcXBlock* __restrict__ xb) {
+  const TcXBlock B = xb[blockIdx.x];
+  const int n = B.rows * B.cols;
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    const int r = e / B.cols, c = e - r * B.cols;
+    const float v = (float)x[B.src + e];
+    x32[B.dst + (int64_t)r * B.ld + c] = v;
+    x32t[B.dstt + (int64_t)c * B.ldt + r] = v;
   }
 }
 
+// FP64 blocks (row-major, stride cols) -> FP32 with row stride ld, one CTA per block
+__global__ void k_mirror(const TcMirror* __restrict__ m) {
+  const TcMirror M = m[blockIdx.x];
+  const int n = M.rows * M.cols;
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    const int r = e / M.cols, c = e - r * M.cols;
+    M.dst[(int64_t)r * M.ld + c] = (float)M.src[e];
+  }
+}
+
+inline void ck(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) throw std::runtime_error(std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+template <typename T>
+T* upload(const std::vector<T>& v, Stream s) {
+  if (v.empty()) return nullptr;
+  T* p = (T*)dev_alloc(v.size() * sizeof(T), s);
+  dev_h2d(p, v.data(), v.size() * sizeof(T), s);
+  return p;
+}
+
+size_t smem_bytes(int floats) { return sizeof(float) * (size_t)floats + 128; }
+
 }  // namespace
 
-void gemm_plan_run_tc(const GemmPlan* p, Stream s) {
-  if (!p || p->ntiles_tc == 0) return;
-  const size_t shm = sizeof(float) * (size_t)(2 * kStageFloats) + 1024;
+struct TcPlan {
+  Tc1Entry* ents = nullptr;
+  Tc1Pack* packs = nullptr;
+  Tc1Unit* u1 = nullptr;      // one-chunk units first, then multi-chunk units
+  int n1_one = 0, n1_multi = 0;
+  Tc2Src* srcs = nullptr;
+  Tc2Task* tasks = nullptr;
+  Tc2Unit* u2 = nullptr;      // tiles of at most 32 rows first, then the others
+  int n2_small = 0, n2 = 0;
+  TcXBlock* xb = nullptr;
+  int nxb = 0;
+  float* x32 = nullptr;
+  float* x32t = nullptr;
+  int64_t n = 0;
+};
+
+TcPlan* tc_plan_upload(const std::vector<Tc1Entry>& e, const std::vector<Tc1Pack>& p,
+                       const std::vector<Tc1Unit>& u1, const std::vector<Tc2Src>& s,
+                       const std::vector<Tc2Task>& t, const std::vector<Tc2Unit>& u2,
+                       const std::vector<TcXBlock>& xb, float* x32, float* x32t, int64_t n,
+                       Stream st) {
+  for (const Tc1Pack& q : p)
+    if (q.e_end - q.e_begin > kMaxPackEntries || q.n > 128) throw std::logic_error("tc pack too large");
+  std::vector<Tc1Unit> ord;
+  ord.reserve(u1.size());
+  for (const Tc1Unit& q : u1)
+    if (q.K <= 32) ord.push_back(q);
+  const int n_one = (int)ord.size();
+  for (const Tc1Unit& q : u1)
+    if (q.K > 32) ord.push_back(q);
+  TcPlan* P = new TcPlan;
+  P->ents = upload(e, st);
+  P->packs = upload(p, st);
+  P->u1 = upload(ord, st);
+  P->n1_one = n_one;
+  P->n1_multi = (int)ord.size() - n_one;
+  P->srcs = upload(s, st);
+  P->tasks = upload(t, st);
+  std::vector<Tc2Unit> ord2;
+  ord2.reserve(u2.size());
+  for (const Tc2Unit& q : u2)
+    if (q.m - q.row0 <= 32) ord2.push_back(q);
+  P->n2_small = (int)ord2.size();
+  for (const Tc2Unit& q : u2)
+    if (q.m - q.row0 > 32) ord2.push_back(q);
+  P->u2 = upload(ord2, st);
+  P->n2 = (int)ord2.size();
+  P->xb = upload(xb, st);
+  P->nxb = (int)xb.size();
+  P->x32 = x32;
+  P->x32t = x32t;
+  P->n = n;
+  return P;
+}
+
+void tc_plan_free(TcPlan* p, Stream s) {
+  if (!p) return;
+  dev_free(p->ents, s);
+  dev_free(p->packs, s);
+  dev_free(p->u1, s);
+  dev_free(p->srcs, s);
+  dev_free(p->tasks, s);
+  dev_free(p->u2, s);
+  dev_free(p->xb, s);
+  delete p;
+}
+
+void tc_plan_run(const TcPlan* p, const double* x, double* y, void* const* ev, Stream s) {
+  cudaStream_t cs = (cudaStream_t)s;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_grouped_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-    if (e != cudaSuccess) throw std::runtime_error(std::string("cuda tc smem attr: ") + cudaGetErrorString(e));
+    ck(cudaFuncSetAttribute(k_tc_phase1<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)smem_bytes(p1_smem_floats<true>())), "tc phase 1 smem");
+    ck(cudaFuncSetAttribute(k_tc_phase1<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)smem_bytes(p1_smem_floats<false>())), "tc phase 1 smem");
+    ck(cudaFuncSetAttribute(k_tc_phase2, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)smem_bytes(2 * kP2BufF)), "tc phase 2 smem");
+    ck(cudaFuncSetAttribute(k_tc_phase2s, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)smem_bytes(kGroups * kP2sStageF)), "tc phase 2 smem");
     attr = true;
   }
-  k_grouped_gemm_tc<<<p->ntiles_tc, kThreads, shm, (cudaStream_t)s>>>(p->tasks, p->groups, p->ngroups);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) throw std::runtime_error(std::string("cuda tc gemm launch: ") + cudaGetErrorString(e));
+  if (ev) event_record(ev[0], s);
+  int launches = 0;
+  if (p->nxb > 0) {
+    k_x_prep<<<p->nxb, 256, 0, cs>>>(x, p->x32, p->x32t, p->xb);
+    ++launches;
+  }
+  ck(cudaMemsetAsync(y, 0, sizeof(double) * (size_t)(p->n > 0 ? p->n : 1), cs), "tc zero y");
+  if (p->n1_one > 0) {
+    k_tc_phase1<true><<<p->n1_one, kThreads, smem_bytes(p1_smem_floats<true>()), cs>>>(p->u1, p->packs, p->ents);
+    ++launches;
+  }
+  if (p->n1_multi > 0) {
+    k_tc_phase1<false><<<p->n1_multi, kThreads, smem_bytes(p1_smem_floats<false>()), cs>>>(
+        p->u1 + p->n1_one, p->packs, p->ents);
+    ++launches;
+  }
+  if (ev) event_record(ev[1], s);
+  if (p->n2_small > 0) {
+    k_tc_phase2s<<<p->n2_small, kP2sThreads, smem_bytes(kGroups * kP2sStageF), cs>>>(p->u2, p->tasks, p->srcs);
+    ++launches;
+  }
+  if (p->n2 > p->n2_small) {
+    k_tc_phase2<<<p->n2 - p->n2_small, kThreads, smem_bytes(2 * kP2BufF), cs>>>(p->u2 + p->n2_small, p->tasks,
+                                                                                 p->srcs);
+    ++launches;
+  }
+  if (ev) event_record(ev[2], s);
+  note_launches(launches);
+  ck(cudaGetLastError(), "tc matvec launch");
+}
+
+void tc_mirror(const std::vector<TcMirror>& m, Stream s) {
+  if (m.empty()) return;
+  TcMirror* d = upload(m, s);
+  k_mirror<<<(int)m.size(), 256, 0, (cudaStream_t)s>>>(d);
+  note_launches(1);
+  ck(cudaGetLastError(), "tc mirror launch");
+  dev_free(d, s);
 }
 
 int tc_error_flag(Stream s) {
   int h = 0;
-  cudaMemcpyFromSymbolAsync(&h, g_tc_error, sizeof(int), 0, cudaMemcpyDeviceToHost, (cudaStream_t)s);
-  cudaStreamSynchronize((cudaStream_t)s);
+  ck(cudaMemcpyFromSymbolAsync(&h, g_tc_error, sizeof(int), 0, cudaMemcpyDeviceToHost, (cudaStream_t)s),
+     "tc error flag");
+  ck(cudaStreamSynchronize((cudaStream_t)s), "tc error flag");
   return h;
 }
 

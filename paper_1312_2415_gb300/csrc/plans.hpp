@@ -4,10 +4,12 @@
 
 namespace dmrg {
 
+void note_launches(int64_t k);  // adds to the count kernel_launches() reports
+
 struct GemmPlan {
   GemmTask* tasks = nullptr;
   GemmGroup* groups = nullptr;
-  int ngroups = 0, ntiles = 0, ntiles_tc = 0;
+  int ngroups = 0, ntiles = 0;
   int64_t ntasks = 0;
 };
 
