@@ -63,6 +63,9 @@ typedef struct {
   /* matvecs done on the tensor cores (precision 1), their flops and device time */
   int64_t tc_matvecs;
   double tc_flops, tc_phase1_ms, tc_phase2_ms;
+  /* per phase of those matvecs: flops, and compulsory bytes (FP32 operands read once
+   * per use, FP32 Z written once, y written once) */
+  double tc_phase1_flops, tc_phase2_flops, tc_phase1_bytes, tc_phase2_bytes;
 } dmrg_stats_t;
 
 /* Sec. 4.1: L orbitals with irreps orb_irrep[L], N electrons (2 <= N <= 2L, needed by

@@ -35,6 +35,8 @@ class Stats(ctypes.Structure):
         ("k_phase2_flops", ctypes.c_double), ("kernels_launched", ctypes.c_int64),
         ("tc_matvecs", ctypes.c_int64), ("tc_flops", ctypes.c_double),
         ("tc_phase1_ms", ctypes.c_double), ("tc_phase2_ms", ctypes.c_double),
+        ("tc_phase1_flops", ctypes.c_double), ("tc_phase2_flops", ctypes.c_double),
+        ("tc_phase1_bytes", ctypes.c_double), ("tc_phase2_bytes", ctypes.c_double),
     ]
 
 

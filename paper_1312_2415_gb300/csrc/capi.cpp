@@ -364,6 +364,10 @@ int dmrg_stats(dmrg_ctx* c, dmrg_stats_t* out) {
     out->tc_flops = s.tc_flops;
     out->tc_phase1_ms = s.tc_phase1_ms;
     out->tc_phase2_ms = s.tc_phase2_ms;
+    out->tc_phase1_flops = s.tc_phase1_flops;
+    out->tc_phase2_flops = s.tc_phase2_flops;
+    out->tc_phase1_bytes = s.tc_phase1_bytes;
+    out->tc_phase2_bytes = s.tc_phase2_bytes;
     return DMRG_OK;
   });
 }

@@ -732,6 +732,7 @@ struct Engine::MatvecPlan {
   std::vector<int> sec_dim;
   TcPlan* tc = nullptr;
   float* tc_zt = nullptr;
+  double tc_bytes1 = 0.0, tc_bytes2 = 0.0;  // compulsory bytes of the two phases
   float* tc_mem[3] = {nullptr, nullptr, nullptr};  // x32, x32t, operator mirrors
 };
 
@@ -1184,6 +1185,26 @@ void Engine::build_tc(MatvecPlan* P) {
         for (int tb = t0; tb < t1; tb += kTasksPerUnit)
           u2.push_back({P->yout + X.off, X.cols, X.rows, X.cols, row0, col0, tb, std::min(t1, tb + kTasksPerUnit)});
   }
+  // compulsory traffic (unpadded FP32 elements): phase 1 reads x and each right-operator
+  // block once and writes every Z; phase 2 reads each task's Z sub-blocks and each
+  // left-operator block once and writes y (FP64)
+  {
+    double b1 = (double)P->n, b2 = 0.0, dz = 0.0;
+    for (const auto& Zg : P->zg) dz += (double)Zg.n * P->tall_rows[Zg.c];
+    std::unordered_map<const double*, int> seen;
+    for (const auto& Zg : P->zg)
+      if (seen.emplace(Zg.D, 1).second) b1 += (double)Zg.n * Zg.K;
+    b1 += dz;
+    for (const auto& w : P->witems) {
+      b2 += (double)(w.src_end - w.src_begin) * w.rows * w.cols;
+      const CombOp& C = P->cl[w.gl];
+      if (C.identity) continue;
+      const BlockRef& cb = (*C.blocks)[w.cbi];
+      if (seen.emplace(C.data + cb.off, 2).second) b2 += (double)cb.rows * cb.cols;
+    }
+    P->tc_bytes1 = 4.0 * b1;
+    P->tc_bytes2 = 4.0 * b2 + 8.0 * P->n;
+  }
   P->tc = tc_plan_upload(ents, packs, u1, srcs, tasks, u2, xbt, x32, x32t, P->n, stream_);
   // the host tables are not needed any more
   std::vector<MatvecPlan::ZGroup>().swap(P->zg);
@@ -1204,6 +1225,10 @@ void Engine::run_matvec(MatvecPlan* p, const double* x, double* y, bool tc) {
     if (y != p->yout) dev_d2d(y, p->yout, sizeof(double) * p->n, stream_);
     st_.tc_matvecs += 1;
     st_.tc_flops += p->flops;
+    st_.tc_phase1_flops += p->flops1;
+    st_.tc_phase2_flops += p->flops2;
+    st_.tc_phase1_bytes += p->tc_bytes1;
+    st_.tc_phase2_bytes += p->tc_bytes2;
     st_.matvecs += 1;
     st_.matvec_flops += p->flops;
     st_.last_matvec_flops = p->flops;

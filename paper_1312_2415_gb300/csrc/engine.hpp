@@ -76,6 +76,7 @@ struct Stats {
   // tensor-core (mixed precision) matvecs
   int64_t tc_matvecs = 0;
   double tc_flops = 0.0, tc_phase1_ms = 0.0, tc_phase2_ms = 0.0;
+  double tc_phase1_flops = 0.0, tc_phase2_flops = 0.0, tc_phase1_bytes = 0.0, tc_phase2_bytes = 0.0;
 };
 
 class Engine {

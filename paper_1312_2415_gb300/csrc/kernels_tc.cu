@@ -365,7 +365,13 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 // ------------------------------------------------------------------ phase 2
 
-// Output tiles of more than 32 rows: all 8 warps stage each step, double-buffered.
+// The tensor core's FP32 accumulation loses accuracy over long runs of products (the
+// error of a 48-task run measured ~10x that of a 2-task run), so phase 2 adds its
+// accumulator into FP32 registers every kSegSteps steps and restarts it.
+constexpr int kSegSteps = 2;
+
+// Output tiles of more than 32 rows: all 8 warps stage each step, double-buffered, and
+// drain the accumulator at segment ends.
 constexpr int kP2BufF = 3 * kTileF;  // A hi, A lo (128 rows), B hi, B lo (64 rows)
 
 __global__ void __launch_bounds__(kThreads, 1)
@@ -374,6 +380,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   extern __shared__ unsigned char smem_dyn[];
   float* sm = (float*)(((uintptr_t)smem_dyn + 127) & ~(uintptr_t)127);
   __shared__ __align__(8) uint64_t mbar_buf[2];
+  __shared__ __align__(8) uint64_t mbar_seg;
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
 
@@ -381,10 +388,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int mv = min(128, u.m - u.row0), nv = min(64, u.n - u.col0);
   const int n16 = (nv + 15) & ~15;
+  const int q = warp & 3, h = warp >> 2;
   if (warp == 0) tmem_alloc(&tmem_slot, 64);
   if (tid == 0) {
     mbar_init(&mbar_buf[0]);
     mbar_init(&mbar_buf[1]);
+    mbar_init(&mbar_seg);
     asm volatile("fence.mbarrier_init.release.cluster;");
     abort_flag = 0;
   }
@@ -392,14 +401,21 @@ __global__ void __launch_bounds__(kThreads, 1)
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_slot;
   const uint32_t idesc = idesc_tf32(n16);
-  uint32_t ph_buf[2] = {0, 0};
-  int s = 0;
+  uint32_t ph_buf[2] = {0, 0}, ph_seg = 0;
+  float acc[2][16];  // this thread's row, columns h*16 + 32*i + j, summed over segments
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 16; ++j) acc[i][j] = 0.0f;
+  int nsteps = 0;
+  for (int t = u.t_begin; t < u.t_end; ++t) nsteps += (tasks[t].K + 31) >> 5;
+  int s = 0, seg_first = 0;
   for (int t = u.t_begin; t < u.t_end && !abort_flag; ++t) {
     const Tc2Task T = tasks[t];
     const int nch = (T.K + 31) >> 5;
     for (int ch = 0; ch < nch; ++ch, ++s) {
       const int b = s & 1;
-      if (s >= 2) {
+      if (s >= 2) {  // the MMA of step s - 2 must be done with this buffer
         if (tid == 0 && !mbar_wait(&mbar_buf[b], ph_buf[b])) {
           atomicExch(&g_tc_error, 1);
           abort_flag = 1;
@@ -419,36 +435,49 @@ __global__ void __launch_bounds__(kThreads, 1)
       stage4_wsum(Bh, Bl, nv, nkg, kval4, srcs, T.s_begin, T.s_end, u.col0, k0, tid, kThreads);
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();
+      const bool seg_end = (s + 1 - seg_first == kSegSteps) || (s + 1 == nsteps);
       if (tid == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;");
-        mma_chunk(tmem, Ah, Al, Bh, Bl, kpad, idesc, s == 0);
+        mma_chunk(tmem, Ah, Al, Bh, Bl, kpad, idesc, s == seg_first);
         mma_commit(&mbar_buf[b]);
+        if (seg_end) mma_commit(&mbar_seg);
       }
-    }
-  }
-  // the last commit covers every product of the unit
-  if (s > 0 && !abort_flag) {
-    const int b = (s - 1) & 1;
-    if (tid == 0 && !mbar_wait(&mbar_buf[b], ph_buf[b])) {
-      atomicExch(&g_tc_error, 1);
-      abort_flag = 1;
+      if (seg_end) {
+        // promote the segment's FP32 accumulator to the register sums, then restart it
+        if (tid == 0 && !mbar_wait(&mbar_seg, ph_seg)) {
+          atomicExch(&g_tc_error, 1);
+          abort_flag = 1;
+        }
+        ph_seg ^= 1;
+        __syncthreads();
+        if (abort_flag) break;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+          const int c0 = h * 16 + 32 * i;
+          if (c0 < n16) {
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) acc[i][j] += v[j];
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        seg_first = s + 1;
+      }
     }
   }
   __syncthreads();
-  if (s > 0 && !abort_flag) {
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    const int q = warp & 3, h = warp >> 2;
-    const int r = q * 32 + lane;
-    for (int c0 = h * 16; c0 < n16; c0 += 32) {
-      float v[16];
-      tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
-      if (r < mv) {
-        double* yr = u.y + (size_t)(u.row0 + r) * u.ldy + u.col0;
+  const int r = q * 32 + lane;
+  if (s > 0 && !abort_flag && r < mv) {
+    double* yr = u.y + (size_t)(u.row0 + r) * u.ldy + u.col0;
 #pragma unroll
-        for (int j = 0; j < 16; ++j)
-          if (c0 + j < nv) atomicAdd(yr + c0 + j, (double)v[j]);
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int c = h * 16 + 32 * i + j;
+        if (c < nv) atomicAdd(yr + c, (double)acc[i][j]);
       }
-    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
@@ -468,9 +497,7 @@ constexpr int kSA = 32 * 32, kSB = 64 * 32;   // floats of an A (32-row) / B (64
 constexpr int kP2sStageF = 2 * kSA + 2 * kSB;  // 24 KB: the 16 KB A footprint stays inside
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
-  uint64_t state;
-  asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(state) : "r"(smem_u32(mbar)) : "memory");
-  (void)state;
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(mbar)) : "memory");
 }
 
 __device__ __forceinline__ void mbar_init_n(uint64_t* mbar, int n) {
@@ -503,7 +530,7 @@ __global__ void __launch_bounds__(kP2sThreads, 2)
   float* sm = (float*)(((uintptr_t)smem_dyn + 127) & ~(uintptr_t)127);
   __shared__ __align__(8) uint64_t full[kGroups];
   __shared__ __align__(8) uint64_t empty[kGroups];
-  __shared__ __align__(8) uint64_t done;
+  __shared__ __align__(8) uint64_t accf[2];
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
 
@@ -511,13 +538,14 @@ __global__ void __launch_bounds__(kP2sThreads, 2)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int mv = u.m - u.row0, nv = min(64, u.n - u.col0);  // mv <= 32 by construction
   const int n16 = (nv + 15) & ~15;
-  if (warp == kGroups * 2) tmem_alloc(&tmem_slot, 64);
+  if (warp == kGroups * 2) tmem_alloc(&tmem_slot, 128);
   if (tid == 0) {
     for (int g = 0; g < kGroups; ++g) {
       mbar_init_n(&full[g], kGroupThreads);
       mbar_init_n(&empty[g], 1);
     }
-    mbar_init_n(&done, 1);
+    mbar_init_n(&accf[0], 1);
+    mbar_init_n(&accf[1], 1);
     asm volatile("fence.mbarrier_init.release.cluster;");
     abort_flag = 0;
   }
@@ -549,47 +577,80 @@ __global__ void __launch_bounds__(kP2sThreads, 2)
         mbar_arrive(&full[g]);
       }
     }
-  } else if (lane == 0) {
-    // ---- MMA issue: steps in order
+  } else {
+    // ---- warp 8: lane 0 issues the MMAs of segment j into accumulator j & 1; the warp
+    // then adds segment j - 1 (accumulator rows 0..31 = TMEM lanes 0..31) to its
+    // registers while the tensor core works on segment j
     const uint32_t idesc = idesc_tf32(n16);
-    int s = 0;
-    for (int t = u.t_begin; t < u.t_end && !abort_flag; ++t) {
+    float acc[64];
+#pragma unroll
+    for (int i = 0; i < 64; ++i) acc[i] = 0.0f;
+    uint32_t ph_acc[2] = {0, 0};
+    auto drain = [&](int a) {
+      int ok = 1;
+      if (lane == 0) ok = mbar_wait_or_abort(&accf[a], ph_acc[a], &abort_flag);
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) return;
+      ph_acc[a] ^= 1;
+      asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        if (16 * i < n16) {
+          float v[16];
+          tmem_ld16(tmem + (uint32_t)(a * 64 + 16 * i), v);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) acc[16 * i + j] += v[j];
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncwarp();
+    };
+    int s = 0, seg = 0, in_seg = 0;
+    bool stop = false;
+    for (int t = u.t_begin; t < u.t_end && !stop; ++t) {
       const int K = tasks[t].K;
       const int nch = (K + 31) >> 5;
       for (int ch = 0; ch < nch; ++ch, ++s) {
         const int g = s & (kGroups - 1);
-        if (!mbar_wait_or_abort(&full[g], (s / kGroups) & 1, &abort_flag)) break;
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        const int kvalid = min(32, K - ch * 32), kpad = (kvalid + 7) & ~7;
-        float* Ah = sm + g * kP2sStageF;
-        mma_chunk(tmem, Ah, Ah + kSA, Ah + 2 * kSA, Ah + 2 * kSA + kSB, kpad, idesc, s == 0);
-        mma_commit(&empty[g]);
+        if (lane == 0) {
+          if (mbar_wait_or_abort(&full[g], (s / kGroups) & 1, &abort_flag)) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const int kvalid = min(32, K - ch * 32), kpad = (kvalid + 7) & ~7;
+            float* Ah = sm + g * kP2sStageF;
+            mma_chunk(tmem + (uint32_t)((seg & 1) * 64), Ah, Ah + kSA, Ah + 2 * kSA, Ah + 2 * kSA + kSB, kpad,
+                      idesc, in_seg == 0);
+            mma_commit(&empty[g]);
+          }
+        }
+        if (__shfl_sync(0xffffffffu, (int)abort_flag, 0)) { stop = true; break; }
+        if (++in_seg == kSegSteps) {
+          if (lane == 0) mma_commit(&accf[seg & 1]);
+          __syncwarp();
+          if (seg > 0) drain((seg - 1) & 1);
+          ++seg;
+          in_seg = 0;
+        }
       }
-      if (abort_flag) break;
     }
-    if (!abort_flag) mma_commit(&done);
-  }
-  __syncthreads();
-  if (tid == 0 && !abort_flag) mbar_wait_or_abort(&done, 0, &abort_flag);
-  __syncthreads();
-  if (!abort_flag && (warp == 0 || warp == 4)) {
-    // accumulator rows 0..31 sit in TMEM lanes 0..31 (warps 0 and 4 reach them)
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    const int h = warp >> 2;
-    for (int c0 = h * 16; c0 < n16; c0 += 32) {
-      float v[16];
-      tmem_ld16(tmem + (uint32_t)c0, v);
-      if (lane < mv) {
+    if (!stop && !__shfl_sync(0xffffffffu, (int)abort_flag, 0)) {
+      if (in_seg > 0) {
+        if (lane == 0) mma_commit(&accf[seg & 1]);
+        __syncwarp();
+        if (seg > 0) drain((seg - 1) & 1);
+        ++seg;
+      }
+      if (seg > 0) drain((seg - 1) & 1);
+      if (!__shfl_sync(0xffffffffu, (int)abort_flag, 0) && lane < mv) {
         double* yr = u.y + (size_t)(u.row0 + lane) * u.ldy + u.col0;
 #pragma unroll
-        for (int j = 0; j < 16; ++j)
-          if (c0 + j < nv) atomicAdd(yr + c0 + j, (double)v[j]);
+        for (int j = 0; j < 64; ++j)
+          if (j < nv) atomicAdd(yr + j, (double)acc[j]);
       }
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  if (warp == kGroups * 2) tmem_free(tmem, 64);
+  if (warp == kGroups * 2) tmem_free(tmem, 128);
 }
 
 // ------------------------------------------------------------------ conversions
