@@ -141,6 +141,12 @@ def allreduce_sum(v, world):
     return float(t.item())
 
 
+def aggregate(flops, ms, world):
+    """Whole-job throughput of replicas: all ranks' flops over the slowest rank's time."""
+    t_max = allreduce_max(ms, world)
+    return allreduce_sum(flops, world) / (t_max * 1e-3) / 1e9, t_max
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     return json.load(open(path)) if os.path.exists(path) else {}
@@ -324,8 +330,7 @@ def run_gb300(args):
     # headline path
     clk = ClockSampler(torch.cuda.current_device())
     ms, delta, energies, clocks, d = timed_steps(ctx, center, D, args.steps, args.warmup, 1, clk, world)
-    t_max = allreduce_max(ms, world)
-    value = allreduce_sum(delta["matvec_flops"], world) / (t_max * 1e-3) / 1e9
+    value, t_max = aggregate(delta["matvec_flops"], ms, world)
     launches = int(delta["kernels_launched"])
     rates = matvec_kernel_rates(delta)
     roof = roofline_mixed(delta, peaks) if args.precision == 1 else roofline_fp64(delta, peak64)
