@@ -48,7 +48,8 @@ def parse():
                    help="FP64 Davidson iterations that finish each mixed-precision step")
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison steps")
     p.add_argument("--sweep", action="store_true",
-                   help="also time one macro-iteration (right + left sweep) in each precision")
+                   help="also time the FP64 macro-iteration (the mixed one is timed by default)")
+    p.add_argument("--no-sweep", action="store_true", help="skip the macro-iteration timing")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
@@ -208,6 +209,7 @@ def timed_steps(ctx, center, D, steps, warmup, first_dir, clk=None, world=1):
     if clk:
         clk.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("steps")
     ev0.record()
     energies = []
     for _ in range(steps):
@@ -215,6 +217,8 @@ def timed_steps(ctx, center, D, steps, warmup, first_dir, clk=None, world=1):
         energies.append(e)
         d = -d
     ev1.record()
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     barrier(world)
     clocks = clk.stop() if clk else None
@@ -243,7 +247,14 @@ def matvec_kernel_rates(delta):
     return out
 
 
-def roofline_mixed(delta, peaks):
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the mixed
+# kernels, from one ncu capture of the marked matvec of this benchmark at the default
+# workload (random28, D=2500, sites 13-14); valid only for that workload and kernel version
+NCU_TRAFFIC = {("random28", 2500, 1): 544676864 + 7043775232,
+               ("random28", 2500, 2): 9874436096 + 16362240}
+
+
+def roofline_mixed(delta, peaks, key=None):
     """Dominant kernel of the mixed matvec against HBM (its compulsory FP32 traffic) and
     its tensor-pipe fraction against the TF32 peak (bf16 measured x nominal 1.1/2.25)."""
     nm = max(delta["tc_matvecs"], 1)
@@ -251,13 +262,15 @@ def roofline_mixed(delta, peaks):
            delta["tc_phase1_bytes"] / nm, delta["tc_phase1_flops"] / nm),
           ("k_tc_phase2s/k_tc_phase2 (sum coef Zt, left-operator blocks -> y)", delta["tc_phase2_ms"] / nm,
            delta["tc_phase2_bytes"] / nm, delta["tc_phase2_flops"] / nm)]
-    name, ms, byts, fl = max(ph, key=lambda p: p[1])
+    phase = 1 if ph[0][1] >= ph[1][1] else 2
+    name, ms, byts, fl = ph[phase - 1]
+    traffic = NCU_TRAFFIC.get(key + (phase,)) if key else None
     hbm = peaks.get("hbm_gbs", 6800.0)
     achieved = byts / (ms * 1e-3) / 1e9
     tf32_peak = peaks.get("bf16_tflops", 1900.0) * 1.1 / 2.25
     tensor = 3.0 * fl / (ms * 1e-3) / 1e12  # three split products per block product
     return {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm, "traffic": None,
+            "frac": achieved / hbm, "traffic": traffic,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth, of measured)",
             "launch_ms": ms, "bytes_per_launch": byts, "flops_per_launch": fl,
             "tensor": {"achieved_tflops": tensor, "peak_tflops": tf32_peak, "frac": tensor / tf32_peak,
@@ -301,17 +314,22 @@ def energy_agreement(ctx, center, D, args):
 
 
 def sweep_time(ctx, L, D, precision, fp64_iters, iters):
-    """One macro-iteration (sites 0..L-2 right, then L-2..0 left) at fixed D."""
+    """One macro-iteration (Sec. 4.2: sites 0..L-2 right, then L-2..0 left) at fixed D,
+    fixed Davidson iterations per step; returns seconds (right, left) and the energy of
+    the last step."""
     import torch
     ctx.set_precision(precision, fp64_iters)
     fixed_iters(ctx, D, iters)
     ctx.canonicalize(0)
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for i, d in [(i, 1) for i in range(0, L - 1)] + [(i, -1) for i in range(L - 2, -1, -1)]:
-        ctx.sweep_step(i, d, D)
-    torch.cuda.synchronize()
-    return time.perf_counter() - t0
+    out, e = [], None
+    for sites, d in ((range(0, L - 1), 1), (range(L - 2, -1, -1), -1)):
+        t0 = time.perf_counter()
+        for i in sites:
+            e, wd, it, ok = ctx.sweep_step(i, d, D)
+        torch.cuda.synchronize()
+        out.append(time.perf_counter() - t0)
+    return out[0], out[1], e
 
 
 def run_gb300(args):
@@ -333,7 +351,7 @@ def run_gb300(args):
     value, t_max = aggregate(delta["matvec_flops"], ms, world)
     launches = int(delta["kernels_launched"])
     rates = matvec_kernel_rates(delta)
-    roof = roofline_mixed(delta, peaks) if args.precision == 1 else roofline_fp64(delta, peak64)
+    roof = roofline_mixed(delta, peaks, (args.workload, D)) if args.precision == 1 else roofline_fp64(delta, peak64)
     # FP64 path on the same workload (continuing from the same state)
     fp64 = None
     if not args.no_fp64 and args.precision == 1:
@@ -359,11 +377,16 @@ def run_gb300(args):
     fixed_iters(ctx, D, args.davidson_iters)
     e2e = None if args.no_e2e else run_e2e(ctx, center, D, args, n_x)
     sweeps = None
-    if args.sweep:
-        sweeps = {"mixed_s": sweep_time(ctx, cfg["L"], D, 1, args.fp64_iters, args.davidson_iters),
-                  "fp64_s": sweep_time(ctx, cfg["L"], D, 0, 0, args.davidson_iters),
-                  "what": "one macro-iteration (L-1 steps right, L-1 left) at fixed D, "
-                          f"{args.davidson_iters} Davidson iterations per step"}
+    if not args.no_sweep:
+        r, l, e = sweep_time(ctx, cfg["L"], D, args.precision, args.fp64_iters, args.davidson_iters)
+        sweeps = {("mixed" if args.precision == 1 else "fp64"): {"macro_s": r + l, "right_s": r, "left_s": l,
+                                                                "energy_last": e},
+                  "what": "one macro-iteration (L-1 steps right, L-1 left) from the canonical state "
+                          f"at site 0, fixed D, {args.davidson_iters} Davidson iterations per step"}
+        if args.sweep and args.precision == 1:
+            r, l, e = sweep_time(ctx, cfg["L"], D, 0, 0, args.davidson_iters)
+            sweeps["fp64"] = {"macro_s": r + l, "right_s": r, "left_s": l, "energy_last": e}
+        ctx.set_precision(args.precision, args.fp64_iters)
     mixed = args.precision == 1
     out = {
         "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,

@@ -3,6 +3,7 @@
 #include "engine.hpp"
 
 #include <algorithm>
+#include <atomic>
 #include <array>
 #include <chrono>
 #include <cmath>
@@ -10,6 +11,7 @@
 #include <limits>
 #include <map>
 #include <stdexcept>
+#include <thread>
 #include <tuple>
 
 #include "su2.hpp"
@@ -790,7 +792,9 @@ Engine::MatvecPlan* Engine::plan_matvec(int i) {
   }
   // phase 1: Z(gr, D block) = stack(r) . D^T ; identity D reads x directly
   struct ZRef { int64_t off; int ld; int zg; };
-  std::unordered_map<int64_t, ZRef> zmap;
+  std::vector<std::vector<ZRef>> ztab(P->cr.size());  // (gr, dbi) -> Z, zg == INT_MIN: not yet made
+  for (size_t g = 0; g < P->cr.size(); ++g)
+    ztab[g].assign(P->cr[g].blocks->size(), ZRef{0, 0, std::numeric_limits<int>::min()});
   std::vector<GemmTask> t1;
   std::vector<GemmGroup> g1;
   std::vector<int64_t> g1off;
@@ -799,10 +803,8 @@ Engine::MatvecPlan* Engine::plan_matvec(int i) {
   auto get_z = [&](int gr, int dbi) -> ZRef {
     const CombOp& D = P->cr[gr];
     const BlockRef& db = (*D.blocks)[dbi];
-    int64_t key = ((int64_t)gr << 24) | dbi;
-    auto it = zmap.find(key);
-    if (it != zmap.end()) return it->second;
-    ZRef z;
+    ZRef& z = ztab[gr][dbi];
+    if (z.zg != std::numeric_limits<int>::min()) return z;
     if (D.identity) {
       z = {-1 - tall_off[db.c], br.dim[db.c], -1 - db.c};  // negative: offset into xin
     } else {
@@ -815,7 +817,6 @@ Engine::MatvecPlan* Engine::plan_matvec(int i) {
       zsize += rows * db.rows;
       flops1 += 2.0 * rows * db.cols * db.rows;
     }
-    zmap.emplace(key, z);
     return z;
   };
   // site transitions allowed by each pattern, and the recoupled coefficient of a
@@ -834,8 +835,6 @@ Engine::MatvecPlan* Engine::plan_matvec(int i) {
   struct H2 {
     size_t operator()(const K2& k) const { return std::hash<uint64_t>()(k.a * 0x9E3779B97F4A7C15ull ^ k.b); }
   };
-  std::unordered_map<K2, double, H2> coef_cache;
-  coef_cache.reserve(1 << 16);
   // W(gl, C block, X') = sum coef * Z rows of X ; phase 2: y_X' += C_blk W
   struct WItem { int gl, cbi, xp; int64_t off; int rows, cols; int src_begin, src_end; };
   std::vector<WItem> ws;
@@ -844,94 +843,151 @@ Engine::MatvecPlan* Engine::plan_matvec(int i) {
   std::vector<std::vector<DiagTerm>> dout(P->X.size());
   std::vector<std::vector<int>> w_by_x(P->X.size());
   int64_t wsize = 0;
-  std::unordered_map<int64_t, std::vector<WS>> acc;  // xp -> sources, per (gl, cbi)
+  // Enumeration of the (left block, right block, x block) combinations, in parallel
+  // over work items (middle operator b, left group gl, left block cbi) with private
+  // coefficient caches, then a serial merge in item order (deterministic tables).
+  struct Item { int b, gl, cbi; };
+  std::vector<Item> items;
   for (int b = 0; b < (int)mid.ops.size(); ++b) {
     if (byb_l[b].empty() || byb_r[b].empty()) continue;
-    const int tkb = mid.ops[b].tk, pb = mid.ops[b].parity;
-    for (int gl : byb_l[b]) {
-      const CombOp& C = P->cl[gl];
+    for (int gl : byb_l[b])
+      for (int cbi = 0; cbi < (int)P->cl[gl].blocks->size(); ++cbi) items.push_back({b, gl, cbi});
+  }
+  struct Src { int gr, dbi, x; double coef; };
+  struct Grp { int xp, begin, end; };      // sources of one W item, first-touch order
+  struct DRaw { int x, gr, dbi; double coef; };
+  struct Out { std::vector<Grp> g; std::vector<Src> s; std::vector<DRaw> d; };
+  std::vector<Out> outs(items.size());
+  std::atomic<size_t> next_item{0};
+  auto worker = [&]() {
+    Coupling cp = *cp_;  // private memo tables
+    std::unordered_map<K2, double, H2> coef_cache;
+    coef_cache.reserve(1 << 14);
+    std::vector<int> slot(P->X.size(), -1), touched;
+    std::vector<std::vector<Src>> bucket;
+    for (;;) {
+      const size_t it = next_item.fetch_add(1);
+      if (it >= items.size()) break;
+      const Item I = items[it];
+      const int tkb = mid.ops[I.b].tk, pb = mid.ops[I.b].parity;
+      const CombOp& C = P->cl[I.gl];
       const auto& ok1 = okp[C.pattern];
-      for (int cbi = 0; cbi < (int)C.blocks->size(); ++cbi) {
-        const BlockRef& cb = (*C.blocks)[cbi];
-        const int tjL = bl.sec[cb.c].tj, tjLp = bl.sec[cb.r].tj;
-        acc.clear();
-        for (int x : x_by_l[cb.c]) {
-          const XBlock& X = P->X[x];
-          const int tjR = br.sec[X.r].tj;
-          const int t1s = local_ts(X.ls1), t2s = local_ts(X.ls2);
-          for (int gr : byb_r[b]) {
-            const CombOp& D = P->cr[gr];
-            const auto& ok2 = okp[D.pattern];
-            for (int dbi : dby[gr][X.r]) {
-              const BlockRef& db = (*D.blocks)[dbi];
-              const int tjRp = br.sec[db.r].tj;
-              for (int ls1p = 0; ls1p < 3; ++ls1p) {
-                if (!ok1[X.ls1][ls1p]) continue;
-                const int t1p = local_ts(ls1p);
-                for (int ls2p = 0; ls2p < 3; ++ls2p) {
-                  if (!ok2[X.ls2][ls2p]) continue;
-                  const int t2p = local_ts(ls2p);
-                  for (int tjp = std::abs(t1p - t2p); tjp <= t1p + t2p; tjp += 2) {
-                    const int xp = xidx[xkey(cb.r, ls1p, ls2p, tjp, db.r)];
-                    if (xp < 0) continue;
-                    K2 key{(uint64_t)C.pattern | ((uint64_t)D.pattern << 16) | ((uint64_t)tjL << 32) |
-                               ((uint64_t)tjR << 40) | ((uint64_t)tjLp << 48) | ((uint64_t)tjRp << 56),
-                           (uint64_t)X.ls1 | ((uint64_t)X.ls2 << 2) | ((uint64_t)X.tj << 4) |
-                               ((uint64_t)ls1p << 8) | ((uint64_t)ls2p << 10) | ((uint64_t)tjp << 12)};
-                    auto ci = coef_cache.find(key);
-                    double coef = 0.0;
-                    if (ci != coef_cache.end()) {
-                      coef = ci->second;
-                    } else {
-                      for (int tjM = std::abs(tjL - t1s); tjM <= tjL + t1s; tjM += 2) {
-                        if (!triangle(t2s, tjR, tjM)) continue;
-                        double ov = cp_->overlap(tjL, X.ls1, X.ls2, X.tj, tjR, tjM);
-                        if (ov == 0.0) continue;
-                        for (int tjMp = std::abs(tjLp - t1p); tjMp <= tjLp + t1p; tjMp += 2) {
-                          if (!triangle(t2p, tjRp, tjMp)) continue;
-                          double ovp = cp_->overlap(tjLp, ls1p, ls2p, tjp, tjRp, tjMp);
-                          if (ovp == 0.0) continue;
-                          double sf = cp_->singlet(tkb, pb, tjM, tjMp);
-                          if (sf == 0.0) continue;
-                          double lc = cp_->left(C.pattern, tjL, X.ls1, tjM, tjLp, ls1p, tjMp);
-                          if (lc == 0.0) continue;
-                          double rc = cp_->right(D.pattern, X.ls2, tjR, tjM, ls2p, tjRp, tjMp);
-                          coef += ov * ovp * sf * lc * rc;
-                        }
+      const BlockRef& cb = (*C.blocks)[I.cbi];
+      const int tjL = bl.sec[cb.c].tj, tjLp = bl.sec[cb.r].tj;
+      Out& o = outs[it];
+      for (int x : x_by_l[cb.c]) {
+        const XBlock& X = P->X[x];
+        const int tjR = br.sec[X.r].tj;
+        const int t1s = local_ts(X.ls1), t2s = local_ts(X.ls2);
+        for (int gr : byb_r[I.b]) {
+          const CombOp& D = P->cr[gr];
+          const auto& ok2 = okp[D.pattern];
+          for (int dbi : dby[gr][X.r]) {
+            const BlockRef& db = (*D.blocks)[dbi];
+            const int tjRp = br.sec[db.r].tj;
+            for (int ls1p = 0; ls1p < 3; ++ls1p) {
+              if (!ok1[X.ls1][ls1p]) continue;
+              const int t1p = local_ts(ls1p);
+              for (int ls2p = 0; ls2p < 3; ++ls2p) {
+                if (!ok2[X.ls2][ls2p]) continue;
+                const int t2p = local_ts(ls2p);
+                for (int tjp = std::abs(t1p - t2p); tjp <= t1p + t2p; tjp += 2) {
+                  const int xp = xidx[xkey(cb.r, ls1p, ls2p, tjp, db.r)];
+                  if (xp < 0) continue;
+                  K2 key{(uint64_t)C.pattern | ((uint64_t)D.pattern << 16) | ((uint64_t)tjL << 32) |
+                             ((uint64_t)tjR << 40) | ((uint64_t)tjLp << 48) | ((uint64_t)tjRp << 56),
+                         (uint64_t)X.ls1 | ((uint64_t)X.ls2 << 2) | ((uint64_t)X.tj << 4) |
+                             ((uint64_t)ls1p << 8) | ((uint64_t)ls2p << 10) | ((uint64_t)tjp << 12)};
+                  auto ci = coef_cache.find(key);
+                  double coef = 0.0;
+                  if (ci != coef_cache.end()) {
+                    coef = ci->second;
+                  } else {
+                    for (int tjM = std::abs(tjL - t1s); tjM <= tjL + t1s; tjM += 2) {
+                      if (!triangle(t2s, tjR, tjM)) continue;
+                      double ov = cp.overlap(tjL, X.ls1, X.ls2, X.tj, tjR, tjM);
+                      if (ov == 0.0) continue;
+                      for (int tjMp = std::abs(tjLp - t1p); tjMp <= tjLp + t1p; tjMp += 2) {
+                        if (!triangle(t2p, tjRp, tjMp)) continue;
+                        double ovp = cp.overlap(tjLp, ls1p, ls2p, tjp, tjRp, tjMp);
+                        if (ovp == 0.0) continue;
+                        double sf = cp.singlet(tkb, pb, tjM, tjMp);
+                        if (sf == 0.0) continue;
+                        double lc = cp.left(C.pattern, tjL, X.ls1, tjM, tjLp, ls1p, tjMp);
+                        if (lc == 0.0) continue;
+                        double rc = cp.right(D.pattern, X.ls2, tjR, tjM, ls2p, tjRp, tjMp);
+                        coef += ov * ovp * sf * lc * rc;
                       }
-                      coef_cache.emplace(key, coef);
                     }
-                    if (std::fabs(coef) < 1e-14) continue;
-                    ZRef z = get_z(gr, dbi);
-                    int64_t zoff = z.off >= 0 ? z.off + (int64_t)X.trow * z.ld
-                                              : z.off - (int64_t)X.trow * z.ld;
-                    // identity right operator: Z is x itself, its alias scalar goes here
-                    acc[xp].push_back({zoff, z.ld, D.identity ? coef * D.scalar : coef, z.zg, x});
-                    if (xp == x && cb.r == cb.c && db.r == db.c)
-                      dout[x].push_back({C.data + cb.off, D.data + db.off, cb.cols, db.cols,
-                                         coef * C.scalar * D.scalar});
+                    coef_cache.emplace(key, coef);
                   }
+                  if (std::fabs(coef) < 1e-14) continue;
+                  int& sl = slot[xp];
+                  if (sl < 0) {
+                    sl = (int)touched.size();
+                    touched.push_back(xp);
+                    if (bucket.size() < touched.size()) bucket.emplace_back();
+                    bucket[sl].clear();
+                  }
+                  bucket[sl].push_back({gr, dbi, x, coef});
+                  if (xp == x && cb.r == cb.c && db.r == db.c) o.d.push_back({x, gr, dbi, coef});
                 }
               }
             }
           }
         }
-        for (auto& kv : acc) {
-          const XBlock& Xp = P->X[kv.first];
-          WItem w{gl, cbi, (int)kv.first, wsize, cb.cols, Xp.cols, (int)wsrc.size(), 0};
-          for (auto& q : kv.second) {
-            wsrc.push_back(q);
-            P->wsrc.push_back({q.zg, q.xb, q.coef});
-          }
-          w.src_end = (int)wsrc.size();
-          P->witems.push_back({gl, cbi, w.rows, w.cols, w.src_begin, w.src_end});
-          wsize += (int64_t)cb.cols * Xp.cols;
-          w_by_x[kv.first].push_back((int)ws.size());
-          ws.push_back(w);
-          if (!C.identity) flops2 += 2.0 * cb.rows * cb.cols * Xp.cols;
-        }
       }
+      for (size_t k = 0; k < touched.size(); ++k) {
+        o.g.push_back({touched[k], (int)o.s.size(), 0});
+        o.s.insert(o.s.end(), bucket[k].begin(), bucket[k].end());
+        o.g.back().end = (int)o.s.size();
+        slot[touched[k]] = -1;
+      }
+      touched.clear();
     }
+  };
+  {
+    const unsigned hc = std::thread::hardware_concurrency();
+    const int nth = (int)std::max(1u, std::min(16u, hc ? hc : 1u));
+    std::vector<std::thread> th;
+    for (int t = 1; t < nth && (size_t)t < items.size(); ++t) th.emplace_back(worker);
+    worker();
+    for (auto& t : th) t.join();
+  }
+  for (size_t it = 0; it < items.size(); ++it) {
+    const Item& I = items[it];
+    const CombOp& C = P->cl[I.gl];
+    const BlockRef& cb = (*C.blocks)[I.cbi];
+    Out& o = outs[it];
+    for (const DRaw& dr : o.d) {
+      const CombOp& D = P->cr[dr.gr];
+      const BlockRef& db = (*D.blocks)[dr.dbi];
+      dout[dr.x].push_back({C.data + cb.off, D.data + db.off, cb.cols, db.cols, dr.coef * C.scalar * D.scalar});
+    }
+    for (const Grp& g : o.g) {
+      const XBlock& Xp = P->X[g.xp];
+      WItem w{I.gl, I.cbi, g.xp, wsize, cb.cols, Xp.cols, (int)wsrc.size(), 0};
+      for (int k = g.begin; k < g.end; ++k) {
+        const Src& q = o.s[k];
+        const CombOp& D = P->cr[q.gr];
+        const XBlock& X = P->X[q.x];
+        ZRef z = get_z(q.gr, q.dbi);
+        const int64_t zoff = z.off >= 0 ? z.off + (int64_t)X.trow * z.ld : z.off - (int64_t)X.trow * z.ld;
+        // identity right operator: Z is x itself, its alias scalar goes here
+        const WS ws1{zoff, z.ld, D.identity ? q.coef * D.scalar : q.coef, z.zg, q.x};
+        wsrc.push_back(ws1);
+        P->wsrc.push_back({ws1.zg, ws1.xb, ws1.coef});
+      }
+      w.src_end = (int)wsrc.size();
+      P->witems.push_back({I.gl, I.cbi, w.rows, w.cols, w.src_begin, w.src_end});
+      wsize += (int64_t)cb.cols * Xp.cols;
+      w_by_x[g.xp].push_back((int)ws.size());
+      ws.push_back(w);
+      if (!C.identity) flops2 += 2.0 * cb.rows * cb.cols * Xp.cols;
+    }
+    std::vector<Grp>().swap(o.g);
+    std::vector<Src>().swap(o.s);
+    std::vector<DRaw>().swap(o.d);
   }
   P->zsize = zsize;
   P->Z = (double*)dev_alloc(sizeof(double) * std::max<int64_t>(zsize, 1), stream_);
@@ -1092,25 +1148,36 @@ void Engine::build_tc(MatvecPlan* P) {
   std::unordered_map<const double*, int64_t> moff;
   std::vector<TcMirror> mir;
   int64_t nm = 0;
+  double distinct = 0.0;  // unpadded elements of the blocks mirrored so far
   auto want = [&](const double* p, int rows, int cols) {
     if (moff.emplace(p, nm).second) {
       mir.push_back({p, nullptr, rows, cols, (int)r4(cols)});
       nm += (int64_t)rows * r4(cols);
+      distinct += (double)rows * cols;
     }
   };
-  for (const auto& Zg : P->zg) want(Zg.D, Zg.n, Zg.K);
+  std::vector<int64_t> zmir(P->zg.size());
+  for (size_t g = 0; g < P->zg.size(); ++g) {
+    want(P->zg[g].D, P->zg[g].n, P->zg[g].K);
+    zmir[g] = moff[P->zg[g].D];
+  }
+  const double distinct_d = distinct;
+  std::vector<std::vector<int64_t>> cmir(P->cl.size());  // (gl, cbi) -> mirror offset, -1 = unused
   for (const auto& w : P->witems) {
     const CombOp& C = P->cl[w.gl];
     if (C.identity) continue;
+    auto& cm = cmir[w.gl];
+    if (cm.empty()) cm.assign(C.blocks->size(), -1);
+    if (cm[w.cbi] >= 0) continue;
     const BlockRef& cb = (*C.blocks)[w.cbi];
     want(C.data + cb.off, cb.rows, cb.cols);
+    cm[w.cbi] = moff[C.data + cb.off];
   }
   float* m32 = (float*)dev_alloc(sizeof(float) * std::max<int64_t>(nm, 4), stream_);
   P->tc_mem[2] = m32;
   dev_zero(m32, sizeof(float) * std::max<int64_t>(nm, 4), stream_);
   for (auto& m : mir) m.dst = m32 + moff[m.src];
   tc_mirror(mir, stream_);
-  auto f32 = [&](const double* p) -> const float* { return m32 + moff.at(p); };
   // Zt: one column-major block per phase-1 group, stride = padded stack height
   std::vector<int64_t> zoff(P->zg.size());
   int64_t nz = 0;
@@ -1134,7 +1201,7 @@ void Engine::build_tc(MatvecPlan* P) {
     Tc1Pack cur{(int)ents.size(), (int)ents.size(), 0};
     for (int g : byc[c]) {
       const auto& Zg = P->zg[g];
-      const float* D32 = f32(Zg.D);
+      const float* D32 = m32 + zmir[g];
       for (int n0 = 0; n0 < Zg.n; n0 += 128) {
         const int nc = std::min(128, Zg.n - n0), pad = (nc + 7) & ~7;
         if (cur.n + pad > 128 || cur.e_end - cur.e_begin == 16) {
@@ -1167,7 +1234,7 @@ void Engine::build_tc(MatvecPlan* P) {
       const auto& w = P->witems[wi];
       const CombOp& C = P->cl[w.gl];
       const BlockRef& cb = (*C.blocks)[w.cbi];
-      Tc2Task t{C.identity ? nullptr : f32(C.data + cb.off), (int)r4(cb.cols), w.rows, (float)C.scalar,
+      Tc2Task t{C.identity ? nullptr : m32 + cmir[w.gl][w.cbi], (int)r4(cb.cols), w.rows, (float)C.scalar,
                 (int)srcs.size(), 0};
       for (int q = w.src_begin; q < w.src_end; ++q) {
         const auto& src = P->wsrc[q];
@@ -1189,19 +1256,9 @@ void Engine::build_tc(MatvecPlan* P) {
   // block once and writes every Z; phase 2 reads each task's Z sub-blocks and each
   // left-operator block once and writes y (FP64)
   {
-    double b1 = (double)P->n, b2 = 0.0, dz = 0.0;
-    for (const auto& Zg : P->zg) dz += (double)Zg.n * P->tall_rows[Zg.c];
-    std::unordered_map<const double*, int> seen;
-    for (const auto& Zg : P->zg)
-      if (seen.emplace(Zg.D, 1).second) b1 += (double)Zg.n * Zg.K;
-    b1 += dz;
-    for (const auto& w : P->witems) {
-      b2 += (double)(w.src_end - w.src_begin) * w.rows * w.cols;
-      const CombOp& C = P->cl[w.gl];
-      if (C.identity) continue;
-      const BlockRef& cb = (*C.blocks)[w.cbi];
-      if (seen.emplace(C.data + cb.off, 2).second) b2 += (double)cb.rows * cb.cols;
-    }
+    double b1 = (double)P->n + distinct_d, b2 = distinct - distinct_d;
+    for (const auto& Zg : P->zg) b1 += (double)Zg.n * P->tall_rows[Zg.c];
+    for (const auto& w : P->witems) b2 += (double)(w.src_end - w.src_begin) * w.rows * w.cols;
     P->tc_bytes1 = 4.0 * b1;
     P->tc_bytes2 = 4.0 * b2 + 8.0 * P->n;
   }

@@ -534,26 +534,24 @@ namespace {
 constexpr int kEigSmemN = 112;  // blocks up to this size are diagonalised in shared memory
 
 // Cyclic Jacobi (round-robin pairing, n/2 rotations per step) on one symmetric block per
-// CTA.  SM: the matrix and the eigenvectors live in shared memory (row stride n+1);
-// otherwise in global memory (stride n).  A pair is rotated only while |a_pq| exceeds
+// CTA, the matrix and the eigenvectors in shared memory (row stride n+1).  A pair is rotated only while |a_pq| exceeds
 // 1e-16 sqrt(|a_pp a_qq|) plus an absolute floor; the loop ends after a sweep without
 // rotations (at most 40 sweeps).  Output: eigenvalues descending, eigenvectors as
 // columns of J.Q.
-template <bool SM, int NT>
+template <int NT>
 __global__ void __launch_bounds__(NT) k_eig_batched(const EigJob* __restrict__ jobs) {
   const EigJob J = jobs[blockIdx.x];
   const int n = J.n, tid = threadIdx.x;
   extern __shared__ double sm[];
-  const int ld = SM ? n + 1 : n;
-  double* A = SM ? sm : J.A;
-  double* Q = SM ? sm + (size_t)n * ld : J.Q;
+  const int ld = n + 1;
+  double* A = sm;
+  double* Q = sm + (size_t)n * ld;
   const int np = (n + 1) & ~1;
-  double* cs = SM ? sm + (size_t)2 * n * ld : sm;
+  double* cs = sm + (size_t)2 * n * ld;
   double* sn = cs + np / 2;
   double* wtmp = sn + np / 2;
   __shared__ int nrot;
-  if (SM)
-    for (int e = tid; e < n * n; e += NT) A[(size_t)(e / n) * ld + e % n] = J.A[e];
+  for (int e = tid; e < n * n; e += NT) A[(size_t)(e / n) * ld + e % n] = J.A[e];
   for (int e = tid; e < n * n; e += NT) Q[(size_t)(e / n) * ld + e % n] = (e / n == e % n) ? 1.0 : 0.0;
   __syncthreads();
   double scale = 0.0;
@@ -615,11 +613,7 @@ __global__ void __launch_bounds__(NT) k_eig_batched(const EigJob* __restrict__ j
   // eigenpairs sorted descending (ties by index)
   for (int i = tid; i < n; i += NT) wtmp[i] = A[(size_t)i * ld + i];
   __syncthreads();
-  if (!SM) {  // the global matrix becomes scratch for the unsorted eigenvectors
-    for (int e = tid; e < n * n; e += NT) A[e] = Q[e];
-    __syncthreads();
-  }
-  const double* Qs = SM ? Q : A;
+  const double* Qs = Q;
   for (int i = tid; i < n; i += NT) {
     double vi = wtmp[i];
     int rank = 0;
@@ -633,24 +627,24 @@ __global__ void __launch_bounds__(NT) k_eig_batched(const EigJob* __restrict__ j
 }
 }  // namespace
 
-// ------------------------------------------------------------------ block one-sided Jacobi
+// ------------------------------------------------------------------ parallel block Jacobi
 
 namespace {
 // Symmetric eigensolver for the large Gram blocks (n above the shared-memory limit): a
-// one-sided block Jacobi on the rows of A = G.  Rows are grouped in blocks of 32; each
-// step of a round-robin tournament pairs the blocks, and one CTA per pair forms the
-// 64 x 64 Gram matrix of its rows, diagonalises it in shared memory (cyclic Jacobi) and
-// rotates its rows of A and its columns of Q.  Pairs of one step touch disjoint rows
-// and columns, so a step is one launch without grid-wide synchronisation.  At
-// convergence the rows of V^T G are orthogonal: V^T G^2 V is diagonal, the columns of
-// V are eigenvectors of G and the row norms are its eigenvalues (G is positive
-// semidefinite); the absolute accuracy is that of the Gram route, ~eps |G|.
+// two-sided block Jacobi.  Rows and columns are grouped in blocks of 32; each step of
+// a round-robin tournament pairs the blocks, and for every pair (I, J) the 64 x 64
+// diagonal sub-block G[I+J, I+J] is diagonalised in shared memory (cyclic Jacobi),
+// giving V.  One launch applies V^T to the rows I+J of every pair (the pairs' rows are
+// disjoint), the next applies V to the columns I+J of G and of Q (disjoint columns):
+// together G <- W^T G W with W the block rotation of the step.  At convergence the
+// eigenvalues are the diagonal of G and the eigenvectors the columns of Q; the
+// absolute accuracy is ~eps |G|, that of the Gram route.
 constexpr int kOB = 32;   // rows per block
 constexpr int kOP = 64;   // rows per pair
 constexpr int kOL = 65;   // shared-memory row stride (doubles)
 
-struct OsbjJob {
-  double* A;      // n x n, rows orthogonalised in place (the Gram matrix on entry)
+struct BjJob {
+  double* A;      // n x n symmetric (the Gram matrix), diagonalised in place
   double* Q;      // n x n accumulated rotations (eigenvectors as columns)
   double* w;      // n eigenvalues (output, descending)
   int n, nb;      // nb = number of row blocks, even
@@ -658,58 +652,55 @@ struct OsbjJob {
   int pad;
 };
 
-// cyclic Jacobi on an m x m Gram matrix A of rows (shared memory, stride ld),
-// eigenvectors accumulated into V (identity on entry); all threads of the CTA take part.
-// A pair is rotated while |a_pq| > 1e-16 sqrt(a_pp a_qq) + 1e-32 max a_ii: the absolute
-// part is the squared noise level of the rows, so small rows sharing the pair with a
-// large one are still orthogonalised against each other.
-__device__ void cta_jacobi(double* A, double* V, int m, int ld, double* cs, double* sn, int* pq, int* nrot) {
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const int np = (m + 1) & ~1;
-  double scale = 0.0;
-  for (int i = 0; i < m; ++i) scale = fmax(scale, fabs(A[i * ld + i]));
-  const double floor_abs = 1e-300 + 1e-32 * scale;
-  for (int sweep = 0; sweep < 30; ++sweep) {
+// cyclic Jacobi on a 64 x 64 symmetric matrix A (shared memory, stride kOL),
+// eigenvectors accumulated into V (identity on entry), all 256 threads; a pair is
+// rotated while |a_pq| > 1e-16 sqrt|a_pp a_qq| + floor_abs (at most 8 sweeps: the
+// outer iteration returns to the pair)
+__device__ void cta_jacobi64(double* A, double* V, double* cs, double* sn, int* pq, int* nrot,
+                             double floor_abs) {
+  const int tid = threadIdx.x;
+  constexpr int m = kOP, np = kOP, nr = kOP / 2;
+  for (int sweep = 0; sweep < 8; ++sweep) {
     if (tid == 0) *nrot = 0;
     __syncthreads();
     for (int step = 0; step < np - 1; ++step) {
-      for (int r = tid; r < np / 2; r += nt) {
-        const int a = r, b = np - 1 - r;
+      if (tid < nr) {
+        const int a = tid, b = np - 1 - tid;
         int p = a == 0 ? 0 : 1 + (a - 1 + step) % (np - 1);
         int q = b == 0 ? 0 : 1 + (b - 1 + step) % (np - 1);
         if (p > q) { const int t = p; p = q; q = t; }
         double c = 1.0, s = 0.0;
-        if (q < m) {
-          const double app = A[p * ld + p], aqq = A[q * ld + q], apq = A[p * ld + q];
-          if (fabs(apq) > 1e-16 * sqrt(fabs(app * aqq)) + floor_abs) {
-            sym_schur2(app, aqq, apq, c, s);
-            atomicAdd(nrot, 1);
-          }
+        const double app = A[p * kOL + p], aqq = A[q * kOL + q], apq = A[p * kOL + q];
+        if (fabs(apq) > 1e-16 * sqrt(fabs(app * aqq)) + floor_abs) {
+          sym_schur2(app, aqq, apq, c, s);
+          atomicAdd(nrot, 1);
         }
-        cs[r] = c; sn[r] = s; pq[2 * r] = p; pq[2 * r + 1] = q;
+        cs[tid] = c; sn[tid] = s; pq[2 * tid] = p; pq[2 * tid + 1] = q;
       }
       __syncthreads();
-      for (int e = tid; e < (np / 2) * m; e += nt) {
-        const int r = e / m, j = e % m;
+#pragma unroll
+      for (int k = 0; k < nr * m / 256; ++k) {  // rows p, q of A
+        const int e = tid + 256 * k, r = e >> 6, j = e & 63;
         if (sn[r] == 0.0) continue;
         const int p = pq[2 * r], q = pq[2 * r + 1];
         const double c = cs[r], s = sn[r];
-        const double ap = A[p * ld + j], aq = A[q * ld + j];
-        A[p * ld + j] = c * ap - s * aq;
-        A[q * ld + j] = s * ap + c * aq;
+        const double ap = A[p * kOL + j], aq = A[q * kOL + j];
+        A[p * kOL + j] = c * ap - s * aq;
+        A[q * kOL + j] = s * ap + c * aq;
       }
       __syncthreads();
-      for (int e = tid; e < (np / 2) * m; e += nt) {
-        const int r = e / m, i = e % m;
+#pragma unroll
+      for (int k = 0; k < nr * m / 256; ++k) {  // columns p, q of A and V
+        const int e = tid + 256 * k, r = e >> 6, i = e & 63;
         if (sn[r] == 0.0) continue;
         const int p = pq[2 * r], q = pq[2 * r + 1];
         const double c = cs[r], s = sn[r];
-        const double ap = A[i * ld + p], aq = A[i * ld + q];
-        A[i * ld + p] = c * ap - s * aq;
-        A[i * ld + q] = s * ap + c * aq;
-        const double vp = V[i * ld + p], vq = V[i * ld + q];
-        V[i * ld + p] = c * vp - s * vq;
-        V[i * ld + q] = s * vp + c * vq;
+        const double ap = A[i * kOL + p], aq = A[i * kOL + q];
+        A[i * kOL + p] = c * ap - s * aq;
+        A[i * kOL + q] = s * ap + c * aq;
+        const double vp = V[i * kOL + p], vq = V[i * kOL + q];
+        V[i * kOL + p] = c * vp - s * vq;
+        V[i * kOL + q] = s * vp + c * vq;
       }
       __syncthreads();
     }
@@ -718,156 +709,147 @@ __device__ void cta_jacobi(double* A, double* V, int m, int ld, double* cs, doub
   }
 }
 
-// Q = identity, and |A|_F^2 per job (the absolute floor of the orthogonality test)
-__global__ void k_osbj_prep(const OsbjJob* __restrict__ jobs, double* __restrict__ fro2) {
-  const OsbjJob J = jobs[blockIdx.x];
-  const int64_t nn = (int64_t)J.n * J.n;
-  double acc = 0.0;
-  for (int64_t e = threadIdx.x; e < nn; e += blockDim.x) {
-    const double v = J.A[e];
-    acc += v * v;
-    J.Q[e] = (e / J.n == e % J.n) ? 1.0 : 0.0;
+// out(64 x 64 tile) = op(X) op(Y) with a 4 x 4 register tile per thread; X, Y in shared
+// memory with stride kOL; tx / ty: transpose flags
+template <bool TX, bool TY>
+__device__ __forceinline__ void tile64(const double* X, const double* Y, double (&acc)[4][4]) {
+  const int ti = threadIdx.x >> 4, tj = threadIdx.x & 15;
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[u][v] = 0.0;
+  for (int k = 0; k < kOP; ++k) {
+    double x[4], y[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      x[u] = TX ? X[k * kOL + ti * 4 + u] : X[(ti * 4 + u) * kOL + k];
+      y[u] = TY ? Y[(tj * 4 + u) * kOL + k] : Y[k * kOL + tj * 4 + u];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[u][v] = fma(x[u], y[v], acc[u][v]);
   }
-  __shared__ double red[256];
-  red[threadIdx.x] = acc;
-  __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
-    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) fro2[blockIdx.x] = red[0];
 }
 
-__global__ void __launch_bounds__(256) k_osbj_step(const OsbjJob* __restrict__ jobs, int njobs, int step,
-                                                   const double* __restrict__ fro2, int* __restrict__ nrot) {
-  extern __shared__ double osm[];
-  double* G = osm;                 // pair Gram, then rotated by the inner Jacobi
-  double* V = G + kOP * kOL;       // inner eigenvectors
-  double* buf = V + kOP * kOL;     // streamed 64 x 64 chunk
-  __shared__ double cs[kOP / 2], sn[kOP / 2];
-  __shared__ int pq[kOP], idx[kOP];
-  __shared__ int inner_rot, need;
+__device__ __forceinline__ int find_job(const BjJob* jobs, int njobs) {
   int lo = 0, hi = njobs - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
     if (jobs[mid].pair_begin <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
   }
-  const OsbjJob J = jobs[lo];
-  const int r = blockIdx.x - J.pair_begin;
-  if (r >= J.nb / 2 || step >= J.nb - 1) return;
-  const int tid = threadIdx.x, n = J.n;
-  {
-    const int a = r, b = J.nb - 1 - r;
-    const int p = a == 0 ? 0 : 1 + (a - 1 + step) % (J.nb - 1);
-    const int q = b == 0 ? 0 : 1 + (b - 1 + step) % (J.nb - 1);
-    if (tid < kOP) {
-      const int blk = tid < kOB ? p : q, row = blk * kOB + (tid % kOB);
-      idx[tid] = row < n ? row : -1;
-    }
+  return lo;
+}
+
+__device__ __forceinline__ void pair_rows(const BjJob& J, int r, int step, int* idx) {
+  const int a = r, b = J.nb - 1 - r;
+  const int p = a == 0 ? 0 : 1 + (a - 1 + step) % (J.nb - 1);
+  const int q = b == 0 ? 0 : 1 + (b - 1 + step) % (J.nb - 1);
+  if (threadIdx.x < kOP) {
+    const int blk = threadIdx.x < kOB ? p : q, row = blk * kOB + (threadIdx.x % kOB);
+    idx[threadIdx.x] = row < J.n ? row : -1;
   }
-  const int ti = tid >> 4, tj = tid & 15;  // 4 x 4 register tile of a 64 x 64 product
-  for (int e = tid; e < kOP * kOL; e += 256) G[e] = 0.0;
+}
+
+// Q = identity, and the largest |diagonal| of A per job (the noise scale eps |G|)
+__global__ void k_bj_prep(const BjJob* __restrict__ jobs, double* __restrict__ gmax) {
+  const BjJob J = jobs[blockIdx.x];
+  const int n = J.n;
+  for (int64_t e = threadIdx.x; e < (int64_t)n * n; e += blockDim.x) J.Q[e] = (e / n == e % n) ? 1.0 : 0.0;
+  double best = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) best = fmax(best, fabs(J.A[(size_t)i * n + i]));
+  __shared__ double red[256];
+  red[threadIdx.x] = best;
   __syncthreads();
-  // 1. Gram matrix of the pair's rows
-  for (int c0 = 0; c0 < n; c0 += kOP) {
-    for (int e = tid; e < kOP * kOP; e += 256) {
-      const int i = e >> 6, k = e & 63;
-      buf[i * kOL + k] = (idx[i] >= 0 && c0 + k < n) ? J.A[(size_t)idx[i] * n + c0 + k] : 0.0;
-    }
-    __syncthreads();
-    double acc[4][4] = {};
-    for (int k = 0; k < kOP; ++k) {
-      double x[4], y[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) { x[u] = buf[(ti * 4 + u) * kOL + k]; y[u] = buf[(tj * 4 + u) * kOL + k]; }
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = fma(x[u], y[v], acc[u][v]);
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-      for (int v = 0; v < 4; ++v) G[(ti * 4 + u) * kOL + tj * 4 + v] += acc[u][v];
+  for (int o = 128; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + o]);
     __syncthreads();
   }
-  // 2. rotate only if two rows of the pair are not yet orthogonal: |a_i . a_j| above
-  // tol |a_i| |a_j| with tol = 8 eps sqrt(n) (the rounding level of a dot product of
-  // length n), or above an absolute floor 1e-15 |G|_F (rows at the noise level)
+  if (threadIdx.x == 0) gmax[blockIdx.x] = red[0];
+}
+
+// step, part 1: V of every pair from its diagonal sub-block, then rows I+J <- V^T rows
+__global__ void __launch_bounds__(256) k_bj_rows(const BjJob* __restrict__ jobs, int njobs, int step,
+                                                 const double* __restrict__ gmax, double* __restrict__ vbuf,
+                                                 int* __restrict__ flag, int* __restrict__ nrot) {
+  extern __shared__ double bsm[];
+  double* S = bsm;              // sub-block, then diagonalised
+  double* V = S + kOP * kOL;    // its eigenvectors
+  double* buf = V + kOP * kOL;  // streamed 64 x 64 chunk
+  __shared__ double cs[kOP / 2], sn[kOP / 2];
+  __shared__ int pq[kOP], idx[kOP];
+  __shared__ int inner_rot, need;
+  const int lo = find_job(jobs, njobs);
+  const BjJob J = jobs[lo];
+  const int r = blockIdx.x - J.pair_begin, tid = threadIdx.x, n = J.n;
+  if (r >= J.nb / 2 || step >= J.nb - 1) {
+    if (tid == 0) flag[blockIdx.x] = 0;
+    return;
+  }
+  pair_rows(J, r, step, idx);
   if (tid == 0) need = 0;
   __syncthreads();
-  {
-    const double fl = 1e-30 * fro2[lo];  // dot products of rows at the noise level eps |G|_F
-    const double tol = 8.0 * 1.1e-16 * sqrt((double)n);
-    for (int e = tid; e < kOP * kOP; e += 256) {
-      const int i = e >> 6, j = e & 63;
-      if (i < j && idx[i] >= 0 && idx[j] >= 0) {
-        const double gij = fabs(G[i * kOL + j]);
-        if (gij > tol * sqrt(fabs(G[i * kOL + i] * G[j * kOL + j])) + fl) need = 1;
-      }
-    }
+  // Rotate while an off-diagonal exceeds 1e-14 sqrt|g_ii g_jj| + 1e-14 |G| (|G| = the
+  // largest diagonal entry): below that it is rounding noise of the rotations (~eps
+  // sqrt(64) |G|), and it moves the eigenvalues only at second order.  The absolute part
+  // must stay above the inner solver's floor, or pairs of null-space directions would
+  // be sent back to it forever.
+  const double fl = 1e-14 * gmax[lo];
+  for (int e = tid; e < kOP * kOP; e += 256) {
+    const int i = e >> 6, j = e & 63;
+    S[i * kOL + j] = (idx[i] >= 0 && idx[j] >= 0) ? J.A[(size_t)idx[i] * n + idx[j]] : 0.0;
   }
   __syncthreads();
-  if (!need) return;
+  for (int e = tid; e < kOP * kOP; e += 256) {
+    const int i = e >> 6, j = e & 63;
+    if (i < j && fabs(S[i * kOL + j]) > 1e-14 * sqrt(fabs(S[i * kOL + i] * S[j * kOL + j])) + fl) need = 1;
+  }
+  __syncthreads();
+  if (!need) {
+    if (tid == 0) flag[blockIdx.x] = 0;
+    return;
+  }
   for (int e = tid; e < kOP * kOL; e += 256) V[e] = ((e / kOL) == (e % kOL)) ? 1.0 : 0.0;
   __syncthreads();
-  cta_jacobi(G, V, kOP, kOL, cs, sn, pq, &inner_rot);
-  // one Newton-Schulz step V <- V (3 I - V^T V) / 2: the rotations leave V orthogonal
-  // to ~1e-13, which would accumulate over the tournament; this makes it O(1e-26)
+  cta_jacobi64(S, V, cs, sn, pq, &inner_rot, 1e-16 * gmax[lo]);  // floor below the outer one
+  // one Newton-Schulz step V <- V (3 I - V^T V) / 2 against the rounding of the rotations
   {
-    double acc[4][4] = {};
-    for (int k = 0; k < kOP; ++k) {  // S = V^T V into G (no longer needed)
-      double x[4], y[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) { x[u] = V[k * kOL + ti * 4 + u]; y[u] = V[k * kOL + tj * 4 + u]; }
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = fma(x[u], y[v], acc[u][v]);
-    }
+    double acc[4][4];
+    tile64<true, false>(V, V, acc);  // V^T V
     __syncthreads();
+    const int ti = tid >> 4, tj = tid & 15;
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
         const int i = ti * 4 + u, j = tj * 4 + v;
-        G[i * kOL + j] = (i == j ? 1.5 : 0.0) - 0.5 * acc[u][v];
+        S[i * kOL + j] = (i == j ? 1.5 : 0.0) - 0.5 * acc[u][v];
       }
     __syncthreads();
-    double out[4][4] = {};
-    for (int k = 0; k < kOP; ++k) {  // buf = V T
-      double x[4], y[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) { x[u] = V[(ti * 4 + u) * kOL + k]; y[u] = G[k * kOL + tj * 4 + u]; }
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) out[u][v] = fma(x[u], y[v], out[u][v]);
-    }
+    tile64<false, false>(V, S, acc);
     __syncthreads();
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
-      for (int v = 0; v < 4; ++v) V[(ti * 4 + u) * kOL + tj * 4 + v] = out[u][v];
+      for (int v = 0; v < 4; ++v) V[(ti * 4 + u) * kOL + tj * 4 + v] = acc[u][v];
     __syncthreads();
   }
-  // 3. rows of A <- V^T rows of A
+  double* vg = vbuf + (size_t)blockIdx.x * kOP * kOP;
+  for (int e = tid; e < kOP * kOP; e += 256) vg[e] = V[(e >> 6) * kOL + (e & 63)];
+  if (tid == 0) {
+    flag[blockIdx.x] = 1;
+    atomicAdd(&nrot[lo], 1);
+  }
+  // rows I+J of A <- V^T rows I+J
+  const int ti = tid >> 4, tj = tid & 15;
   for (int c0 = 0; c0 < n; c0 += kOP) {
     for (int e = tid; e < kOP * kOP; e += 256) {
       const int i = e >> 6, k = e & 63;
       buf[i * kOL + k] = (idx[i] >= 0 && c0 + k < n) ? J.A[(size_t)idx[i] * n + c0 + k] : 0.0;
     }
     __syncthreads();
-    double acc[4][4] = {};
-    for (int k = 0; k < kOP; ++k) {
-      double x[4], y[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) { x[u] = V[k * kOL + ti * 4 + u]; y[u] = buf[k * kOL + tj * 4 + u]; }
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = fma(x[u], y[v], acc[u][v]);
-    }
+    double acc[4][4];
+    tile64<true, false>(V, buf, acc);
     __syncthreads();
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
@@ -878,54 +860,60 @@ __global__ void __launch_bounds__(256) k_osbj_step(const OsbjJob* __restrict__ j
         if (c0 + tj * 4 + v < n) J.A[(size_t)row * n + c0 + tj * 4 + v] = acc[u][v];
     }
   }
-  // 4. columns of Q <- columns of Q times V
-  for (int r0 = 0; r0 < n; r0 += kOP) {
-    for (int e = tid; e < kOP * kOP; e += 256) {
-      const int rr = e >> 6, k = e & 63;
-      buf[rr * kOL + k] = (idx[k] >= 0 && r0 + rr < n) ? J.Q[(size_t)(r0 + rr) * n + idx[k]] : 0.0;
-    }
-    __syncthreads();
-    double acc[4][4] = {};
-    for (int k = 0; k < kOP; ++k) {
-      double x[4], y[4];
+}
+
+// step, part 2: columns I+J of A and of Q <- columns times V
+__global__ void __launch_bounds__(256) k_bj_cols(const BjJob* __restrict__ jobs, int njobs, int step,
+                                                 const double* __restrict__ vbuf, const int* __restrict__ flag) {
+  extern __shared__ double bsm[];
+  double* V = bsm;
+  double* buf = V + kOP * kOL;
+  __shared__ int idx[kOP];
+  if (!flag[blockIdx.x]) return;
+  const int lo = find_job(jobs, njobs);
+  const BjJob J = jobs[lo];
+  const int r = blockIdx.x - J.pair_begin, tid = threadIdx.x, n = J.n;
+  pair_rows(J, r, step, idx);
+  const double* vg = vbuf + (size_t)blockIdx.x * kOP * kOP;
+  for (int e = tid; e < kOP * kOP; e += 256) V[(e >> 6) * kOL + (e & 63)] = vg[e];
+  __syncthreads();
+  const int ti = tid >> 4, tj = tid & 15;
+  for (int mat = 0; mat < 2; ++mat) {
+    double* M = mat == 0 ? J.A : J.Q;
+    for (int r0 = 0; r0 < n; r0 += kOP) {
+      for (int e = tid; e < kOP * kOP; e += 256) {
+        const int rr = e >> 6, k = e & 63;
+        buf[rr * kOL + k] = (idx[k] >= 0 && r0 + rr < n) ? M[(size_t)(r0 + rr) * n + idx[k]] : 0.0;
+      }
+      __syncthreads();
+      double acc[4][4];
+      tile64<false, false>(buf, V, acc);
+      __syncthreads();
 #pragma unroll
-      for (int u = 0; u < 4; ++u) { x[u] = buf[(ti * 4 + u) * kOL + k]; y[u] = V[k * kOL + tj * 4 + u]; }
+      for (int u = 0; u < 4; ++u) {
+        const int rr = r0 + ti * 4 + u;
+        if (rr >= n) continue;
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = fma(x[u], y[v], acc[u][v]);
-    }
-    __syncthreads();
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int rr = r0 + ti * 4 + u;
-      if (rr >= n) continue;
-#pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        const int col = idx[tj * 4 + v];
-        if (col >= 0) J.Q[(size_t)rr * n + col] = acc[u][v];
+        for (int v = 0; v < 4; ++v) {
+          const int col = idx[tj * 4 + v];
+          if (col >= 0) M[(size_t)rr * n + col] = acc[u][v];
+        }
       }
     }
   }
-  if (tid == 0) atomicAdd(&nrot[lo], 1);
 }
 
-// eigenvalues = Rayleigh quotients q_i^T G q_i / q_i^T q_i = (row i of V^T G) . q_i /
-// |q_i|^2 (second order in the eigenvector error), sorted descending (ties by index)
-// with the normalised columns of Q; A is scratch for the unsorted eigenvectors
-__global__ void k_osbj_finish(const OsbjJob* __restrict__ jobs) {
-  const OsbjJob J = jobs[blockIdx.x];
+// eigenvalues = diagonal of the rotated A, sorted descending (ties by index) with the
+// normalised columns of Q; A is scratch for the unsorted eigenvectors
+__global__ void k_bj_finish(const BjJob* __restrict__ jobs) {
+  const BjJob J = jobs[blockIdx.x];
   const int n = J.n, tid = threadIdx.x;
   extern __shared__ double wn[];
   double* qn = wn + n;
   for (int i = tid; i < n; i += blockDim.x) {
-    double s = 0.0, q2 = 0.0;
-    for (int j = 0; j < n; ++j) {
-      const double qji = J.Q[(size_t)j * n + i];
-      s += J.A[(size_t)i * n + j] * qji;
-      q2 += qji * qji;
-    }
-    wn[i] = s / q2;
+    wn[i] = J.A[(size_t)i * n + i];
+    double q2 = 0.0;
+    for (int j = 0; j < n; ++j) q2 += J.Q[(size_t)j * n + i] * J.Q[(size_t)j * n + i];
     qn[i] = 1.0 / sqrt(q2);
   }
   __syncthreads();
@@ -945,39 +933,43 @@ __global__ void k_osbj_finish(const OsbjJob* __restrict__ jobs) {
 
 }  // namespace
 
-static void eig_osbj(const std::vector<EigJob>& jobs, Stream s) {
+static void eig_block_jacobi(const std::vector<EigJob>& jobs, Stream s) {
   if (jobs.empty()) return;
-  std::vector<OsbjJob> oj;
+  std::vector<BjJob> bj;
   int pairs = 0, nbmax = 0, nmax = 0;
   for (const EigJob& j : jobs) {
     int nb = (j.n + kOB - 1) / kOB;
     nb += nb & 1;
-    oj.push_back({j.A, j.Q, j.w, j.n, nb, pairs, 0});
+    bj.push_back({j.A, j.Q, j.w, j.n, nb, pairs, 0});
     pairs += nb / 2;
     nbmax = std::max(nbmax, nb);
     nmax = std::max(nmax, j.n);
   }
-  const int nj = (int)oj.size();
-  OsbjJob* d = (OsbjJob*)dev_alloc(sizeof(OsbjJob) * nj, s);
-  dev_h2d(d, oj.data(), sizeof(OsbjJob) * nj, s);
-  double* fro2 = (double*)dev_alloc(sizeof(double) * nj, s);
+  const int nj = (int)bj.size();
+  BjJob* d = (BjJob*)dev_alloc(sizeof(BjJob) * nj, s);
+  dev_h2d(d, bj.data(), sizeof(BjJob) * nj, s);
+  double* gmax = (double*)dev_alloc(sizeof(double) * nj, s);
+  double* vbuf = (double*)dev_alloc(sizeof(double) * (size_t)pairs * kOP * kOP, s);
+  int* flag = (int*)dev_alloc(sizeof(int) * pairs, s);
   int* nrot = (int*)dev_alloc(sizeof(int) * nj, s);
   std::vector<int> hrot(nj);
-  k_osbj_prep<<<nj, 256, 0, S(s)>>>(d, fro2);
+  k_bj_prep<<<nj, 256, 0, S(s)>>>(d, gmax);
   ++g_launches;
-  const size_t shm = sizeof(double) * 3 * kOP * kOL;
+  const size_t shr = sizeof(double) * 3 * kOP * kOL, shc = sizeof(double) * 2 * kOP * kOL;
   static bool attr = false;
   if (!attr) {
-    ck(cudaFuncSetAttribute(k_osbj_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm), "osbj smem");
+    ck(cudaFuncSetAttribute(k_bj_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shr), "bj smem");
+    ck(cudaFuncSetAttribute(k_bj_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shc), "bj smem");
     attr = true;
   }
   for (int sweep = 0; sweep < 40; ++sweep) {
-    ck(cudaMemsetAsync(nrot, 0, sizeof(int) * nj, S(s)), "osbj counters");
+    ck(cudaMemsetAsync(nrot, 0, sizeof(int) * nj, S(s)), "bj counters");
     for (int step = 0; step < nbmax - 1; ++step) {
-      k_osbj_step<<<pairs, 256, shm, S(s)>>>(d, nj, step, fro2, nrot);
-      ++g_launches;
+      k_bj_rows<<<pairs, 256, shr, S(s)>>>(d, nj, step, gmax, vbuf, flag, nrot);
+      k_bj_cols<<<pairs, 256, shc, S(s)>>>(d, nj, step, vbuf, flag);
+      g_launches += 2;
     }
-    ck(cudaGetLastError(), "osbj step");
+    ck(cudaGetLastError(), "bj step");
     dev_d2h(hrot.data(), nrot, sizeof(int) * nj, s);
     dev_sync(s);
     bool any = false;
@@ -987,12 +979,14 @@ static void eig_osbj(const std::vector<EigJob>& jobs, Stream s) {
   const size_t shf = sizeof(double) * 2 * nmax;
   if (shf > 220 * 1024) throw std::runtime_error("eig_batched: block too large");
   if (shf > 48 * 1024)
-    ck(cudaFuncSetAttribute(k_osbj_finish, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shf), "osbj finish smem");
-  k_osbj_finish<<<nj, 256, shf, S(s)>>>(d);
+    ck(cudaFuncSetAttribute(k_bj_finish, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shf), "bj finish smem");
+  k_bj_finish<<<nj, 256, shf, S(s)>>>(d);
   ++g_launches;
-  ck(cudaGetLastError(), "osbj finish");
+  ck(cudaGetLastError(), "bj finish");
   dev_free(nrot, s);
-  dev_free(fro2, s);
+  dev_free(flag, s);
+  dev_free(vbuf, s);
+  dev_free(gmax, s);
   dev_free(d, s);
 }
 
@@ -1009,12 +1003,12 @@ void eig_batched(const std::vector<EigJob>& jobs, Stream s) {
     dev_h2d(d, small.data(), small.size() * sizeof(EigJob), s);
     const int np = (nmax_s + 1) & ~1;
     size_t shm = sizeof(double) * ((size_t)2 * nmax_s * (nmax_s + 1) + np + nmax_s) + 64;
-    ck(cudaFuncSetAttribute(k_eig_batched<true, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm), "eig smem");
-    k_eig_batched<true, 256><<<(int)small.size(), 256, shm, S(s)>>>(d);
+    ck(cudaFuncSetAttribute(k_eig_batched<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm), "eig smem");
+    k_eig_batched<256><<<(int)small.size(), 256, shm, S(s)>>>(d);
     ++g_launches;
     ck(cudaGetLastError(), "eig_batched (shared)");
   }
-  if (!large.empty()) eig_osbj(large, s);
+  if (!large.empty()) eig_block_jacobi(large, s);
   dev_free(d, s);
 }
 
