@@ -332,8 +332,97 @@ def sweep_time(ctx, L, D, precision, fp64_iters, iters):
     return out[0], out[1], e
 
 
+# 32 independent instances of uneven size for the batched launch: Hubbard chains
+# (t=1, U=4, C1) L = 8..24 and random-integral systems (D2h, round-robin irreps, built as
+# the L=12 system) L = 10..20, N = L, S in {0, 1}, D_SU(2) in {64..1024}
+BATCH_HUB_L = [8, 10, 12, 14, 16, 18, 20, 22, 24]
+BATCH_RND_L = [10, 12, 14, 16, 18, 20]
+BATCH_D = [64, 128, 256, 512, 1024]
+
+
+def batch_instances():
+    out = []
+    for k in range(32):
+        kind = "hubbard" if k % 2 == 0 else "random"
+        L = BATCH_HUB_L[(k // 2) % len(BATCH_HUB_L)] if kind == "hubbard" else BATCH_RND_L[(k // 2) % len(BATCH_RND_L)]
+        out.append((kind, L, 0 if (k // 4) % 2 == 0 else 2, BATCH_D[k % len(BATCH_D)], 2415300 + k))
+    return out
+
+
+def run_batch(args):
+    """batch32: the mixed-precision matvecs of 32 instances, one at a time (one grouped
+    launch sequence per instance) against one batched, graph-replayed launch sequence
+    over all of them; value = their summed flops over the batched time."""
+    import torch
+    from paper_1312_2415_gb300 import Batch, Context
+    from workloads import hubbard_chain, random_integrals, round_robin_irreps
+    torch.cuda.set_device(0)
+    ctxs, sites, xs, ys = [], [], [], []
+    t_setup = time.perf_counter()
+    for kind, L, tS, D, seed in batch_instances():
+        if kind == "hubbard":
+            irr, (h, V), group = [0] * L, hubbard_chain(L, 1.0, 4.0), 0
+        else:
+            irr = round_robin_irreps(L)
+            (h, V), group = random_integrals(irr, seed), 7
+        c = Context(L, irr, L, tS, 0, group=group)
+        c.set_integrals(h, V)
+        fixed_iters(c, D, args.davidson_iters)
+        c.set_precision(1, args.fp64_iters)
+        c.init_mps(seed)
+        i = L // 2 - 1
+        c.canonicalize(i)
+        x = torch.tensor(c.tt_to_x(i), dtype=torch.float64, device="cuda")
+        y = torch.empty_like(x)
+        c.matvec(i, x, y)  # prepares the instance's tables
+        ctxs.append(c); sites.append(i); xs.append(x); ys.append(y)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t_setup
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+
+    def sequential():
+        for c, i, x, y in zip(ctxs, sites, xs, ys):
+            c.matvec(i, x, y)
+    seq_ms = timed(sequential)
+    b = Batch(ctxs, sites, autotune=True)
+    info = b.info()
+    clk = ClockSampler(torch.cuda.current_device())
+    l0 = ctxs[0].stats()["kernels_launched"]
+    clk.start()
+    bat_ms = timed(lambda: b.run(xs, ys))
+    clocks = clk.stop()
+    launches = int(ctxs[0].stats()["kernels_launched"] - l0)
+    flops = info["flops"]
+    out = {"metric": METRIC, "value": flops / (bat_ms * 1e-3) / 1e9, "unit": "GFLOP/s", "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": bat_ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "tf32x3-f32acc", "data": "synthetic",
+           "config": {"workload": "batch32: 32 instances, Hubbard L=8..24 and random-integral L=10..20, "
+                                  "N=L, S in {0,1}, D in {64..1024}, middle sites, one matvec each per step",
+                      "instances": [list(q[:4]) for q in batch_instances()], "flops_per_step": flops,
+                      "l2": "inputs of the larger instances exceed L2"},
+           "sequential": {"ms_per_step": seq_ms, "value": flops / (seq_ms * 1e-3) / 1e9,
+                          "what": "the same 32 matvecs one instance at a time (their own launches)"},
+           "speedup_vs_sequential": seq_ms / bat_ms, "autotune": info, "setup_s": t_setup,
+           "clocks": clocks, "gpu_launches": launches}
+    print(json.dumps(out), flush=True)
+    b.close()
+
+
 def run_gb300(args):
     import torch
+    if args.workload == "batch32":
+        return run_batch(args)
     rank, world, local = dist_env()
     if world > 1:
         import torch.distributed as dist

@@ -175,6 +175,49 @@ int dmrg_truncate(dmrg_ctx* ctx, int site, int dir, int D, double noise, const d
 int dmrg_sweep_step(dmrg_ctx* ctx, int site, int dir, int D, double gamma, double* energy,
                     double* w_disc, int* iters);
 
+/* Extrapolation data of the last dmrg_solve (Sec. 4.3): for each schedule instruction,
+ * D, the lowest micro-iteration energy of its last macro-iteration and the largest
+ * discarded weight of that macro-iteration (Eq. 15, max over the micro-iterations).
+ * *n: capacity of the arrays on entry, number of instructions on return (arrays may be
+ * NULL to query it). */
+int dmrg_solve_history(dmrg_ctx* ctx, int* n, int* D, double* energy, double* w_disc);
+
+/* Eq. 16: least-squares fit of E(D) = E_exact + C1 w_disc(D) over n >= 2 points (host
+ * only).  DMRG_EINVAL for n < 2, NULL pointers or equal discarded weights. */
+int dmrg_extrapolate(const double* w_disc, const double* energy, int n, double* e_exact,
+                     double* c1);
+
+/* Batched mixed-precision matvecs (no counterpart in the paper, which treats one
+ * problem at a time): y_i = H_eff(ctx[i], site[i]) x_i for `count` independent
+ * contexts, computed with the split-TF32 tensor-core products of precision 1 (whatever
+ * precision the contexts were created with) and run as ONE grouped launch per phase
+ * over the symmetry blocks of all instances, replayed from a CUDA graph.
+ * dmrg_batch_create prepares each context's tables at its site (as a first
+ * dmrg_heff_matvec would), merges them and, if autotune != 0, times the candidate unit
+ * sizes (packs of right-operator blocks per phase-1 unit, tasks per phase-2 unit) and
+ * keeps the fastest, then captures the launch sequence in a CUDA graph.  Failures are
+ * reported through dmrg_last_error(ctx[0]).  The batch stays valid while no context
+ * rebuilds its tables (a matvec at another site, a truncation or a sweep step does):
+ * dmrg_batch_run then fails with DMRG_EINVAL. */
+typedef struct dmrg_batch dmrg_batch;
+int dmrg_batch_create(dmrg_batch** out, dmrg_ctx* const* ctx, const int* site, int count,
+                      int autotune);
+/* Device buffers of instance i: the input the graph reads (x, n doubles, the layout of
+ * dmrg_two_site_layout) and the output it writes (y). */
+int dmrg_batch_io(dmrg_batch* b, int i, double** x, double** y, int64_t* n);
+/* Queue the batched matvec on `stream` (0 = the default stream) without waiting.  x and y
+ * (arrays of count DEVICE pointers, or NULL) are copied into / out of the batch's
+ * buffers around the graph; NULL entries (or NULL arrays) use the buffers in place.
+ * Runs that overlap in time, or that overlap a matvec of one of the contexts at the
+ * same site, race on those buffers. */
+int dmrg_batch_run(dmrg_batch* b, const double* const* x, double* const* y, uintptr_t stream);
+/* flops of one batched matvec (planner-counted), the chosen unit sizes, the measured
+ * time of one launch sequence in the autotuner (0 without it) and the autotuner's time. */
+int dmrg_batch_info(dmrg_batch* b, double* flops, int* packs_per_unit, int* tasks_per_unit,
+                    double* launch_ms, double* tune_ms);
+const char* dmrg_batch_last_error(dmrg_batch* b);
+void dmrg_batch_destroy(dmrg_batch* b);
+
 int dmrg_stats(dmrg_ctx* ctx, dmrg_stats_t* out);
 const char* dmrg_last_error(dmrg_ctx* ctx);
 void dmrg_destroy(dmrg_ctx* ctx);

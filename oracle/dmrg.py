@@ -78,3 +78,12 @@ def sweep(prob, m, D, n_macro, log=None):
         if log is not None:
             log(it, energies[-1])
     return min(energies), energies
+
+
+def extrapolate(w_disc, energy):
+    """Eq. 16: the linear relation E(D) = E_exact + C1 w_disc(D) fitted by least squares
+    to the (w_disc, E) pairs of several D; returns (E_exact, C1)."""
+    w = np.asarray(w_disc, dtype=np.float64)
+    A = np.stack([np.ones_like(w), w], axis=1)
+    (e0, c1), *_ = np.linalg.lstsq(A, np.asarray(energy, dtype=np.float64), rcond=None)
+    return float(e0), float(c1)

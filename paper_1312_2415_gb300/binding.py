@@ -67,6 +67,17 @@ _SIGS = {
                                      ctypes.c_void_p, ctypes.c_size_t, _D]),
     "dmrg_sweep_step": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                        _D, _D, _I]),
+    "dmrg_solve_history": (ctypes.c_int, [_P, _I, _I, _D, _D]),
+    "dmrg_extrapolate": (ctypes.c_int, [_D, _D, ctypes.c_int, _D, _D]),
+    "dmrg_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(_P), _I, ctypes.c_int,
+                                         ctypes.c_int]),
+    "dmrg_batch_io": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p),
+                                     ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int64)]),
+    "dmrg_batch_run": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                                      ctypes.c_size_t]),
+    "dmrg_batch_info": (ctypes.c_int, [_P, _D, _I, _I, _D, _D]),
+    "dmrg_batch_last_error": (ctypes.c_char_p, [_P]),
+    "dmrg_batch_destroy": (None, [_P]),
     "dmrg_stats": (ctypes.c_int, [_P, ctypes.POINTER(Stats)]),
     "dmrg_last_error": (ctypes.c_char_p, [_P]),
     "dmrg_destroy": (None, [_P]),
@@ -158,6 +169,16 @@ class Context:
         self._check(self.lib.dmrg_set_schedule(self.h, n, Da, _dptr(Ea), Na, _dptr(Za),
                                                float(davidson_tol), int(davidson_max_iter)))
 
+    def solve_history(self):
+        """(D, energy, w_disc) per schedule instruction of the last solve (Sec. 4.3)."""
+        n = ctypes.c_int(0)
+        self._check(self.lib.dmrg_solve_history(self.h, ctypes.byref(n), None, None, None))
+        D = np.zeros(n.value, dtype=np.int32)
+        E, W = np.zeros(n.value), np.zeros(n.value)
+        self._check(self.lib.dmrg_solve_history(self.h, ctypes.byref(n), D.ctypes.data_as(_I), _dptr(E),
+                                                _dptr(W)))
+        return D, E, W
+
     def set_precision(self, precision, fp64_iters=0):
         self._check(self.lib.dmrg_set_precision(self.h, int(precision), int(fp64_iters)))
 
@@ -243,3 +264,72 @@ class Context:
         st = Stats()
         self._check(self.lib.dmrg_stats(self.h, ctypes.byref(st)))
         return {k: getattr(st, k) for k, _ in Stats._fields_}
+
+
+def extrapolate(w_disc, energy, path=None):
+    """Eq. 16: least-squares E(D) = E_exact + C1 w_disc(D); returns (E_exact, C1)."""
+    lib = load(path)
+    w = np.ascontiguousarray(w_disc, dtype=np.float64)
+    e = np.ascontiguousarray(energy, dtype=np.float64)
+    e0, c1 = ctypes.c_double(), ctypes.c_double()
+    rc = lib.dmrg_extrapolate(_dptr(w), _dptr(e), int(w.size), ctypes.byref(e0), ctypes.byref(c1))
+    if rc != OK:
+        raise DMRGError(rc, "extrapolate: need two or more points with different discarded weights")
+    return e0.value, c1.value
+
+
+class Batch:
+    """Batched mixed-precision matvecs of several contexts (dmrg_batch_*): one grouped
+    launch per phase over all instances, replayed from a CUDA graph."""
+
+    def __init__(self, contexts, sites, autotune=True):
+        self.contexts = list(contexts)
+        self.lib = self.contexts[0].lib
+        n = len(self.contexts)
+        arr = (_P * n)(*[c.h for c in self.contexts])
+        st = (ctypes.c_int * n)(*[int(s) for s in sites])
+        h = _P()
+        rc = self.lib.dmrg_batch_create(ctypes.byref(h), arr, st, n, int(bool(autotune)))
+        if rc != OK:
+            raise DMRGError(rc, self.lib.dmrg_last_error(self.contexts[0].h).decode())
+        self.h = h
+
+    def io(self, i):
+        """(x pointer, y pointer, n) of instance i: the batch's device buffers."""
+        x, y, n = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_int64()
+        rc = self.lib.dmrg_batch_io(self.h, int(i), ctypes.byref(x), ctypes.byref(y), ctypes.byref(n))
+        if rc != OK:
+            raise DMRGError(rc, "batch io")
+        return x.value, y.value, n.value
+
+    def run(self, xs=None, ys=None):
+        """Queue y_i = H_eff x_i for all instances on the current torch stream; xs / ys:
+        lists of float64 CUDA tensors (or None for the batch's own buffers)."""
+        import torch  # device memory / streams only
+        n = len(self.contexts)
+        xp = (ctypes.c_void_p * n)(*[(t.data_ptr() if t is not None else None) for t in (xs or [None] * n)])
+        yp = (ctypes.c_void_p * n)(*[(t.data_ptr() if t is not None else None) for t in (ys or [None] * n)])
+        s = torch.cuda.current_stream().cuda_stream or _default_stream_handle(None)
+        rc = self.lib.dmrg_batch_run(self.h, xp, yp, s)
+        if rc != OK:
+            raise DMRGError(rc, self.lib.dmrg_batch_last_error(self.h).decode())
+
+    def info(self):
+        f, ms, tms = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        ppu, tpu = ctypes.c_int(), ctypes.c_int()
+        self.lib.dmrg_batch_info(self.h, ctypes.byref(f), ctypes.byref(ppu), ctypes.byref(tpu), ctypes.byref(ms),
+                                 ctypes.byref(tms))
+        return {"flops": f.value, "packs_per_unit": ppu.value, "tasks_per_unit": tpu.value,
+                "launch_ms": ms.value, "tune_ms": tms.value}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.dmrg_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+

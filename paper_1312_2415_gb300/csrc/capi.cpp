@@ -1,11 +1,13 @@
 // extern "C" boundary: argument checks, host/device pointer handling, error codes.
 #include <cuda_runtime.h>
 
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <new>
 #include <stdexcept>
 #include <string>
+#include <vector>
 
 #include "../../include/dmrg_gb300.h"
 #include "engine.hpp"
@@ -17,30 +19,42 @@ struct dmrg_ctx {
   int L = 0;
 };
 
+struct dmrg_batch {
+  std::vector<dmrg_ctx*> ctx;
+  std::vector<int> site;
+  std::vector<uint64_t> serial;
+  std::vector<double*> x, y;
+  std::vector<int64_t> n;
+  dmrg::TcPlan* plan = nullptr;
+  void* graph = nullptr;
+  dmrg::TcTune tune;
+  double flops = 0.0, best_ms = 0.0, tune_ms = 0.0;
+  std::string err;
+};
+
 namespace {
 
 const int kGroupOrder[8] = {1, 2, 2, 2, 4, 4, 4, 8};
 
 template <class F>
-int guard(dmrg_ctx* c, F&& f) {
-  if (!c) return DMRG_EINVAL;
+int guard_err(std::string& err, F&& f) {
   try {
-    c->err.clear();
+    err.clear();
     return f();
   } catch (const std::bad_alloc& e) {
-    c->err = std::string("allocation failed: ") + e.what();
+    err = std::string("allocation failed: ") + e.what();
     return DMRG_ENOMEM;
   } catch (const std::domain_error& e) {
-    c->err = e.what();
+    err = e.what();
     return DMRG_ESYMM;
   } catch (const std::invalid_argument& e) {
-    c->err = e.what();
+    err = e.what();
     return DMRG_EINVAL;
   } catch (const std::out_of_range& e) {
-    c->err = e.what();
+    err = e.what();
     return DMRG_EINVAL;
   } catch (const std::runtime_error& e) {
-    c->err = e.what();
+    err = e.what();
     std::string m = e.what();
     if (m.find("out of memory") != std::string::npos) return DMRG_ENOMEM;
     return m.find("cuda") != std::string::npos || m.find("launch") != std::string::npos ||
@@ -48,9 +62,15 @@ int guard(dmrg_ctx* c, F&& f) {
                ? DMRG_ECUDA
                : DMRG_EINTERNAL;
   } catch (...) {
-    c->err = "unknown failure";
+    err = "unknown failure";
     return DMRG_EINTERNAL;
   }
+}
+
+template <class F>
+int guard(dmrg_ctx* c, F&& f) {
+  if (!c) return DMRG_EINVAL;
+  return guard_err(c->err, std::forward<F>(f));
 }
 
 // Runs f(dev_in_or_out...) with device buffers: for host pointers, copies in/out.
@@ -379,6 +399,173 @@ void dmrg_destroy(dmrg_ctx* c) {
   delete c->eng;
   if (c->stream) cudaStreamDestroy(c->stream);
   delete c;
+}
+
+int dmrg_solve_history(dmrg_ctx* c, int* n, int* D, double* energy, double* w_disc) {
+  return guard(c, [&] {
+    if (!n || *n < 0) return DMRG_EINVAL;
+    const auto& hd = c->eng->hist_D();
+    const int m = std::min<int>(*n, (int)hd.size());
+    for (int k = 0; k < m; ++k) {
+      if (D) D[k] = hd[k];
+      if (energy) energy[k] = c->eng->hist_E()[k];
+      if (w_disc) w_disc[k] = c->eng->hist_w()[k];
+    }
+    *n = (int)hd.size();
+    return DMRG_OK;
+  });
+}
+
+int dmrg_extrapolate(const double* w_disc, const double* energy, int n, double* e_exact, double* c1) {
+  if (!w_disc || !energy || n < 2 || !e_exact || !c1) return DMRG_EINVAL;
+  // least squares of E = e_exact + c1 w (Eq. 16),
+  // centred sums for accuracy
+  double mw = 0.0, me = 0.0;
+  for (int k = 0; k < n; ++k) {
+    mw += w_disc[k];
+    me += energy[k];
+  }
+  mw /= n;
+  me /= n;
+  double sww = 0.0, swe = 0.0;
+  for (int k = 0; k < n; ++k) {
+    sww += (w_disc[k] - mw) * (w_disc[k] - mw);
+    swe += (w_disc[k] - mw) * (energy[k] - me);
+  }
+  if (!(sww > 0.0)) return DMRG_EINVAL;  // all discarded weights equal
+  *c1 = swe / sww;
+  *e_exact = me - *c1 * mw;
+  return DMRG_OK;
+}
+
+// ---------------------------------------------------------------- batched matvecs
+
+int dmrg_batch_create(dmrg_batch** out, dmrg_ctx* const* ctx, const int* site, int count, int autotune) {
+  if (!out || !ctx || !site || count <= 0) return DMRG_EINVAL;
+  *out = nullptr;
+  for (int i = 0; i < count; ++i)
+    if (!ctx[i]) return DMRG_EINVAL;
+  dmrg_batch* b = new (std::nothrow) dmrg_batch;
+  if (!b) return DMRG_ENOMEM;
+  const int rc = guard_err(ctx[0]->err, [&] {
+    std::vector<const dmrg::TcHost*> hosts;
+    for (int i = 0; i < count; ++i) {
+      dmrg_ctx* c = ctx[i];
+      dmrg::Stream s = dev_stream(c);
+      dmrg::Engine::TcView v = c->eng->prepare_tc(site[i]);
+      dmrg::dev_sync(s);
+      hosts.push_back(v.host);
+      b->ctx.push_back(c);
+      b->site.push_back(site[i]);
+      b->serial.push_back(v.serial);
+      b->x.push_back(v.x);
+      b->y.push_back(v.y);
+      b->n.push_back(v.n);
+      b->flops += v.flops;
+    }
+    cudaStream_t st;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) throw std::runtime_error("cuda stream");
+    std::vector<dmrg::TcTune> cand;
+    if (autotune) {
+      for (int ppu : {4, 8, 16})
+        for (int tpu : {16, 32, 48, 96}) cand.push_back({ppu, tpu});
+    } else {
+      cand.push_back(dmrg::TcTune());
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const auto t0 = std::chrono::steady_clock::now();
+    for (const dmrg::TcTune& t : cand) {
+      dmrg::TcPlan* p = dmrg::tc_plan_build(hosts, t, (dmrg::Stream)st);
+      float ms = 0.0f;
+      if (cand.size() > 1) {
+        dmrg::tc_plan_launch(p, nullptr, (dmrg::Stream)st);  // warm-up
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 3; ++r) dmrg::tc_plan_launch(p, nullptr, (dmrg::Stream)st);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) throw std::runtime_error("cuda autotune sync");
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= 3.0f;
+      }
+      if (!b->plan || ms < b->best_ms) {
+        if (b->plan) dmrg::tc_plan_free(b->plan, (dmrg::Stream)st);
+        b->plan = p;
+        b->tune = t;
+        b->best_ms = ms;
+      } else {
+        dmrg::tc_plan_free(p, (dmrg::Stream)st);
+      }
+    }
+    b->tune_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    dmrg::dev_sync((dmrg::Stream)st);
+    cudaStreamDestroy(st);
+    if (dmrg::tc_error_flag((dmrg::Stream)cudaStreamLegacy)) throw std::runtime_error("cuda: tensor-core wait timed out");
+    b->graph = dmrg::tc_graph_create(b->plan);
+    return DMRG_OK;
+  });
+  if (rc != DMRG_OK) {
+    dmrg_batch_destroy(b);
+    return rc;
+  }
+  *out = b;
+  return DMRG_OK;
+}
+
+int dmrg_batch_io(dmrg_batch* b, int i, double** x, double** y, int64_t* n) {
+  if (!b || i < 0 || i >= (int)b->ctx.size()) return DMRG_EINVAL;
+  if (x) *x = b->x[i];
+  if (y) *y = b->y[i];
+  if (n) *n = b->n[i];
+  return DMRG_OK;
+}
+
+int dmrg_batch_run(dmrg_batch* b, const double* const* x, double* const* y, uintptr_t stream) {
+  if (!b || !b->graph) return DMRG_EINVAL;
+  return guard_err(b->err, [&] {
+    for (size_t i = 0; i < b->ctx.size(); ++i)
+      if (b->ctx[i]->eng->tc_serial(b->site[i]) != b->serial[i])
+        throw std::invalid_argument("a context of the batch changed its tables since the batch was made");
+    cudaStream_t s = stream ? (cudaStream_t)stream : cudaStreamLegacy;
+    for (size_t i = 0; x && i < b->ctx.size(); ++i)
+      if (x[i] && x[i] != b->x[i])
+        if (cudaMemcpyAsync(b->x[i], x[i], sizeof(double) * b->n[i], cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+          throw std::runtime_error("cuda batch input copy");
+    dmrg::tc_graph_launch(b->graph, (dmrg::Stream)s);
+    for (size_t i = 0; y && i < b->ctx.size(); ++i)
+      if (y[i] && y[i] != b->y[i])
+        if (cudaMemcpyAsync(y[i], b->y[i], sizeof(double) * b->n[i], cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+          throw std::runtime_error("cuda batch output copy");
+    return DMRG_OK;
+  });
+}
+
+int dmrg_batch_info(dmrg_batch* b, double* flops, int* packs_per_unit, int* tasks_per_unit, double* launch_ms,
+                    double* tune_ms) {
+  if (!b) return DMRG_EINVAL;
+  if (flops) *flops = b->flops;
+  if (packs_per_unit) *packs_per_unit = b->tune.packs_per_unit;
+  if (tasks_per_unit) *tasks_per_unit = b->tune.tasks_per_unit;
+  if (launch_ms) *launch_ms = b->best_ms;
+  if (tune_ms) *tune_ms = b->tune_ms;
+  return DMRG_OK;
+}
+
+const char* dmrg_batch_last_error(dmrg_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+void dmrg_batch_destroy(dmrg_batch* b) {
+  if (!b) return;
+  try {
+    if (b->graph) dmrg::tc_graph_free(b->graph);
+    if (b->plan) {
+      dmrg::tc_plan_free(b->plan, (dmrg::Stream)cudaStreamLegacy);
+      dmrg::dev_sync((dmrg::Stream)cudaStreamLegacy);
+    }
+  } catch (...) {
+  }
+  delete b;
 }
 
 }  // extern "C"

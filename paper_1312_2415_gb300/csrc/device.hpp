@@ -164,23 +164,42 @@ struct Tc2Unit {
   int ldy, m, n, row0, col0;
   int t_begin, t_end;
 };
-// one x block (rows x cols at src in the FP64 vector) and its places in the FP32 stack
-// (row-major, stride ld) and in the transposed stack (column-major, stride ldt)
-struct TcXBlock { int64_t src, dst, dstt; int rows, cols, ld, ldt; };
+// one x block (rows x cols, row-major FP64) and its places in the FP32 stack (row-major,
+// stride ld) and in the transposed stack (column-major, stride ldt)
+struct TcXBlock { const double* src; float* dst; float* dstt; int rows, cols, ld, ldt; };
 // one FP64 block converted to FP32 with row stride ld (a multiple of 4)
 struct TcMirror { const double* src; float* dst; int rows, cols, ld; };
+// Host description of one instance's mixed-precision matvec: the tables of both phases
+// and the ranges units are cut from (phase 1: the packs of one 128-row stack tile;
+// phase 2: the tasks of one output tile), reading x from xin and writing y to yout.
+struct TcHost {
+  std::vector<Tc1Entry> e;
+  std::vector<Tc1Pack> p;
+  std::vector<Tc1Unit> r1;  // p_begin / p_end span every pack of the tile
+  std::vector<Tc2Src> s;
+  std::vector<Tc2Task> t;
+  std::vector<Tc2Unit> r2;  // t_begin / t_end span every task of the tile
+  std::vector<TcXBlock> xb;
+  double* yout = nullptr;
+  int64_t n = 0;
+};
+// how ranges are cut into units (one CTA each): packs per phase-1 unit, tasks per
+// phase-2 unit
+struct TcTune { int packs_per_unit = 8, tasks_per_unit = 48; };
 struct TcPlan;
-TcPlan* tc_plan_upload(const std::vector<Tc1Entry>& e, const std::vector<Tc1Pack>& p,
-                       const std::vector<Tc1Unit>& u1, const std::vector<Tc2Src>& s,
-                       const std::vector<Tc2Task>& t, const std::vector<Tc2Unit>& u2,
-                       const std::vector<TcXBlock>& xb, float* x32, float* x32t, int64_t n,
-                       Stream st);
-// y = H x: x (FP64) -> the FP32 stacks, phase 1, phase 2 (y zeroed first); ev (3 events or
-// nullptr) are recorded before phase 1, between the phases and after
-void tc_plan_run(const TcPlan* p, const double* x, double* y, void* const* ev, Stream s);
+// device tables of one or several instances (one grouped launch per phase for all)
+TcPlan* tc_plan_build(const std::vector<const TcHost*>& inst, TcTune tune, Stream st);
+// clear every y, x -> FP32 stacks, phase 1, phase 2; ev (3 events or nullptr) are
+// recorded before phase 1, between the phases and after.  All pointers are fixed, so
+// the sequence can be captured in a CUDA graph.
+void tc_plan_launch(const TcPlan* p, void* const* ev, Stream s);
 void tc_plan_free(TcPlan* p, Stream s);
 int tc_error_flag(Stream s);  // 1 if a tensor-core kernel timed out on a wait
 void tc_mirror(const std::vector<TcMirror>& m, Stream s);  // blocks -> FP32, padding untouched
+// CUDA graph of tc_plan_launch(p) (captured on a private stream), its replay and release
+void* tc_graph_create(const TcPlan* p);
+void tc_graph_launch(void* g, Stream s);
+void tc_graph_free(void* g);
 
 // ---- allocation-free matvec: runs prepared matvec tables with the scratch in a
 // fixed device array (capacity in doubles) and x / y redirected to caller buffers ----

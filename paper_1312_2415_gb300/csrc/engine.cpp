@@ -732,8 +732,10 @@ struct Engine::MatvecPlan {
   std::vector<std::vector<int>> w_by_x;
   std::vector<int64_t> tall_off, tall_rows;
   std::vector<int> sec_dim;
+  TcHost tch;              // mixed-precision tables (host), kept for batched launches
   TcPlan* tc = nullptr;
   float* tc_zt = nullptr;
+  uint64_t serial = 0;      // distinguishes successive plans of an engine
   double tc_bytes1 = 0.0, tc_bytes2 = 0.0;  // compulsory bytes of the two phases
   float* tc_mem[3] = {nullptr, nullptr, nullptr};  // x32, x32t, operator mirrors
 };
@@ -1090,6 +1092,7 @@ Engine::MatvecPlan* Engine::plan_for(int i) {
   if (cached_ && cached_site_ == i) return cached_;
   if (cached_) { free_plan(cached_); cached_ = nullptr; cached_site_ = -1; }
   cached_ = plan_matvec(i);
+  cached_->serial = ++plan_serial_;
   cached_site_ = i;
   return cached_;
 }
@@ -1136,13 +1139,14 @@ void Engine::build_tc(MatvecPlan* P) {
   P->tc_mem[1] = x32t;
   dev_zero(x32, sizeof(float) * std::max<int64_t>(nx, 4), stream_);
   dev_zero(x32t, sizeof(float) * std::max<int64_t>(nxt, 4), stream_);
-  std::vector<TcXBlock> xbt;
-  xbt.reserve(P->X.size());
+  TcHost& H = P->tch;
+  H = TcHost();
+  H.xb.reserve(P->X.size());
   for (int x = 0; x < (int)P->X.size(); ++x) {
     const XBlock& X = P->X[x];
     const int ld = (int)r4(P->sec_dim[X.r]);
-    xbt.push_back({X.off, xoff[X.r] + trow_pad[x] * ld, xtoff[X.r] + trow_pad[x], X.rows, X.cols, ld,
-                   (int)rpad[X.r]});
+    H.xb.push_back({P->xin + X.off, x32 + xoff[X.r] + trow_pad[x] * ld, x32t + xtoff[X.r] + trow_pad[x], X.rows,
+                    X.cols, ld, (int)rpad[X.r]});
   }
   // operator mirrors: every block phase 1 or phase 2 reads
   std::unordered_map<const double*, int64_t> moff;
@@ -1190,10 +1194,8 @@ void Engine::build_tc(MatvecPlan* P) {
   // phase 1
   std::vector<std::vector<int>> byc(nr);
   for (int g = 0; g < (int)P->zg.size(); ++g) byc[P->zg[g].c].push_back(g);
-  std::vector<Tc1Entry> ents;
-  std::vector<Tc1Pack> packs;
-  std::vector<Tc1Unit> u1;
-  constexpr int kPacksPerUnit = 8;
+  std::vector<Tc1Entry>& ents = H.e;
+  std::vector<Tc1Pack>& packs = H.p;
   for (int c = 0; c < nr; ++c) {
     if (byc[c].empty()) continue;
     const int M = (int)rpad[c], K = P->sec_dim[c], lda = (int)r4(K);
@@ -1216,17 +1218,13 @@ void Engine::build_tc(MatvecPlan* P) {
     if (cur.e_end > cur.e_begin) packs.push_back(cur);
     const int p1 = (int)packs.size();
     for (int row0 = 0; row0 < M; row0 += 128)
-      for (int pb = p0; pb < p1; pb += kPacksPerUnit)
-        u1.push_back({x32 + xoff[c] + (int64_t)row0 * lda, lda, std::min(128, M - row0), K, row0, pb,
-                      std::min(p1, pb + kPacksPerUnit)});
+      H.r1.push_back({x32 + xoff[c] + (int64_t)row0 * lda, lda, std::min(128, M - row0), K, row0, p0, p1});
   }
   // phase 2
-  std::vector<Tc2Src> srcs;
-  std::vector<Tc2Task> tasks;
-  std::vector<Tc2Unit> u2;
+  std::vector<Tc2Src>& srcs = H.s;
+  std::vector<Tc2Task>& tasks = H.t;
   srcs.reserve(P->wsrc.size());
   tasks.reserve(P->witems.size());
-  constexpr int kTasksPerUnit = 48;
   for (int x = 0; x < (int)P->X.size(); ++x) {
     const XBlock& X = P->X[x];
     const int t0 = (int)tasks.size();
@@ -1249,9 +1247,10 @@ void Engine::build_tc(MatvecPlan* P) {
     if (t1 == t0) continue;
     for (int row0 = 0; row0 < X.rows; row0 += 128)
       for (int col0 = 0; col0 < X.cols; col0 += 64)
-        for (int tb = t0; tb < t1; tb += kTasksPerUnit)
-          u2.push_back({P->yout + X.off, X.cols, X.rows, X.cols, row0, col0, tb, std::min(t1, tb + kTasksPerUnit)});
+        H.r2.push_back({P->yout + X.off, X.cols, X.rows, X.cols, row0, col0, t0, t1});
   }
+  H.yout = P->yout;
+  H.n = P->n;
   // compulsory traffic (unpadded FP32 elements): phase 1 reads x and each right-operator
   // block once and writes every Z; phase 2 reads each task's Z sub-blocks and each
   // left-operator block once and writes y (FP64)
@@ -1262,7 +1261,7 @@ void Engine::build_tc(MatvecPlan* P) {
     P->tc_bytes1 = 4.0 * b1;
     P->tc_bytes2 = 4.0 * b2 + 8.0 * P->n;
   }
-  P->tc = tc_plan_upload(ents, packs, u1, srcs, tasks, u2, xbt, x32, x32t, P->n, stream_);
+  P->tc = tc_plan_build({&H}, tune_, stream_);
   // the host tables are not needed any more
   std::vector<MatvecPlan::ZGroup>().swap(P->zg);
   std::vector<MatvecPlan::WSrc>().swap(P->wsrc);
@@ -1271,12 +1270,25 @@ void Engine::build_tc(MatvecPlan* P) {
   st_.t_plan_ms += tm.ms();
 }
 
+Engine::TcView Engine::prepare_tc(int i) {
+  check_ready();
+  if (i < 0 || i > L_ - 2) throw std::out_of_range("site out of range");
+  MatvecPlan* p = plan_for(i);
+  if (!p->tc) build_tc(p);
+  return {&p->tch, p->serial, p->xin, p->yout, p->n, p->flops};
+}
+
+uint64_t Engine::tc_serial(int i) const {
+  return (cached_ && cached_site_ == i && cached_->tc) ? cached_->serial : 0;
+}
+
 void Engine::run_matvec(MatvecPlan* p, const double* x, double* y, bool tc) {
   if (tc) {
     flush_events();
     if (!ev_[0]) for (auto& e : ev_) e = event_create();
     if (!p->tc) build_tc(p);
-    tc_plan_run(p->tc, x, p->yout, ev_, stream_);
+    if (x != p->xin) dev_d2d(p->xin, x, sizeof(double) * p->n, stream_);
+    tc_plan_launch(p->tc, ev_, stream_);
     ev_pending_ = true;
     ev_tc_ = true;
     if (y != p->yout) dev_d2d(y, p->yout, sizeof(double) * p->n, stream_);
@@ -2008,12 +2020,18 @@ double Engine::solve(double* e_last_out) {
   double e_min = std::numeric_limits<double>::infinity(), e_last = 0.0;
   double e_prev = std::numeric_limits<double>::infinity();
   bool all_conv = true;
+  hist_D_.clear();
+  hist_E_.clear();
+  hist_w_.clear();
   for (size_t s = 0; s < sched_D_.size(); ++s) {
     const int D = sched_D_[s];
+    double e_mac = 0.0, w_mac = 0.0;  // lowest energy / largest discarded weight of the last macro-iteration
     const double econv = s < sched_econv_.size() ? sched_econv_[s] : 1e-8;
     const int nmax = s < sched_nmax_.size() ? sched_nmax_[s] : 1;
     const double gamma = s < sched_noise_.size() ? sched_noise_[s] : 0.0;
     for (int it = 0; it < nmax; ++it) {
+      e_mac = std::numeric_limits<double>::infinity();
+      w_mac = 0.0;
       for (int dir = 1; dir >= -1; dir -= 2) {
         double wmax = 0.0;
         for (int step = 0; step < L_ - 1; ++step) {
@@ -2026,6 +2044,8 @@ double Engine::solve(double* e_last_out) {
           e_min = std::min(e_min, e);
           e_last = e;
           wmax = std::max(wmax, w);
+          e_mac = std::min(e_mac, e);
+          w_mac = std::max(w_mac, w);
           st_.micro_iters += 1;
         }
         w_prev_ = wmax;
@@ -2034,6 +2054,9 @@ double Engine::solve(double* e_last_out) {
       e_prev = e_last;
       if (done) break;
     }
+    hist_D_.push_back(D);
+    hist_E_.push_back(e_mac);
+    hist_w_.push_back(w_mac);
   }
   st_.t_total_ms += total.ms();
   if (e_last_out) *e_last_out = e_last;

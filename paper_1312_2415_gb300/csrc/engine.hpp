@@ -120,6 +120,16 @@ class Engine {
   // Davidson, finished by FP64 Davidson iterations from the mixed-precision vector
   void set_precision(int p, int refine_iters) { precision_ = p; refine_iters_ = refine_iters; }
   int precision() const { return precision_; }
+  // Batched matvecs: the mixed-precision tables of site i (built if needed), the plan's
+  // serial (changes whenever the tables are rebuilt), its input / output buffers and
+  // flops.  The tables stay valid until the MPS or the site of the engine changes.
+  struct TcView { const TcHost* host; uint64_t serial; double* x; double* y; int64_t n; double flops; };
+  TcView prepare_tc(int i);
+  uint64_t tc_serial(int i) const;
+  void set_tune(TcTune t) { tune_ = t; }
+  const std::vector<int>& hist_D() const { return hist_D_; }
+  const std::vector<double>& hist_E() const { return hist_E_; }
+  const std::vector<double>& hist_w() const { return hist_w_; }
   int L() const { return L_; }
 
  private:
@@ -177,6 +187,12 @@ class Engine {
   bool ev_tc_ = false;
   int precision_ = 0;
   int refine_iters_ = 0;  // FP64 finishing iterations in mixed mode (0: up to the cap)
+  TcTune tune_;           // unit sizes of the tensor-core matvec
+  // per schedule instruction of the last solve: D, lowest energy and largest discarded
+  // weight of its last macro-iteration (the data of the extrapolation, Sec. 4.3)
+  std::vector<int> hist_D_;
+  std::vector<double> hist_E_, hist_w_;
+  uint64_t plan_serial_ = 0;
 };
 
 }  // namespace dmrg

@@ -655,16 +655,15 @@ __global__ void __launch_bounds__(kP2sThreads, 2)
 
 // ------------------------------------------------------------------ conversions
 
-// x (FP64) -> x32 (row-major stacks) and x32t (column-major stacks), one CTA per x block
-__global__ void k_x_prep(const double* __restrict__ x, float* __restrict__ x32, float* __restrict__ x32t,
-                         const TcXBlock* __restrict__ xb) {
+// x (FP64) -> the FP32 stacks (row-major) and their transposes, one CTA per x block
+__global__ void k_x_prep(const TcXBlock* __restrict__ xb) {
   const TcXBlock B = xb[blockIdx.x];
   const int n = B.rows * B.cols;
   for (int e = threadIdx.x; e < n; e += blockDim.x) {
     const int r = e / B.cols, c = e - r * B.cols;
-    const float v = (float)x[B.src + e];
-    x32[B.dst + (int64_t)r * B.ld + c] = v;
-    x32t[B.dstt + (int64_t)c * B.ldt + r] = v;
+    const float v = (float)B.src[e];
+    B.dst[(int64_t)r * B.ld + c] = v;
+    B.dstt[(int64_t)c * B.ldt + r] = v;
   }
 }
 
@@ -705,47 +704,67 @@ struct TcPlan {
   int n2_small = 0, n2 = 0;
   TcXBlock* xb = nullptr;
   int nxb = 0;
-  float* x32 = nullptr;
-  float* x32t = nullptr;
-  int64_t n = 0;
+  std::vector<std::pair<double*, int64_t>> clear;  // outputs zeroed before the products
+  int launches = 0;           // kernels of one launch sequence
 };
 
-TcPlan* tc_plan_upload(const std::vector<Tc1Entry>& e, const std::vector<Tc1Pack>& p,
-                       const std::vector<Tc1Unit>& u1, const std::vector<Tc2Src>& s,
-                       const std::vector<Tc2Task>& t, const std::vector<Tc2Unit>& u2,
-                       const std::vector<TcXBlock>& xb, float* x32, float* x32t, int64_t n,
-                       Stream st) {
-  for (const Tc1Pack& q : p)
-    if (q.e_end - q.e_begin > kMaxPackEntries || q.n > 128) throw std::logic_error("tc pack too large");
-  std::vector<Tc1Unit> ord;
-  ord.reserve(u1.size());
-  for (const Tc1Unit& q : u1)
-    if (q.K <= 32) ord.push_back(q);
-  const int n_one = (int)ord.size();
-  for (const Tc1Unit& q : u1)
-    if (q.K > 32) ord.push_back(q);
+TcPlan* tc_plan_build(const std::vector<const TcHost*>& inst, TcTune tune, Stream st) {
+  if (tune.packs_per_unit < 1 || tune.tasks_per_unit < 1) throw std::invalid_argument("tc tuning");
+  std::vector<Tc1Entry> e;
+  std::vector<Tc1Pack> p;
+  std::vector<Tc1Unit> u1, u1m;
+  std::vector<Tc2Src> sr;
+  std::vector<Tc2Task> t;
+  std::vector<Tc2Unit> u2, u2g;
+  std::vector<TcXBlock> xb;
   TcPlan* P = new TcPlan;
+  for (const TcHost* H : inst) {
+    const int e0 = (int)e.size(), p0 = (int)p.size(), s0 = (int)sr.size(), t0 = (int)t.size();
+    e.insert(e.end(), H->e.begin(), H->e.end());
+    for (Tc1Pack q : H->p) {
+      if (q.e_end - q.e_begin > kMaxPackEntries || q.n > 128) throw std::logic_error("tc pack too large");
+      q.e_begin += e0;
+      q.e_end += e0;
+      p.push_back(q);
+    }
+    for (const Tc1Unit& r : H->r1)
+      for (int pb = r.p_begin; pb < r.p_end; pb += tune.packs_per_unit) {
+        Tc1Unit u = r;
+        u.p_begin = p0 + pb;
+        u.p_end = p0 + std::min(r.p_end, pb + tune.packs_per_unit);
+        (r.K <= 32 ? u1 : u1m).push_back(u);
+      }
+    sr.insert(sr.end(), H->s.begin(), H->s.end());
+    for (Tc2Task q : H->t) {
+      q.s_begin += s0;
+      q.s_end += s0;
+      t.push_back(q);
+    }
+    for (const Tc2Unit& r : H->r2)
+      for (int tb = r.t_begin; tb < r.t_end; tb += tune.tasks_per_unit) {
+        Tc2Unit u = r;
+        u.t_begin = t0 + tb;
+        u.t_end = t0 + std::min(r.t_end, tb + tune.tasks_per_unit);
+        (r.m - r.row0 <= 32 ? u2 : u2g).push_back(u);
+      }
+    xb.insert(xb.end(), H->xb.begin(), H->xb.end());
+    if (H->yout && H->n > 0) P->clear.push_back({H->yout, H->n});
+  }
+  P->n1_one = (int)u1.size();
+  P->n1_multi = (int)u1m.size();
+  u1.insert(u1.end(), u1m.begin(), u1m.end());
+  P->n2_small = (int)u2.size();
+  u2.insert(u2.end(), u2g.begin(), u2g.end());
+  P->n2 = (int)u2.size();
   P->ents = upload(e, st);
   P->packs = upload(p, st);
-  P->u1 = upload(ord, st);
-  P->n1_one = n_one;
-  P->n1_multi = (int)ord.size() - n_one;
-  P->srcs = upload(s, st);
+  P->u1 = upload(u1, st);
+  P->srcs = upload(sr, st);
   P->tasks = upload(t, st);
-  std::vector<Tc2Unit> ord2;
-  ord2.reserve(u2.size());
-  for (const Tc2Unit& q : u2)
-    if (q.m - q.row0 <= 32) ord2.push_back(q);
-  P->n2_small = (int)ord2.size();
-  for (const Tc2Unit& q : u2)
-    if (q.m - q.row0 > 32) ord2.push_back(q);
-  P->u2 = upload(ord2, st);
-  P->n2 = (int)ord2.size();
+  P->u2 = upload(u2, st);
   P->xb = upload(xb, st);
   P->nxb = (int)xb.size();
-  P->x32 = x32;
-  P->x32t = x32t;
-  P->n = n;
+  P->launches = (P->nxb > 0) + (P->n1_one > 0) + (P->n1_multi > 0) + (P->n2_small > 0) + (P->n2 > P->n2_small);
   return P;
 }
 
@@ -761,49 +780,88 @@ void tc_plan_free(TcPlan* p, Stream s) {
   delete p;
 }
 
-void tc_plan_run(const TcPlan* p, const double* x, double* y, void* const* ev, Stream s) {
-  cudaStream_t cs = (cudaStream_t)s;
+namespace {
+
+void tc_set_attributes() {
   static bool attr = false;
-  if (!attr) {
-    ck(cudaFuncSetAttribute(k_tc_phase1<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            (int)smem_bytes(p1_smem_floats<true>())), "tc phase 1 smem");
-    ck(cudaFuncSetAttribute(k_tc_phase1<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            (int)smem_bytes(p1_smem_floats<false>())), "tc phase 1 smem");
-    ck(cudaFuncSetAttribute(k_tc_phase2, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            (int)smem_bytes(2 * kP2BufF)), "tc phase 2 smem");
-    ck(cudaFuncSetAttribute(k_tc_phase2s, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            (int)smem_bytes(kGroups * kP2sStageF)), "tc phase 2 smem");
-    attr = true;
-  }
-  if (ev) event_record(ev[0], s);
-  int launches = 0;
-  if (p->nxb > 0) {
-    k_x_prep<<<p->nxb, 256, 0, cs>>>(x, p->x32, p->x32t, p->xb);
-    ++launches;
-  }
-  ck(cudaMemsetAsync(y, 0, sizeof(double) * (size_t)(p->n > 0 ? p->n : 1), cs), "tc zero y");
-  if (p->n1_one > 0) {
+  if (attr) return;
+  ck(cudaFuncSetAttribute(k_tc_phase1<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)smem_bytes(p1_smem_floats<true>())), "tc phase 1 smem");
+  ck(cudaFuncSetAttribute(k_tc_phase1<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)smem_bytes(p1_smem_floats<false>())), "tc phase 1 smem");
+  ck(cudaFuncSetAttribute(k_tc_phase2, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)smem_bytes(2 * kP2BufF)), "tc phase 2 smem");
+  ck(cudaFuncSetAttribute(k_tc_phase2s, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)smem_bytes(kGroups * kP2sStageF)), "tc phase 2 smem");
+  attr = true;
+}
+
+void tc_enqueue(const TcPlan* p, void* const* ev, cudaStream_t cs) {
+  if (ev) event_record(ev[0], cs);
+  for (const auto& c : p->clear) ck(cudaMemsetAsync(c.first, 0, sizeof(double) * (size_t)c.second, cs), "tc zero y");
+  if (p->nxb > 0) k_x_prep<<<p->nxb, 256, 0, cs>>>(p->xb);
+  if (p->n1_one > 0)
     k_tc_phase1<true><<<p->n1_one, kThreads, smem_bytes(p1_smem_floats<true>()), cs>>>(p->u1, p->packs, p->ents);
-    ++launches;
-  }
-  if (p->n1_multi > 0) {
+  if (p->n1_multi > 0)
     k_tc_phase1<false><<<p->n1_multi, kThreads, smem_bytes(p1_smem_floats<false>()), cs>>>(
         p->u1 + p->n1_one, p->packs, p->ents);
-    ++launches;
-  }
-  if (ev) event_record(ev[1], s);
-  if (p->n2_small > 0) {
+  if (ev) event_record(ev[1], cs);
+  if (p->n2_small > 0)
     k_tc_phase2s<<<p->n2_small, kP2sThreads, smem_bytes(kGroups * kP2sStageF), cs>>>(p->u2, p->tasks, p->srcs);
-    ++launches;
-  }
-  if (p->n2 > p->n2_small) {
+  if (p->n2 > p->n2_small)
     k_tc_phase2<<<p->n2 - p->n2_small, kThreads, smem_bytes(2 * kP2BufF), cs>>>(p->u2 + p->n2_small, p->tasks,
                                                                                  p->srcs);
-    ++launches;
-  }
-  if (ev) event_record(ev[2], s);
-  note_launches(launches);
+  if (ev) event_record(ev[2], cs);
   ck(cudaGetLastError(), "tc matvec launch");
+}
+
+struct TcGraph {
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ex = nullptr;
+  int launches = 0;
+};
+
+}  // namespace
+
+void tc_plan_launch(const TcPlan* p, void* const* ev, Stream s) {
+  tc_set_attributes();
+  tc_enqueue(p, ev, (cudaStream_t)s);
+  note_launches(p->launches);
+}
+
+void* tc_graph_create(const TcPlan* p) {
+  tc_set_attributes();
+  cudaStream_t cs;
+  ck(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "graph stream");
+  TcGraph* G = new TcGraph;
+  G->launches = p->launches;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    tc_enqueue(p, nullptr, cs);
+    e = cudaStreamEndCapture(cs, &G->g);
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&G->ex, G->g, 0);
+  cudaStreamDestroy(cs);
+  if (e != cudaSuccess) {
+    if (G->g) cudaGraphDestroy(G->g);
+    delete G;
+    throw std::runtime_error(std::string("cuda graph of the batched matvec: ") + cudaGetErrorString(e));
+  }
+  return G;
+}
+
+void tc_graph_launch(void* g, Stream s) {
+  TcGraph* G = (TcGraph*)g;
+  ck(cudaGraphLaunch(G->ex, (cudaStream_t)s), "graph launch");
+  note_launches(G->launches);
+}
+
+void tc_graph_free(void* g) {
+  TcGraph* G = (TcGraph*)g;
+  if (!G) return;
+  if (G->ex) cudaGraphExecDestroy(G->ex);
+  if (G->g) cudaGraphDestroy(G->g);
+  delete G;
 }
 
 void tc_mirror(const std::vector<TcMirror>& m, Stream s) {
