@@ -23,7 +23,7 @@ def test_energy_extrapolation_towards_fci():
     h, V = hubbard_chain(8, 1.0, 4.0)
     ctx = Context(8, [0] * 8, 8, 0, 0)
     ctx.set_integrals(h, V)
-    Ds = [16, 24, 32, 48]
+    Ds = [8, 10, 12, 14]  # below the chain's Schmidt rank: energies 3e-3 .. 4e-5 Eh above FCI
     ctx.set_schedule(Ds, [1e-9] * 4, [6] * 4, [0.0] * 4, 1e-10, 200)
     ctx.init_mps(5)
     ctx.solve()
@@ -33,4 +33,4 @@ def test_energy_extrapolation_towards_fci():
     assert all(W[k] > W[k + 1] for k in range(3))
     e0, c1 = extrapolate(W, E)
     assert c1 > 0.0
-    assert abs(e0 - e_fci) < abs(E[-1] - e_fci), (e0, E[-1], e_fci)
+    assert abs(e0 - e_fci) < 0.1 * abs(E[-1] - e_fci), (e0, E[-1], e_fci)
