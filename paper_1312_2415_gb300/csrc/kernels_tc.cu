@@ -169,23 +169,45 @@ __device__ __forceinline__ Item item(int e) { return {(e >> 6) * 8 + (e & 7), (e
 // Stage rows [0, nrows) of a 32-column chunk into hi / lo tiles from row-major FP32 data:
 // tile(row_base + r, k) = a X[r ld + k0 + k] for the first kval4 groups of 4 columns,
 // zero for the following groups up to nkg (kpad / 4).  Columns past K inside the last
-// group read the zero padding of X.  Threads t0, t0 + nthr, ... of the caller.
+// group read the zero padding of X.  Threads t0, t0 + nthr, ... of the caller; each
+// thread issues the loads of up to four items before it uses any of them.
 __device__ __forceinline__ void stage4(float* hi, float* lo, int row_base, int nrows, int nkg, int kval4,
                                        const float* __restrict__ X, int ld, int k0, float a, int t0,
                                        int nthr) {
   const int ne = ((nrows + 7) >> 3) * 64;
-  for (int e = t0; e < ne; e += nthr) {
-    const Item it = item(e);
-    if (it.r >= nrows || it.kb >= nkg) continue;
-    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (it.kb < kval4) {
-      v = ldg4(X + (size_t)it.r * ld + k0 + it.kb * 4);
-      v.x *= a;
-      v.y *= a;
-      v.z *= a;
-      v.w *= a;
-    }
+  if (ne <= nthr) {  // one item per thread at most
+    if (t0 >= ne) return;
+    const Item it = item(t0);
+    if (it.r >= nrows || it.kb >= nkg) return;
+    float4 v = it.kb < kval4 ? ldg4(X + (size_t)it.r * ld + k0 + it.kb * 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+    v.x *= a;
+    v.y *= a;
+    v.z *= a;
+    v.w *= a;
     put_split4(hi, lo, kmo(row_base + it.r, it.kb * 4), v);
+    return;
+  }
+  for (int e0 = 0; e0 < ne; e0 += 4 * nthr) {
+    float4 v[4];
+    Item it[4];
+    bool st[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int e = e0 + t0 + i * nthr;
+      it[i] = item(e);
+      st[i] = e < ne && it[i].r < nrows && it[i].kb < nkg;
+      v[i] = (st[i] && it[i].kb < kval4) ? ldg4(X + (size_t)it[i].r * ld + k0 + it[i].kb * 4)
+                                         : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (st[i]) {
+        v[i].x *= a;
+        v[i].y *= a;
+        v[i].z *= a;
+        v[i].w *= a;
+        put_split4(hi, lo, kmo(row_base + it[i].r, it[i].kb * 4), v[i]);
+      }
   }
 }
 
@@ -203,7 +225,8 @@ __device__ __forceinline__ void stage4_identity(float* hi, float* lo, int nrows,
   }
 }
 
-// B = W^T rows col0 .. col0 + nrows - 1: sum over sources of coef * z[(col0 + j) ldz + k0 + k]
+// B = W^T rows col0 .. col0 + nrows - 1: sum over sources of coef * z[(col0 + j) ldz + k0 + k].
+// Up to four items per thread; the loads of two sources are issued before their sums.
 __device__ __forceinline__ void stage4_wsum(float* hi, float* lo, int nrows, int nkg, int kval4,
                                             const Tc2Src* __restrict__ srcs, int s_begin, int s_end, int col0,
                                             int k0, int t0, int nthr) {
@@ -211,19 +234,29 @@ __device__ __forceinline__ void stage4_wsum(float* hi, float* lo, int nrows, int
   for (int e0 = 0; e0 < ne; e0 += 4 * nthr) {
     float4 acc[4];
     Item it[4];
+    bool ld[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int e = e0 + t0 + i * nthr;
       it[i] = item(e);
       if (e >= ne) it[i].r = 1 << 20;
+      ld[i] = it[i].r < nrows && it[i].kb < kval4;
       acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    for (int si = s_begin; si < s_end; ++si) {
-      const Tc2Src S = srcs[si];
-      const float* zb = S.z + (size_t)col0 * S.ldz + k0;
+    for (int si = s_begin; si < s_end; si += 2) {
+      const bool two = si + 1 < s_end;
+      const Tc2Src S0 = srcs[si];
+      const Tc2Src S1 = two ? srcs[si + 1] : S0;
+      const float* z0 = S0.z + (size_t)col0 * S0.ldz + k0;
+      const float* z1 = S1.z + (size_t)col0 * S1.ldz + k0;
+      float4 v0[4], v1[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
-        if (it[i].r < nrows && it[i].kb < kval4) acc[i] = fma4(S.coef, ldg4(zb + (size_t)it[i].r * S.ldz + it[i].kb * 4), acc[i]);
+      for (int i = 0; i < 4; ++i) {
+        v0[i] = ld[i] ? ldg4(z0 + (size_t)it[i].r * S0.ldz + it[i].kb * 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+        v1[i] = (ld[i] && two) ? ldg4(z1 + (size_t)it[i].r * S1.ldz + it[i].kb * 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) acc[i] = fma4(S1.coef, v1[i], fma4(S0.coef, v0[i], acc[i]));
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i)
@@ -492,6 +525,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 // rows of W^T (hi, lo); the MMA still reads 128 rows of A, and rows 32..127 fall on the
 // rest of the same stage: they only produce accumulator rows that are never read.
 constexpr int kGroups = 4, kGroupThreads = 64;
+constexpr int kAcc = 4;  // TMEM accumulators (64 columns each) of the MMA warp's segments
+constexpr int kUnitTasks = 128, kUnitSrcs = 384;  // descriptors held in shared memory
 constexpr int kP2sThreads = kGroups * kGroupThreads + 32;
 constexpr int kSA = 32 * 32, kSB = 64 * 32;   // floats of an A (32-row) / B (64-row) tile
 constexpr int kP2sStageF = 2 * kSA + 2 * kSB;  // 24 KB: the 16 KB A footprint stays inside
@@ -530,22 +565,31 @@ __global__ void __launch_bounds__(kP2sThreads, 2)
   float* sm = (float*)(((uintptr_t)smem_dyn + 127) & ~(uintptr_t)127);
   __shared__ __align__(8) uint64_t full[kGroups];
   __shared__ __align__(8) uint64_t empty[kGroups];
-  __shared__ __align__(8) uint64_t accf[2];
+  __shared__ __align__(8) uint64_t accf[kAcc];
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
+  // the unit's task and source descriptors, loaded once (the loops would otherwise put
+  // a dependent global load in front of every step)
+  __shared__ Tc2Task stask[kUnitTasks];
+  __shared__ Tc2Src ssrc[kUnitSrcs];
 
   const Tc2Unit u = units[blockIdx.x];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int mv = u.m - u.row0, nv = min(64, u.n - u.col0);  // mv <= 32 by construction
   const int n16 = (nv + 15) & ~15;
-  if (warp == kGroups * 2) tmem_alloc(&tmem_slot, 128);
+  const int ntask = u.t_end - u.t_begin;  // <= kUnitTasks by construction
+  const int s0 = tasks[u.t_begin].s_begin, nsrc = tasks[u.t_end - 1].s_end - s0;
+  const Tc2Src* S = nsrc <= kUnitSrcs ? ssrc : srcs + s0;  // sources relative to s0
+  for (int k = tid; k < ntask; k += kP2sThreads) stask[k] = tasks[u.t_begin + k];
+  if (nsrc <= kUnitSrcs)
+    for (int k = tid; k < nsrc; k += kP2sThreads) ssrc[k] = srcs[s0 + k];
+  if (warp == kGroups * 2) tmem_alloc(&tmem_slot, 64 * kAcc);
   if (tid == 0) {
     for (int g = 0; g < kGroups; ++g) {
       mbar_init_n(&full[g], kGroupThreads);
       mbar_init_n(&empty[g], 1);
     }
-    mbar_init_n(&accf[0], 1);
-    mbar_init_n(&accf[1], 1);
+    for (int a = 0; a < kAcc; ++a) mbar_init_n(&accf[a], 1);
     asm volatile("fence.mbarrier_init.release.cluster;");
     abort_flag = 0;
   }
@@ -561,8 +605,8 @@ __global__ void __launch_bounds__(kP2sThreads, 2)
     float* Bh = Al + kSA;
     float* Bl = Bh + kSB;
     int s = 0;
-    for (int t = u.t_begin; t < u.t_end && !abort_flag; ++t) {
-      const Tc2Task T = tasks[t];
+    for (int t = 0; t < ntask && !abort_flag; ++t) {
+      const Tc2Task& T = stask[t];
       const int nch = (T.K + 31) >> 5;
       for (int ch = 0; ch < nch; ++ch, ++s) {
         if ((s & (kGroups - 1)) != g) continue;
@@ -572,20 +616,22 @@ __global__ void __launch_bounds__(kP2sThreads, 2)
         const int nkg = kpad >> 2, kval4 = (kvalid + 3) >> 2;
         if (T.C) stage4(Ah, Al, 0, mv, nkg, kval4, T.C + (size_t)u.row0 * T.ldc, T.ldc, k0, T.alpha, gt, kGroupThreads);
         else stage4_identity(Ah, Al, mv, nkg, kvalid, u.row0, k0, T.alpha, gt, kGroupThreads);
-        stage4_wsum(Bh, Bl, nv, nkg, kval4, srcs, T.s_begin, T.s_end, u.col0, k0, gt, kGroupThreads);
+        stage4_wsum(Bh, Bl, nv, nkg, kval4, S, T.s_begin - s0, T.s_end - s0, u.col0, k0, gt, kGroupThreads);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive(&full[g]);
       }
     }
   } else {
-    // ---- warp 8: lane 0 issues the MMAs of segment j into accumulator j & 1; the warp
-    // then adds segment j - 1 (accumulator rows 0..31 = TMEM lanes 0..31) to its
-    // registers while the tensor core works on segment j
+    // ---- warp 8: lane 0 issues the MMAs of segment j into accumulator j % kAcc; the
+    // warp adds finished segments (accumulator rows 0..31 = TMEM lanes 0..31) to its
+    // registers kAcc - 1 segments behind, so the tensor core always has work queued
     const uint32_t idesc = idesc_tf32(n16);
     float acc[64];
 #pragma unroll
     for (int i = 0; i < 64; ++i) acc[i] = 0.0f;
-    uint32_t ph_acc[2] = {0, 0};
+    uint32_t ph_acc[kAcc];
+#pragma unroll
+    for (int a = 0; a < kAcc; ++a) ph_acc[a] = 0;
     auto drain = [&](int a) {
       int ok = 1;
       if (lane == 0) ok = mbar_wait_or_abort(&accf[a], ph_acc[a], &abort_flag);
@@ -605,10 +651,10 @@ __global__ void __launch_bounds__(kP2sThreads, 2)
       asm volatile("tcgen05.fence::before_thread_sync;");
       __syncwarp();
     };
-    int s = 0, seg = 0, in_seg = 0;
+    int s = 0, seg = 0, in_seg = 0, drained = 0;
     bool stop = false;
-    for (int t = u.t_begin; t < u.t_end && !stop; ++t) {
-      const int K = tasks[t].K;
+    for (int t = 0; t < ntask && !stop; ++t) {
+      const int K = stask[t].K;
       const int nch = (K + 31) >> 5;
       for (int ch = 0; ch < nch; ++ch, ++s) {
         const int g = s & (kGroups - 1);
@@ -617,29 +663,29 @@ __global__ void __launch_bounds__(kP2sThreads, 2)
             asm volatile("tcgen05.fence::after_thread_sync;");
             const int kvalid = min(32, K - ch * 32), kpad = (kvalid + 7) & ~7;
             float* Ah = sm + g * kP2sStageF;
-            mma_chunk(tmem + (uint32_t)((seg & 1) * 64), Ah, Ah + kSA, Ah + 2 * kSA, Ah + 2 * kSA + kSB, kpad,
+            mma_chunk(tmem + (uint32_t)((seg % kAcc) * 64), Ah, Ah + kSA, Ah + 2 * kSA, Ah + 2 * kSA + kSB, kpad,
                       idesc, in_seg == 0);
             mma_commit(&empty[g]);
           }
         }
         if (__shfl_sync(0xffffffffu, (int)abort_flag, 0)) { stop = true; break; }
         if (++in_seg == kSegSteps) {
-          if (lane == 0) mma_commit(&accf[seg & 1]);
+          if (lane == 0) mma_commit(&accf[seg % kAcc]);
           __syncwarp();
-          if (seg > 0) drain((seg - 1) & 1);
           ++seg;
           in_seg = 0;
+          // the accumulator of segment `seg` is reused next: keep at most kAcc - 1 pending
+          while (seg - drained > kAcc - 1) drain(drained++ % kAcc);
         }
       }
     }
     if (!stop && !__shfl_sync(0xffffffffu, (int)abort_flag, 0)) {
       if (in_seg > 0) {
-        if (lane == 0) mma_commit(&accf[seg & 1]);
+        if (lane == 0) mma_commit(&accf[seg % kAcc]);
         __syncwarp();
-        if (seg > 0) drain((seg - 1) & 1);
         ++seg;
       }
-      if (seg > 0) drain((seg - 1) & 1);
+      while (drained < seg) drain(drained++ % kAcc);
       if (!__shfl_sync(0xffffffffu, (int)abort_flag, 0) && lane < mv) {
         double* yr = u.y + (size_t)(u.row0 + lane) * u.ldy + u.col0;
 #pragma unroll
@@ -650,7 +696,7 @@ __global__ void __launch_bounds__(kP2sThreads, 2)
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  if (warp == kGroups * 2) tmem_free(tmem, 128);
+  if (warp == kGroups * 2) tmem_free(tmem, 64 * kAcc);
 }
 
 // ------------------------------------------------------------------ conversions
@@ -709,7 +755,8 @@ struct TcPlan {
 };
 
 TcPlan* tc_plan_build(const std::vector<const TcHost*>& inst, TcTune tune, Stream st) {
-  if (tune.packs_per_unit < 1 || tune.tasks_per_unit < 1) throw std::invalid_argument("tc tuning");
+  if (tune.packs_per_unit < 1 || tune.tasks_per_unit < 1 || tune.tasks_per_unit > kUnitTasks)
+    throw std::invalid_argument("tc tuning");
   std::vector<Tc1Entry> e;
   std::vector<Tc1Pack> p;
   std::vector<Tc1Unit> u1, u1m;
