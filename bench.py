@@ -155,7 +155,7 @@ def measured_peaks():
 
 def fp64_peak_measured():
     """FP64 roof on this GPU: cuBLAS DGEMM 8192^3 throughput (best of 3), measured here
-    because the driver's peak file carries HBM and bf16 only."""
+    because the measured-peaks file carries HBM and bf16 only."""
     import torch
     n = 8192
     a = torch.randn(n, n, device="cuda", dtype=torch.float64)

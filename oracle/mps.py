@@ -1,6 +1,6 @@
 """Reduced spin-adapted MPS for the oracle (plain loops, FP64).
 
-Conventions (each a reading of the paper, listed in the design doc):
+Conventions (each a reading of the paper where it leaves the choice open):
   * Sec. 3.2 local states of orbital k: index 0 = empty (s=0, N=0, I=0),
     1 = singly occupied (s=1/2, N=1, I=I_k), 2 = doubly occupied (s=0, N=2, I=0);
     m-resolved |up> = a+_{k,up}|0>, |dn> = a+_{k,dn}|0>, |2> = a+_{k,up} a+_{k,dn}|0>.
