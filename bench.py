@@ -467,12 +467,15 @@ def run_gb300(args):
     e2e = None if args.no_e2e else run_e2e(ctx, center, D, args, n_x)
     sweeps = None
     if not args.no_sweep:
+        start = ctx.get_mps() if args.sweep else None  # both precisions start from this state
         r, l, e = sweep_time(ctx, cfg["L"], D, args.precision, args.fp64_iters, args.davidson_iters)
         sweeps = {("mixed" if args.precision == 1 else "fp64"): {"macro_s": r + l, "right_s": r, "left_s": l,
                                                                 "energy_last": e},
                   "what": "one macro-iteration (L-1 steps right, L-1 left) from the canonical state "
-                          f"at site 0, fixed D, {args.davidson_iters} Davidson iterations per step"}
+                          f"at site 0, fixed D, {args.davidson_iters} Davidson iterations per step "
+                          "(with --sweep both precisions start from the same state)"}
         if args.sweep and args.precision == 1:
+            ctx.set_mps(start)
             r, l, e = sweep_time(ctx, cfg["L"], D, 0, 0, args.davidson_iters)
             sweeps["fp64"] = {"macro_s": r + l, "right_s": r, "left_s": l, "energy_last": e}
         ctx.set_precision(args.precision, args.fp64_iters)
