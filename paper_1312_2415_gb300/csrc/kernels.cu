@@ -531,7 +531,7 @@ void vec_add_noise(double* x, int64_t n, double amp, uint64_t seed, Stream s) {
 // ------------------------------------------------------------------ batched Jacobi
 
 namespace {
-constexpr int kEigSmemN = 112;  // blocks up to this size are diagonalised in shared memory
+constexpr int kEigSmemN = 64;  // blocks up to this size are diagonalised in shared memory
 
 // Cyclic Jacobi (round-robin pairing, n/2 rotations per step) on one symmetric block per
 // CTA, the matrix and the eigenvectors in shared memory (row stride n+1).  A pair is rotated only while |a_pq| exceeds
@@ -654,13 +654,14 @@ struct BjJob {
 
 // cyclic Jacobi on a 64 x 64 symmetric matrix A (shared memory, stride kOL),
 // eigenvectors accumulated into V (identity on entry), all 256 threads; a pair is
-// rotated while |a_pq| > 1e-16 sqrt|a_pp a_qq| + floor_abs (at most 8 sweeps: the
-// outer iteration returns to the pair)
+// rotated while |a_pq| > 1e-16 sqrt|a_pp a_qq| + floor_abs, for at most 3 sweeps: the
+// outer iteration returns to every pair until it is diagonal, and full inner
+// convergence in the early outer sweeps costs more than it saves (measured)
 __device__ void cta_jacobi64(double* A, double* V, double* cs, double* sn, int* pq, int* nrot,
                              double floor_abs) {
   const int tid = threadIdx.x;
   constexpr int m = kOP, np = kOP, nr = kOP / 2;
-  for (int sweep = 0; sweep < 8; ++sweep) {
+  for (int sweep = 0; sweep < 3; ++sweep) {
     if (tid == 0) *nrot = 0;
     __syncthreads();
     for (int step = 0; step < np - 1; ++step) {
