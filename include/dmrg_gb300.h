@@ -121,6 +121,21 @@ int dmrg_canonicalize(dmrg_ctx* ctx, int center);
  * energy of all micro-iterations (including E_const), *e_last = the last one. */
 int dmrg_solve(dmrg_ctx* ctx, double* e_min, double* e_last);
 
+/* Spin-summed one- and two-particle reduced density matrices of the current MPS, the
+ * derivatives of its energy with respect to the integrals (the quantities DMRG-SCF
+ * consumes, Sec. 6; energy of Sec. 4.1):
+ *   Gamma[((i*L + j)*L + k)*L + l] = sum_st <a+_is a+_jt a_lt a_ks>, projected onto the
+ *     eight index permutations under which V is invariant (the only part an energy with
+ *     such a V depends on), so that dE/dV_ijkl = Gamma_ijkl / 2 for symmetric changes;
+ *   gamma[i*L + k] = sum_s <a+_is a_ks> = sum_j Gamma_ijkj / (N - 1) = dE/dh_ik;
+ *   E = E_const + sum h gamma + 1/2 sum V Gamma.
+ * Computed on the device by the adjoint of the H_eff matvec (Eq. 9) with respect to the
+ * scalars of the operator recursion (Sec. 2.5), one pass over the site pairs with the
+ * centre moving right; afterwards the MPS is in mixed canonical form around L-2 (same
+ * state).  gamma (L*L doubles) and Gamma (L^4 doubles) are device pointers when stream
+ * != 0, host pointers when stream == 0.  DMRG_EINVAL on NULL outputs. */
+int dmrg_rdm(dmrg_ctx* ctx, double* gamma, double* Gamma, uintptr_t stream);
+
 /* Block table of x for sites (site, site+1): n_blocks rows of 12 int64 (2jL, NL, IL,
  * s1, s2, 2j, 2jR, NR, IR, dL, dR, offset) with s1, s2 the local states 0|1|2 and the
  * block stored row-major at x + offset.  table may be NULL (sizes only). */

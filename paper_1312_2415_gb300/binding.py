@@ -60,6 +60,7 @@ _SIGS = {
     "dmrg_tt_to_x": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t]),
     "dmrg_heff_matvec": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
     "dmrg_heff_diag": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t]),
+    "dmrg_rdm": (ctypes.c_int, [_P, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
     "dmrg_heff_matvec_noalloc": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                                 ctypes.c_size_t]),
     "dmrg_davidson": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, _D, _I]),
@@ -236,6 +237,18 @@ class Context:
         p, s = _ptr_and_stream(out)
         self._check(self.lib.dmrg_heff_diag(self.h, site, p, s))
         return out
+
+    def rdm(self, gamma=None, Gamma=None):
+        """Spin-summed 1- and 2-RDMs of the current MPS (dmrg_rdm): gamma (L, L) and
+        Gamma (L, L, L, L), numpy (host) or float64 CUDA tensors (device)."""
+        L = self.L
+        if gamma is None:
+            gamma, Gamma = np.zeros((L, L)), np.zeros((L,) * 4)
+        p1, s = _ptr_and_stream(gamma)
+        p2, _ = _ptr_and_stream(Gamma)
+        assert gamma.shape == (L, L) and Gamma.shape == (L,) * 4
+        self._check(self.lib.dmrg_rdm(self.h, p1, p2, s))
+        return gamma, Gamma
 
     def davidson(self, site, x):
         p, s = _ptr_and_stream(x)

@@ -279,6 +279,25 @@ int dmrg_heff_matvec_noalloc(dmrg_ctx* c, int site, const double* x, double* y, 
   });
 }
 
+int dmrg_rdm(dmrg_ctx* c, double* gamma, double* Gamma, uintptr_t stream) {
+  return guard(c, [&] {
+    if (!gamma || !Gamma) return DMRG_EINVAL;
+    wait_user(stream);
+    const int64_t L = c->eng->L();
+    dmrg::Stream s = dev_stream(c);
+    if (stream) {
+      c->eng->rdm(gamma, Gamma);
+    } else {
+      DevBuf d1(L * L, s), d2(L * L * L * L, s);
+      c->eng->rdm(d1.p, d2.p);
+      dmrg::dev_d2h(gamma, d1.p, sizeof(double) * L * L, s);
+      dmrg::dev_d2h(Gamma, d2.p, sizeof(double) * L * L * L * L, s);
+    }
+    dmrg::dev_sync(s);
+    return DMRG_OK;
+  });
+}
+
 int dmrg_heff_diag(dmrg_ctx* c, int site, double* d, uintptr_t stream) {
   return guard(c, [&] {
     if (!d) return DMRG_EINVAL;

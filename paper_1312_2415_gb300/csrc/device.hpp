@@ -83,6 +83,23 @@ DiagPlan* diag_plan_upload(const std::vector<DiagTerm>& t, const std::vector<Dia
 void diag_plan_run(const DiagPlan* p, Stream s);
 void diag_plan_free(DiagPlan* p, Stream s);
 
+// ---- grouped Frobenius products: *out_g += sum_t alpha_t sum_ij A_t(i,j) B_t(i,j) ----
+struct DotTask {
+  const double* A;
+  const double* B;
+  int lda, ldb, rows, cols;
+  double alpha;
+};
+struct DotGroup {
+  double* out;       // distinct across the groups of one call
+  int task_begin, task_end;
+};
+void dot_grouped(const std::vector<DotTask>& t, const std::vector<DotGroup>& g, Stream s);
+// RDMs from the derivatives dg = dE/dg_ijkl of the energy with respect to the folded
+// integrals of Eq. 11: Gamma = 2 x (average of dg over the eight permutations of V),
+// gamma_ik = sum_j Gamma_ijkj / (N - 1)
+void rdm_finish(const double* dg, int L, int N, double* gamma, double* Gamma, Stream s);
+
 // ---- dense vector kernels for Davidson (FP64) ----
 // out[j] = <V_j, w>, j < m; V is column-block storage V + j*ldv.
 void vec_multidot(const double* V, int64_t ldv, int m, const double* w, int64_t n, double* out,

@@ -113,6 +113,8 @@ void Engine::set_integrals(double econst, const double* h, const double* V) {
             if (std::fabs(v - s) > tol) throw std::domain_error("V lacks eightfold symmetry");
         }
   g_.L = L;
+  g_.ir = ir;
+  g_.keep_zero = false;
   g_.g.assign((size_t)L * L * L * L, 0.0);
   const double f = 1.0 / (N_ - 1);
   for (int i = 0; i < L; ++i)
@@ -128,6 +130,7 @@ void Engine::set_integrals(double econst, const double* h, const double* V) {
   Timer t;
   W_.assign(L, {});
   for (int k = 0; k < L; ++k) W_[k] = build_site_recursion(k, opsets_[k], opsets_[k + 1], g_, pt_);
+  Wg_.clear();
   st_.t_plan_ms += t.ms();
   have_integrals_ = true;
   for (auto& e : lenv_) free_env(e);
@@ -491,6 +494,7 @@ void Engine::group_left(int i, std::vector<CombOp>& out, double** scratch, int64
       it = idx.find(key);
     }
     out[it->second].sources.push_back({w.a, w.scalar});
+    out[it->second].grad.push_back({w.gi, w.gc});
   }
   const int id_op = opsets_[i].find({OP_I, -1, -1, 0});
   for (auto& c : out)
@@ -523,6 +527,7 @@ void Engine::group_right(int j, std::vector<CombOp>& out, double** scratch, int6
       it = idx.find(key);
     }
     out[it->second].sources.push_back({w.b, w.scalar});
+    out[it->second].grad.push_back({w.gi, w.gc});
   }
   const int h_op = opsets_[j + 1].find({OP_H, -1, -1, 0});
   for (auto& c : out)
@@ -724,7 +729,9 @@ struct Engine::MatvecPlan {
   int64_t zsize = 0;
   // host tables kept for the mixed-precision plan (built on first use, then released)
   struct ZGroup { const double* D; int n, K; double alpha; int c; int64_t off; };
-  struct WSrc { int zg, xb; double coef; };  // source x block xb; zg < 0: D is the identity
+  // source x block xb; zg < 0: D is the identity; right group gr, coefficient without
+  // the group's scalar craw
+  struct WSrc { int zg, xb; double coef; int gr; double craw; };
   struct WItem { int gl, cbi, rows, cols, src_begin, src_end; };
   std::vector<ZGroup> zg;
   std::vector<WSrc> wsrc;
@@ -978,7 +985,7 @@ Engine::MatvecPlan* Engine::plan_matvec(int i) {
         // identity right operator: Z is x itself, its alias scalar goes here
         const WS ws1{zoff, z.ld, D.identity ? q.coef * D.scalar : q.coef, z.zg, q.x};
         wsrc.push_back(ws1);
-        P->wsrc.push_back({ws1.zg, ws1.xb, ws1.coef});
+        P->wsrc.push_back({ws1.zg, ws1.xb, ws1.coef, q.gr, q.coef});
       }
       w.src_end = (int)wsrc.size();
       P->witems.push_back({I.gl, I.cbi, w.rows, w.cols, w.src_begin, w.src_end});
@@ -1971,6 +1978,200 @@ void Engine::canonicalize(int center) {
     left_normalize_site(i);
   }
   (void)tm;
+}
+
+// ---------------------------------------------------------------- RDMs
+//
+// For a fixed state the energy is linear in the folded integrals g of Eq. 11,
+// E = E_c + 1/2 sum g_ijkl Gamma_ijkl, so the RDMs are the derivatives dE/dg.  The
+// integrals enter the operator recursion only through the scalars s_e of its terms
+// (s_e = gc_e g[gi_e]), and with the folded Hamiltonian written as the chain of site
+// recursions, dE/ds_e for a term of site k is the expectation value of
+// L_a(bond k) (x) [site pattern] (x) R_b(bond k+1): with the two-site object x at sites
+// (k, k+1) that is x^T (L_a (x) P_e (x) D_b) x / x^T x, D_b the right combined operator
+// of the matvec (Eq. 9).  This is the adjoint of the matvec with respect to its left
+// operator blocks: if y = sum C W (phase 2), d(x^T y)/dC = sum x_out W^T =: Gbar, and
+// dE/ds_e = <L_a, Gbar_C> summed over the blocks of the combined operator C that holds
+// the term.  The sweep therefore visits every site pair once with the centre moving
+// right; the terms of the last site (whose right partner is the 1 x 1 end operator) are
+// differentiated through the right combined operators at the last pair instead:
+// dE/dd = sum coef <C^T x_out, x_src> for a right operator of value d.
+void Engine::rdm(double* gamma, double* Gamma) {
+  check_ready();
+  if (Wg_.empty()) {
+    Integrals gz = g_;
+    gz.keep_zero = true;
+    Wg_.assign(L_, {});
+    for (int k = 0; k < L_; ++k) Wg_[k] = build_site_recursion(k, opsets_[k], opsets_[k + 1], gz, pt_);
+  }
+  // the recursion with every allowed term holds the same operator values; it is swapped
+  // in for the sweep and back out whatever happens
+  struct Swap {
+    std::vector<std::vector<WEntry>>& a;
+    std::vector<std::vector<WEntry>>& b;
+    Swap(std::vector<std::vector<WEntry>>& x, std::vector<std::vector<WEntry>>& y) : a(x), b(y) { std::swap(a, b); }
+    ~Swap() { std::swap(a, b); }
+  } swap_in(W_, Wg_);
+  canonicalize(0);
+  const int64_t L4 = (int64_t)L_ * L_ * L_ * L_;
+  double* dg = (double*)dev_alloc(sizeof(double) * L4, stream_);
+  dev_zero(dg, sizeof(double) * L4, stream_);
+  try {
+    for (int i = 0; i <= L_ - 2; ++i) {
+      MatvecPlan* P = plan_matvec(i);
+      try {
+        tt_to_x(i, P->xin);
+        rdm_site(P, i, dg, i == L_ - 2);
+      } catch (...) {
+        free_plan(P);
+        throw;
+      }
+      free_plan(P);
+      if (i < L_ - 2) {
+        left_normalize_site(i);
+        left_normalize_site(i);
+      }
+    }
+    rdm_finish(dg, L_, N_, gamma, Gamma, stream_);
+  } catch (...) {
+    dev_free(dg, stream_);
+    for (auto& e : lenv_) free_env(e);
+    for (auto& e : renv_) free_env(e);
+    throw;
+  }
+  dev_free(dg, stream_);
+  // the environments were built from the full recursion: same values, other tables
+  for (auto& e : lenv_) free_env(e);
+  for (auto& e : renv_) free_env(e);
+  dev_sync(stream_);
+}
+
+void Engine::rdm_site(MatvecPlan* P, int i, double* dg, bool last) {
+  const int64_t n = P->n;
+  // |x|^2 (tasks of at most 2^30 elements)
+  double* nrm = (double*)dev_alloc(sizeof(double), stream_);
+  dev_zero(nrm, sizeof(double), stream_);
+  {
+    std::vector<DotTask> t;
+    for (int64_t o = 0; o < n; o += (int64_t)1 << 30) {
+      const int c = (int)std::min<int64_t>((int64_t)1 << 30, n - o);
+      t.push_back({P->xin + o, P->xin + o, c, c, 1, c, 1.0});
+    }
+    dot_grouped(t, {{nrm, 0, (int)t.size()}}, stream_);
+  }
+  double n2 = 0.0;
+  dev_d2h(&n2, nrm, sizeof(double), stream_);
+  dev_sync(stream_);
+  dev_free(nrm, stream_);
+  if (!(n2 > 0.0)) throw std::runtime_error("two-site object has zero norm");
+  // W = sum coef Z (phases 1 and the combine of the FP64 matvec)
+  if (P->zsize) dev_zero(P->Z, sizeof(double) * P->zsize, stream_);
+  gemm_plan_run(P->p1, stream_);
+  comb_plan_run(P->pc, stream_);
+  const size_t nw = P->witems.size();
+  std::vector<int64_t> woff(nw);
+  std::vector<int> wxp(nw, -1);
+  {
+    int64_t o = 0;
+    for (size_t k = 0; k < nw; ++k) {
+      woff[k] = o;
+      o += (int64_t)P->witems[k].rows * P->witems[k].cols;
+    }
+    for (int x = 0; x < (int)P->w_by_x.size(); ++x)
+      for (int k : P->w_by_x[x]) wxp[k] = x;
+  }
+  // Gbar(gl, cbi) = sum over its W items of x_out W^T / |x|^2
+  std::map<std::pair<int, int>, std::vector<int>> by_blk;
+  for (size_t k = 0; k < nw; ++k) by_blk[{P->witems[k].gl, P->witems[k].cbi}].push_back((int)k);
+  std::vector<GemmTask> gt;
+  std::vector<GemmGroup> gg;
+  std::vector<int64_t> goff;
+  int64_t gsize = 0;
+  for (auto& kv : by_blk) {
+    const CombOp& C = P->cl[kv.first.first];
+    const BlockRef& cb = (*C.blocks)[kv.first.second];
+    const int b0 = (int)gt.size();
+    for (int k : kv.second) {
+      const XBlock& Xp = P->X[wxp[k]];
+      gt.push_back({P->xin + Xp.off, P->W + woff[k], Xp.cols, Xp.cols, Xp.cols, 0, 1, 1.0 / n2});
+    }
+    goff.push_back(gsize);
+    gg.push_back({nullptr, cb.cols, cb.rows, cb.cols, b0, (int)gt.size(), 0});
+    gsize += (int64_t)cb.rows * cb.cols;
+  }
+  double* Gb = (double*)dev_alloc(sizeof(double) * std::max<int64_t>(gsize, 1), stream_);
+  dev_zero(Gb, sizeof(double) * std::max<int64_t>(gsize, 1), stream_);
+  for (size_t q = 0; q < gg.size(); ++q) gg[q].C = Gb + goff[q];
+  {
+    GemmPlan* p = gemm_plan_upload(gt, gg, stream_);
+    gemm_plan_run(p, stream_);
+    gemm_plan_free(p, stream_);
+  }
+  // dE/dg[gi] += gc <L_a, Gbar> over the terms of every left combined operator
+  std::map<int64_t, std::vector<DotTask>> dots;
+  const OpStore& E = lenv_[i];
+  {
+    size_t q = 0;
+    for (auto& kv : by_blk) {
+      const CombOp& C = P->cl[kv.first.first];
+      const BlockRef& cb = (*C.blocks)[kv.first.second];
+      const double* gb = Gb + goff[q++];
+      for (size_t s = 0; s < C.sources.size(); ++s) {
+        const int64_t gi = C.grad[s].first;
+        if (gi < 0) continue;
+        const int a = C.sources[s].first;
+        auto it = E.at[a].find(bkey(cb.r, cb.c));
+        if (it == E.at[a].end()) continue;
+        const BlockRef& lb = E.blocks[a][it->second];
+        dots[gi].push_back({E.data + lb.off, gb, lb.cols, cb.cols, cb.rows, cb.cols, C.grad[s].second});
+      }
+    }
+  }
+  double* U = nullptr;
+  if (last) {
+    // the site's right terms all end in the 1 x 1 operator H(bond L) = 1:
+    // dE/ds_e = sum over W items and their sources of this group of craw <C^T x_out, x_src>
+    U = (double*)dev_alloc(sizeof(double) * std::max<int64_t>(P->wsize, 1), stream_);
+    dev_zero(U, sizeof(double) * std::max<int64_t>(P->wsize, 1), stream_);
+    std::vector<GemmTask> ut;
+    std::vector<GemmGroup> ug;
+    for (size_t k = 0; k < nw; ++k) {
+      const auto& w = P->witems[k];
+      const CombOp& C = P->cl[w.gl];
+      const BlockRef& cb = (*C.blocks)[w.cbi];
+      const XBlock& Xp = P->X[wxp[k]];
+      const int b0 = (int)ut.size();
+      if (C.identity) ut.push_back({nullptr, P->xin + Xp.off, 0, Xp.cols, Xp.cols, 0, 0, C.scalar});
+      else ut.push_back({C.data + cb.off, P->xin + Xp.off, cb.cols, Xp.cols, cb.rows, 1, 0, C.scalar});
+      ug.push_back({U + woff[k], Xp.cols, cb.cols, Xp.cols, b0, b0 + 1, 0});
+      for (int q = w.src_begin; q < w.src_end; ++q) {
+        const auto& src = P->wsrc[q];
+        const CombOp& D = P->cr[src.gr];
+        const XBlock& Xs = P->X[src.xb];
+        if (Xs.rows != cb.cols || Xs.cols != Xp.cols)
+          throw std::logic_error("rdm: right end operator is not 1 x 1");
+        for (size_t s = 0; s < D.sources.size(); ++s) {
+          const int64_t gi = D.grad[s].first;
+          if (gi < 0) continue;
+          dots[gi].push_back({U + woff[k], P->xin + Xs.off, Xp.cols, Xs.cols, cb.cols, Xp.cols,
+                              src.craw * D.grad[s].second / n2});
+        }
+      }
+    }
+    GemmPlan* p = gemm_plan_upload(ut, ug, stream_);
+    gemm_plan_run(p, stream_);
+    gemm_plan_free(p, stream_);
+  }
+  std::vector<DotTask> dt;
+  std::vector<DotGroup> dgp;
+  for (auto& kv : dots) {
+    const int b0 = (int)dt.size();
+    dt.insert(dt.end(), kv.second.begin(), kv.second.end());
+    dgp.push_back({dg + kv.first, b0, (int)dt.size()});
+  }
+  dot_grouped(dt, dgp, stream_);
+  dev_free(Gb, stream_);
+  if (U) dev_free(U, stream_);
 }
 
 // True if sites 1..L-1 satisfy the reduced right-normalisation of Eq. 6,

@@ -61,6 +61,7 @@ struct CombOp {
   std::vector<BlockRef> own_blocks;
   std::unordered_map<int64_t, int> own_at;
   std::vector<std::pair<int, double>> sources;  // (operator index, scalar)
+  std::vector<std::pair<int64_t, double>> grad;  // (gi, gc) of each source's recursion term
 };
 
 struct Stats {
@@ -109,6 +110,11 @@ class Engine {
   // Eqs. 26-28 and the operator update in the sweep direction
   double sweep_step(int i, int dir, int D, double gamma, double* w_disc, int* iters, bool* conv);
   void canonicalize(int center);
+  // Spin-summed 1- and 2-RDMs of the current MPS (device outputs, L^2 and L^4 doubles,
+  // row-major): Gamma_ijkl = sum_st <a+_is a+_jt a_lt a_ks> projected onto the eight
+  // permutations under which V is invariant, gamma_ik = sum_j Gamma_ijkj / (N - 1).
+  // Leaves the MPS in mixed canonical form around site L-2 (the state is unchanged).
+  void rdm(double* gamma_dev, double* Gamma_dev);
   bool is_right_canonical();
   void right_normalize_site(int k);
   void left_normalize_site(int k);
@@ -157,6 +163,7 @@ class Engine {
   void alloc_site(int k);
   void free_site(int k);
   void identity_fill(OpStore& e, int op);
+  void rdm_site(MatvecPlan* P, int i, double* dg, bool last);
 
   int L_, N_, two_S_, irrep_;
   Symmetry sym_;
@@ -167,6 +174,7 @@ class Engine {
   PatternTable pt_;
   std::unique_ptr<Coupling> cp_;
   std::vector<std::vector<WEntry>> W_;
+  std::vector<std::vector<WEntry>> Wg_;  // W_ with the terms of every allowed integral
   std::vector<Bond> bonds_;
   std::vector<std::map<Sector, int>> fci_;  // FCI-capped sector dimensions per bond
   std::vector<Site> sites_;

@@ -296,6 +296,81 @@ void diag_plan_free(DiagPlan* p, Stream s) {
   delete p;
 }
 
+// ------------------------------------------------------------------ grouped Frobenius products
+
+namespace {
+// one CTA per group: the threads stride over every element of every task of the group,
+// then a block reduction; the group's output is written by this CTA only
+__global__ void __launch_bounds__(256) k_dot_grouped(const DotTask* __restrict__ t,
+                                                    const DotGroup* __restrict__ g) {
+  const DotGroup G = g[blockIdx.x];
+  double s = 0.0;
+  for (int k = G.task_begin; k < G.task_end; ++k) {
+    const DotTask T = t[k];
+    const int64_t ne = (int64_t)T.rows * T.cols;
+    double u = 0.0;
+    for (int64_t e = threadIdx.x; e < ne; e += blockDim.x) {
+      const int r = (int)(e / T.cols), c = (int)(e % T.cols);
+      u = fma(T.A[(size_t)r * T.lda + c], T.B[(size_t)r * T.ldb + c], u);
+    }
+    s = fma(T.alpha, u, s);
+  }
+  __shared__ double sh[256];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *G.out += sh[0];
+}
+
+// Gamma_ijkl = 2 x mean of dg over (ijkl), (jilk), (klij), (lkji), (kjil), (ilkj), (lijk), (jkli)
+__global__ void k_rdm2(const double* __restrict__ dg, int L, double* __restrict__ Gamma) {
+  const int64_t L4 = (int64_t)L * L * L * L;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < L4; e += (int64_t)gridDim.x * blockDim.x) {
+    const int l = (int)(e % L), k = (int)(e / L % L), j = (int)(e / L / L % L), i = (int)(e / L / L / L);
+    auto at = [&](int a, int b, int c, int d) { return dg[(((int64_t)a * L + b) * L + c) * L + d]; };
+    const double s = at(i, j, k, l) + at(j, i, l, k) + at(k, l, i, j) + at(l, k, j, i) + at(k, j, i, l) +
+                     at(i, l, k, j) + at(l, i, j, k) + at(j, k, l, i);
+    Gamma[e] = 0.25 * s;
+  }
+}
+
+__global__ void k_rdm1(const double* __restrict__ Gamma, int L, int N, double* __restrict__ gamma) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= L * L) return;
+  const int i = e / L, k = e % L;
+  double s = 0.0;
+  for (int j = 0; j < L; ++j) s += Gamma[(((int64_t)i * L + j) * L + k) * L + j];
+  gamma[e] = s / (N - 1);
+}
+}  // namespace
+
+void dot_grouped(const std::vector<DotTask>& t, const std::vector<DotGroup>& g, Stream s) {
+  if (g.empty()) return;
+  DotTask* dt = (DotTask*)dev_alloc(std::max<size_t>(t.size(), 1) * sizeof(DotTask), s);
+  DotGroup* dgp = (DotGroup*)dev_alloc(g.size() * sizeof(DotGroup), s);
+  if (!t.empty()) dev_h2d(dt, t.data(), t.size() * sizeof(DotTask), s);
+  dev_h2d(dgp, g.data(), g.size() * sizeof(DotGroup), s);
+  for (size_t off = 0; off < g.size(); off += 65535) {
+    const int n = (int)std::min<size_t>(65535, g.size() - off);
+    k_dot_grouped<<<n, 256, 0, S(s)>>>(dt, dgp + off);
+    ++g_launches;
+  }
+  ck(cudaGetLastError(), "dot launch");
+  dev_free(dt, s);
+  dev_free(dgp, s);
+}
+
+void rdm_finish(const double* dg, int L, int N, double* gamma, double* Gamma, Stream s) {
+  const int64_t L4 = (int64_t)L * L * L * L;
+  k_rdm2<<<(int)std::min<int64_t>((L4 + 255) / 256, 4096), 256, 0, S(s)>>>(dg, L, Gamma);
+  k_rdm1<<<(L * L + 255) / 256, 256, 0, S(s)>>>(Gamma, L, N, gamma);
+  g_launches += 2;
+  ck(cudaGetLastError(), "rdm launch");
+}
+
 // ------------------------------------------------------------------ vector kernels
 
 namespace {

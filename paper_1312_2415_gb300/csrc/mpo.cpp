@@ -157,7 +157,14 @@ struct Rule {
   Elem src;
   Mat4 O;
   double scalar;
+  int64_t gi = -1;   // scalar = gc * g[gi] (gi >= 0) or gc
+  double gc = 1.0;
 };
+// rule whose scalar is c times the folded integral g(p, q, r, s)
+Rule grule(int rule, int i0, int i1, const Elem& src, const Mat4& O, double c, const Integrals& g,
+           int p, int q, int r, int s) {
+  return {rule, i0, i1, src, O, c * g.at(p, q, r, s), g.idx(p, q, r, s), c};
+}
 
 enum {
   R_ID = 1, R_NEW, R_CC_P, R_CC_Q, R_CC_L, R_AA_P, R_AA_Q, R_AA_L, R_CA_P, R_CA_T, R_CA_L,
@@ -174,29 +181,28 @@ void rc_rules(int r, int s, int k, const Integrals& g, std::vector<Rule>& out) {
   {
     Mat4 O = zero4();
     for (int t = -1; t <= 1; t += 2) O = add(O, mul(mul(cdag(s), cdag(t)), cann(t)));
-    double v = g.at(k, k, r, k);
-    if (v != 0.0) out.push_back({R_RC_2, -1, -1, {E_I, 0, 0, 0, 0}, O, v});
+    if (g.use(k, k, r, k)) out.push_back(grule(R_RC_2, -1, -1, {E_I, 0, 0, 0, 0}, O, 1.0, g, k, k, r, k));
   }
   Mat4 nk = num();
   for (int a = 0; a < k; ++a) {
     for (int b = 0; b < k; ++b) {
-      double v3 = g.at(k, a, r, b);   // p = k: sum_t a+_{a t} a_{b t} . a+_{k s}
-      double v4 = g.at(a, k, r, b);   // q = k: - a+_{a s} a_{b t} . a+_{k t}
-      double v5 = g.at(a, b, r, k);   // u = k: a+_{a s} a+_{b t} . a_{k t}
+      const bool u3 = g.use(k, a, r, b);   // p = k: sum_t a+_{a t} a_{b t} . a+_{k s}
+      const bool u4 = g.use(a, k, r, b);   // q = k: - a+_{a s} a_{b t} . a+_{k t}
+      const bool u5 = g.use(a, b, r, k);   // u = k: a+_{a s} a+_{b t} . a_{k t}
       for (int t = -1; t <= 1; t += 2) {
-        if (v3 != 0.0) out.push_back({R_RC_3, a, b, {E_CA, a, t, b, t}, cdag(s), v3});
-        if (v4 != 0.0) out.push_back({R_RC_4, a, b, {E_CA, a, s, b, t}, cdag(t), -v4});
-        if (v5 != 0.0) out.push_back({R_RC_5, a, b, {E_CC, a, s, b, t}, cann(t), v5});
+        if (u3) out.push_back(grule(R_RC_3, a, b, {E_CA, a, t, b, t}, cdag(s), 1.0, g, k, a, r, b));
+        if (u4) out.push_back(grule(R_RC_4, a, b, {E_CA, a, s, b, t}, cdag(t), -1.0, g, a, k, r, b));
+        if (u5) out.push_back(grule(R_RC_5, a, b, {E_CC, a, s, b, t}, cann(t), 1.0, g, a, b, r, k));
       }
     }
-    double v6 = g.at(k, k, r, a);     // p = q = k: a_{a t} . a+_{k s} a+_{k t}
-    double v7 = g.at(k, a, r, k);     // p = u = k: - a+_{a t} . a+_{k s} a_{k t}
-    double v8 = g.at(a, k, r, k);     // q = u = k: a+_{a s} . n_k
+    const bool u6 = g.use(k, k, r, a);     // p = q = k: a_{a t} . a+_{k s} a+_{k t}
+    const bool u7 = g.use(k, a, r, k);     // p = u = k: - a+_{a t} . a+_{k s} a_{k t}
+    const bool u8 = g.use(a, k, r, k);     // q = u = k: a+_{a s} . n_k
     for (int t = -1; t <= 1; t += 2) {
-      if (v6 != 0.0) out.push_back({R_RC_6, a, -1, {E_A, a, t, 0, 0}, mul(cdag(s), cdag(t)), v6});
-      if (v7 != 0.0) out.push_back({R_RC_7, a, -1, {E_C, a, t, 0, 0}, mul(cdag(s), cann(t)), -v7});
+      if (u6) out.push_back(grule(R_RC_6, a, -1, {E_A, a, t, 0, 0}, mul(cdag(s), cdag(t)), 1.0, g, k, k, r, a));
+      if (u7) out.push_back(grule(R_RC_7, a, -1, {E_C, a, t, 0, 0}, mul(cdag(s), cann(t)), -1.0, g, k, a, r, k));
     }
-    if (v8 != 0.0) out.push_back({R_RC_8, a, -1, {E_C, a, s, 0, 0}, nk, v8});
+    if (u8) out.push_back(grule(R_RC_8, a, -1, {E_C, a, s, 0, 0}, nk, 1.0, g, a, k, r, k));
   }
 }
 
@@ -210,20 +216,19 @@ void h_rules(int k, const Integrals& g, std::vector<Rule>& out) {
     for (int s = -1; s <= 1; s += 2)
       for (int t = -1; t <= 1; t += 2)
         O = add(O, mul(mul(cdag(s), cdag(t)), mul(cann(t), cann(s))));
-    double v = g.at(k, k, k, k);
-    if (v != 0.0) out.push_back({R_H_LOC, -1, -1, {E_I, 0, 0, 0, 0}, scale(O, 0.5), v});
+    if (g.use(k, k, k, k))
+      out.push_back(grule(R_H_LOC, -1, -1, {E_I, 0, 0, 0, 0}, scale(O, 0.5), 1.0, g, k, k, k, k));
   }
   for (int p = 0; p < k; ++p) {
-    double v = g.at(p, k, k, k);
-    if (v == 0.0) continue;
+    if (!g.use(p, k, k, k)) continue;
     for (int s = -1; s <= 1; s += 2) {
       Mat4 Oc = zero4(), Oa = zero4();
       for (int t = -1; t <= 1; t += 2) {
         Oc = add(Oc, mul(mul(cdag(t), cann(t)), cann(s)));
         Oa = add(Oa, mul(mul(cdag(s), cdag(t)), cann(t)));
       }
-      out.push_back({R_H_C, p, -1, {E_C, p, s, 0, 0}, Oc, v});
-      out.push_back({R_H_A, p, -1, {E_A, p, s, 0, 0}, Oa, -v});
+      out.push_back(grule(R_H_C, p, -1, {E_C, p, s, 0, 0}, Oc, 1.0, g, p, k, k, k));
+      out.push_back(grule(R_H_A, p, -1, {E_A, p, s, 0, 0}, Oa, -1.0, g, p, k, k, k));
     }
   }
   for (int s = -1; s <= 1; s += 2) {
@@ -233,17 +238,17 @@ void h_rules(int k, const Integrals& g, std::vector<Rule>& out) {
   Mat4 nk = num();
   for (int p = 0; p < k; ++p)
     for (int q = 0; q < k; ++q) {
-      double ve = g.at(p, q, k, k);
-      double vn = g.at(p, k, q, k);
-      double vx = g.at(p, k, k, q);
+      const bool ue = g.use(p, q, k, k);
+      const bool un = g.use(p, k, q, k);
+      const bool ux = g.use(p, k, k, q);
       for (int s = -1; s <= 1; s += 2) {
-        if (vn != 0.0) out.push_back({R_H_BN, p, q, {E_CA, p, s, q, s}, nk, vn});
+        if (un) out.push_back(grule(R_H_BN, p, q, {E_CA, p, s, q, s}, nk, 1.0, g, p, k, q, k));
         for (int t = -1; t <= 1; t += 2) {
-          if (ve != 0.0) {
-            out.push_back({R_H_CC, p, q, {E_CC, p, s, q, t}, mul(cann(t), cann(s)), 0.5 * ve});
-            out.push_back({R_H_AA, p, q, {E_AA, q, t, p, s}, mul(cdag(s), cdag(t)), 0.5 * ve});
+          if (ue) {
+            out.push_back(grule(R_H_CC, p, q, {E_CC, p, s, q, t}, mul(cann(t), cann(s)), 0.5, g, p, q, k, k));
+            out.push_back(grule(R_H_AA, p, q, {E_AA, q, t, p, s}, mul(cdag(s), cdag(t)), 0.5, g, p, q, k, k));
           }
-          if (vx != 0.0) out.push_back({R_H_BX, p, q, {E_CA, p, s, q, t}, mul(cdag(t), cann(s)), -vx});
+          if (ux) out.push_back(grule(R_H_BX, p, q, {E_CA, p, s, q, t}, mul(cdag(t), cann(s)), -1.0, g, p, k, k, q));
         }
       }
     }
@@ -288,7 +293,7 @@ void rules(const Elem& e, int k, const Integrals& g, std::vector<Rule>& out) {
       for (auto& r : tmp) {
         // (X . O)^dagger = (-1)^{p(X) p(O)} X^dagger . O^dagger
         double sg = (elem_parity(r.src) && mat_parity(r.O)) ? -1.0 : 1.0;
-        out.push_back({r.rule + R_ADJ, r.i0, r.i1, adjoint(r.src), tr(r.O), sg * r.scalar});
+        out.push_back({r.rule + R_ADJ, r.i0, r.i1, adjoint(r.src), tr(r.O), sg * r.scalar, r.gi, sg * r.gc});
       }
       break;
     }
@@ -368,7 +373,7 @@ std::vector<WEntry> build_site_recursion(int k, const OpSet& from, const OpSet& 
   std::vector<Src> srcs;
   for (int bi = 0; bi < (int)to.ops.size(); ++bi) {
     const OpInfo& b = to.ops[bi];
-    struct Acc { std::vector<double> w; double scalar; int a; };
+    struct Acc { std::vector<double> w; double scalar; int a; int64_t gi; double gc; };
     std::map<std::tuple<int, int, int, int>, Acc> acc;
     for (int tqb = -b.tk; tqb <= b.tk; tqb += 2) {
       int qb = (tqb + b.tk) / 2;
@@ -392,6 +397,8 @@ std::vector<WEntry> build_site_recursion(int k, const OpSet& from, const OpSet& 
               z.w.assign((size_t)(ai.tk + 1) * (b.tk + 1) * 16, 0.0);
               z.scalar = r.scalar;
               z.a = a;
+              z.gi = r.gi;
+              z.gc = r.gc;
               it = acc.emplace(key, std::move(z)).first;
             }
             int qa = (s.tqa + ai.tk) / 2;
@@ -409,7 +416,7 @@ std::vector<WEntry> build_site_recursion(int k, const OpSet& from, const OpSet& 
         if (std::fabs(v) < 1e-13) v = 0.0;
         mx = std::max(mx, std::fabs(v));
       }
-      if (mx == 0.0 || z.scalar == 0.0) continue;
+      if (mx == 0.0 || (z.scalar == 0.0 && !g.keep_zero)) continue;
       Pattern p;
       p.tka = from.ops[z.a].tk;
       p.tkb = b.tk;
@@ -417,7 +424,7 @@ std::vector<WEntry> build_site_recursion(int k, const OpSet& from, const OpSet& 
       p.pO = (p.pa + b.parity) & 1;
       p.w = z.w;
       int pid = pt.intern(p);
-      out.push_back({z.a, bi, pid, z.scalar});
+      out.push_back({z.a, bi, pid, z.scalar, z.gi, z.gc});
     }
   }
   return out;

@@ -68,16 +68,28 @@ struct PatternTable {
 };
 
 // One term of the recursion at a site: L_b(bond k+1) += scalar * [L_a(bond k) x pattern].
+// scalar = gc * g[gi] for a term that carries one folded integral, gc for gi < 0.
 struct WEntry {
   int a, b, pattern;
   double scalar;
+  int64_t gi;
+  double gc;
 };
 
-// Integrals after the folding of Eq. 11: g[((p*L+q)*L+r)*L+s] = (pq|h|rs).
+// Integrals after the folding of Eq. 11: g[((p*L+q)*L+r)*L+s] = (pq|h|rs).  With
+// keep_zero set, the recursion keeps the terms of integrals that vanish but are allowed
+// by the point group (ir = orbital irreps), so that derivatives with respect to every
+// allowed integral can be taken on it.
 struct Integrals {
   int L = 0;
   std::vector<double> g;
-  double at(int p, int q, int r, int s) const { return g[(((size_t)p * L + q) * L + r) * L + s]; }
+  bool keep_zero = false;
+  std::vector<int> ir;
+  int64_t idx(int p, int q, int r, int s) const { return (((int64_t)p * L + q) * L + r) * L + s; }
+  double at(int p, int q, int r, int s) const { return g[(size_t)idx(p, q, r, s)]; }
+  bool use(int p, int q, int r, int s) const {
+    return at(p, q, r, s) != 0.0 || (keep_zero && (ir[p] ^ ir[q] ^ ir[r] ^ ir[s]) == 0);
+  }
 };
 
 // Recursion entries of site k, mapping bond-k operators to bond-(k+1) operators.
