@@ -7,6 +7,9 @@ Each micro-iteration follows Secs. 2.3, 2.4 and 3.4:
 A macro-iteration is a sweep to the right followed by a sweep to the left (Sec. 4.2);
 Solve reports the minimum energy over all micro-iterations (Sec. 4.3).
 The lowest eigenpair of the dense H_eff is taken from numpy.linalg.eigh.
+Excited states (Sec. 4.3): the Hamiltonian H_m = H_0 + sum_k eta_{k+1} |Psi_k><Psi_k| of
+the m-th state adds eta v v^T per lower state to H_eff, v the projection of Psi_k onto
+the current two-site basis (`excited_hamiltonian`).
 """
 import numpy as np
 from .fci import FCISpace
@@ -48,8 +51,34 @@ def matvec(prob, m, i, x):
     return proj.unflatten(H @ v)
 
 
-def micro_iteration(prob, m, i, D, direction, noise=0.0, noise_values=None, w_prev=0.0):
-    H, _, proj = effective_hamiltonian(prob, m, i)
+def determinant_components(prob, m):
+    """The state of an MPS in the determinant basis, one vector per Sz component f
+    (restricted to the symmetry sector), from the two-site expansion at sites (0, 1)."""
+    proj = TwoSiteProjector(m, 0, prob.spaces)
+    x = proj.flatten(tt_to_x(m, 0))
+    return [P[prob.idx[f]] @ x for f, P in enumerate(proj.P)]
+
+
+def projected_state(prob, proj, psi):
+    """v = P^T |psi> / |psi| in the reduced two-site basis of `proj` (norm summed over the
+    Sz components, the inner product in which P^T P = 1)."""
+    nrm = np.sqrt(sum(float(c @ c) for c in psi))
+    return sum(P[prob.idx[f]].T @ psi[f] for f, P in enumerate(proj.P)) / nrm
+
+
+def excited_hamiltonian(prob, m, i, lower):
+    """Effective Hamiltonian of H_m = H_0 + sum_k eta_{k+1} |Psi_k><Psi_k| (Sec. 4.3,
+    excited states): H_eff of Eq. 9 plus eta v v^T for every lower state, v its
+    projection onto the two-site basis.  lower = [(MPS of Psi_k, eta_{k+1}), ...]."""
+    H, G, proj = effective_hamiltonian(prob, m, i)
+    for mk, eta in lower:
+        v = projected_state(prob, proj, determinant_components(prob, mk))
+        H = H + eta * np.outer(v, v)
+    return H, G, proj
+
+
+def micro_iteration(prob, m, i, D, direction, noise=0.0, noise_values=None, w_prev=0.0, lower=()):
+    H, _, proj = excited_hamiltonian(prob, m, i, lower) if lower else effective_hamiltonian(prob, m, i)
     w, U = np.linalg.eigh(H)
     e = float(w[0])
     v = U[:, 0]
@@ -63,17 +92,17 @@ def micro_iteration(prob, m, i, D, direction, noise=0.0, noise_values=None, w_pr
     return e, w_disc
 
 
-def sweep(prob, m, D, n_macro, log=None):
+def sweep(prob, m, D, n_macro, log=None, lower=()):
     """Right sweep then left sweep per macro-iteration; returns (min energy, list of
-    per-micro-iteration energies)."""
+    per-micro-iteration energies).  `lower`: projected lower states (excited_hamiltonian)."""
     energies = []
     L = m.L
     for it in range(n_macro):
         for i in range(0, L - 1):
-            e, wd = micro_iteration(prob, m, i, D, "right")
+            e, wd = micro_iteration(prob, m, i, D, "right", lower=lower)
             energies.append(e)
         for i in range(L - 2, -1, -1):
-            e, wd = micro_iteration(prob, m, i, D, "left")
+            e, wd = micro_iteration(prob, m, i, D, "left", lower=lower)
             energies.append(e)
         if log is not None:
             log(it, energies[-1])
