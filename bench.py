@@ -419,10 +419,91 @@ def run_batch(args):
     b.close()
 
 
+def rdm_cpu_baseline(bounded_seconds=10.0):
+    """The oracle's RDMs (determinant expansion of the state + E_pq products) of an L=8,
+    N=8, D2h random-integral state at D=60, repeated for a bounded time."""
+    from oracle import mps as om
+    from oracle.rdm import mps_state, rdm_from_vector
+    from workloads import round_robin_irreps, uniform_pm1
+    irr = round_robin_irreps(8)
+    m = om.right_canonicalize(om.random_mps(irr, 8, 0, 0, 60, uniform_pm1(5, 10 ** 6)))
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        rdm_from_vector(*mps_state(m))
+        n += 1
+        if time.perf_counter() - t0 > bounded_seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": dt / n, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{n} oracle RDM evaluations of an L=8, N=8, S=0, D2h state at D=60 "
+                      f"(the oracle cannot expand the L=16 state), {dt:.1f} s"}
+
+
+def run_rdm(args):
+    """random16: the spin-summed 1- and 2-RDMs (dE/dh, dE/dV) of an L=16, N=16, S=0, D2h
+    random-integral state at D=1000 (the initial MPS of Sec. 4.3): one step = one
+    dmrg_rdm pass (the adjoint of the H_eff matvec at every site pair, the centre moving
+    right), outputs in device memory."""
+    import numpy as np
+    import torch
+    from paper_1312_2415_gb300 import Context
+    from workloads import make_problem
+    torch.cuda.set_device(0)
+    cfg, h, V = make_problem("random16")
+    L, D = cfg["L"], args.D or cfg["D"]
+    ctx = Context(L, cfg["group_irreps"], cfg["N"], cfg["two_S"], cfg["irrep"], group=7)
+    ctx.set_integrals(h, V)
+    fixed_iters(ctx, D, args.davidson_iters)
+    ctx.init_mps(cfg["seed"])
+    gamma = torch.empty((L, L), dtype=torch.float64, device="cuda")
+    Gamma = torch.empty((L,) * 4, dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup):
+        ctx.rdm(gamma, Gamma)
+    torch.cuda.synchronize()
+    st0 = ctx.stats()
+    clk = ClockSampler(torch.cuda.current_device())
+    clk.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        ctx.rdm(gamma, Gamma)
+    e1.record()
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    st1 = ctx.stats()
+    flops = (st1["rdm_flops"] - st0["rdm_flops"]) / args.steps
+    plan_ms = (st1["t_plan_ms"] - st0["t_plan_ms"]) / args.steps
+    launches = int(st1["kernels_launched"] - st0["kernels_launched"])
+    out = {"metric": "1-/2-RDM pass (dE/dh, dE/dV by the adjoint of the H_eff matvec)",
+           "value": ms * 1e-3, "unit": "s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"random16: random integrals L={L} N={cfg['N']} S=0 Ag D2h round-robin, "
+                                  f"D_SU(2)={D}, initial MPS of Sec. 4.3 (seed {cfg['seed']}), outputs "
+                                  f"gamma (L^2) and Gamma (L^4) on the device",
+                      "l2": "operators and two-site objects exceed L2"},
+           "gflops": flops / (ms * 1e-3) / 1e9, "flops_per_step": flops,
+           "host_plan_ms_per_step": plan_ms, "clocks": clocks, "gpu_launches": launches}
+    if not args.no_e2e:
+        g_h, G_h = np.zeros((L, L)), np.zeros((L,) * 4)
+        t0 = time.perf_counter()
+        ctx.rdm(g_h, G_h)
+        dt = time.perf_counter() - t0
+        out["e2e"] = {"value": dt, "unit": "s", "h2d_bytes_per_step": 0,
+                      "d2h_bytes_per_step": 8 * (L * L + L ** 4)}
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = rdm_cpu_baseline()
+    print(json.dumps(out), flush=True)
+
+
 def run_gb300(args):
     import torch
     if args.workload == "batch32":
         return run_batch(args)
+    if args.workload == "random16":
+        return run_rdm(args)
     rank, world, local = dist_env()
     if world > 1:
         import torch.distributed as dist

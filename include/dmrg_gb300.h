@@ -66,6 +66,10 @@ typedef struct {
   /* per phase of those matvecs: flops, and compulsory bytes (FP32 operands read once
    * per use, FP32 Z written once, y written once) */
   double tc_phase1_flops, tc_phase2_flops, tc_phase1_bytes, tc_phase2_bytes;
+  /* dmrg_rdm passes: count, host wall clock (ms, the planning included) and the flops of
+   * their block products (matvec phase 1, the adjoint GEMMs, the Frobenius products) */
+  int64_t rdm_passes;
+  double rdm_ms, rdm_flops;
 } dmrg_stats_t;
 
 /* Sec. 4.1: L orbitals with irreps orb_irrep[L], N electrons (2 <= N <= 2L, needed by
@@ -135,6 +139,19 @@ int dmrg_solve(dmrg_ctx* ctx, double* e_min, double* e_last);
  * state).  gamma (L*L doubles) and Gamma (L^4 doubles) are device pointers when stream
  * != 0, host pointers when stream == 0.  DMRG_EINVAL on NULL outputs. */
 int dmrg_rdm(dmrg_ctx* ctx, double* gamma, double* Gamma, uintptr_t stream);
+
+/* Excited states (Sec. 4.3): dmrg_push_excitation stores the current MPS as the next
+ * lower state |Psi_k> (normalised; the current MPS is left right-canonical, same state)
+ * with weight eta = eta_{k+1}, so that every later H_eff (dmrg_heff_matvec, Davidson,
+ * dmrg_solve) is that of H_m = H_0 + sum_k eta_{k+1} |Psi_k><Psi_k|: the two-site
+ * projection v_k of each lower state (through its overlaps with the current basis) adds
+ * eta_{k+1} v_k (v_k . x) to y.  Start the next state from a new MPS (dmrg_init_mps) or
+ * the current one.  dmrg_heff_matvec_noalloc and dmrg_batch_create reject contexts with
+ * lower states (DMRG_EINVAL).  dmrg_clear_excitations drops them all.  *count: the
+ * number of stored lower states. */
+int dmrg_push_excitation(dmrg_ctx* ctx, double eta);
+int dmrg_clear_excitations(dmrg_ctx* ctx);
+int dmrg_excitation_count(dmrg_ctx* ctx, int* count);
 
 /* Block table of x for sites (site, site+1): n_blocks rows of 12 int64 (2jL, NL, IL,
  * s1, s2, 2j, 2jR, NR, IR, dL, dR, offset) with s1, s2 the local states 0|1|2 and the

@@ -37,6 +37,7 @@ class Stats(ctypes.Structure):
         ("tc_phase1_ms", ctypes.c_double), ("tc_phase2_ms", ctypes.c_double),
         ("tc_phase1_flops", ctypes.c_double), ("tc_phase2_flops", ctypes.c_double),
         ("tc_phase1_bytes", ctypes.c_double), ("tc_phase2_bytes", ctypes.c_double),
+        ("rdm_passes", ctypes.c_int64), ("rdm_ms", ctypes.c_double), ("rdm_flops", ctypes.c_double),
     ]
 
 
@@ -61,6 +62,9 @@ _SIGS = {
     "dmrg_heff_matvec": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
     "dmrg_heff_diag": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t]),
     "dmrg_rdm": (ctypes.c_int, [_P, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
+    "dmrg_push_excitation": (ctypes.c_int, [_P, ctypes.c_double]),
+    "dmrg_clear_excitations": (ctypes.c_int, [_P]),
+    "dmrg_excitation_count": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
     "dmrg_heff_matvec_noalloc": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                                 ctypes.c_size_t]),
     "dmrg_davidson": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, _D, _I]),
@@ -249,6 +253,18 @@ class Context:
         assert gamma.shape == (L, L) and Gamma.shape == (L,) * 4
         self._check(self.lib.dmrg_rdm(self.h, p1, p2, s))
         return gamma, Gamma
+
+    def push_excitation(self, eta):
+        """Store the current MPS as the next lower state with weight eta (Sec. 4.3)."""
+        self._check(self.lib.dmrg_push_excitation(self.h, float(eta)))
+
+    def clear_excitations(self):
+        self._check(self.lib.dmrg_clear_excitations(self.h))
+
+    def excitation_count(self):
+        n = ctypes.c_int()
+        self._check(self.lib.dmrg_excitation_count(self.h, ctypes.byref(n)))
+        return n.value
 
     def davidson(self, site, x):
         p, s = _ptr_and_stream(x)

@@ -298,6 +298,32 @@ int dmrg_rdm(dmrg_ctx* c, double* gamma, double* Gamma, uintptr_t stream) {
   });
 }
 
+int dmrg_push_excitation(dmrg_ctx* c, double eta) {
+  return guard(c, [&] {
+    dev_stream(c);
+    c->eng->push_excitation(eta);
+    dmrg::dev_sync(c->eng->stream());
+    return DMRG_OK;
+  });
+}
+
+int dmrg_clear_excitations(dmrg_ctx* c) {
+  return guard(c, [&] {
+    dev_stream(c);
+    c->eng->clear_excitations();
+    dmrg::dev_sync(c->eng->stream());
+    return DMRG_OK;
+  });
+}
+
+int dmrg_excitation_count(dmrg_ctx* c, int* count) {
+  return guard(c, [&] {
+    if (!count) return DMRG_EINVAL;
+    *count = c->eng->n_excitations();
+    return DMRG_OK;
+  });
+}
+
 int dmrg_heff_diag(dmrg_ctx* c, int site, double* d, uintptr_t stream) {
   return guard(c, [&] {
     if (!d) return DMRG_EINVAL;
@@ -407,6 +433,9 @@ int dmrg_stats(dmrg_ctx* c, dmrg_stats_t* out) {
     out->tc_phase2_flops = s.tc_phase2_flops;
     out->tc_phase1_bytes = s.tc_phase1_bytes;
     out->tc_phase2_bytes = s.tc_phase2_bytes;
+    out->rdm_passes = s.rdm_passes;
+    out->rdm_ms = s.rdm_ms;
+    out->rdm_flops = s.rdm_flops;
     return DMRG_OK;
   });
 }

@@ -69,9 +69,11 @@ Engine::~Engine() {
     flush_events();
     for (auto& e : ev_) event_destroy(e);
     if (cached_) free_plan(cached_);
+    cached_ = nullptr;
     for (auto& e : lenv_) free_env(e);
     for (auto& e : renv_) free_env(e);
     for (int k = 0; k < L_; ++k) free_site(k);
+    clear_excitations();
     dev_sync(stream_);
   } catch (...) {
   }
@@ -205,6 +207,7 @@ void Engine::init_mps(uint64_t seed) {
   have_mps_ = true;
   invalidate_envs_from_site(-1);
   for (auto& e : lenv_) free_env(e);
+  for (auto& e : renv_) free_env(e);
 }
 
 // Serialised MPS: int32 magic, version, L, N, 2S, irrep; per bond: nsec then
@@ -338,6 +341,7 @@ void Engine::alloc_env(OpStore& e, int bond, const OpSet& ops) {
   e.data = (double*)dev_alloc(sizeof(double) * std::max<int64_t>(off, 1), stream_);
   dev_zero(e.data, sizeof(double) * std::max<int64_t>(off, 1), stream_);
   e.valid = false;
+  e.serial = ++env_serial_;
 }
 
 void Engine::identity_fill(OpStore& e, int op) {
@@ -382,10 +386,12 @@ void Engine::ensure_right(int k) {
 
 // Blocks ordered by right sector first, so that all blocks with the same right sector
 // form one row-major stack (rows = sum dL, cols = dR) that a single GEMM can multiply.
-std::vector<XBlock> Engine::x_layout(int i, int64_t* n) const {
+std::vector<XBlock> Engine::x_layout(int i, int64_t* n) const { return x_layout_of(bonds_, i, n); }
+
+std::vector<XBlock> Engine::x_layout_of(const std::vector<Bond>& bonds, int i, int64_t* n) const {
   std::vector<XBlock> X;
-  const Bond& bl = bonds_[i];
-  const Bond& br = bonds_[i + 2];
+  const Bond& bl = bonds[i];
+  const Bond& br = bonds[i + 2];
   int64_t off = 0;
   for (int r = 0; r < (int)br.sec.size(); ++r) {
     const Sector& b = br.sec[r];
@@ -743,6 +749,12 @@ struct Engine::MatvecPlan {
   TcPlan* tc = nullptr;
   float* tc_zt = nullptr;
   uint64_t serial = 0;      // distinguishes successive plans of an engine
+  // excited states: projections v_k of the lower states (nlow x n, row k = v_k) and
+  // eta_k v_k, the coefficients c_k = v_k . x and their reduction scratch
+  int nlow = 0;
+  double* lowv = nullptr;
+  double* loww = nullptr;
+  double* lowc = nullptr;
   double tc_bytes1 = 0.0, tc_bytes2 = 0.0;  // compulsory bytes of the two phases
   float* tc_mem[3] = {nullptr, nullptr, nullptr};  // x32, x32t, operator mirrors
 };
@@ -1063,6 +1075,19 @@ Engine::MatvecPlan* Engine::plan_matvec(int i) {
   DiagPlan* pd = diag_plan_upload(dt, dov, stream_);
   diag_plan_run(pd, stream_);
   diag_plan_free(pd, stream_);
+  if (!low_.empty()) {
+    // the lower states' projections onto this pair's basis: + eta |v><v| in every matvec
+    const int m = (int)low_.size();
+    P->nlow = m;
+    P->lowv = (double*)dev_alloc(sizeof(double) * std::max<int64_t>(P->n * m, 1), stream_);
+    P->loww = (double*)dev_alloc(sizeof(double) * std::max<int64_t>(P->n * m, 1), stream_);
+    P->lowc = (double*)dev_alloc(sizeof(double) * (m + (int64_t)m * 512), stream_);
+    for (int k = 0; k < m; ++k) {
+      low_projection(low_[k], i, P->X, P->lowv + (int64_t)k * P->n);
+      dev_zero(P->loww + (int64_t)k * P->n, sizeof(double) * P->n, stream_);
+      vec_axpby(low_[k].eta, P->lowv + (int64_t)k * P->n, 0.0, P->loww + (int64_t)k * P->n, P->n, stream_);
+    }
+  }
   P->flops1 = flops1;
   P->flops2 = flops2;
   P->flops = flops1 + flops2;
@@ -1092,6 +1117,9 @@ void Engine::free_plan(MatvecPlan* p) {
   dev_free(p->diag, stream_);
   if (p->scr_l) dev_free(p->scr_l, stream_);
   if (p->scr_r) dev_free(p->scr_r, stream_);
+  if (p->lowv) dev_free(p->lowv, stream_);
+  if (p->loww) dev_free(p->loww, stream_);
+  if (p->lowc) dev_free(p->lowc, stream_);
   delete p;
 }
 
@@ -1279,6 +1307,7 @@ void Engine::build_tc(MatvecPlan* P) {
 
 Engine::TcView Engine::prepare_tc(int i) {
   check_ready();
+  if (!low_.empty()) throw std::invalid_argument("batched matvecs do not carry excited-state projectors");
   if (i < 0 || i > L_ - 2) throw std::out_of_range("site out of range");
   MatvecPlan* p = plan_for(i);
   if (!p->tc) build_tc(p);
@@ -1298,6 +1327,7 @@ void Engine::run_matvec(MatvecPlan* p, const double* x, double* y, bool tc) {
     tc_plan_launch(p->tc, ev_, stream_);
     ev_pending_ = true;
     ev_tc_ = true;
+    add_projectors(p);
     if (y != p->yout) dev_d2d(y, p->yout, sizeof(double) * p->n, stream_);
     st_.tc_matvecs += 1;
     st_.tc_flops += p->flops;
@@ -1324,6 +1354,7 @@ void Engine::run_matvec(MatvecPlan* p, const double* x, double* y, bool tc) {
   event_record(ev_[2], stream_);
   ev_pending_ = true;
   ev_tc_ = false;
+  add_projectors(p);
   st_.k_launches += 1;
   st_.k_phase1_flops += p->flops1;
   st_.k_phase2_flops += p->flops2;
@@ -1342,7 +1373,16 @@ void Engine::matvec(int i, const double* x, double* y) {
   if (precision_ == 1 && tc_error_flag(stream_)) throw std::runtime_error("cuda: tensor-core wait timed out");
 }
 
+// y += sum_k eta_k v_k (v_k . x): the projectors of the excited-state Hamiltonian
+void Engine::add_projectors(MatvecPlan* p) {
+  if (!p->nlow) return;
+  vec_multidot(p->lowv, p->n, p->nlow, p->xin, p->n, p->lowc, p->lowc + p->nlow, stream_);
+  vec_combine(p->loww, p->n, p->nlow, p->lowc, 1.0, p->yout, p->n, stream_);
+}
+
 void Engine::matvec_noalloc(int i, const double* x, double* y, Stream s) {
+  if (!low_.empty())
+    throw std::invalid_argument("the allocation-free matvec does not carry excited-state projectors");
   if (!cached_ || cached_site_ != i)
     throw std::invalid_argument(
         "no prepared matvec for this site: call dmrg_heff_matvec (or dmrg_davidson) at this site "
@@ -1363,13 +1403,17 @@ void Engine::diag(int i, double* d) {
 void Engine::tt_to_x(int i, double* x) {
   check_ready();
   if (i < 0 || i > L_ - 2) throw std::out_of_range("site out of range");
+  tt_to_x_of(bonds_, sites_, i, x);
+}
+
+void Engine::tt_to_x_of(const std::vector<Bond>& bonds, const std::vector<Site>& sites, int i, double* x) {
   int64_t n;
-  auto X = x_layout(i, &n);
-  const Bond& bl = bonds_[i];
-  const Bond& bm = bonds_[i + 1];
-  const Bond& br = bonds_[i + 2];
-  const Site& A = sites_[i];
-  const Site& B = sites_[i + 1];
+  auto X = x_layout_of(bonds, i, &n);
+  const Bond& bl = bonds[i];
+  const Bond& bm = bonds[i + 1];
+  const Bond& br = bonds[i + 2];
+  const Site& A = sites[i];
+  const Site& B = sites[i + 1];
   std::map<std::tuple<int, int, int>, int> ia, ib;  // (ls, l, r) -> block
   for (int t = 0; t < (int)A.blocks.size(); ++t) ia[{A.blocks[t].ls, A.blocks[t].l, A.blocks[t].r}] = t;
   for (int t = 0; t < (int)B.blocks.size(); ++t) ib[{B.blocks[t].ls, B.blocks[t].l, B.blocks[t].r}] = t;
@@ -1998,6 +2042,7 @@ void Engine::canonicalize(int center) {
 // dE/dd = sum coef <C^T x_out, x_src> for a right operator of value d.
 void Engine::rdm(double* gamma, double* Gamma) {
   check_ready();
+  Timer tm;
   if (Wg_.empty()) {
     Integrals gz = g_;
     gz.keep_zero = true;
@@ -2044,6 +2089,8 @@ void Engine::rdm(double* gamma, double* Gamma) {
   for (auto& e : lenv_) free_env(e);
   for (auto& e : renv_) free_env(e);
   dev_sync(stream_);
+  st_.rdm_passes += 1;
+  st_.rdm_ms += tm.ms();
 }
 
 void Engine::rdm_site(MatvecPlan* P, int i, double* dg, bool last) {
@@ -2107,6 +2154,9 @@ void Engine::rdm_site(MatvecPlan* P, int i, double* dg, bool last) {
     gemm_plan_run(p, stream_);
     gemm_plan_free(p, stream_);
   }
+  double flops = P->flops1;
+  for (size_t q = 0; q < gg.size(); ++q)
+    for (int k = gg[q].task_begin; k < gg[q].task_end; ++k) flops += 2.0 * gg[q].m * gg[q].n * gt[k].k;
   // dE/dg[gi] += gc <L_a, Gbar> over the terms of every left combined operator
   std::map<int64_t, std::vector<DotTask>> dots;
   const OpStore& E = lenv_[i];
@@ -2161,9 +2211,14 @@ void Engine::rdm_site(MatvecPlan* P, int i, double* dg, bool last) {
     GemmPlan* p = gemm_plan_upload(ut, ug, stream_);
     gemm_plan_run(p, stream_);
     gemm_plan_free(p, stream_);
+    for (size_t q = 0; q < ug.size(); ++q)
+      if (ut[q].A) flops += 2.0 * ug[q].m * ug[q].n * ut[q].k;
   }
   std::vector<DotTask> dt;
   std::vector<DotGroup> dgp;
+  for (auto& kv : dots)
+    for (const DotTask& t : kv.second) flops += 2.0 * t.rows * t.cols;
+  st_.rdm_flops += flops;
   for (auto& kv : dots) {
     const int b0 = (int)dt.size();
     dt.insert(dt.end(), kv.second.begin(), kv.second.end());
@@ -2172,6 +2227,260 @@ void Engine::rdm_site(MatvecPlan* P, int i, double* dg, bool last) {
   dot_grouped(dt, dgp, stream_);
   dev_free(Gb, stream_);
   if (U) dev_free(U, stream_);
+}
+
+// ---------------------------------------------------------------- excited states
+//
+// H_m = H_0 + sum_k eta_{k+1} |Psi_k><Psi_k| (Sec. 4.3).  In the two-site basis of
+// sites (i, i+1) the projector is eta v v^T with v = O_L(i) x_k O_R(i+2)^T blockwise:
+// x_k the lower state's own two-site object (Eq. 25, x = sqrt(2jR+1) S), O_L / O_R the
+// overlaps of the current renormalised basis with the lower state's, per sector:
+//   O_L(k+1)[r] = sum_{s, l} T_cur[s, l, r]^T O_L(k)[l] T_low[s, l, r]          (O_L(0) = 1)
+//   O_R(k)[l]   = sum_{s, r} (2jR+1)/(2jL+1) T_cur[s, l, r] O_R(k+1)[r] T_low[s, l, r]^T
+// (the reduced recursions whose fixed points are the normalisations of Eqs. 5 and 6).
+// An overlap is rebuilt whenever the operator environment of the same bond and side has
+// been (both depend on the same current tensors).
+
+void Engine::push_excitation(double eta) {
+  check_ready();
+  canonicalize(0);  // |Psi| = 1
+  LowState S;
+  S.eta = eta;
+  S.bonds = bonds_;
+  S.sites.resize(L_);
+  for (int k = 0; k < L_; ++k) {
+    S.sites[k].blocks = sites_[k].blocks;
+    S.sites[k].size = sites_[k].size;
+    S.sites[k].data = (double*)dev_alloc(sizeof(double) * std::max<int64_t>(sites_[k].size, 1), stream_);
+    dev_d2d(S.sites[k].data, sites_[k].data, sizeof(double) * sites_[k].size, stream_);
+  }
+  S.left.resize(L_ + 1);
+  S.right.resize(L_ + 1);
+  low_.push_back(std::move(S));
+  if (cached_) { free_plan(cached_); cached_ = nullptr; cached_site_ = -1; }
+}
+
+void Engine::clear_excitations() {
+  for (auto& S : low_) {
+    for (auto& t : S.sites)
+      if (t.data) dev_free(t.data, stream_);
+    for (auto& o : S.left) free_overlap(o);
+    for (auto& o : S.right) free_overlap(o);
+  }
+  low_.clear();
+  if (cached_) { free_plan(cached_); cached_ = nullptr; cached_site_ = -1; }
+}
+
+void Engine::free_overlap(Overlap& o) {
+  if (o.data) dev_free(o.data, stream_);
+  o = Overlap();
+}
+
+namespace {
+// blocks for the sectors present in both bonds
+void overlap_layout(Overlap& O, const Bond& cur, const Bond& low) {
+  int64_t off = 0;
+  for (int c = 0; c < (int)cur.sec.size(); ++c) {
+    const int l = low.find(cur.sec[c]);
+    if (l < 0) continue;
+    O.by_cur[c] = (int)O.cur.size();
+    O.cur.push_back(c);
+    O.low.push_back(l);
+    O.rows.push_back(cur.dim[c]);
+    O.cols.push_back(low.dim[l]);
+    O.off.push_back(off);
+    off += (int64_t)cur.dim[c] * low.dim[l];
+  }
+  O.size = off;
+}
+}  // namespace
+
+void Engine::ensure_ov_left(LowState& S, int k) {
+  ensure_left(k);
+  Overlap& O = S.left[k];
+  if (O.valid && O.env_serial == lenv_[k].serial) return;
+  if (k > 0) ensure_ov_left(S, k - 1);
+  free_overlap(O);
+  overlap_layout(O, bonds_[k], S.bonds[k]);
+  O.data = (double*)dev_alloc(sizeof(double) * std::max<int64_t>(O.size, 1), stream_);
+  dev_zero(O.data, sizeof(double) * std::max<int64_t>(O.size, 1), stream_);
+  if (k == 0) {
+    const double one = 1.0;
+    for (size_t e = 0; e < O.cur.size(); ++e) dev_h2d(O.data + O.off[e], &one, sizeof(double), stream_);
+    dev_sync(stream_);
+  } else {
+    const Overlap& P = S.left[k - 1];
+    const Site& Tc = sites_[k - 1];
+    const Site& Tl = S.sites[k - 1];
+    const Bond& lowl = S.bonds[k - 1];
+    const Bond& lowr = S.bonds[k];
+    std::map<std::tuple<int, int, int>, int> lb;  // (ls, low left sector, low right sector)
+    for (int t = 0; t < (int)Tl.blocks.size(); ++t) lb[{Tl.blocks[t].ls, Tl.blocks[t].l, Tl.blocks[t].r}] = t;
+    std::vector<GemmTask> t1, t2;
+    std::vector<GemmGroup> g1;
+    std::map<int, std::vector<GemmTask>> out;  // overlap block -> tasks
+    std::vector<int64_t> zoff;
+    int64_t zsize = 0;
+    for (const SiteBlock& c : Tc.blocks) {
+      auto pl = P.by_cur.find(c.l);
+      auto orr = O.by_cur.find(c.r);
+      if (pl == P.by_cur.end() || orr == O.by_cur.end()) continue;
+      const int ll = P.low[pl->second], lr = O.low[orr->second];
+      auto it = lb.find({c.ls, ll, lr});
+      if (it == lb.end()) continue;
+      const SiteBlock& b = Tl.blocks[it->second];
+      // Z = O_L(k-1)[l] (d_cur(l) x d_low(l)) . T_low (d_low(l) x d_low(r))
+      const int dcl = P.rows[pl->second], dll = lowl.dim[ll], dlr = lowr.dim[lr];
+      t1.push_back({P.data + P.off[pl->second], Tl.data + b.off, dll, dlr, dll, 0, 0, 1.0});
+      g1.push_back({nullptr, dlr, dcl, dlr, (int)t1.size() - 1, (int)t1.size(), 0});
+      zoff.push_back(zsize);
+      zsize += (int64_t)dcl * dlr;
+      // O_L(k)[r] += T_cur^T (d_cur(r) x d_cur(l)) . Z
+      out[orr->second].push_back({Tc.data + c.off, (const double*)(intptr_t)(g1.size() - 1), c.cols, dlr,
+                                  c.rows, 1, 0, 1.0});
+    }
+    double* Z = (double*)dev_alloc(sizeof(double) * std::max<int64_t>(zsize, 1), stream_);
+    dev_zero(Z, sizeof(double) * std::max<int64_t>(zsize, 1), stream_);
+    for (size_t z = 0; z < g1.size(); ++z) g1[z].C = Z + zoff[z];
+    std::vector<GemmGroup> g2;
+    for (auto& kv : out) {
+      const int e = kv.first;
+      const int b0 = (int)t2.size();
+      for (GemmTask t : kv.second) {
+        t.B = Z + zoff[(size_t)(intptr_t)t.B];
+        t2.push_back(t);
+      }
+      g2.push_back({O.data + O.off[e], O.cols[e], O.rows[e], O.cols[e], b0, (int)t2.size(), 0});
+    }
+    GemmPlan* p1 = gemm_plan_upload(t1, g1, stream_);
+    GemmPlan* p2 = gemm_plan_upload(t2, g2, stream_);
+    gemm_plan_run(p1, stream_);
+    gemm_plan_run(p2, stream_);
+    gemm_plan_free(p1, stream_);
+    gemm_plan_free(p2, stream_);
+    dev_free(Z, stream_);
+  }
+  O.valid = true;
+  O.env_serial = lenv_[k].serial;
+}
+
+void Engine::ensure_ov_right(LowState& S, int k) {
+  ensure_right(k);
+  Overlap& O = S.right[k];
+  if (O.valid && O.env_serial == renv_[k].serial) return;
+  if (k < L_) ensure_ov_right(S, k + 1);
+  free_overlap(O);
+  overlap_layout(O, bonds_[k], S.bonds[k]);
+  O.data = (double*)dev_alloc(sizeof(double) * std::max<int64_t>(O.size, 1), stream_);
+  dev_zero(O.data, sizeof(double) * std::max<int64_t>(O.size, 1), stream_);
+  if (k == L_) {
+    const double one = 1.0;
+    for (size_t e = 0; e < O.cur.size(); ++e) dev_h2d(O.data + O.off[e], &one, sizeof(double), stream_);
+    dev_sync(stream_);
+  } else {
+    const Overlap& P = S.right[k + 1];
+    const Site& Tc = sites_[k];
+    const Site& Tl = S.sites[k];
+    const Bond& lowl = S.bonds[k];
+    const Bond& lowr = S.bonds[k + 1];
+    std::map<std::tuple<int, int, int>, int> lb;
+    for (int t = 0; t < (int)Tl.blocks.size(); ++t) lb[{Tl.blocks[t].ls, Tl.blocks[t].l, Tl.blocks[t].r}] = t;
+    std::vector<GemmTask> t1, t2;
+    std::vector<GemmGroup> g1;
+    std::map<int, std::vector<GemmTask>> out;
+    std::vector<int64_t> zoff;
+    int64_t zsize = 0;
+    for (const SiteBlock& c : Tc.blocks) {
+      auto pr = P.by_cur.find(c.r);
+      auto ol = O.by_cur.find(c.l);
+      if (pr == P.by_cur.end() || ol == O.by_cur.end()) continue;
+      const int lr = P.low[pr->second], ll = O.low[ol->second];
+      auto it = lb.find({c.ls, ll, lr});
+      if (it == lb.end()) continue;
+      const SiteBlock& b = Tl.blocks[it->second];
+      const double w = (double)(bonds_[k + 1].sec[c.r].tj + 1) / (double)(bonds_[k].sec[c.l].tj + 1);
+      // Z = O_R(k+1)[r] (d_cur(r) x d_low(r)) . T_low^T (d_low(r) x d_low(l))
+      const int dcr = P.rows[pr->second], dlr = lowr.dim[lr], dll = lowl.dim[ll];
+      t1.push_back({P.data + P.off[pr->second], Tl.data + b.off, dlr, dlr, dlr, 0, 1, 1.0});
+      g1.push_back({nullptr, dll, dcr, dll, (int)t1.size() - 1, (int)t1.size(), 0});
+      zoff.push_back(zsize);
+      zsize += (int64_t)dcr * dll;
+      // O_R(k)[l] += w T_cur (d_cur(l) x d_cur(r)) . Z
+      out[ol->second].push_back({Tc.data + c.off, (const double*)(intptr_t)(g1.size() - 1), c.cols, dll,
+                                 c.cols, 0, 0, w});
+    }
+    double* Z = (double*)dev_alloc(sizeof(double) * std::max<int64_t>(zsize, 1), stream_);
+    dev_zero(Z, sizeof(double) * std::max<int64_t>(zsize, 1), stream_);
+    for (size_t z = 0; z < g1.size(); ++z) g1[z].C = Z + zoff[z];
+    std::vector<GemmGroup> g2;
+    for (auto& kv : out) {
+      const int e = kv.first;
+      const int b0 = (int)t2.size();
+      for (GemmTask t : kv.second) {
+        t.B = Z + zoff[(size_t)(intptr_t)t.B];
+        t2.push_back(t);
+      }
+      g2.push_back({O.data + O.off[e], O.cols[e], O.rows[e], O.cols[e], b0, (int)t2.size(), 0});
+    }
+    GemmPlan* p1 = gemm_plan_upload(t1, g1, stream_);
+    GemmPlan* p2 = gemm_plan_upload(t2, g2, stream_);
+    gemm_plan_run(p1, stream_);
+    gemm_plan_run(p2, stream_);
+    gemm_plan_free(p1, stream_);
+    gemm_plan_free(p2, stream_);
+    dev_free(Z, stream_);
+  }
+  O.valid = true;
+  O.env_serial = renv_[k].serial;
+}
+
+void Engine::low_projection(LowState& S, int i, const std::vector<XBlock>& X, double* v) {
+  ensure_ov_left(S, i);
+  ensure_ov_right(S, i + 2);
+  const Overlap& OL = S.left[i];
+  const Overlap& OR = S.right[i + 2];
+  int64_t nl = 0;
+  auto XL = x_layout_of(S.bonds, i, &nl);
+  double* xl = (double*)dev_alloc(sizeof(double) * std::max<int64_t>(nl, 1), stream_);
+  tt_to_x_of(S.bonds, S.sites, i, xl);
+  std::map<std::tuple<int, int, int, int, int>, int> at;  // (l, ls1, ls2, tj, r) in low sectors
+  for (int q = 0; q < (int)XL.size(); ++q) at[{XL[q].l, XL[q].ls1, XL[q].ls2, XL[q].tj, XL[q].r}] = q;
+  std::vector<GemmTask> t1, t2;
+  std::vector<GemmGroup> g1, g2;
+  std::vector<int64_t> zoff;
+  int64_t zsize = 0;
+  for (const XBlock& b : X) {
+    auto pl = OL.by_cur.find(b.l);
+    auto pr = OR.by_cur.find(b.r);
+    if (pl == OL.by_cur.end() || pr == OR.by_cur.end()) continue;
+    auto it = at.find({OL.low[pl->second], b.ls1, b.ls2, b.tj, OR.low[pr->second]});
+    if (it == at.end()) continue;
+    const XBlock& c = XL[it->second];
+    // Z = x_low (d_low(l) x d_low(r)) . O_R[r]^T (d_low(r) x d_cur(r)); v = O_L[l] . Z
+    t1.push_back({xl + c.off, OR.data + OR.off[pr->second], c.cols, c.cols, c.cols, 0, 1, 1.0});
+    g1.push_back({nullptr, b.cols, c.rows, b.cols, (int)t1.size() - 1, (int)t1.size(), 0});
+    zoff.push_back(zsize);
+    zsize += (int64_t)c.rows * b.cols;
+    t2.push_back({OL.data + OL.off[pl->second], nullptr, c.rows, b.cols, c.rows, 0, 0, 1.0});
+    g2.push_back({v + b.off, b.cols, b.rows, b.cols, (int)t2.size() - 1, (int)t2.size(), 0});
+  }
+  double* Z = (double*)dev_alloc(sizeof(double) * std::max<int64_t>(zsize, 1), stream_);
+  dev_zero(Z, sizeof(double) * std::max<int64_t>(zsize, 1), stream_);
+  for (size_t z = 0; z < g1.size(); ++z) {
+    g1[z].C = Z + zoff[z];
+    t2[z].B = Z + zoff[z];
+  }
+  int64_t n = 0;
+  for (const XBlock& b : X) n = std::max<int64_t>(n, b.off + (int64_t)b.rows * b.cols);
+  dev_zero(v, sizeof(double) * std::max<int64_t>(n, 1), stream_);
+  GemmPlan* p1 = gemm_plan_upload(t1, g1, stream_);
+  GemmPlan* p2 = gemm_plan_upload(t2, g2, stream_);
+  gemm_plan_run(p1, stream_);
+  gemm_plan_run(p2, stream_);
+  gemm_plan_free(p1, stream_);
+  gemm_plan_free(p2, stream_);
+  dev_free(Z, stream_);
+  dev_free(xl, stream_);
 }
 
 // True if sites 1..L-1 satisfy the reduced right-normalisation of Eq. 6,

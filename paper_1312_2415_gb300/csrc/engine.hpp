@@ -24,6 +24,7 @@ struct BlockRef {
 struct OpStore {
   bool valid = false;
   int bond = -1;
+  uint64_t serial = 0;  // distinct for every allocation (overlaps record the one they match)
   std::vector<std::vector<BlockRef>> blocks;         // per operator
   std::vector<std::unordered_map<int64_t, int>> at;  // (r << 32 | c) -> block index
   double* data = nullptr;
@@ -64,6 +65,28 @@ struct CombOp {
   std::vector<std::pair<int64_t, double>> grad;  // (gi, gc) of each source's recursion term
 };
 
+// Overlap of the current MPS's renormalised basis at one bond with a stored state's, for
+// every sector present in both: block e is d_cur(cur[e]) x d_low(low[e]), row-major.
+struct Overlap {
+  bool valid = false;
+  uint64_t env_serial = 0;  // serial of the operator environment of the same bond and side
+  std::vector<int> cur, low, rows, cols;
+  std::vector<int64_t> off;
+  std::unordered_map<int, int> by_cur;  // current sector -> block
+  double* data = nullptr;
+  int64_t size = 0;
+};
+
+// A lower state of the excited-state Hamiltonian H_m = H_0 + sum eta_k |Psi_k><Psi_k|
+// (Sec. 4.3): its bonds and reduced tensors, its weight, and its overlaps with the
+// current basis on both sides of every bond.
+struct LowState {
+  double eta = 0.0;
+  std::vector<Bond> bonds;
+  std::vector<Site> sites;
+  std::vector<Overlap> left, right;
+};
+
 struct Stats {
   int64_t matvecs = 0, davidson_iters = 0, micro_iters = 0;
   double matvec_flops = 0.0, last_matvec_flops = 0.0, last_matvec_ms = 0.0;
@@ -78,6 +101,8 @@ struct Stats {
   int64_t tc_matvecs = 0;
   double tc_flops = 0.0, tc_phase1_ms = 0.0, tc_phase2_ms = 0.0;
   double tc_phase1_flops = 0.0, tc_phase2_flops = 0.0, tc_phase1_bytes = 0.0, tc_phase2_bytes = 0.0;
+  int64_t rdm_passes = 0;
+  double rdm_ms = 0.0, rdm_flops = 0.0;
 };
 
 class Engine {
@@ -115,6 +140,11 @@ class Engine {
   // permutations under which V is invariant, gamma_ik = sum_j Gamma_ijkj / (N - 1).
   // Leaves the MPS in mixed canonical form around site L-2 (the state is unchanged).
   void rdm(double* gamma_dev, double* Gamma_dev);
+  // Excited states (Sec. 4.3): store the current MPS (normalised, right-canonical) as the
+  // next lower state with weight eta; from then on H_eff carries + eta |Psi><Psi|.
+  void push_excitation(double eta);
+  void clear_excitations();
+  int n_excitations() const { return (int)low_.size(); }
   bool is_right_canonical();
   void right_normalize_site(int k);
   void left_normalize_site(int k);
@@ -164,6 +194,14 @@ class Engine {
   void free_site(int k);
   void identity_fill(OpStore& e, int op);
   void rdm_site(MatvecPlan* P, int i, double* dg, bool last);
+  void add_projectors(MatvecPlan* p);
+  void free_overlap(Overlap& o);
+  void ensure_ov_left(LowState& S, int k);
+  void ensure_ov_right(LowState& S, int k);
+  // v = projection of S onto the current two-site basis of sites (i, i+1) (layout X)
+  void low_projection(LowState& S, int i, const std::vector<XBlock>& X, double* v);
+  void tt_to_x_of(const std::vector<Bond>& bonds, const std::vector<Site>& sites, int i, double* x);
+  std::vector<XBlock> x_layout_of(const std::vector<Bond>& bonds, int i, int64_t* n) const;
 
   int L_, N_, two_S_, irrep_;
   Symmetry sym_;
@@ -179,6 +217,8 @@ class Engine {
   std::vector<std::map<Sector, int>> fci_;  // FCI-capped sector dimensions per bond
   std::vector<Site> sites_;
   std::vector<OpStore> lenv_, renv_;
+  uint64_t env_serial_ = 0;
+  std::vector<LowState> low_;
   std::vector<int> sched_D_, sched_nmax_;
   std::vector<double> sched_econv_, sched_noise_;
   double dav_tol_ = 1e-10;
