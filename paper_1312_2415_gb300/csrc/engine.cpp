@@ -22,6 +22,25 @@ namespace {
 
 inline int64_t bkey(int r, int c) { return ((int64_t)r << 32) | (uint32_t)c; }
 
+// f(begin, end) over [0, n) in chunks, on up to 16 threads (the caller's included)
+template <class F>
+void parallel_chunks(size_t n, size_t chunk, F f) {
+  std::atomic<size_t> next{0};
+  auto run = [&]() {
+    for (;;) {
+      const size_t b = next.fetch_add(chunk);
+      if (b >= n) break;
+      f(b, std::min(n, b + chunk));
+    }
+  };
+  const unsigned hc = std::thread::hardware_concurrency();
+  const size_t nth = std::min<size_t>(std::max(1u, std::min(16u, hc ? hc : 1u)), (n + chunk - 1) / chunk);
+  std::vector<std::thread> th;
+  for (size_t t = 1; t < nth; ++t) th.emplace_back(run);
+  run();
+  for (auto& t : th) t.join();
+}
+
 uint64_t splitmix64_next(uint64_t& state) {
   state += 0x9E3779B97F4A7C15ull;
   uint64_t z = state;
@@ -859,8 +878,6 @@ Engine::MatvecPlan* Engine::plan_matvec(int i) {
   // W(gl, C block, X') = sum coef * Z rows of X ; phase 2: y_X' += C_blk W
   struct WItem { int gl, cbi, xp; int64_t off; int rows, cols; int src_begin, src_end; };
   std::vector<WItem> ws;
-  struct WS { int64_t zoff; int ld; double coef; int zg, xb; };  // zoff < 0: into xin (-1 - off)
-  std::vector<WS> wsrc;
   std::vector<std::vector<DiagTerm>> dout(P->X.size());
   std::vector<std::vector<int>> w_by_x(P->X.size());
   int64_t wsize = 0;
@@ -975,41 +992,34 @@ Engine::MatvecPlan* Engine::plan_matvec(int i) {
     worker();
     for (auto& t : th) t.join();
   }
-  for (size_t it = 0; it < items.size(); ++it) {
-    const Item& I = items[it];
-    const CombOp& C = P->cl[I.gl];
-    const BlockRef& cb = (*C.blocks)[I.cbi];
-    Out& o = outs[it];
+  // Merge in item order (deterministic tables).  Z groups get their ids in (right
+  // group, block) order among the blocks some source uses; the W items and sources of
+  // every item go to offsets from prefix sums over the items, filled in parallel.
+  for (const Out& o : outs)
+    for (const Src& q : o.s) ztab[q.gr][q.dbi].ld = 1;  // mark used (zg still unset)
+  for (int gr = 0; gr < (int)P->cr.size(); ++gr)
+    for (int dbi = 0; dbi < (int)ztab[gr].size(); ++dbi)
+      if (ztab[gr][dbi].ld == 1) get_z(gr, dbi);
+  const size_t nit = items.size();
+  std::vector<int64_t> it_w(nit + 1, 0), it_s(nit + 1, 0), it_off(nit + 1, 0);
+  for (size_t it = 0; it < nit; ++it) {
+    const Out& o = outs[it];
+    const BlockRef& cb = (*P->cl[items[it].gl].blocks)[items[it].cbi];
+    int64_t wb = 0;
+    for (const Grp& g : o.g) wb += (int64_t)cb.cols * P->X[g.xp].cols;
+    it_w[it + 1] = it_w[it] + (int64_t)o.g.size();
+    it_s[it + 1] = it_s[it] + (int64_t)o.s.size();
+    it_off[it + 1] = it_off[it] + wb;
+    const CombOp& C = P->cl[items[it].gl];
     for (const DRaw& dr : o.d) {
       const CombOp& D = P->cr[dr.gr];
       const BlockRef& db = (*D.blocks)[dr.dbi];
       dout[dr.x].push_back({C.data + cb.off, D.data + db.off, cb.cols, db.cols, dr.coef * C.scalar * D.scalar});
     }
-    for (const Grp& g : o.g) {
-      const XBlock& Xp = P->X[g.xp];
-      WItem w{I.gl, I.cbi, g.xp, wsize, cb.cols, Xp.cols, (int)wsrc.size(), 0};
-      for (int k = g.begin; k < g.end; ++k) {
-        const Src& q = o.s[k];
-        const CombOp& D = P->cr[q.gr];
-        const XBlock& X = P->X[q.x];
-        ZRef z = get_z(q.gr, q.dbi);
-        const int64_t zoff = z.off >= 0 ? z.off + (int64_t)X.trow * z.ld : z.off - (int64_t)X.trow * z.ld;
-        // identity right operator: Z is x itself, its alias scalar goes here
-        const WS ws1{zoff, z.ld, D.identity ? q.coef * D.scalar : q.coef, z.zg, q.x};
-        wsrc.push_back(ws1);
-        P->wsrc.push_back({ws1.zg, ws1.xb, ws1.coef, q.gr, q.coef});
-      }
-      w.src_end = (int)wsrc.size();
-      P->witems.push_back({I.gl, I.cbi, w.rows, w.cols, w.src_begin, w.src_end});
-      wsize += (int64_t)cb.cols * Xp.cols;
-      w_by_x[g.xp].push_back((int)ws.size());
-      ws.push_back(w);
-      if (!C.identity) flops2 += 2.0 * cb.rows * cb.cols * Xp.cols;
-    }
-    std::vector<Grp>().swap(o.g);
-    std::vector<Src>().swap(o.s);
-    std::vector<DRaw>().swap(o.d);
   }
+  if (it_w[nit] > std::numeric_limits<int>::max() || it_s[nit] > std::numeric_limits<int>::max())
+    throw std::runtime_error("matvec tables exceed 2^31 entries");
+  wsize = it_off[nit];
   P->zsize = zsize;
   P->Z = (double*)dev_alloc(sizeof(double) * std::max<int64_t>(zsize, 1), stream_);
   P->W = (double*)dev_alloc(sizeof(double) * std::max<int64_t>(wsize, 1), stream_);
@@ -1023,36 +1033,79 @@ Engine::MatvecPlan* Engine::plan_matvec(int i) {
       zo += (int64_t)g1[z].m * g1[z].n;
     }
   }
-  // combine plan for W
-  std::vector<CombSrc> cs;
-  std::vector<CombDst> cd;
-  cs.reserve(wsrc.size());
-  cd.reserve(ws.size());
-  for (auto& w : ws) {
-    CombDst d{P->W + w.off, w.cols, w.rows, w.cols, (int)cs.size(), 0, 0};
-    for (int q = w.src_begin; q < w.src_end; ++q) {
-      const WS& src = wsrc[q];
-      const double* ptr = src.zoff >= 0 ? P->Z + src.zoff : P->xin + (-1 - src.zoff);
-      cs.push_back({ptr, src.ld, src.coef});
-    }
-    d.src_end = (int)cs.size();
-    cd.push_back(d);
+  // combine plan for W (one destination per W item, its sources in order)
+  std::vector<CombSrc> cs(it_s[nit]);
+  std::vector<CombDst> cd(it_w[nit]);
+  ws.resize(it_w[nit]);
+  P->wsrc.resize(it_s[nit]);
+  P->witems.resize(it_w[nit]);
+  std::vector<double> it_flops(nit, 0.0);
+  {
+    auto fill = [&](size_t ib, size_t ie) {
+        for (size_t it = ib; it < ie; ++it) {
+          const Item& I = items[it];
+          const CombOp& C = P->cl[I.gl];
+          const BlockRef& cb = (*C.blocks)[I.cbi];
+          Out& o = outs[it];
+          int64_t wi = it_w[it], si = it_s[it], off = it_off[it];
+          for (const Grp& g : o.g) {
+            const XBlock& Xp = P->X[g.xp];
+            WItem w{I.gl, I.cbi, g.xp, off, cb.cols, Xp.cols, (int)si, 0};
+            for (int k = g.begin; k < g.end; ++k, ++si) {
+              const Src& q = o.s[k];
+              const CombOp& D = P->cr[q.gr];
+              const XBlock& X = P->X[q.x];
+              const ZRef z = ztab[q.gr][q.dbi];
+              const int64_t zoff = z.off >= 0 ? z.off + (int64_t)X.trow * z.ld : z.off - (int64_t)X.trow * z.ld;
+              // identity right operator: Z is x itself, its alias scalar goes here
+              const double coef = D.identity ? q.coef * D.scalar : q.coef;
+              cs[si] = {zoff >= 0 ? P->Z + zoff : P->xin + (-1 - zoff), z.ld, coef};
+              P->wsrc[si] = {z.zg, q.x, coef, q.gr, q.coef};
+            }
+            w.src_end = (int)si;
+            P->witems[wi] = {I.gl, I.cbi, w.rows, w.cols, w.src_begin, w.src_end};
+            cd[wi] = {P->W + w.off, w.cols, w.rows, w.cols, w.src_begin, w.src_end, 0};
+            ws[wi++] = w;
+            off += (int64_t)cb.cols * Xp.cols;
+            if (!C.identity) it_flops[it] += 2.0 * cb.rows * cb.cols * Xp.cols;
+          }
+          std::vector<Grp>().swap(o.g);
+          std::vector<Src>().swap(o.s);
+          std::vector<DRaw>().swap(o.d);
+        }
+    };
+    parallel_chunks(nit, 64, fill);
   }
-  // phase 2 grouped by output block
-  std::vector<GemmTask> t2;
-  std::vector<GemmGroup> g2;
-  for (int x = 0; x < (int)P->X.size(); ++x) {
-    const XBlock& X = P->X[x];
-    int b0 = (int)t2.size();
-    for (int wi : w_by_x[x]) {
-      const WItem& w = ws[wi];
-      const CombOp& C = P->cl[w.gl];
-      const BlockRef& cb = (*C.blocks)[w.cbi];
-      if (C.identity) t2.push_back({nullptr, P->W + w.off, 0, w.cols, w.rows, 0, 0, C.scalar});
-      else t2.push_back({C.data + cb.off, P->W + w.off, cb.cols, w.cols, cb.cols, 0, 0, C.scalar});
-    }
-    if ((int)t2.size() > b0) g2.push_back({P->yout + X.off, X.cols, X.rows, X.cols, b0, (int)t2.size(), 0});
+  for (size_t it = 0; it < nit; ++it) flops2 += it_flops[it];
+  {
+    std::vector<int> cnt(P->X.size(), 0);
+    for (const WItem& w : ws) ++cnt[w.xp];
+    for (size_t x = 0; x < P->X.size(); ++x) w_by_x[x].reserve(cnt[x]);
+    for (int k = 0; k < (int)ws.size(); ++k) w_by_x[ws[k].xp].push_back(k);
   }
+  // phase 2 grouped by output block: the tasks of block x at the prefix of |w_by_x|
+  std::vector<int64_t> xt(P->X.size() + 1, 0), xg(P->X.size() + 1, 0);
+  for (size_t x = 0; x < P->X.size(); ++x) {
+    xt[x + 1] = xt[x] + (int64_t)w_by_x[x].size();
+    xg[x + 1] = xg[x] + (w_by_x[x].empty() ? 0 : 1);
+  }
+  std::vector<GemmTask> t2(xt[P->X.size()]);
+  std::vector<GemmGroup> g2(xg[P->X.size()]);
+  parallel_chunks(P->X.size(), 256, [&](size_t xb, size_t xe) {
+    for (size_t x = xb; x < xe; ++x) {
+      if (w_by_x[x].empty()) continue;
+      const XBlock& X = P->X[x];
+      int64_t k = xt[x];
+      for (int wi : w_by_x[x]) {
+        const WItem& w = ws[wi];
+        const CombOp& C = P->cl[w.gl];
+        const BlockRef& cb = (*C.blocks)[w.cbi];
+        if (C.identity) t2[k++] = {nullptr, P->W + w.off, 0, w.cols, w.rows, 0, 0, C.scalar};
+        else t2[k++] = {C.data + cb.off, P->W + w.off, cb.cols, w.cols, cb.cols, 0, 0, C.scalar};
+      }
+      g2[xg[x]] = {P->yout + X.off, X.cols, X.rows, X.cols, (int)xt[x], (int)xt[x + 1], 0};
+    }
+  });
   // diagonal
   std::vector<DiagTerm> dt;
   std::vector<DiagOut> dov;
@@ -1255,35 +1308,49 @@ void Engine::build_tc(MatvecPlan* P) {
     for (int row0 = 0; row0 < M; row0 += 128)
       H.r1.push_back({x32 + xoff[c] + (int64_t)row0 * lda, lda, std::min(128, M - row0), K, row0, p0, p1});
   }
-  // phase 2
+  // phase 2: the tasks, sources and units of output block x at prefix offsets
   std::vector<Tc2Src>& srcs = H.s;
   std::vector<Tc2Task>& tasks = H.t;
-  srcs.reserve(P->wsrc.size());
-  tasks.reserve(P->witems.size());
-  for (int x = 0; x < (int)P->X.size(); ++x) {
+  const size_t nX = P->X.size();
+  std::vector<int64_t> xt(nX + 1, 0), xs(nX + 1, 0), xu(nX + 1, 0);
+  for (size_t x = 0; x < nX; ++x) {
+    int64_t ns = 0;
+    for (int wi : P->w_by_x[x]) ns += P->witems[wi].src_end - P->witems[wi].src_begin;
     const XBlock& X = P->X[x];
-    const int t0 = (int)tasks.size();
-    for (int wi : P->w_by_x[x]) {
-      const auto& w = P->witems[wi];
-      const CombOp& C = P->cl[w.gl];
-      const BlockRef& cb = (*C.blocks)[w.cbi];
-      Tc2Task t{C.identity ? nullptr : m32 + cmir[w.gl][w.cbi], (int)r4(cb.cols), w.rows, (float)C.scalar,
-                (int)srcs.size(), 0};
-      for (int q = w.src_begin; q < w.src_end; ++q) {
-        const auto& src = P->wsrc[q];
-        const int c = P->X[src.xb].r;
-        if (src.zg >= 0) srcs.push_back({zt + zoff[src.zg] + trow_pad[src.xb], (int)rpad[c], (float)src.coef});
-        else srcs.push_back({x32t + xtoff[c] + trow_pad[src.xb], (int)rpad[c], (float)src.coef});
-      }
-      t.s_end = (int)srcs.size();
-      tasks.push_back(t);
-    }
-    const int t1 = (int)tasks.size();
-    if (t1 == t0) continue;
-    for (int row0 = 0; row0 < X.rows; row0 += 128)
-      for (int col0 = 0; col0 < X.cols; col0 += 64)
-        H.r2.push_back({P->yout + X.off, X.cols, X.rows, X.cols, row0, col0, t0, t1});
+    xt[x + 1] = xt[x] + (int64_t)P->w_by_x[x].size();
+    xs[x + 1] = xs[x] + ns;
+    xu[x + 1] = xu[x] + (P->w_by_x[x].empty() ? 0 : (int64_t)((X.rows + 127) / 128) * ((X.cols + 63) / 64));
   }
+  if (xs[nX] > std::numeric_limits<int>::max()) throw std::runtime_error("tensor-core tables exceed 2^31 entries");
+  srcs.resize(xs[nX]);
+  tasks.resize(xt[nX]);
+  H.r2.resize(xu[nX]);
+  parallel_chunks(nX, 256, [&](size_t xb, size_t xe) {
+    for (size_t x = xb; x < xe; ++x) {
+      if (P->w_by_x[x].empty()) continue;
+      const XBlock& X = P->X[x];
+      int64_t t = xt[x], q = xs[x];
+      for (int wi : P->w_by_x[x]) {
+        const auto& w = P->witems[wi];
+        const CombOp& C = P->cl[w.gl];
+        const BlockRef& cb = (*C.blocks)[w.cbi];
+        Tc2Task tk{C.identity ? nullptr : m32 + cmir[w.gl][w.cbi], (int)r4(cb.cols), w.rows, (float)C.scalar,
+                   (int)q, 0};
+        for (int k = w.src_begin; k < w.src_end; ++k) {
+          const auto& src = P->wsrc[k];
+          const int c = P->X[src.xb].r;
+          if (src.zg >= 0) srcs[q++] = {zt + zoff[src.zg] + trow_pad[src.xb], (int)rpad[c], (float)src.coef};
+          else srcs[q++] = {x32t + xtoff[c] + trow_pad[src.xb], (int)rpad[c], (float)src.coef};
+        }
+        tk.s_end = (int)q;
+        tasks[t++] = tk;
+      }
+      int64_t u = xu[x];
+      for (int row0 = 0; row0 < X.rows; row0 += 128)
+        for (int col0 = 0; col0 < X.cols; col0 += 64)
+          H.r2[u++] = {P->yout + X.off, X.cols, X.rows, X.cols, row0, col0, (int)xt[x], (int)xt[x + 1]};
+    }
+  });
   H.yout = P->yout;
   H.n = P->n;
   // compulsory traffic (unpadded FP32 elements): phase 1 reads x and each right-operator
