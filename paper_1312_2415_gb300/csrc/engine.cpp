@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <functional>
 #include <array>
 #include <chrono>
 #include <cmath>
@@ -21,6 +22,27 @@ namespace dmrg {
 namespace {
 
 inline int64_t bkey(int r, int c) { return ((int64_t)r << 32) | (uint32_t)c; }
+
+// Tasks tagged with an output index, grouped per output in increasing index order
+// (stable: a group's tasks keep their order); zs[id] gives the Z offset of a task whose
+// B holds a Z id.
+struct TaggedTask { int64_t out; GemmTask t; };
+void group_by_output(std::vector<TaggedTask>& tagged, int64_t nout, double* Z, const std::vector<int64_t>& zoff,
+                     const std::function<void(int64_t, int, int, std::vector<GemmGroup>&)>& make_group,
+                     std::vector<GemmTask>& t2, std::vector<GemmGroup>& g2) {
+  std::vector<int> cnt(nout + 1, 0);
+  for (const auto& q : tagged) ++cnt[q.out + 1];
+  for (int64_t o = 0; o < nout; ++o) cnt[o + 1] += cnt[o];
+  t2.resize(tagged.size());
+  std::vector<int> pos(cnt.begin(), cnt.end() - 1);
+  for (const auto& q : tagged) {
+    GemmTask t = q.t;
+    t.B = Z + zoff[(size_t)(intptr_t)t.B];
+    t2[pos[q.out]++] = t;
+  }
+  for (int64_t o = 0; o < nout; ++o)
+    if (cnt[o + 1] > cnt[o]) make_group(o, cnt[o], cnt[o + 1], g2);
+}
 
 // f(begin, end) over [0, n) in chunks, on up to 16 threads (the caller's included)
 template <class F>
@@ -93,6 +115,7 @@ Engine::~Engine() {
     for (auto& e : renv_) free_env(e);
     for (int k = 0; k < L_; ++k) free_site(k);
     clear_excitations();
+    if (reaper_.joinable()) reaper_.join();
     dev_sync(stream_);
   } catch (...) {
   }
@@ -579,7 +602,9 @@ void Engine::update_left_from(int i, std::vector<CombOp>& comb) {
   const int id_op = opsets_[i + 1].find({OP_I, -1, -1, 0});
   std::vector<GemmTask> t1, t2;
   std::vector<GemmGroup> g1;
-  std::map<std::pair<int, int>, std::vector<GemmTask>> out2;  // (op, block) -> tasks
+  std::vector<int64_t> bbase(E.blocks.size() + 1, 0);  // first output index of each operator
+  for (size_t o = 0; o < E.blocks.size(); ++o) bbase[o + 1] = bbase[o] + (int64_t)E.blocks[o].size();
+  std::vector<TaggedTask> out2;
   int64_t zsize = 0;
   struct ZRef { int64_t off; int rows, cols; };
   std::vector<ZRef> zs;
@@ -604,9 +629,8 @@ void Engine::update_left_from(int i, std::vector<CombOp>& comb) {
             t1.push_back({c.data + cb.off, T.data + tb.off, cb.cols, tb.cols, cb.cols, 0, 0, 1.0});
             g1.push_back({nullptr, tb.cols, cb.rows, tb.cols, (int)t1.size() - 1, (int)t1.size(), 0});
           }
-          out2[{c.target, it->second}].push_back(
-              {T.data + tpb.off, nullptr, tpb.cols, tb.cols, tpb.rows, 1, 0, coef});
-          out2[{c.target, it->second}].back().B = (const double*)(intptr_t)zid;
+          out2.push_back({bbase[c.target] + it->second,
+                          {T.data + tpb.off, (const double*)(intptr_t)zid, tpb.cols, tb.cols, tpb.rows, 1, 0, coef}});
         }
       }
     }
@@ -615,14 +639,17 @@ void Engine::update_left_from(int i, std::vector<CombOp>& comb) {
   for (size_t z = 0; z < g1.size(); ++z) g1[z].C = Z + zs[z].off;
   dev_zero(Z, sizeof(double) * std::max<int64_t>(zsize, 1), stream_);
   std::vector<GemmGroup> g2;
-  for (auto& kv : out2) {
-    const BlockRef& ob = E.blocks[kv.first.first][kv.first.second];
-    int b0 = (int)t2.size();
-    for (auto t : kv.second) {
-      t.B = Z + zs[(int)(intptr_t)t.B].off;
-      t2.push_back(t);
-    }
-    g2.push_back({E.data + ob.off, ob.cols, ob.rows, ob.cols, b0, (int)t2.size(), 0});
+  {
+    std::vector<int64_t> zoff(zs.size());
+    for (size_t z = 0; z < zs.size(); ++z) zoff[z] = zs[z].off;
+    std::vector<std::pair<int, int>> at(bbase.back());  // output index -> (op, block)
+    for (size_t o = 0; o + 1 < bbase.size(); ++o)
+      for (int64_t b = bbase[o]; b < bbase[o + 1]; ++b) at[b] = {(int)o, (int)(b - bbase[o])};
+    group_by_output(out2, bbase.back(), Z, zoff,
+                    [&](int64_t id, int b0, int b1, std::vector<GemmGroup>& g) {
+                      const BlockRef& ob = E.blocks[at[id].first][at[id].second];
+                      g.push_back({E.data + ob.off, ob.cols, ob.rows, ob.cols, b0, b1, 0});
+                    }, t2, g2);
   }
   GemmPlan* p1 = gemm_plan_upload(t1, g1, stream_);
   GemmPlan* p2 = gemm_plan_upload(t2, g2, stream_);
@@ -653,7 +680,9 @@ void Engine::update_right_from(int j, std::vector<CombOp>& comb) {
   };
   std::vector<GemmTask> t1, t2;
   std::vector<GemmGroup> g1;
-  std::map<std::pair<int, int>, std::vector<GemmTask>> out2;
+  std::vector<int64_t> bbase(E.blocks.size() + 1, 0);  // first output index of each operator
+  for (size_t o = 0; o < E.blocks.size(); ++o) bbase[o + 1] = bbase[o] + (int64_t)E.blocks[o].size();
+  std::vector<TaggedTask> out2;
   int64_t zsize = 0;
   struct ZRef { int64_t off; int rows, cols; };
   std::vector<ZRef> zs;
@@ -679,8 +708,8 @@ void Engine::update_right_from(int j, std::vector<CombOp>& comb) {
             t1.push_back({c.data + db.off, T.data + tb.off, db.cols, tb.cols, db.cols, 0, 1, 1.0});
             g1.push_back({nullptr, tb.rows, db.rows, tb.rows, (int)t1.size() - 1, (int)t1.size(), 0});
           }
-          GemmTask tk{T.data + tpb.off, (const double*)(intptr_t)zid, tpb.cols, tb.rows, tpb.cols, 0, 0, coef};
-          out2[{c.target, it->second}].push_back(tk);
+          out2.push_back({bbase[c.target] + it->second,
+                          {T.data + tpb.off, (const double*)(intptr_t)zid, tpb.cols, tb.rows, tpb.cols, 0, 0, coef}});
         }
       }
     }
@@ -689,14 +718,17 @@ void Engine::update_right_from(int j, std::vector<CombOp>& comb) {
   for (size_t z = 0; z < g1.size(); ++z) g1[z].C = Z + zs[z].off;
   dev_zero(Z, sizeof(double) * std::max<int64_t>(zsize, 1), stream_);
   std::vector<GemmGroup> g2;
-  for (auto& kv : out2) {
-    const BlockRef& ob = E.blocks[kv.first.first][kv.first.second];
-    int b0 = (int)t2.size();
-    for (auto t : kv.second) {
-      t.B = Z + zs[(int)(intptr_t)t.B].off;
-      t2.push_back(t);
-    }
-    g2.push_back({E.data + ob.off, ob.cols, ob.rows, ob.cols, b0, (int)t2.size(), 0});
+  {
+    std::vector<int64_t> zoff(zs.size());
+    for (size_t z = 0; z < zs.size(); ++z) zoff[z] = zs[z].off;
+    std::vector<std::pair<int, int>> at(bbase.back());  // output index -> (op, block)
+    for (size_t o = 0; o + 1 < bbase.size(); ++o)
+      for (int64_t b = bbase[o]; b < bbase[o + 1]; ++b) at[b] = {(int)o, (int)(b - bbase[o])};
+    group_by_output(out2, bbase.back(), Z, zoff,
+                    [&](int64_t id, int b0, int b1, std::vector<GemmGroup>& g) {
+                      const BlockRef& ob = E.blocks[at[id].first][at[id].second];
+                      g.push_back({E.data + ob.off, ob.cols, ob.rows, ob.cols, b0, b1, 0});
+                    }, t2, g2);
   }
   GemmPlan* p1 = gemm_plan_upload(t1, g1, stream_);
   GemmPlan* p2 = gemm_plan_upload(t2, g2, stream_);
@@ -1173,7 +1205,10 @@ void Engine::free_plan(MatvecPlan* p) {
   if (p->lowv) dev_free(p->lowv, stream_);
   if (p->loww) dev_free(p->loww, stream_);
   if (p->lowc) dev_free(p->lowc, stream_);
-  delete p;
+  // the host tables (millions of entries) are released on a helper thread, one plan at
+  // a time, while the caller goes on
+  if (reaper_.joinable()) reaper_.join();
+  reaper_ = std::thread([p]() { delete p; });
 }
 
 Engine::MatvecPlan* Engine::plan_for(int i) {

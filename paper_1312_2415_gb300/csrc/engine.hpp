@@ -4,6 +4,7 @@
 #include <map>
 #include <memory>
 #include <string>
+#include <thread>
 #include <unordered_map>
 #include <vector>
 
@@ -241,6 +242,7 @@ class Engine {
   std::vector<int> hist_D_;
   std::vector<double> hist_E_, hist_w_;
   uint64_t plan_serial_ = 0;
+  std::thread reaper_;  // releases the host tables of the last freed plan
 };
 
 }  // namespace dmrg

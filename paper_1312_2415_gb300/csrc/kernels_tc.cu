@@ -765,14 +765,19 @@ TcPlan* tc_plan_build(const std::vector<const TcHost*>& inst, TcTune tune, Strea
   std::vector<Tc2Unit> u2, u2g;
   std::vector<TcXBlock> xb;
   TcPlan* P = new TcPlan;
+  // one instance: its tables are uploaded as they are (indices need no offsets)
+  const bool single = inst.size() == 1;
   for (const TcHost* H : inst) {
     const int e0 = (int)e.size(), p0 = (int)p.size(), s0 = (int)sr.size(), t0 = (int)t.size();
-    e.insert(e.end(), H->e.begin(), H->e.end());
-    for (Tc1Pack q : H->p) {
+    for (const Tc1Pack& q : H->p)
       if (q.e_end - q.e_begin > kMaxPackEntries || q.n > 128) throw std::logic_error("tc pack too large");
-      q.e_begin += e0;
-      q.e_end += e0;
-      p.push_back(q);
+    if (!single) {
+      e.insert(e.end(), H->e.begin(), H->e.end());
+      for (Tc1Pack q : H->p) {
+        q.e_begin += e0;
+        q.e_end += e0;
+        p.push_back(q);
+      }
     }
     for (const Tc1Unit& r : H->r1)
       for (int pb = r.p_begin; pb < r.p_end; pb += tune.packs_per_unit) {
@@ -781,11 +786,13 @@ TcPlan* tc_plan_build(const std::vector<const TcHost*>& inst, TcTune tune, Strea
         u.p_end = p0 + std::min(r.p_end, pb + tune.packs_per_unit);
         (r.K <= 32 ? u1 : u1m).push_back(u);
       }
-    sr.insert(sr.end(), H->s.begin(), H->s.end());
-    for (Tc2Task q : H->t) {
-      q.s_begin += s0;
-      q.s_end += s0;
-      t.push_back(q);
+    if (!single) {
+      sr.insert(sr.end(), H->s.begin(), H->s.end());
+      for (Tc2Task q : H->t) {
+        q.s_begin += s0;
+        q.s_end += s0;
+        t.push_back(q);
+      }
     }
     for (const Tc2Unit& r : H->r2)
       for (int tb = r.t_begin; tb < r.t_end; tb += tune.tasks_per_unit) {
@@ -794,7 +801,7 @@ TcPlan* tc_plan_build(const std::vector<const TcHost*>& inst, TcTune tune, Strea
         u.t_end = t0 + std::min(r.t_end, tb + tune.tasks_per_unit);
         (r.m - r.row0 <= 32 ? u2 : u2g).push_back(u);
       }
-    xb.insert(xb.end(), H->xb.begin(), H->xb.end());
+    if (!single) xb.insert(xb.end(), H->xb.begin(), H->xb.end());
     if (H->yout && H->n > 0) P->clear.push_back({H->yout, H->n});
   }
   P->n1_one = (int)u1.size();
@@ -803,14 +810,15 @@ TcPlan* tc_plan_build(const std::vector<const TcHost*>& inst, TcTune tune, Strea
   P->n2_small = (int)u2.size();
   u2.insert(u2.end(), u2g.begin(), u2g.end());
   P->n2 = (int)u2.size();
-  P->ents = upload(e, st);
-  P->packs = upload(p, st);
+  const TcHost* H0 = single ? inst[0] : nullptr;
+  P->ents = upload(single ? H0->e : e, st);
+  P->packs = upload(single ? H0->p : p, st);
   P->u1 = upload(u1, st);
-  P->srcs = upload(sr, st);
-  P->tasks = upload(t, st);
+  P->srcs = upload(single ? H0->s : sr, st);
+  P->tasks = upload(single ? H0->t : t, st);
   P->u2 = upload(u2, st);
-  P->xb = upload(xb, st);
-  P->nxb = (int)xb.size();
+  P->xb = upload(single ? H0->xb : xb, st);
+  P->nxb = (int)(single ? H0->xb.size() : xb.size());
   P->launches = (P->nxb > 0) + (P->n1_one > 0) + (P->n1_multi > 0) + (P->n2_small > 0) + (P->n2 > P->n2_small);
   return P;
 }
