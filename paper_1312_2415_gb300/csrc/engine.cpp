@@ -926,7 +926,12 @@ Engine::MatvecPlan* Engine::plan_matvec(int i) {
   struct Src { int gr, dbi, x; double coef; };
   struct Grp { int xp, begin, end; };      // sources of one W item, first-touch order
   struct DRaw { int x, gr, dbi; double coef; };
-  struct Out { std::vector<Grp> g; std::vector<Src> s; std::vector<DRaw> d; };
+  struct Out { std::vector<Grp> g; std::vector<Src> s; std::vector<DRaw> d; int64_t wb = 0; };
+  // right-operator blocks some source uses (set by the workers; Z groups are made for these)
+  std::vector<int64_t> zbase(P->cr.size() + 1, 0);
+  for (size_t g = 0; g < P->cr.size(); ++g) zbase[g + 1] = zbase[g] + (int64_t)P->cr[g].blocks->size();
+  std::unique_ptr<std::atomic<uint8_t>[]> zused(new std::atomic<uint8_t>[std::max<int64_t>(zbase.back(), 1)]);
+  for (int64_t z = 0; z < zbase.back(); ++z) zused[z].store(0, std::memory_order_relaxed);
   std::vector<Out> outs(items.size());
   std::atomic<size_t> next_item{0};
   auto worker = [&]() {
@@ -1011,8 +1016,10 @@ Engine::MatvecPlan* Engine::plan_matvec(int i) {
         o.g.push_back({touched[k], (int)o.s.size(), 0});
         o.s.insert(o.s.end(), bucket[k].begin(), bucket[k].end());
         o.g.back().end = (int)o.s.size();
+        o.wb += (int64_t)cb.cols * P->X[touched[k]].cols;
         slot[touched[k]] = -1;
       }
+      for (const Src& q : o.s) zused[zbase[q.gr] + q.dbi].store(1, std::memory_order_relaxed);
       touched.clear();
     }
   };
@@ -1027,18 +1034,15 @@ Engine::MatvecPlan* Engine::plan_matvec(int i) {
   // Merge in item order (deterministic tables).  Z groups get their ids in (right
   // group, block) order among the blocks some source uses; the W items and sources of
   // every item go to offsets from prefix sums over the items, filled in parallel.
-  for (const Out& o : outs)
-    for (const Src& q : o.s) ztab[q.gr][q.dbi].ld = 1;  // mark used (zg still unset)
   for (int gr = 0; gr < (int)P->cr.size(); ++gr)
     for (int dbi = 0; dbi < (int)ztab[gr].size(); ++dbi)
-      if (ztab[gr][dbi].ld == 1) get_z(gr, dbi);
+      if (zused[zbase[gr] + dbi].load(std::memory_order_relaxed)) get_z(gr, dbi);
   const size_t nit = items.size();
   std::vector<int64_t> it_w(nit + 1, 0), it_s(nit + 1, 0), it_off(nit + 1, 0);
   for (size_t it = 0; it < nit; ++it) {
     const Out& o = outs[it];
     const BlockRef& cb = (*P->cl[items[it].gl].blocks)[items[it].cbi];
-    int64_t wb = 0;
-    for (const Grp& g : o.g) wb += (int64_t)cb.cols * P->X[g.xp].cols;
+    const int64_t wb = o.wb;
     it_w[it + 1] = it_w[it] + (int64_t)o.g.size();
     it_s[it + 1] = it_s[it] + (int64_t)o.s.size();
     it_off[it + 1] = it_off[it] + wb;
@@ -1273,21 +1277,23 @@ void Engine::build_tc(MatvecPlan* P) {
   }
   // operator mirrors: every block phase 1 or phase 2 reads
   std::unordered_map<const double*, int64_t> moff;
+  moff.reserve(P->zg.size() + P->cl.size() * 4 + 16);
   std::vector<TcMirror> mir;
+  std::vector<int64_t> mir_off;
   int64_t nm = 0;
   double distinct = 0.0;  // unpadded elements of the blocks mirrored so far
-  auto want = [&](const double* p, int rows, int cols) {
-    if (moff.emplace(p, nm).second) {
+  auto want = [&](const double* p, int rows, int cols) -> int64_t {
+    auto ins = moff.emplace(p, nm);
+    if (ins.second) {
       mir.push_back({p, nullptr, rows, cols, (int)r4(cols)});
+      mir_off.push_back(nm);
       nm += (int64_t)rows * r4(cols);
       distinct += (double)rows * cols;
     }
+    return ins.first->second;
   };
   std::vector<int64_t> zmir(P->zg.size());
-  for (size_t g = 0; g < P->zg.size(); ++g) {
-    want(P->zg[g].D, P->zg[g].n, P->zg[g].K);
-    zmir[g] = moff[P->zg[g].D];
-  }
+  for (size_t g = 0; g < P->zg.size(); ++g) zmir[g] = want(P->zg[g].D, P->zg[g].n, P->zg[g].K);
   const double distinct_d = distinct;
   std::vector<std::vector<int64_t>> cmir(P->cl.size());  // (gl, cbi) -> mirror offset, -1 = unused
   for (const auto& w : P->witems) {
@@ -1297,13 +1303,12 @@ void Engine::build_tc(MatvecPlan* P) {
     if (cm.empty()) cm.assign(C.blocks->size(), -1);
     if (cm[w.cbi] >= 0) continue;
     const BlockRef& cb = (*C.blocks)[w.cbi];
-    want(C.data + cb.off, cb.rows, cb.cols);
-    cm[w.cbi] = moff[C.data + cb.off];
+    cm[w.cbi] = want(C.data + cb.off, cb.rows, cb.cols);
   }
   float* m32 = (float*)dev_alloc(sizeof(float) * std::max<int64_t>(nm, 4), stream_);
   P->tc_mem[2] = m32;
   dev_zero(m32, sizeof(float) * std::max<int64_t>(nm, 4), stream_);
-  for (auto& m : mir) m.dst = m32 + moff[m.src];
+  for (size_t q = 0; q < mir.size(); ++q) mir[q].dst = m32 + mir_off[q];
   tc_mirror(mir, stream_);
   // Zt: one column-major block per phase-1 group, stride = padded stack height
   std::vector<int64_t> zoff(P->zg.size());
