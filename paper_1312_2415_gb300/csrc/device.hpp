@@ -26,6 +26,11 @@ void event_destroy(void* e);
 void event_record(void* e, Stream s);
 float event_elapsed_ms(void* a, void* b);  // both must have completed
 void host_pinned_free(void* p);
+// a private non-blocking stream, and ordering across streams by events
+Stream stream_create();
+void stream_destroy(Stream s);
+void stream_wait(Stream s, void* ev);  // work queued on s after this waits for ev
+void event_sync(void* ev);
 
 // ---- grouped GEMM: C_g = C_g + sum_t alpha_t op(A_t) op(B_t), row-major blocks;
 // A == nullptr means op(A) = identity (C_g += alpha op(B)) ----

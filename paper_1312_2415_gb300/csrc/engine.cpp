@@ -116,6 +116,13 @@ Engine::~Engine() {
     for (int k = 0; k < L_; ++k) free_site(k);
     clear_excitations();
     if (reaper_.joinable()) reaper_.join();
+    if (side_) {
+      dev_sync(side_);
+      stream_destroy(side_);
+      event_destroy(ev_side_[0]);
+      event_destroy(ev_side_[1]);
+      dev_free(rq_dev_, stream_);
+    }
     dev_sync(stream_);
   } catch (...) {
   }
@@ -1555,6 +1562,10 @@ void Engine::tt_to_x_of(const std::vector<Bond>& bonds, const std::vector<Site>&
 // FP64: subspace up to 32 vectors, restart on the 3 lowest Ritz vectors, diagonal
 // preconditioner, two classical Gram-Schmidt passes, convergence on ||r||_2.
 double Engine::davidson(int i, double* x, int* iters, bool* converged) {
+  return davidson_ex(i, x, iters, converged, false);
+}
+
+double Engine::davidson_ex(int i, double* x, int* iters, bool* converged, bool defer) {
   check_ready();
   MatvecPlan* P = plan_for(i);
   if (precision_ != 1) return davidson_core(P, x, dav_tol_, dav_max_, false, iters, converged);
@@ -1564,10 +1575,56 @@ double Engine::davidson(int i, double* x, int* iters, bool* converged) {
   bool c1 = false, c2 = false;
   davidson_core(P, x, std::max(dav_tol_, 1e-6), dav_max_, true, &it1, &c1);
   if (tc_error_flag(stream_)) throw std::runtime_error("cuda: tensor-core wait timed out");
+  if (defer && refine_iters_ == 1) {
+    start_rq(P, x);
+    *iters = it1 + 1;
+    *converged = false;
+    return std::numeric_limits<double>::quiet_NaN();
+  }
   double e = davidson_core(P, x, dav_tol_, refine_iters_ > 0 ? refine_iters_ : dav_max_, false, &it2, &c2);
   *iters = it1 + it2;
   *converged = c2;
   return e;
+}
+
+// E = x.Hx / x.x with the FP64 matvec on the side stream: x is copied into the plan's
+// input on the engine's stream first (so later changes of x do not race), the side
+// stream waits for that copy, and the engine's stream waits for the side stream in
+// finish_rq before anything the side stream reads can be released.
+void Engine::start_rq(MatvecPlan* P, const double* x) {
+  if (!side_) {
+    side_ = stream_create();
+    ev_side_[0] = event_create();
+    ev_side_[1] = event_create();
+    rq_dev_ = (double*)dev_alloc(sizeof(double) * (2 + 2 * 512), stream_);
+  }
+  dev_d2d(P->xin, x, sizeof(double) * P->n, stream_);
+  event_record(ev_side_[0], stream_);
+  stream_wait(side_, ev_side_[0]);
+  Stream keep = stream_;
+  stream_ = side_;
+  try {
+    run_matvec(P, P->xin, P->yout, false);
+    vec_multidot(P->xin, P->n, 1, P->yout, P->n, rq_dev_, rq_dev_ + 2, side_);
+    vec_multidot(P->xin, P->n, 1, P->xin, P->n, rq_dev_ + 1, rq_dev_ + 2 + 512, side_);
+    event_record(ev_side_[1], side_);
+  } catch (...) {
+    stream_ = keep;
+    throw;
+  }
+  stream_ = keep;
+  rq_pending_ = true;
+}
+
+double Engine::finish_rq() {
+  if (!rq_pending_) return std::numeric_limits<double>::quiet_NaN();
+  rq_pending_ = false;
+  stream_wait(stream_, ev_side_[1]);
+  double h[2];
+  dev_d2h(h, rq_dev_, sizeof(h), side_);
+  dev_sync(side_);
+  if (!(h[1] > 0.0)) throw std::runtime_error("Ritz vector has zero norm");
+  return h[0] / h[1];
 }
 
 double Engine::davidson_core(MatvecPlan* P, double* x, double tol, int maxit, bool tc, int* iters,
@@ -2687,7 +2744,7 @@ double Engine::sweep_step(int i, int dir, int D, double gamma, double* w_disc, i
   MatvecPlan* P = plan_for(i);
   double* x = (double*)dev_alloc(sizeof(double) * std::max<int64_t>(P->n, 1), stream_);
   tt_to_x(i, x);
-  double e = davidson(i, x, iters, conv) + econst_;
+  double e = davidson_ex(i, x, iters, conv, true) + econst_;
   if (gamma > 0.0 && w_prev_ > 0.0) {
     // Sec. 4.2: noise bounded by 0.5 gamma w_disc(previous half sweep), then the
     // decomposition renormalises through kappa
@@ -2695,9 +2752,16 @@ double Engine::sweep_step(int i, int dir, int D, double gamma, double* w_disc, i
   }
   cached_ = nullptr;  // keep P's combined operators for the update below
   cached_site_ = -1;
-  double w = truncate(i, dir, D, x, 0.0);
-  if (dir > 0) update_left_from(i, P->cl);
-  else update_right_from(i + 1, P->cr);
+  double w;
+  try {
+    w = truncate(i, dir, D, x, 0.0);
+    if (dir > 0) update_left_from(i, P->cl);
+    else update_right_from(i + 1, P->cr);
+  } catch (...) {
+    if (rq_pending_) { try { finish_rq(); } catch (...) {} }
+    throw;
+  }
+  if (rq_pending_) e = finish_rq() + econst_;
   free_plan(P);
   dev_free(x, stream_);
   st_.micro_iters += 1;

@@ -130,6 +130,10 @@ class Engine {
   // allocates nothing (throws invalid_argument if no table is prepared for i)
   void matvec_noalloc(int i, const double* x_dev, double* y_dev, Stream s);
   double davidson(int i, double* x_dev, int* iters, bool* converged);
+  // mixed precision with one FP64 iteration (which only evaluates the FP64 Rayleigh
+  // quotient of the tensor-core Ritz vector): with defer set the FP64 matvec is queued on
+  // a side stream and the energy is collected by finish_rq()
+  double davidson_ex(int i, double* x_dev, int* iters, bool* converged, bool defer);
   double truncate(int i, int dir, int D, const double* x_dev, double noise);
   double solve(double* e_last);
   // one micro-iteration of a sweep at sites (i, i+1): Eq. 25, Davidson, noise,
@@ -196,6 +200,8 @@ class Engine {
   void identity_fill(OpStore& e, int op);
   void rdm_site(MatvecPlan* P, int i, double* dg, bool last);
   void add_projectors(MatvecPlan* p);
+  void start_rq(MatvecPlan* P, const double* x);
+  double finish_rq();
   void free_overlap(Overlap& o);
   void ensure_ov_left(LowState& S, int k);
   void ensure_ov_right(LowState& S, int k);
@@ -243,6 +249,12 @@ class Engine {
   std::vector<double> hist_E_, hist_w_;
   uint64_t plan_serial_ = 0;
   std::thread reaper_;  // releases the host tables of the last freed plan
+  // side stream of the deferred FP64 Rayleigh quotient: events (input copied, done),
+  // device results (x.Hx, x.x) and reduction scratch
+  Stream side_ = nullptr;
+  void* ev_side_[2] = {nullptr, nullptr};
+  double* rq_dev_ = nullptr;
+  bool rq_pending_ = false;
 };
 
 }  // namespace dmrg

@@ -82,6 +82,16 @@ void event_destroy(void* e) {
   if (e) cudaEventDestroy((cudaEvent_t)e);
 }
 void event_record(void* e, Stream s) { ck(cudaEventRecord((cudaEvent_t)e, S(s)), "cudaEventRecord"); }
+Stream stream_create() {
+  cudaStream_t s;
+  ck(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "cudaStreamCreate");
+  return (Stream)s;
+}
+void stream_destroy(Stream s) {
+  if (s) cudaStreamDestroy(S(s));
+}
+void stream_wait(Stream s, void* ev) { ck(cudaStreamWaitEvent(S(s), (cudaEvent_t)ev, 0), "cudaStreamWaitEvent"); }
+void event_sync(void* ev) { ck(cudaEventSynchronize((cudaEvent_t)ev), "cudaEventSynchronize"); }
 float event_elapsed_ms(void* a, void* b) {
   float ms = 0.f;
   ck(cudaEventSynchronize((cudaEvent_t)b), "cudaEventSynchronize");
