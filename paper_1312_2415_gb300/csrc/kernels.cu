@@ -854,14 +854,13 @@ __global__ void k_bj_prep(const BjJob* __restrict__ jobs, double* __restrict__ g
   if (threadIdx.x == 0) gmax[blockIdx.x] = red[0];
 }
 
-// step, part 1: V of every pair from its diagonal sub-block, then rows I+J <- V^T rows
+// step, part 1: V of every pair from its diagonal sub-block (one CTA per pair)
 __global__ void __launch_bounds__(256) k_bj_rows(const BjJob* __restrict__ jobs, int njobs, int step,
                                                  const double* __restrict__ gmax, double* __restrict__ vbuf,
                                                  int* __restrict__ flag, int* __restrict__ nrot) {
   extern __shared__ double bsm[];
   double* S = bsm;              // sub-block, then diagonalised
   double* V = S + kOP * kOL;    // its eigenvectors
-  double* buf = V + kOP * kOL;  // streamed 64 x 64 chunk
   __shared__ double cs[kOP / 2], sn[kOP / 2];
   __shared__ int pq[kOP], idx[kOP];
   __shared__ int inner_rot, need;
@@ -926,29 +925,45 @@ __global__ void __launch_bounds__(256) k_bj_rows(const BjJob* __restrict__ jobs,
     flag[blockIdx.x] = 1;
     atomicAdd(&nrot[lo], 1);
   }
-  // rows I+J of A <- V^T rows I+J
+}
+
+// step, part 2: rows I+J of A <- V^T rows I+J, one 64-column chunk per CTA (grid.y)
+__global__ void __launch_bounds__(256) k_bj_rowapply(const BjJob* __restrict__ jobs, int njobs, int step,
+                                                     const double* __restrict__ vbuf, const int* __restrict__ flag) {
+  extern __shared__ double bsm[];
+  double* V = bsm;
+  double* buf = V + kOP * kOL;
+  __shared__ int idx[kOP];
+  if (!flag[blockIdx.x]) return;
+  const int lo = find_job(jobs, njobs);
+  const BjJob J = jobs[lo];
+  const int r = blockIdx.x - J.pair_begin, tid = threadIdx.x, n = J.n;
+  const int c0 = blockIdx.y * kOP;
+  if (c0 >= n) return;
+  pair_rows(J, r, step, idx);
+  const double* vg = vbuf + (size_t)blockIdx.x * kOP * kOP;
+  for (int e = tid; e < kOP * kOP; e += 256) V[(e >> 6) * kOL + (e & 63)] = vg[e];
+  __syncthreads();
+  for (int e = tid; e < kOP * kOP; e += 256) {
+    const int i = e >> 6, k = e & 63;
+    buf[i * kOL + k] = (idx[i] >= 0 && c0 + k < n) ? J.A[(size_t)idx[i] * n + c0 + k] : 0.0;
+  }
+  __syncthreads();
+  double acc[4][4];
+  tile64<true, false>(V, buf, acc);
   const int ti = tid >> 4, tj = tid & 15;
-  for (int c0 = 0; c0 < n; c0 += kOP) {
-    for (int e = tid; e < kOP * kOP; e += 256) {
-      const int i = e >> 6, k = e & 63;
-      buf[i * kOL + k] = (idx[i] >= 0 && c0 + k < n) ? J.A[(size_t)idx[i] * n + c0 + k] : 0.0;
-    }
-    __syncthreads();
-    double acc[4][4];
-    tile64<true, false>(V, buf, acc);
-    __syncthreads();
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int row = idx[ti * 4 + u];
-      if (row < 0) continue;
+  for (int u = 0; u < 4; ++u) {
+    const int row = idx[ti * 4 + u];
+    if (row < 0) continue;
 #pragma unroll
-      for (int v = 0; v < 4; ++v)
-        if (c0 + tj * 4 + v < n) J.A[(size_t)row * n + c0 + tj * 4 + v] = acc[u][v];
-    }
+    for (int v = 0; v < 4; ++v)
+      if (c0 + tj * 4 + v < n) J.A[(size_t)row * n + c0 + tj * 4 + v] = acc[u][v];
   }
 }
 
-// step, part 2: columns I+J of A and of Q <- columns times V
+// step, part 3: columns I+J of A (grid.z = 0) and of Q (grid.z = 1) <- columns times V,
+// one 64-row chunk per CTA (grid.y)
 __global__ void __launch_bounds__(256) k_bj_cols(const BjJob* __restrict__ jobs, int njobs, int step,
                                                  const double* __restrict__ vbuf, const int* __restrict__ flag) {
   extern __shared__ double bsm[];
@@ -964,27 +979,24 @@ __global__ void __launch_bounds__(256) k_bj_cols(const BjJob* __restrict__ jobs,
   for (int e = tid; e < kOP * kOP; e += 256) V[(e >> 6) * kOL + (e & 63)] = vg[e];
   __syncthreads();
   const int ti = tid >> 4, tj = tid & 15;
-  for (int mat = 0; mat < 2; ++mat) {
-    double* M = mat == 0 ? J.A : J.Q;
-    for (int r0 = 0; r0 < n; r0 += kOP) {
-      for (int e = tid; e < kOP * kOP; e += 256) {
-        const int rr = e >> 6, k = e & 63;
-        buf[rr * kOL + k] = (idx[k] >= 0 && r0 + rr < n) ? M[(size_t)(r0 + rr) * n + idx[k]] : 0.0;
-      }
-      __syncthreads();
-      double acc[4][4];
-      tile64<false, false>(buf, V, acc);
-      __syncthreads();
+  double* M = blockIdx.z == 0 ? J.A : J.Q;
+  const int r0 = blockIdx.y * kOP;
+  if (r0 >= n) return;
+  for (int e = tid; e < kOP * kOP; e += 256) {
+    const int rr = e >> 6, k = e & 63;
+    buf[rr * kOL + k] = (idx[k] >= 0 && r0 + rr < n) ? M[(size_t)(r0 + rr) * n + idx[k]] : 0.0;
+  }
+  __syncthreads();
+  double acc[4][4];
+  tile64<false, false>(buf, V, acc);
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int rr = r0 + ti * 4 + u;
-        if (rr >= n) continue;
+  for (int u = 0; u < 4; ++u) {
+    const int rr = r0 + ti * 4 + u;
+    if (rr >= n) continue;
 #pragma unroll
-        for (int v = 0; v < 4; ++v) {
-          const int col = idx[tj * 4 + v];
-          if (col >= 0) M[(size_t)rr * n + col] = acc[u][v];
-        }
-      }
+    for (int v = 0; v < 4; ++v) {
+      const int col = idx[tj * 4 + v];
+      if (col >= 0) M[(size_t)rr * n + col] = acc[u][v];
     }
   }
 }
@@ -1032,6 +1044,7 @@ static void eig_block_jacobi(const std::vector<EigJob>& jobs, Stream s) {
     nmax = std::max(nmax, j.n);
   }
   const int nj = (int)bj.size();
+  const int nch = (nmax + kOP - 1) / kOP;  // 64-wide chunks of the largest matrix
   BjJob* d = (BjJob*)dev_alloc(sizeof(BjJob) * nj, s);
   dev_h2d(d, bj.data(), sizeof(BjJob) * nj, s);
   double* gmax = (double*)dev_alloc(sizeof(double) * nj, s);
@@ -1041,19 +1054,21 @@ static void eig_block_jacobi(const std::vector<EigJob>& jobs, Stream s) {
   std::vector<int> hrot(nj);
   k_bj_prep<<<nj, 256, 0, S(s)>>>(d, gmax);
   ++g_launches;
-  const size_t shr = sizeof(double) * 3 * kOP * kOL, shc = sizeof(double) * 2 * kOP * kOL;
+  const size_t shr = sizeof(double) * 2 * kOP * kOL, shc = sizeof(double) * 2 * kOP * kOL;
   static bool attr = false;
   if (!attr) {
     ck(cudaFuncSetAttribute(k_bj_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shr), "bj smem");
     ck(cudaFuncSetAttribute(k_bj_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shc), "bj smem");
+    ck(cudaFuncSetAttribute(k_bj_rowapply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shc), "bj smem");
     attr = true;
   }
   for (int sweep = 0; sweep < 40; ++sweep) {
     ck(cudaMemsetAsync(nrot, 0, sizeof(int) * nj, S(s)), "bj counters");
     for (int step = 0; step < nbmax - 1; ++step) {
       k_bj_rows<<<pairs, 256, shr, S(s)>>>(d, nj, step, gmax, vbuf, flag, nrot);
-      k_bj_cols<<<pairs, 256, shc, S(s)>>>(d, nj, step, vbuf, flag);
-      g_launches += 2;
+      k_bj_rowapply<<<dim3(pairs, nch), 256, shc, S(s)>>>(d, nj, step, vbuf, flag);
+      k_bj_cols<<<dim3(pairs, nch, 2), 256, shc, S(s)>>>(d, nj, step, vbuf, flag);
+      g_launches += 3;
     }
     ck(cudaGetLastError(), "bj step");
     dev_d2h(hrot.data(), nrot, sizeof(int) * nj, s);
