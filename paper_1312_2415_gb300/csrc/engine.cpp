@@ -1600,6 +1600,15 @@ void Engine::start_rq(MatvecPlan* P, const double* x) {
   }
   dev_d2d(P->xin, x, sizeof(double) * P->n, stream_);
   event_record(ev_side_[0], stream_);
+  rq_plan_ = P;
+  rq_pending_ = true;
+}
+
+// queue the side stream's FP64 matvec and dot products of the copy start_rq made
+void Engine::launch_rq() {
+  if (!rq_pending_ || !rq_plan_) return;
+  MatvecPlan* P = rq_plan_;
+  rq_plan_ = nullptr;
   stream_wait(side_, ev_side_[0]);
   Stream keep = stream_;
   stream_ = side_;
@@ -1610,14 +1619,15 @@ void Engine::start_rq(MatvecPlan* P, const double* x) {
     event_record(ev_side_[1], side_);
   } catch (...) {
     stream_ = keep;
+    rq_pending_ = false;
     throw;
   }
   stream_ = keep;
-  rq_pending_ = true;
 }
 
 double Engine::finish_rq() {
   if (!rq_pending_) return std::numeric_limits<double>::quiet_NaN();
+  launch_rq();
   rq_pending_ = false;
   stream_wait(stream_, ev_side_[1]);
   double h[2];
@@ -2755,6 +2765,7 @@ double Engine::sweep_step(int i, int dir, int D, double gamma, double* w_disc, i
   double w;
   try {
     w = truncate(i, dir, D, x, 0.0);
+    launch_rq();  // after the decomposition, whose kernels would otherwise queue behind it
     if (dir > 0) update_left_from(i, P->cl);
     else update_right_from(i + 1, P->cr);
   } catch (...) {

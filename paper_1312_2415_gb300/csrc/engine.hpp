@@ -201,6 +201,7 @@ class Engine {
   void rdm_site(MatvecPlan* P, int i, double* dg, bool last);
   void add_projectors(MatvecPlan* p);
   void start_rq(MatvecPlan* P, const double* x);
+  void launch_rq();
   double finish_rq();
   void free_overlap(Overlap& o);
   void ensure_ov_left(LowState& S, int k);
@@ -255,6 +256,7 @@ class Engine {
   void* ev_side_[2] = {nullptr, nullptr};
   double* rq_dev_ = nullptr;
   bool rq_pending_ = false;
+  MatvecPlan* rq_plan_ = nullptr;  // plan whose FP64 Rayleigh quotient is still to be queued
 };
 
 }  // namespace dmrg
