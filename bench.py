@@ -250,8 +250,8 @@ def matvec_kernel_rates(delta):
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the mixed
 # kernels, from one ncu capture of the marked matvec of this benchmark at the default
 # workload (random28, D=2500, sites 13-14); valid only for that workload and kernel version
-NCU_TRAFFIC = {("random28", 2500, 1): 544676864 + 7043775232,
-               ("random28", 2500, 2): 9874436096 + 16362240}
+NCU_TRAFFIC = {("random28", 2500, 1): 522166016 + 7039842048,
+               ("random28", 2500, 2): 11486021888 + 33594368}
 
 
 def roofline_mixed(delta, peaks, key=None):

@@ -207,7 +207,7 @@ struct TcHost {
 };
 // how ranges are cut into units (one CTA each): packs per phase-1 unit, tasks per
 // phase-2 unit
-struct TcTune { int packs_per_unit = 8, tasks_per_unit = 48; };
+struct TcTune { int packs_per_unit = 8, tasks_per_unit = 96; };
 struct TcPlan;
 // device tables of one or several instances (one grouped launch per phase for all)
 TcPlan* tc_plan_build(const std::vector<const TcHost*>& inst, TcTune tune, Stream st);
