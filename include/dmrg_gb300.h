@@ -125,9 +125,9 @@ int dmrg_canonicalize(dmrg_ctx* ctx, int center);
  * energy of all micro-iterations (including E_const), *e_last = the last one. */
 int dmrg_solve(dmrg_ctx* ctx, double* e_min, double* e_last);
 
-/* Spin-summed one- and two-particle reduced density matrices of the current MPS, the
- * derivatives of its energy with respect to the integrals (the quantities DMRG-SCF
- * consumes, Sec. 6; energy of Sec. 4.1):
+/* Spin-summed one- and two-particle reduced density matrices of the current MPS (the
+ * Gamma^A of Sec. 4.3, calc2DM, which DMRG-SCF consumes, Sec. 4.4), obtained as the
+ * derivatives of its energy with respect to the integrals (energy of Sec. 4.1):
  *   Gamma[((i*L + j)*L + k)*L + l] = sum_st <a+_is a+_jt a_lt a_ks>, projected onto the
  *     eight index permutations under which V is invariant (the only part an energy with
  *     such a V depends on), so that dE/dV_ijkl = Gamma_ijkl / 2 for symmetric changes;

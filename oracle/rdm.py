@@ -2,14 +2,15 @@
 
 Test infrastructure only: the library never imports this module.
 
-Definitions, in the index order of the Hamiltonian of Sec. 4.1 (physics notation):
+Definitions (Sec. 4.3, the spin-summed 2-RDM Gamma^A and the 1-RDM as its partial trace),
+in the index order of the Hamiltonian of Sec. 4.1 (physics notation):
     gamma_ik   = sum_s  <a+_is a_ks>               = <E_ik>
     Gamma_ijkl = sum_st <a+_is a+_jt a_lt a_ks>    = <E_ik E_jl> - delta_jk <E_il>
 with E_pq = sum_s a+_ps a_qs.  For a normalised state
     <H> = E_c + sum_ik h_ik gamma_ik + 1/2 sum_ijkl V_ijkl Gamma_ijkl,
 which is linear in (h, V) at a fixed state: dE/dh_ik = gamma_ik and
 dE/dV_ijkl = Gamma_ijkl / 2.  For an exact eigenstate these are also the derivatives
-of the eigenvalue (Hellmann-Feynman), which is what DMRG-SCF consumes (Sec. 6).
+of the eigenvalue (Hellmann-Feynman), which is what DMRG-SCF consumes (Sec. 4.4).
 Sec. 4.1 requires V to be invariant under eight index permutations; an energy
 written with such a V sees only the part of Gamma with the same invariance, the
 projection `sym8`.

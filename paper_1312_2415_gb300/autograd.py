@@ -3,8 +3,8 @@
 Forward sets the integrals (Sec. 4.1: h, V with eightfold symmetry, physics notation),
 runs the convergence scheme (Sec. 4.3) from the context's current MPS and returns the
 energy of the last micro-iteration.  Backward returns dE/dh = gamma and
-dE/dV = Gamma / 2, the spin-summed RDMs of the final MPS computed by the library's
-adjoint of the H_eff matvec (dmrg_rdm).  For a converged state these are the exact
+dE/dV = Gamma / 2, the spin-summed RDMs of the final MPS (Gamma^A of Sec. 4.3) computed
+by the library's adjoint of the H_eff matvec (dmrg_rdm).  For a converged state these are the exact
 derivatives of the eigenvalue (Hellmann-Feynman); V's gradient is the part that is
 invariant under V's eight index permutations, so a symmetric change dV of V changes
 the energy by sum(grad_V * dV).  torch is used for tensors and streams only.
