@@ -313,6 +313,32 @@ def energy_agreement(ctx, center, D, args):
     return out
 
 
+def swept_state_matvec(ctx, center, reps=4):
+    """Matvec rates (mixed and FP64) at the middle pair of the state one macro-iteration
+    leaves (sectors fewer and larger than the initial MPS's), re-centred at that pair."""
+    import torch
+    ctx.canonicalize(center)
+    n, table = ctx.layout(center)
+    x = torch.empty(n, dtype=torch.float64, device="cuda")
+    ctx.tt_to_x(center, x)
+    y = torch.empty_like(x)
+    out = {"two_site_elements": n, "largest_block_rows": int(table[:, 9].max()),
+           "largest_block_cols": int(table[:, 10].max())}
+    for prec, name in ((1, "mixed"), (0, "fp64")):
+        ctx.set_precision(prec, 1)
+        ctx.matvec(center, x, y)  # tables
+        torch.cuda.synchronize()
+        s0 = ctx.stats()
+        for _ in range(reps):
+            ctx.matvec(center, x, y)
+        torch.cuda.synchronize()
+        s1 = ctx.stats()
+        r = matvec_kernel_rates({k: s1[k] - s0[k] for k in s1}).get(name)
+        if r:
+            out[name] = r
+    return out
+
+
 def sweep_time(ctx, L, D, precision, fp64_iters, iters):
     """One macro-iteration (Sec. 4.2: sites 0..L-2 right, then L-2..0 left) at fixed D,
     fixed Davidson iterations per step; returns seconds (right, left) and the energy of
@@ -559,6 +585,10 @@ def run_gb300(args):
             ctx.set_mps(start)
             r, l, e = sweep_time(ctx, cfg["L"], D, 0, 0, args.davidson_iters)
             sweeps["fp64"] = {"macro_s": r + l, "right_s": r, "left_s": l, "energy_last": e}
+        try:
+            sweeps["matvec_after_sweep"] = swept_state_matvec(ctx, center)
+        except Exception as exc:  # reported, not fatal: the headline numbers are above
+            sweeps["matvec_after_sweep"] = {"error": str(exc)[:200]}
         ctx.set_precision(args.precision, args.fp64_iters)
     mixed = args.precision == 1
     out = {

@@ -3,14 +3,16 @@
 #include "engine.hpp"
 
 #include <algorithm>
-#include <atomic>
-#include <functional>
 #include <array>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <exception>
+#include <functional>
 #include <limits>
 #include <map>
+#include <mutex>
 #include <stdexcept>
 #include <thread>
 #include <tuple>
@@ -45,14 +47,23 @@ void group_by_output(std::vector<TaggedTask>& tagged, int64_t nout, double* Z, c
 }
 
 // f(begin, end) over [0, n) in chunks, on up to 16 threads (the caller's included)
+// (an exception in any chunk stops the others and is rethrown on the caller's thread)
 template <class F>
 void parallel_chunks(size_t n, size_t chunk, F f) {
   std::atomic<size_t> next{0};
+  std::mutex mu;
+  std::exception_ptr err;
   auto run = [&]() {
-    for (;;) {
-      const size_t b = next.fetch_add(chunk);
-      if (b >= n) break;
-      f(b, std::min(n, b + chunk));
+    try {
+      for (;;) {
+        const size_t b = next.fetch_add(chunk);
+        if (b >= n) break;
+        f(b, std::min(n, b + chunk));
+      }
+    } catch (...) {
+      std::lock_guard<std::mutex> lk(mu);
+      if (!err) err = std::current_exception();
+      next.store(n);
     }
   };
   const unsigned hc = std::thread::hardware_concurrency();
@@ -61,6 +72,7 @@ void parallel_chunks(size_t n, size_t chunk, F f) {
   for (size_t t = 1; t < nth; ++t) th.emplace_back(run);
   run();
   for (auto& t : th) t.join();
+  if (err) std::rethrow_exception(err);
 }
 
 uint64_t splitmix64_next(uint64_t& state) {
@@ -907,13 +919,7 @@ Engine::MatvecPlan* Engine::plan_matvec(int i) {
     for (int a = 0; a < 3; ++a)
       for (int c = 0; c < 3; ++c) okp[q][a][c] = ok[a][c];
   }
-  struct K2 {
-    uint64_t a, b;
-    bool operator==(const K2& o) const { return a == o.a && b == o.b; }
-  };
-  struct H2 {
-    size_t operator()(const K2& k) const { return std::hash<uint64_t>()(k.a * 0x9E3779B97F4A7C15ull ^ k.b); }
-  };
+  using K2 = CoefKey;
   // W(gl, C block, X') = sum coef * Z rows of X ; phase 2: y_X' += C_blk W
   struct WItem { int gl, cbi, xp; int64_t off; int rows, cols; int src_begin, src_end; };
   std::vector<WItem> ws;
@@ -941,10 +947,17 @@ Engine::MatvecPlan* Engine::plan_matvec(int i) {
   for (int64_t z = 0; z < zbase.back(); ++z) zused[z].store(0, std::memory_order_relaxed);
   std::vector<Out> outs(items.size());
   std::atomic<size_t> next_item{0};
-  auto worker = [&]() {
+  const unsigned hcw = std::thread::hardware_concurrency();
+  const int nthw = (int)std::max(1u, std::min(16u, hcw ? hcw : 1u));
+  std::vector<std::unordered_map<K2, double, CoefKeyHash>> new_coefs(nthw);
+  std::atomic<int> next_worker{0};
+  const auto& master = coef_master_;  // read-only while the workers run
+  std::mutex worker_mu;
+  std::exception_ptr worker_err;
+  auto worker_body = [&]() {
     Coupling cp = *cp_;  // private memo tables
-    std::unordered_map<K2, double, H2> coef_cache;
-    coef_cache.reserve(1 << 14);
+    auto& coef_cache = new_coefs[next_worker.fetch_add(1)];
+    coef_cache.reserve(1 << 12);
     std::vector<int> slot(P->X.size(), -1), touched;
     std::vector<std::vector<Src>> bucket;
     for (;;) {
@@ -981,9 +994,12 @@ Engine::MatvecPlan* Engine::plan_matvec(int i) {
                          (uint64_t)X.ls1 | ((uint64_t)X.ls2 << 2) | ((uint64_t)X.tj << 4) |
                              ((uint64_t)ls1p << 8) | ((uint64_t)ls2p << 10) | ((uint64_t)tjp << 12)};
                   auto ci = coef_cache.find(key);
+                  auto mi = ci == coef_cache.end() ? master.find(key) : master.end();
                   double coef = 0.0;
                   if (ci != coef_cache.end()) {
                     coef = ci->second;
+                  } else if (mi != master.end()) {
+                    coef = mi->second;
                   } else {
                     for (int tjM = std::abs(tjL - t1s); tjM <= tjL + t1s; tjM += 2) {
                       if (!triangle(t2s, tjR, tjM)) continue;
@@ -1034,10 +1050,22 @@ Engine::MatvecPlan* Engine::plan_matvec(int i) {
     const unsigned hc = std::thread::hardware_concurrency();
     const int nth = (int)std::max(1u, std::min(16u, hc ? hc : 1u));
     std::vector<std::thread> th;
+    auto worker = [&]() {
+      try {
+        worker_body();
+      } catch (...) {
+        std::lock_guard<std::mutex> lk(worker_mu);
+        if (!worker_err) worker_err = std::current_exception();
+        next_item.store(items.size());
+      }
+    };
     for (int t = 1; t < nth && (size_t)t < items.size(); ++t) th.emplace_back(worker);
     worker();
     for (auto& t : th) t.join();
+    if (worker_err) std::rethrow_exception(worker_err);
   }
+  for (auto& m : new_coefs)
+    for (auto& kv : m) coef_master_.emplace(kv.first, kv.second);
   // Merge in item order (deterministic tables).  Z groups get their ids in (right
   // group, block) order among the blocks some source uses; the W items and sources of
   // every item go to offsets from prefix sums over the items, filled in parallel.

@@ -106,6 +106,16 @@ struct Stats {
   double rdm_ms = 0.0, rdm_flops = 0.0;
 };
 
+// key of a recoupled matvec coefficient: (left pattern, right pattern, the spins of the
+// blocks and of the local states) packed in two words
+struct CoefKey {
+  uint64_t a, b;
+  bool operator==(const CoefKey& o) const { return a == o.a && b == o.b; }
+};
+struct CoefKeyHash {
+  size_t operator()(const CoefKey& k) const { return std::hash<uint64_t>()(k.a * 0x9E3779B97F4A7C15ull ^ k.b); }
+};
+
 class Engine {
  public:
   Engine(int L, int n_irrep, const std::vector<int>& orb_ir, int N, int two_S, int irrep,
@@ -250,6 +260,9 @@ class Engine {
   std::vector<double> hist_E_, hist_w_;
   uint64_t plan_serial_ = 0;
   std::thread reaper_;  // releases the host tables of the last freed plan
+  // recoupled matvec coefficients of every plan so far (they depend on pattern ids and
+  // spins only); read by the planner's workers, extended after each plan
+  std::unordered_map<CoefKey, double, CoefKeyHash> coef_master_;
   // side stream of the deferred FP64 Rayleigh quotient: events (input copied, done),
   // device results (x.Hx, x.x) and reduction scratch
   Stream side_ = nullptr;
