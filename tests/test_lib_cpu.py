@@ -87,3 +87,21 @@ def test_device_calls_fail_cleanly_without_gpu(lib):
     with pytest.raises(DMRGError) as e:
         ctx.init_mps(1)
     assert e.value.code == -5
+
+
+def test_rdm_and_excitation_calls_check_their_state(lib):
+    """Without an MPS the RDM and excited-state calls are rejected cleanly (DMRG_EINVAL
+    from the state check, or DMRG_ECUDA where there is no device to set up a stream on);
+    the count of lower states starts at zero."""
+    from paper_1312_2415_gb300 import Context, DMRGError
+    h, V = hubbard_chain(4)
+    ctx = Context(4, [0] * 4, 4, 0, 0)
+    assert ctx.excitation_count() == 0
+    with pytest.raises(DMRGError) as e:
+        ctx.rdm()
+    assert e.value.code in (-1, -5)
+    ctx.set_integrals(h, V)
+    with pytest.raises(DMRGError) as e:
+        ctx.push_excitation(1.0)
+    assert e.value.code in (-1, -5)
+    assert ctx.excitation_count() == 0
