@@ -619,6 +619,7 @@ def run_gb300(args):
     if rank == 0:
         if not args.no_cpu_baseline and world == 1:
             out["cpu_baseline"] = cpu_baseline(bounded_seconds=15.0)
+            out["cpu_baseline"]["single_core"] = single_core_baseline(5.0)
         print(json.dumps(out), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -696,6 +697,24 @@ def cpu_baseline(bounded_seconds=15.0, flops=None):
             "sample": f"{n} oracle H_eff matvecs (P^T H P, determinant basis) at sites (3,4) of "
                       f"the L=8 Hubbard chain, D=64, {dt:.1f} s; flops counted by the planner "
                       f"for the same matvec ({flops:.3e})"}
+
+
+def single_core_baseline(bounded_seconds=5.0):
+    """The same oracle sample with the BLAS / OpenMP thread pools of a fresh process held
+    to one thread (the 1-core figure beside the all-cores one); None if it cannot run."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               BLIS_NUM_THREADS="1")
+    code = ("import json, sys; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench.cpu_baseline(bounded_seconds=%r)))" % (ROOT, float(bounded_seconds)))
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                           timeout=bounded_seconds * 4 + 120)
+        if r.returncode != 0:
+            return None
+        d = json.loads(r.stdout.strip().splitlines()[-1])
+        return {"value": d["value"], "unit": d["unit"], "cores": 1, "sample": d["sample"]}
+    except Exception:
+        return None
 
 
 def run_reference(args):
