@@ -4,7 +4,7 @@
  * Van Neck, "CheMPS2", Sec. 4): a Hamiltonian given by E_const, one-body h_ij and
  * two-body V_ijkl in physics notation (Sec. 4.1), the target spin, particle number and
  * point-group irrep (Sec. 4.1 "Problem"), a convergence scheme of (D, E_conv, N_max,
- * gamma_noise) instructions (Sec. 4.2) and the two-site sweep (Secs. 2.3-2.4, 3.3-3.4).
+ * gamma_noise) instructions (Sec. 4.2) and the two-site sweep (Secs. 2.3-2.4, 3.2-3.3).
  *
  * Conventions shared by every call:
  *  - Spins are passed doubled (two_S = 2S, tj = 2j).  Irreps are 0..7 of a real
@@ -198,7 +198,7 @@ int dmrg_davidson(dmrg_ctx* ctx, int site, double* x, uintptr_t stream, double* 
 int dmrg_truncate(dmrg_ctx* ctx, int site, int dir, int D, double noise, const double* x,
                   uintptr_t stream, double* w_disc);
 
-/* One micro-iteration of a sweep (Secs. 2.3-2.5, 3.4): Eq. 25 from T[site], T[site+1],
+/* One micro-iteration of a sweep (Secs. 2.3-2.5, 3.3): Eq. 25 from T[site], T[site+1],
  * Davidson with the scheme's tolerance and cap, noise gamma * 0.5 * w_disc(previous
  * half sweep), Eqs. 26-28 to D, and the renormalised / complementary operator update
  * for the next site in direction dir (+1 right, -1 left).  Outputs: energy (with

@@ -1,6 +1,6 @@
 """Two-site spin-adapted DMRG sweep for the oracle (plain dense algebra).
 
-Each micro-iteration follows Secs. 2.3, 2.4 and 3.4:
+Each micro-iteration follows Secs. 2.3, 2.4 and 3.3:
   x = Eq. 25 from T[i] T[i+1]  ->  H_eff x = lambda x (Eq. 9) with H_eff = P^T H P,
   its plain definition (P: reduced two-site basis -> determinants, H: Sec. 4.1)
   ->  Eqs. 26-28 block SVD and truncation to D  ->  new T[i], T[i+1].

@@ -1,6 +1,6 @@
 """Writes tests/golden/energies.json from the oracle only (no library code).
 
-  hubbard8_dmrg_d64: the oracle's two-site DMRG (Secs. 2.3-2.4, 3.4, 4.2) on the open
+  hubbard8_dmrg_d64: the oracle's two-site DMRG (Secs. 2.3-2.4, 3.3, 4.2) on the open
       Hubbard chain L=8, N=8, S=0, t=1, U=4, C1, D=64, 6 macro-iterations, started
       from the right-normalised initial MPS of Sec. 4.3 filled by splitmix64 seed
       2415001; the minimum micro-iteration energy (Sec. 4.3) and the last one.
