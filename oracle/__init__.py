@@ -12,7 +12,7 @@ most direct form available:
                definition of the Hamiltonian of Sec. 4.1 (physics notation), the
                one-body folding of Eq. 11, and S^2 for spin checks.
   * mps.py   - reduced MPS tensors (Eq. 22), the symmetry sectors of Sec. 3, the
-               initial equal distribution of D (Sec. 4.4), the reduced two-site
+               initial equal distribution of D (Sec. 4.3), the reduced two-site
                object (Eq. 25) and its back-transform (Eq. 26), the block SVD and
                truncation (Eqs. 27-28, discarded weight Eq. 15), and the expansion of
                the reduced two-site basis into determinants, from which the effective

@@ -59,7 +59,7 @@ def sector_order(keys):
 
 
 def distribute(fci, D):
-    """Sec. 4.4: D spread equally over the sectors, none above its FCI dimension
+    """Sec. 4.3: D spread equally over the sectors, none above its FCI dimension
     (water-filling in sector order until D is used or every sector is full)."""
     keys = sector_order(fci)
     alloc = {k: 0 for k in keys}
@@ -111,7 +111,7 @@ def initial_dims(irreps, N, two_S, I_G, D):
 
 
 def random_mps(irreps, N, two_S, I_G, D, values):
-    """Initial MPS of Sec. 4.4 filled from the stream `values` (consumed in order:
+    """Initial MPS of Sec. 4.3 filled from the stream `values` (consumed in order:
     site, then block order, then row-major)."""
     m = MPS(irreps, N, two_S, I_G, initial_dims(irreps, N, two_S, I_G, D))
     pos = 0

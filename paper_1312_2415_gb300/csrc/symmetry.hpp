@@ -37,7 +37,7 @@ struct Symmetry {
   std::vector<int> orb_ir;
   // FCI-capped reduced dimensions per bond (0..L).
   std::vector<std::map<Sector, int>> fci_dims() const;
-  // Sec. 4.4: D spread equally over the sectors of every bond, none above its FCI
+  // Sec. 4.3: D spread equally over the sectors of every bond, none above its FCI
   // dimension (water-filling in sector order).
   std::vector<Bond> initial_bonds(int D) const;
 };
