@@ -47,10 +47,12 @@ def parse():
     p.add_argument("--fp64-iters", type=int, default=1,
                    help="FP64 Davidson iterations that finish each mixed-precision step")
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison steps")
-    p.add_argument("--sweep", action="store_true",
-                   help="also time the FP64 macro-iteration (the mixed one is timed by default)")
-    p.add_argument("--no-sweep", action="store_true", help="skip the macro-iteration timing")
+    p.add_argument("--no-sweep", action="store_true",
+                   help="skip both macro-iterations (the headline steps then run on the initial MPS)")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-fp64-sweep", action="store_true", help="skip the FP64 macro-iteration")
+    p.add_argument("--fp64-steps", type=int, default=3, help="timed FP64 steps on the swept state")
+    p.add_argument("--e2e-steps", type=int, default=5, help="steps of the host-buffer e2e run")
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
 
@@ -172,6 +174,45 @@ def fp64_peak_measured():
     return best  # GFLOP/s
 
 
+def tf32_peak_measured():
+    """TF32 tensor roof on this GPU: cuBLAS FP32 GEMM 8192^3 with TF32 allowed (best of 3),
+    measured here because the measured-peaks file carries HBM and bf16 only."""
+    import torch
+    n = 8192
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = True
+    try:
+        a = torch.randn(n, n, device="cuda", dtype=torch.float32)
+        b = torch.randn(n, n, device="cuda", dtype=torch.float32)
+        torch.matmul(a, b)
+        torch.cuda.synchronize()
+        best = 0.0
+        for _ in range(3):
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record(); torch.matmul(a, b); e.record(); torch.cuda.synchronize()
+            best = max(best, 2.0 * n ** 3 / (s.elapsed_time(e) * 1e-3) / 1e9)
+        del a, b
+        torch.cuda.empty_cache()
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    return best  # GFLOP/s
+
+
+def block_histogram(table):
+    """Block-size histogram of a two-site layout (rows dL, columns dR of every block)."""
+    import numpy as np
+    edges = [1, 8, 16, 32, 64, 128, 256, 512, 10 ** 9]
+    out = {}
+    for name, col in (("dL", 9), ("dR", 10)):
+        v = table[:, col]
+        out[name] = {f"{edges[k]}-{edges[k + 1] - 1 if edges[k + 1] < 10 ** 9 else 'max'}":
+                     int(((v >= edges[k]) & (v < edges[k + 1])).sum()) for k in range(len(edges) - 1)}
+    out["blocks"] = int(table.shape[0])
+    out["largest"] = [int(table[:, 9].max()), int(table[:, 10].max())]
+    out["elements_in_blocks_above_64"] = int((table[:, 9] * table[:, 10] * ((table[:, 9] > 64) | (table[:, 10] > 64))).sum())
+    return out
+
+
 def setup_context(args):
     from paper_1312_2415_gb300 import Context
     from workloads import make_problem
@@ -248,33 +289,47 @@ def matvec_kernel_rates(delta):
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the mixed
-# kernels, from one ncu capture of the marked matvec of this benchmark at the default
-# workload (random28, D=2500, sites 13-14); valid only for that workload and kernel version
-NCU_TRAFFIC = {("random28", 2500, 1): 522166016 + 7039842048,
-               ("random28", 2500, 2): 11486021888 + 33594368}
+# matvec's main kernel from one ncu capture (a smaller case scaled to a full launch by the
+# units processed, as the profile summary states), keyed by the workload and the SHA-256
+# prefix of the kernel source it was taken with: a changed kernel reports traffic null.
+NCU_TRAFFIC = {}
 
 
-def roofline_mixed(delta, peaks, key=None):
-    """Dominant kernel of the mixed matvec against HBM (its compulsory FP32 traffic) and
-    its tensor-pipe fraction against the TF32 peak (bf16 measured x nominal 1.1/2.25)."""
+def kernel_source_hash():
+    import hashlib
+    path = os.path.join(ROOT, "paper_1312_2415_gb300", "csrc", "kernels_tc.cu")
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+
+
+def roofline_mixed(delta, peaks, peak_tf32, workload=None):
+    """Main kernel of the mixed-precision matvec against both of its roofs: HBM with the
+    algorithmic bytes of a matvec (every operator block it reads, once, in its FP32
+    mirror, x read and y written once, in FP64), and the TF32 tensor pipe with the
+    method's flops (2 m k n per block product, one product per block pair however many
+    split products run).  `bound` is the roof that gives the longer time; `frac` is
+    achieved / peak on that roof; the other roof is reported beside it."""
     nm = max(delta["tc_matvecs"], 1)
-    ph = [("k_tc_phase1 (x stack x right-operator blocks -> Zt)", delta["tc_phase1_ms"] / nm,
-           delta["tc_phase1_bytes"] / nm, delta["tc_phase1_flops"] / nm),
-          ("k_tc_phase2s/k_tc_phase2 (sum coef Zt, left-operator blocks -> y)", delta["tc_phase2_ms"] / nm,
-           delta["tc_phase2_bytes"] / nm, delta["tc_phase2_flops"] / nm)]
-    phase = 1 if ph[0][1] >= ph[1][1] else 2
-    name, ms, byts, fl = ph[phase - 1]
-    traffic = NCU_TRAFFIC.get(key + (phase,)) if key else None
-    hbm = peaks.get("hbm_gbs", 6800.0)
-    achieved = byts / (ms * 1e-3) / 1e9
-    tf32_peak = peaks.get("bf16_tflops", 1900.0) * 1.1 / 2.25
-    tensor = 3.0 * fl / (ms * 1e-3) / 1e12  # three split products per block product
-    return {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm, "traffic": traffic,
-            "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth, of measured)",
-            "launch_ms": ms, "bytes_per_launch": byts, "flops_per_launch": fl,
-            "tensor": {"achieved_tflops": tensor, "peak_tflops": tf32_peak, "frac": tensor / tf32_peak,
-                       "peak_source": "bf16_tflops (of measured) x 1.1/2.25 nominal TF32/BF16"}}
+    ms = delta["tc_phase2_ms"] / nm
+    byts = delta["tc_phase2_bytes"] / nm
+    fl = delta["tc_phase2_flops"] / nm
+    if "hbm_gbs" in peaks:
+        hbm, hsrc = peaks["hbm_gbs"], "MEASURED_PEAKS.json hbm_gbs (copy bandwidth, of measured)"
+    else:
+        hbm, hsrc = 6800.0, "profiling recipe fallback 6.8 TB/s (of fallback)"
+    t_hbm, t_tc = byts / (hbm * 1e9), fl / (peak_tf32 * 1e9)
+    gbs = byts / (ms * 1e-3) / 1e9
+    tfs = fl / (ms * 1e-3) / 1e12
+    traffic = NCU_TRAFFIC.get((workload, kernel_source_hash())) if workload else None
+    hbm_roof = {"achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "peak_source": hsrc}
+    tc_roof = {"achieved": tfs, "peak": peak_tf32 / 1e3, "unit": "TFLOP/s", "frac": tfs / (peak_tf32 / 1e3),
+               "peak_source": "cuBLAS FP32 GEMM with TF32, 8192^3, measured by bench.py in this run (of measured)"}
+    main, other = (tc_roof, hbm_roof) if t_tc >= t_hbm else (hbm_roof, tc_roof)
+    return {"bound": "tensor" if t_tc >= t_hbm else "hbm", "kernel": "k_tc_matvec (fused split-TF32 block "
+            "products: x D^T in tensor memory, then C W, per output tile)",
+            "achieved": main["achieved"], "peak": main["peak"], "unit": main["unit"], "frac": main["frac"],
+            "traffic": traffic, "peak_source": main["peak_source"], "launch_ms": ms,
+            "algorithmic_bytes": byts, "method_flops": fl,
+            "other_roof": {"bound": "hbm" if main is tc_roof else "tensor", **other}}
 
 
 def roofline_fp64(delta, peak64):
@@ -313,49 +368,26 @@ def energy_agreement(ctx, center, D, args):
     return out
 
 
-def swept_state_matvec(ctx, center, reps=4):
-    """Matvec rates (mixed and FP64) at the middle pair of the state one macro-iteration
-    leaves (sectors fewer and larger than the initial MPS's), re-centred at that pair."""
-    import torch
-    ctx.canonicalize(center)
-    n, table = ctx.layout(center)
-    x = torch.empty(n, dtype=torch.float64, device="cuda")
-    ctx.tt_to_x(center, x)
-    y = torch.empty_like(x)
-    out = {"two_site_elements": n, "largest_block_rows": int(table[:, 9].max()),
-           "largest_block_cols": int(table[:, 10].max())}
-    for prec, name in ((1, "mixed"), (0, "fp64")):
-        ctx.set_precision(prec, 1)
-        ctx.matvec(center, x, y)  # tables
-        torch.cuda.synchronize()
-        s0 = ctx.stats()
-        for _ in range(reps):
-            ctx.matvec(center, x, y)
-        torch.cuda.synchronize()
-        s1 = ctx.stats()
-        r = matvec_kernel_rates({k: s1[k] - s0[k] for k in s1}).get(name)
-        if r:
-            out[name] = r
-    return out
-
-
 def sweep_time(ctx, L, D, precision, fp64_iters, iters):
     """One macro-iteration (Sec. 4.2: sites 0..L-2 right, then L-2..0 left) at fixed D,
-    fixed Davidson iterations per step; returns seconds (right, left) and the energy of
-    the last step."""
+    fixed Davidson iterations per step, from the state the context holds (right-canonical
+    form first); returns a record with the seconds of both half sweeps, the energy of the
+    last step and the lowest one (Sec. 4.3), and the step count."""
     import torch
     ctx.set_precision(precision, fp64_iters)
     fixed_iters(ctx, D, iters)
     ctx.canonicalize(0)
     torch.cuda.synchronize()
-    out, e = [], None
+    out, es = [], []
     for sites, d in ((range(0, L - 1), 1), (range(L - 2, -1, -1), -1)):
         t0 = time.perf_counter()
         for i in sites:
             e, wd, it, ok = ctx.sweep_step(i, d, D)
+            es.append(e)
         torch.cuda.synchronize()
         out.append(time.perf_counter() - t0)
-    return out[0], out[1], e
+    return {"macro_s": out[0] + out[1], "right_s": out[0], "left_s": out[1], "energy_last": es[-1],
+            "energy_min": min(es), "steps": len(es)}
 
 
 # 32 independent instances of uneven size for the batched launch: Hubbard chains
@@ -525,6 +557,14 @@ def run_rdm(args):
 
 
 def run_gb300(args):
+    """The headline workload (random28, D=2500).  Order of the run:
+    1. one mixed-precision macro-iteration from the initial MPS of Sec. 4.3 (the metric's
+       mixed sweep time); its end state is the swept state the headline steps use;
+    2. one FP64 macro-iteration from the same initial MPS with the same Davidson settings
+       (the FP64 sweep time) and the agreement of the two sweeps' energies;
+    3. the timed micro-iterations at the middle pair of the swept state (value), the same
+       steps on the FP64 path, the converged-Davidson energy agreement at that pair, the
+       roofline of the matvec kernel, and e2e through the host-buffer C ABI."""
     import torch
     if args.workload == "batch32":
         return run_batch(args)
@@ -539,25 +579,59 @@ def run_gb300(args):
         torch.cuda.set_device(0)
     peaks = measured_peaks()
     peak64 = fp64_peak_measured()
+    peak_tf32 = tf32_peak_measured()
     ctx, cfg, D, center = setup_context(args)
-    n_x, _ = ctx.layout(center)
-    # headline path
+    L = cfg["L"]
+    mixed = args.precision == 1
+    # 1-2: macro-iterations from the initial state (the metric's sweep time)
+    ctx.canonicalize(0)
+    start = ctx.get_mps()
+    sweeps = {"what": "one macro-iteration (L-1 steps right, L-1 left) from the initial MPS of Sec. 4.3 "
+                      f"at fixed D, {args.davidson_iters} Davidson iterations per step; both precisions "
+                      "start from the same state"}
+    if not args.no_sweep:
+        sweeps["mixed" if mixed else "fp64"] = sweep_time(ctx, L, D, args.precision, args.fp64_iters,
+                                                          args.davidson_iters)
+        swept = ctx.get_mps()
+        if mixed and not args.no_fp64 and not args.no_fp64_sweep:
+            ctx.set_mps(start)
+            sweeps["fp64"] = sweep_time(ctx, L, D, 0, 0, args.davidson_iters)
+            sweeps["agreement"] = {
+                "abs_diff_last_eh": abs(sweeps["mixed"]["energy_last"] - sweeps["fp64"]["energy_last"]),
+                "abs_diff_min_eh": abs(sweeps["mixed"]["energy_min"] - sweeps["fp64"]["energy_min"]),
+                "target_eh": 1e-6}
+            sweeps["speedup_mixed_vs_fp64"] = sweeps["fp64"]["macro_s"] / sweeps["mixed"]["macro_s"]
+        ctx.set_mps(swept)
+        state = "the state one mixed macro-iteration at D leaves (swept state)"
+    else:
+        state = "the initial MPS of Sec. 4.3"
+    ctx.set_precision(args.precision, args.fp64_iters)
+    fixed_iters(ctx, D, args.davidson_iters)
+    ctx.canonicalize(center)
+    swept_state = ctx.get_mps()
+    n_x, table = ctx.layout(center)
+    hist = block_histogram(table)
+    # 3: headline steps on that state
     clk = ClockSampler(torch.cuda.current_device())
     ms, delta, energies, clocks, d = timed_steps(ctx, center, D, args.steps, args.warmup, 1, clk, world)
     value, t_max = aggregate(delta["matvec_flops"], ms, world)
     launches = int(delta["kernels_launched"])
     rates = matvec_kernel_rates(delta)
-    roof = roofline_mixed(delta, peaks, (args.workload, D)) if args.precision == 1 else roofline_fp64(delta, peak64)
-    # FP64 path on the same workload (continuing from the same state)
+    roof = roofline_mixed(delta, peaks, peak_tf32, (args.workload, D)) if mixed else roofline_fp64(delta, peak64)
     fp64 = None
-    if not args.no_fp64 and args.precision == 1:
+    if not args.no_fp64 and mixed:
+        ctx.set_mps(swept_state)
         ctx.set_precision(0, 0)
-        ms64, d64, e64, _, d = timed_steps(ctx, center, D, args.steps, 1, d)
+        ctx.canonicalize(center)
+        k64 = max(1, min(args.steps, args.fp64_steps))
+        ms64, d64, e64, _, _ = timed_steps(ctx, center, D, k64, 1, 1)
         r64 = matvec_kernel_rates(d64)
-        fp64 = {"ms_per_step": ms64 / args.steps,
+        fp64 = {"steps": k64, "ms_per_step": ms64 / k64,
                 "value": d64["matvec_flops"] / (ms64 * 1e-3) / 1e9, "unit": "GFLOP/s",
                 "matvec": r64.get("fp64"), "roofline": roofline_fp64(d64, peak64)}
         ctx.set_precision(args.precision, args.fp64_iters)
+    ctx.set_mps(swept_state)
+    ctx.canonicalize(center)
     acc = energy_agreement(ctx, center, D, args) if not args.no_fp64 else None
     # one marked matvec in each precision after the timed region (NVTX range for profilers)
     xprof = torch.tensor(ctx.tt_to_x(center), dtype=torch.float64, device="cuda")
@@ -571,49 +645,36 @@ def run_gb300(args):
         torch.cuda.nvtx.range_pop()
     ctx.set_precision(args.precision, args.fp64_iters)
     fixed_iters(ctx, D, args.davidson_iters)
-    e2e = None if args.no_e2e else run_e2e(ctx, center, D, args, n_x)
-    sweeps = None
-    if not args.no_sweep:
-        start = ctx.get_mps() if args.sweep else None  # both precisions start from this state
-        r, l, e = sweep_time(ctx, cfg["L"], D, args.precision, args.fp64_iters, args.davidson_iters)
-        sweeps = {("mixed" if args.precision == 1 else "fp64"): {"macro_s": r + l, "right_s": r, "left_s": l,
-                                                                "energy_last": e},
-                  "what": "one macro-iteration (L-1 steps right, L-1 left) from the canonical state "
-                          f"at site 0, fixed D, {args.davidson_iters} Davidson iterations per step "
-                          "(with --sweep both precisions start from the same state)"}
-        if args.sweep and args.precision == 1:
-            ctx.set_mps(start)
-            r, l, e = sweep_time(ctx, cfg["L"], D, 0, 0, args.davidson_iters)
-            sweeps["fp64"] = {"macro_s": r + l, "right_s": r, "left_s": l, "energy_last": e}
-        try:
-            sweeps["matvec_after_sweep"] = swept_state_matvec(ctx, center)
-        except Exception as exc:  # reported, not fatal: the headline numbers are above
-            sweeps["matvec_after_sweep"] = {"error": str(exc)[:200]}
-        ctx.set_precision(args.precision, args.fp64_iters)
-    mixed = args.precision == 1
+    e2e = None
+    if not args.no_e2e:
+        ctx.set_mps(swept_state)
+        ctx.canonicalize(center)
+        e2e = run_e2e(ctx, center, D, args, n_x)
     out = {
         "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "tf32x3-f32acc+f64" if mixed else "f64",
         "data": "synthetic",
-        "config": {"workload": f"{args.workload}: random integrals L={cfg['L']} N={cfg['N']} S=0 Ag "
-                               f"D2h 8/3/3/2/6/2/2/2, D_SU(2)={D}, middle sites ({center},{center + 1})",
-                   "L": cfg["L"], "N": cfg["N"], "D": D, "site": center, "two_site_elements": n_x,
+        "config": {"workload": f"{args.workload}: random integrals L={L} N={cfg['N']} S=0 Ag "
+                               f"D2h 8/3/3/2/6/2/2/2, D_SU(2)={D}, middle sites ({center},{center + 1}) of "
+                               + state,
+                   "L": L, "N": cfg["N"], "D": D, "site": center, "two_site_elements": n_x,
                    "davidson_iters_per_step": args.davidson_iters,
                    "precision": ("split-TF32 tensor-core block products (FP32 data and accumulation) in "
                                  f"Davidson, then {args.fp64_iters} FP64 Davidson iteration(s)") if mixed
                                 else "FP64 block products",
                    "parallelism": f"replicas x{world}",
-                   "l2": "inputs larger than L2 (renormalised operators of both environments and the "
-                         "Z intermediates, several GB)"},
-        "matvec": rates, "fp64": fp64, "energy_agreement": acc,
+                   "l2": "inputs larger than L2 (renormalised operators of both environments, several GB)",
+                   "block_histogram": hist},
+        "matvec": rates, "fp64": fp64, "energy_agreement": acc, "sweep": sweeps,
         "micro_iteration_s": t_max / args.steps / 1e3,
         "energy_last": energies[-1] if energies else None,
         "clocks": clocks, "gpu_launches": launches, "roofline": roof,
+        "peaks_measured_here": {"fp64_gflops": peak64, "tf32_gflops": peak_tf32,
+                                "how": "cuBLAS through torch.matmul, 8192^3, best of 3 (FP64; FP32 with TF32 "
+                                       "allowed)"},
     }
-    if sweeps:
-        out["sweep"] = sweeps
     if e2e:
         out["e2e"] = e2e
     if rank == 0:
@@ -627,25 +688,36 @@ def run_gb300(args):
 
 
 def run_e2e(ctx, center, D, args, n_x):
-    """Same steps through the host-pointer C ABI: x crosses host<->device every step
-    (tt_to_x to pinned host, Davidson from / to host, truncation from host)."""
-    import numpy as np
+    """The headline step through the host-buffer C ABI (stream 0): dmrg_tt_to_x into
+    pinned host memory, dmrg_davidson from and to it, dmrg_truncate from it and
+    dmrg_update_operators: the work of dmrg_sweep_step (Eq. 25, Davidson, Eqs. 26-28, the
+    operator update), with the two-site vector crossing host <-> device every step; the
+    energy is read back on the host."""
     import torch
     x = torch.empty(n_x, dtype=torch.float64).pin_memory().numpy()
+    steps = max(1, min(args.steps, args.e2e_steps))
+    d = 1
+    for _ in range(1):  # warm-up step (tables, environments)
+        ctx.tt_to_x(center, x); ctx.davidson(center, x); ctx.truncate(center, d, D, x)
+        ctx.update_operators(center, d)
+        d = -d
     st0 = ctx.stats()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for k in range(args.steps):
+    for _ in range(steps):
         ctx.tt_to_x(center, x)
-        ctx.davidson(center, x)
-        ctx.truncate(center, 1 if k % 2 == 0 else -1, D, x)
+        e, it, ok = ctx.davidson(center, x)
+        ctx.truncate(center, d, D, x)
+        ctx.update_operators(center, d)
+        d = -d
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     st1 = ctx.stats()
     flops = st1["matvec_flops"] - st0["matvec_flops"]
-    return {"value": flops / dt / 1e9, "unit": "GFLOP/s", "h2d_bytes_per_step": 2 * 8 * n_x,
-            "d2h_bytes_per_step": 2 * 8 * n_x + 8,
-            "path": "dmrg_tt_to_x / dmrg_davidson / dmrg_truncate with host buffers"}
+    return {"value": flops / dt / 1e9, "unit": "GFLOP/s", "steps": steps, "s_per_step": dt / steps,
+            "h2d_bytes_per_step": 2 * 8 * n_x, "d2h_bytes_per_step": 2 * 8 * n_x + 8,
+            "path": "dmrg_tt_to_x / dmrg_davidson / dmrg_truncate / dmrg_update_operators with host "
+                    "buffers (the work of dmrg_sweep_step)"}
 
 
 def oracle_sample():
@@ -748,8 +820,11 @@ def run_reference(args):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic",
-           "config": {"workload": f"{args.workload}: random integrals L={cfg['L']} N={cfg['N']} S=0 Ag "
-                                  f"D2h 8/3/3/2/6/2/2/2, D_SU(2)={args.D or cfg['D']}, middle sites",
+           "config": {"workload": "hubbard8: Hubbard chain L=8 N=8 S=0 C1 t=1 U=4, D_SU(2)=64, sites (3,4), "
+                                  "one oracle H_eff matvec per step",
+                      "stands_in_for": f"{args.workload}: random integrals L={cfg['L']} N={cfg['N']} S=0 Ag "
+                                       f"D2h 8/3/3/2/6/2/2/2, D_SU(2)={args.D or cfg['D']}, middle sites (the "
+                                       "GPU arm's workload, beyond the oracle's dense projection)",
                       "sample": sample},
            "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
                             "sample": sample},

@@ -165,21 +165,27 @@ int dmrg_tt_to_x(dmrg_ctx* ctx, int site, double* x, uintptr_t stream);
 /* y = H_eff x (Eq. 9) with the renormalised and complementary operators of Sec. 2.5. */
 int dmrg_heff_matvec(dmrg_ctx* ctx, int site, const double* x, double* y, uintptr_t stream);
 
-/* Allocation-free variant of dmrg_heff_matvec (no counterpart in the paper; it exists
- * for callers that may not allocate device memory when they apply H_eff: code running
- * inside a CUDA graph capture or under a fixed memory budget, where cudaMalloc is
- * forbidden or must not grow the footprint).  It computes the same y = H_eff x with the
- * tables that an earlier dmrg_heff_matvec / dmrg_davidson call prepared for this site
- * (DMRG_EINVAL if there are none) and keeps its intermediate products in one fixed
- * device array of the library (64 MiB, per device, held until the process exits);
- * problems that need more scratch are rejected with DMRG_EINVAL and a message.  It
- * calls no cudaMalloc / cudaFree and no allocating library routine.
- * x and y are DEVICE pointers of n_elem doubles (see dmrg_two_site_layout); the work is
- * queued on `stream` (0 = the default stream) and the call returns without waiting for
- * it.  The first call on a device looks up the array's address (cudaGetSymbolAddress):
- * make that first call before any stream capture.  All calls share the array, which
- * keeps the previous call's contents (the call clears what must start at zero), so
- * calls whose device work overlaps in time race on it: serialise them. */
+/* Allocation-free variant of dmrg_heff_matvec (no counterpart in the paper).  It is for
+ * callers that cannot allocate device memory at the moment they apply H_eff: a process
+ * that reserved its device memory up front and must not grow it (a serving process
+ * sharing the GPU with other work, where a new cudaMalloc can fail or force others
+ * out), or a host framework whose own allocator owns the GPU and forbids side
+ * allocations.  It runs the FP64 tables that an earlier dmrg_heff_matvec /
+ * dmrg_davidson call prepared for this site (DMRG_EINVAL if there are none), with the
+ * FP64 block products whatever the context's precision mode: for a precision-1 context
+ * its y is the FP64 product, not the split-TF32 one dmrg_heff_matvec returns.  Its
+ * intermediate products live in one fixed device array of the library (64 MiB per
+ * device, held until the process exits); problems that need more scratch are rejected
+ * with DMRG_EINVAL and a message.  It calls no cudaMalloc / cudaFree and no allocating
+ * library routine.  x and y are DEVICE pointers of n_elem doubles (see
+ * dmrg_two_site_layout); the work is queued on `stream` (0 = the default stream) behind
+ * the context's own queued work, and the call returns without waiting for it.  The
+ * context's next call waits on the device for that work before it runs anything that
+ * could free or rewrite the tables it reads.  The first call on a device looks up the
+ * array's address (cudaGetSymbolAddress): make that first call before any stream
+ * capture.  All calls share the array, which keeps the previous call's contents (the
+ * call clears what must start at zero), so calls whose device work overlaps in time
+ * race on it: serialise them. */
 int dmrg_heff_matvec_noalloc(dmrg_ctx* ctx, int site, const double* x, double* y,
                              uintptr_t stream);
 
@@ -197,6 +203,15 @@ int dmrg_davidson(dmrg_ctx* ctx, int site, double* x, uintptr_t stream, double* 
  * first.  *w_disc = discarded weight (Eq. 15). */
 int dmrg_truncate(dmrg_ctx* ctx, int site, int dir, int D, double noise, const double* x,
                   uintptr_t stream, double* w_disc);
+
+/* Sec. 2.5: the renormalised and complementary operators of the block that the sweep
+ * grows, from the operators of the environment it extends: dir = +1 grows the left
+ * block by orbital `site` (T[site] must be left-normalised, as after dmrg_truncate with
+ * dir = +1), dir = -1 grows the right block by orbital site+1 (T[site+1] right-normalised,
+ * as after dmrg_truncate with dir = -1).  dmrg_tt_to_x, dmrg_davidson, dmrg_truncate and
+ * this call, in that order, do the work of one dmrg_sweep_step (without its noise) with
+ * the two-site vector passing through the caller's buffers. */
+int dmrg_update_operators(dmrg_ctx* ctx, int site, int dir);
 
 /* One micro-iteration of a sweep (Secs. 2.3-2.5, 3.3): Eq. 25 from T[site], T[site+1],
  * Davidson with the scheme's tolerance and cap, noise gamma * 0.5 * w_disc(previous
@@ -249,6 +264,16 @@ int dmrg_batch_info(dmrg_batch* b, double* flops, int* packs_per_unit, int* task
                     double* launch_ms, double* tune_ms);
 const char* dmrg_batch_last_error(dmrg_batch* b);
 void dmrg_batch_destroy(dmrg_batch* b);
+
+/* Device memory held by the library (all contexts of the process, in bytes), and an
+ * optional cap on it (no counterpart in the paper, whose program states its memory use in
+ * Sec. 5: 10 MB - 64 GB).  With a cap set (bytes > 0), a call whose next device
+ * allocation would exceed it fails with DMRG_ENOMEM before the allocation is made; what
+ * that call had allocated is released, the context keeps its previous state and can be
+ * used again (with the cap raised or removed, bytes = 0).  Library-wide, not per
+ * context. */
+int dmrg_set_device_memory_cap(size_t bytes);
+int dmrg_device_memory_in_use(size_t* bytes);
 
 int dmrg_stats(dmrg_ctx* ctx, dmrg_stats_t* out);
 const char* dmrg_last_error(dmrg_ctx* ctx);

@@ -70,6 +70,7 @@ _SIGS = {
     "dmrg_davidson": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, _D, _I]),
     "dmrg_truncate": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                      ctypes.c_void_p, ctypes.c_size_t, _D]),
+    "dmrg_update_operators": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
     "dmrg_sweep_step": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                        _D, _D, _I]),
     "dmrg_solve_history": (ctypes.c_int, [_P, _I, _I, _D, _D]),
@@ -83,6 +84,8 @@ _SIGS = {
     "dmrg_batch_info": (ctypes.c_int, [_P, _D, _I, _I, _D, _D]),
     "dmrg_batch_last_error": (ctypes.c_char_p, [_P]),
     "dmrg_batch_destroy": (None, [_P]),
+    "dmrg_set_device_memory_cap": (ctypes.c_int, [ctypes.c_size_t]),
+    "dmrg_device_memory_in_use": (ctypes.c_int, [ctypes.POINTER(ctypes.c_size_t)]),
     "dmrg_stats": (ctypes.c_int, [_P, ctypes.POINTER(Stats)]),
     "dmrg_last_error": (ctypes.c_char_p, [_P]),
     "dmrg_destroy": (None, [_P]),
@@ -281,6 +284,10 @@ class Context:
                                            ctypes.byref(w)))
         return w.value
 
+    def update_operators(self, site, direction):
+        """The operator update of a sweep step (after truncate in the same direction)."""
+        self._check(self.lib.dmrg_update_operators(self.h, int(site), int(direction)))
+
     def sweep_step(self, site, direction, D, gamma=0.0):
         e, w, it = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
         rc = self.lib.dmrg_sweep_step(self.h, int(site), int(direction), int(D), float(gamma),
@@ -293,6 +300,21 @@ class Context:
         st = Stats()
         self._check(self.lib.dmrg_stats(self.h, ctypes.byref(st)))
         return {k: getattr(st, k) for k, _ in Stats._fields_}
+
+
+def set_device_memory_cap(nbytes, path=None):
+    """Cap on the device memory the library holds (0 = none); see the header."""
+    rc = load(path).dmrg_set_device_memory_cap(int(nbytes))
+    if rc != OK:
+        raise DMRGError(rc, "dmrg_set_device_memory_cap")
+
+
+def device_memory_in_use(path=None):
+    n = ctypes.c_size_t(0)
+    rc = load(path).dmrg_device_memory_in_use(ctypes.byref(n))
+    if rc != OK:
+        raise DMRGError(rc, "dmrg_device_memory_in_use")
+    return n.value
 
 
 def extrapolate(w_disc, energy, path=None):

@@ -17,6 +17,11 @@ struct dmrg_ctx {
   cudaStream_t stream = nullptr;
   std::string err;
   int L = 0;
+  // allocation-free matvecs run on the caller's stream and read the context's tables:
+  // `tables` orders them after the context's stream, `noalloc_done` orders the context's
+  // next work (which may free or rewrite those tables) after them
+  cudaEvent_t tables = nullptr, noalloc_done = nullptr;
+  bool noalloc_pending = false;
 };
 
 struct dmrg_batch {
@@ -88,6 +93,13 @@ dmrg::Stream dev_stream(dmrg_ctx* c) {
     cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) throw std::runtime_error(std::string("cuda stream: ") + cudaGetErrorString(e));
     c->eng->set_stream((dmrg::Stream)c->stream);
+  }
+  if (c->noalloc_pending) {
+    // work queued from here on (including stream-ordered frees) waits for the
+    // allocation-free matvecs still reading the context's tables
+    cudaError_t e = cudaStreamWaitEvent(c->stream, c->noalloc_done, 0);
+    if (e != cudaSuccess) throw std::runtime_error(std::string("cuda stream wait: ") + cudaGetErrorString(e));
+    c->noalloc_pending = false;
   }
   return (dmrg::Stream)c->stream;
 }
@@ -271,10 +283,21 @@ int dmrg_heff_matvec(dmrg_ctx* c, int site, const double* x, double* y, uintptr_
 int dmrg_heff_matvec_noalloc(dmrg_ctx* c, int site, const double* x, double* y, uintptr_t stream) {
   return guard(c, [&] {
     if (!x || !y || !c->stream) return DMRG_EINVAL;
-    // the prepared tables were written on the context's stream
-    cudaError_t e = cudaStreamSynchronize(c->stream);
-    if (e != cudaSuccess) throw std::runtime_error(std::string("cuda stream: ") + cudaGetErrorString(e));
-    c->eng->matvec_noalloc(site, x, y, (dmrg::Stream)stream);
+    auto ck = [](cudaError_t e, const char* what) {
+      if (e != cudaSuccess) throw std::runtime_error(std::string("cuda ") + what + ": " + cudaGetErrorString(e));
+    };
+    if (!c->tables) {
+      ck(cudaEventCreateWithFlags(&c->tables, cudaEventDisableTiming), "event");
+      ck(cudaEventCreateWithFlags(&c->noalloc_done, cudaEventDisableTiming), "event");
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    // the prepared tables were written on the context's stream: the caller's stream
+    // waits for them on the device (no host synchronisation)
+    ck(cudaEventRecord(c->tables, c->stream), "event record");
+    ck(cudaStreamWaitEvent(s, c->tables, 0), "stream wait");
+    c->eng->matvec_noalloc(site, x, y, (dmrg::Stream)s);
+    ck(cudaEventRecord(c->noalloc_done, s), "event record");
+    c->noalloc_pending = true;
     return DMRG_OK;
   });
 }
@@ -385,6 +408,16 @@ int dmrg_truncate(dmrg_ctx* c, int site, int dir, int D, double noise, const dou
   });
 }
 
+int dmrg_update_operators(dmrg_ctx* c, int site, int dir) {
+  return guard(c, [&] {
+    if (dir != 1 && dir != -1) return DMRG_EINVAL;
+    dmrg::Stream s = dev_stream(c);
+    c->eng->update(site, dir);
+    dmrg::dev_sync(s);
+    return DMRG_OK;
+  });
+}
+
 int dmrg_sweep_step(dmrg_ctx* c, int site, int dir, int D, double gamma, double* energy,
                     double* w_disc, int* iters) {
   return guard(c, [&] {
@@ -440,12 +473,26 @@ int dmrg_stats(dmrg_ctx* c, dmrg_stats_t* out) {
   });
 }
 
+int dmrg_set_device_memory_cap(size_t bytes) {
+  dmrg::dev_set_cap(bytes);
+  return DMRG_OK;
+}
+
+int dmrg_device_memory_in_use(size_t* bytes) {
+  if (!bytes) return DMRG_EINVAL;
+  *bytes = dmrg::dev_bytes_in_use();
+  return DMRG_OK;
+}
+
 const char* dmrg_last_error(dmrg_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
 void dmrg_destroy(dmrg_ctx* c) {
   if (!c) return;
+  if (c->noalloc_pending) cudaStreamWaitEvent(c->stream, c->noalloc_done, 0);
   delete c->eng;
   if (c->stream) cudaStreamDestroy(c->stream);
+  if (c->tables) cudaEventDestroy(c->tables);
+  if (c->noalloc_done) cudaEventDestroy(c->noalloc_done);
   delete c;
 }
 

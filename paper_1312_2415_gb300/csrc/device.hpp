@@ -17,6 +17,8 @@ void dev_d2h(void* dst, const void* src, size_t bytes, Stream s);
 void dev_d2d(void* dst, const void* src, size_t bytes, Stream s);
 void dev_zero(void* p, size_t bytes, Stream s);
 void dev_sync(Stream s);
+size_t dev_bytes_in_use();     // device bytes held by the library (all contexts)
+void dev_set_cap(size_t bytes);  // 0 = no cap; otherwise dev_alloc beyond it throws bad_alloc
 int64_t kernel_launches();  // number of this library's kernel launches so far
 int dev_check(const char** msg);  // 0 if no CUDA error is pending
 void* host_pinned_alloc(size_t bytes);

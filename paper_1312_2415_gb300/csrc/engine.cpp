@@ -269,6 +269,16 @@ void Engine::init_mps(uint64_t seed) {
   invalidate_envs_from_site(-1);
   for (auto& e : lenv_) free_env(e);
   for (auto& e : renv_) free_env(e);
+  reset_noise();
+}
+
+// A new state starts without a previous half sweep: no noise until one has ended, and
+// the noise streams are numbered from 0 again.
+void Engine::reset_noise() {
+  w_prev_ = 0.0;
+  half_dir_ = 0;
+  half_wmax_ = 0.0;
+  noise_counter_ = 0;
 }
 
 // Serialised MPS: int32 magic, version, L, N, 2S, irrep; per bond: nsec then
@@ -369,6 +379,7 @@ void Engine::set_mps(const char* buf, size_t len) {
   for (auto& e : lenv_) free_env(e);
   for (auto& e : renv_) free_env(e);
   if (cached_) { free_plan(cached_); cached_ = nullptr; cached_site_ = -1; }
+  reset_noise();
 }
 
 // ------------------------------------------------------------------ environments
@@ -848,6 +859,12 @@ Engine::MatvecPlan* Engine::plan_matvec(int i) {
   ensure_left(i);
   ensure_right(i + 2);
   MatvecPlan* P = new MatvecPlan;
+  // a plan whose build fails (for instance on the device memory cap) is released whole
+  struct Guard {
+    Engine* e;
+    MatvecPlan* p;
+    ~Guard() { if (p) e->free_plan(p); }
+  } guard{this, P};
   P->site = i;
   P->X = x_layout(i, &P->n);
   group_left(i, P->cl, &P->scr_l, &P->scr_l_n);
@@ -1218,6 +1235,7 @@ Engine::MatvecPlan* Engine::plan_matvec(int i) {
   P->ntasks = (int64_t)t1.size() + (int64_t)t2.size() + (int64_t)cs.size();
   P->wsize = wsize;
   st_.t_plan_ms += tm.ms();
+  guard.p = nullptr;
   return P;
 }
 
@@ -1225,12 +1243,20 @@ Engine::MatvecPlan* Engine::plan_matvec(int i) {
 
 namespace dmrg {
 
+void Engine::release_tc(MatvecPlan* p) {
+  tc_plan_free(p->tc, stream_);
+  p->tc = nullptr;
+  for (float*& m : p->tc_mem) {
+    if (m) dev_free(m, stream_);
+    m = nullptr;
+  }
+  if (p->tc_zt) dev_free(p->tc_zt, stream_);
+  p->tc_zt = nullptr;
+}
+
 void Engine::free_plan(MatvecPlan* p) {
   if (!p) return;
-  tc_plan_free(p->tc, stream_);
-  for (float* m : p->tc_mem)
-    if (m) dev_free(m, stream_);
-  if (p->tc_zt) dev_free(p->tc_zt, stream_);
+  release_tc(p);
   gemm_plan_free(p->p1, stream_);
   gemm_plan_free(p->p2, stream_);
   comb_plan_free(p->pc, stream_);
@@ -1464,7 +1490,14 @@ void Engine::run_matvec(MatvecPlan* p, const double* x, double* y, bool tc) {
   if (tc) {
     flush_events();
     if (!ev_[0]) for (auto& e : ev_) e = event_create();
-    if (!p->tc) build_tc(p);
+    if (!p->tc) {
+      try {
+        build_tc(p);
+      } catch (...) {
+        release_tc(p);  // a failed build keeps nothing
+        throw;
+      }
+    }
     if (x != p->xin) dev_d2d(p->xin, x, sizeof(double) * p->n, stream_);
     tc_plan_launch(p->tc, ev_, stream_);
     ev_pending_ = true;
@@ -1670,24 +1703,32 @@ double Engine::davidson_core(MatvecPlan* P, double* x, double tol, int maxit, bo
   const int64_t n = P->n;
   const int mmax = std::min<int64_t>(32, std::max<int64_t>(n, 1));
   const int nkeep = std::min(3, mmax - 1 > 0 ? mmax - 1 : 1);
-  double* V = (double*)dev_alloc(sizeof(double) * n * (mmax + 1), stream_);
-  double* AV = (double*)dev_alloc(sizeof(double) * n * (mmax + 1), stream_);
-  double* G = (double*)dev_alloc(sizeof(double) * mmax * mmax, stream_);
-  double* C = (double*)dev_alloc(sizeof(double) * mmax * mmax, stream_);
-  double* th = (double*)dev_alloc(sizeof(double) * mmax, stream_);
-  double* sc = (double*)dev_alloc(sizeof(double) * mmax * 520, stream_);
-  double* dots = (double*)dev_alloc(sizeof(double) * (mmax + 2), stream_);
-  double* r = (double*)dev_alloc(sizeof(double) * n, stream_);
-  double* t = (double*)dev_alloc(sizeof(double) * n, stream_);
-  double* tmp = (double*)dev_alloc(sizeof(double) * n * nkeep * 2, stream_);
-  dev_zero(G, sizeof(double) * mmax * mmax, stream_);
-  double* hs = (double*)host_pinned_alloc(sizeof(double) * 4);
+  double *V = nullptr, *AV = nullptr, *G = nullptr, *C = nullptr, *th = nullptr, *sc = nullptr;
+  double *dots = nullptr, *r = nullptr, *t = nullptr, *tmp = nullptr, *x0 = nullptr, *hs = nullptr;
+  double theta = 0.0;
+  bool conv = false;
+  int it = 0;
   auto cleanup = [&]() {
     dev_free(V, stream_); dev_free(AV, stream_); dev_free(G, stream_); dev_free(C, stream_);
     dev_free(th, stream_); dev_free(sc, stream_); dev_free(dots, stream_); dev_free(r, stream_);
-    dev_free(t, stream_); dev_free(tmp, stream_);
+    dev_free(t, stream_); dev_free(tmp, stream_); dev_free(x0, stream_);
     host_pinned_free(hs);
   };
+  try {
+  V = (double*)dev_alloc(sizeof(double) * n * (mmax + 1), stream_);
+  AV = (double*)dev_alloc(sizeof(double) * n * (mmax + 1), stream_);
+  G = (double*)dev_alloc(sizeof(double) * mmax * mmax, stream_);
+  C = (double*)dev_alloc(sizeof(double) * mmax * mmax, stream_);
+  th = (double*)dev_alloc(sizeof(double) * mmax, stream_);
+  sc = (double*)dev_alloc(sizeof(double) * mmax * 520, stream_);
+  dots = (double*)dev_alloc(sizeof(double) * (mmax + 2), stream_);
+  r = (double*)dev_alloc(sizeof(double) * n, stream_);
+  t = (double*)dev_alloc(sizeof(double) * n, stream_);
+  tmp = (double*)dev_alloc(sizeof(double) * n * nkeep * 2, stream_);
+  x0 = (double*)dev_alloc(sizeof(double) * n, stream_);  // the starting vector
+  dev_zero(G, sizeof(double) * mmax * mmax, stream_);
+  hs = (double*)host_pinned_alloc(sizeof(double) * 4);
+  dev_d2d(x0, x, sizeof(double) * n, stream_);
   // v0 = x / |x|
   dev_d2d(V, x, sizeof(double) * n, stream_);
   vec_multidot(V, n, 1, V, n, dots, sc, stream_);
@@ -1695,9 +1736,6 @@ double Engine::davidson_core(MatvecPlan* P, double* x, double tol, int maxit, bo
   run_matvec(P, V, AV, tc);
   vec_multidot(V, n, 1, AV, n, G, sc, stream_);
   int m = 1;
-  double theta = 0.0;
-  bool conv = false;
-  int it = 0;
   for (; it < maxit; ++it) {
     small_eig(G, mmax, m, std::min(m, nkeep), th, C, stream_);
     // u = V c0 -> x ; r = AV c0 - theta u
@@ -1761,6 +1799,17 @@ double Engine::davidson_core(MatvecPlan* P, double* x, double tol, int maxit, bo
     // row m of the Rayleigh matrix (lower triangle is what small_eig reads)
     vec_multidot(V, n, m + 1, AV + (size_t)m * n, n, G + (size_t)m * mmax, sc, stream_);
     ++m;
+  }
+  // sign of the eigenvector: non-negative overlap with the starting vector, so that
+  // what is added to it afterwards (the noise of Sec. 4.2) does not depend on the
+  // arbitrary sign of the small eigensolver
+  vec_multidot(x, n, 1, x0, n, dots, sc, stream_);
+  dev_d2h(hs + 3, dots, sizeof(double), stream_);
+  dev_sync(stream_);
+  if (hs[3] < 0.0) vec_axpby(0.0, x0, -1.0, x, n, stream_);
+  } catch (...) {
+    cleanup();
+    throw;
   }
   cleanup();
   *iters = it + 1;
@@ -2758,9 +2807,7 @@ double Engine::solve(double* e_last_out) {
           wmax = std::max(wmax, w);
           e_mac = std::min(e_mac, e);
           w_mac = std::max(w_mac, w);
-          st_.micro_iters += 1;
         }
-        w_prev_ = wmax;
       }
       const bool done = std::fabs(e_last - e_prev) < econv;
       e_prev = e_last;
@@ -2776,9 +2823,42 @@ double Engine::solve(double* e_last_out) {
   return e_min;
 }
 
+// The last part of a sweep step on its own (Sec. 2.5): the operators of the block grown
+// by site i (dir > 0, from the left-normalised T[i]) or by site i+1 (dir < 0, from the
+// right-normalised T[i+1]), from the combined operators of the environment they extend.
+void Engine::update(int i, int dir) {
+  check_ready();
+  if (i < 0 || i > L_ - 2) throw std::out_of_range("site out of range");
+  std::vector<CombOp> comb;
+  double* scr = nullptr;
+  int64_t scr_n = 0;
+  try {
+    if (dir > 0) {
+      ensure_left(i);
+      group_left(i, comb, &scr, &scr_n);
+      update_left_from(i, comb);
+    } else {
+      ensure_right(i + 2);
+      group_right(i + 1, comb, &scr, &scr_n);
+      update_right_from(i + 1, comb);
+    }
+  } catch (...) {
+    if (scr) dev_free(scr, stream_);
+    throw;
+  }
+  if (scr) dev_free(scr, stream_);
+}
+
 double Engine::sweep_step(int i, int dir, int D, double gamma, double* w_disc, int* iters, bool* conv) {
   check_ready();
   if (i < 0 || i > L_ - 2) throw std::out_of_range("site out of range");
+  // a change of direction starts a half sweep: the noise of its steps is bounded by the
+  // largest discarded weight of the previous one (Sec. 4.2)
+  if (dir != half_dir_) {
+    w_prev_ = half_dir_ == 0 ? 0.0 : half_wmax_;
+    half_wmax_ = 0.0;
+    half_dir_ = dir;
+  }
   MatvecPlan* P = plan_for(i);
   double* x = (double*)dev_alloc(sizeof(double) * std::max<int64_t>(P->n, 1), stream_);
   tt_to_x(i, x);
@@ -2793,6 +2873,7 @@ double Engine::sweep_step(int i, int dir, int D, double gamma, double* w_disc, i
   double w;
   try {
     w = truncate(i, dir, D, x, 0.0);
+    half_wmax_ = std::max(half_wmax_, w);
     launch_rq();  // after the decomposition, whose kernels would otherwise queue behind it
     if (dir > 0) update_left_from(i, P->cl);
     else update_right_from(i + 1, P->cr);

@@ -149,6 +149,8 @@ class Engine {
   // one micro-iteration of a sweep at sites (i, i+1): Eq. 25, Davidson, noise,
   // Eqs. 26-28 and the operator update in the sweep direction
   double sweep_step(int i, int dir, int D, double gamma, double* w_disc, int* iters, bool* conv);
+  // the operator update of a sweep step in direction dir, after truncate(i, dir, ...)
+  void update(int i, int dir);
   void canonicalize(int center);
   // Spin-summed 1- and 2-RDMs of the current MPS (device outputs, L^2 and L^4 doubles,
   // row-major): Gamma_ijkl = sum_st <a+_is a+_jt a_lt a_ks> projected onto the eight
@@ -193,12 +195,14 @@ class Engine {
   void build_left(int k);
   void build_right(int k);
   void invalidate_envs_from_site(int k);
+  void reset_noise();
   std::vector<XBlock> x_layout(int i, int64_t* n) const;
   void group_left(int i, std::vector<CombOp>& out, double** scratch, int64_t* scratch_n);
   void group_right(int i, std::vector<CombOp>& out, double** scratch, int64_t* scratch_n);
   void build_tc(MatvecPlan* p);
   MatvecPlan* plan_matvec(int i);
   void free_plan(MatvecPlan* p);
+  void release_tc(MatvecPlan* p);  // frees the tensor-core tables of a plan
   MatvecPlan* plan_for(int i);
   void run_matvec(MatvecPlan* p, const double* x, double* y, bool tc = false);
   double davidson_core(MatvecPlan* P, double* x, double tol, int maxit, bool tc, int* iters,
@@ -245,7 +249,12 @@ class Engine {
   Stats st_;
   MatvecPlan* cached_ = nullptr;
   int cached_site_ = -1;
+  // noise of Sec. 4.2: largest discarded weight of the previous half sweep, direction
+  // and running maximum of the current one (a half sweep ends where the direction of
+  // sweep_step changes), and the counter that seeds each noisy step's stream
   double w_prev_ = 0.0;
+  int half_dir_ = 0;
+  double half_wmax_ = 0.0;
   uint64_t noise_counter_ = 0;
   void* ev_[3] = {nullptr, nullptr, nullptr};
   void flush_events();

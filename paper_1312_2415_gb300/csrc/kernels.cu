@@ -8,6 +8,7 @@
 #include <mutex>
 #include <stdexcept>
 #include <string>
+#include <unordered_map>
 
 #include "device.hpp"
 #include "plans.hpp"
@@ -34,14 +35,51 @@ inline int nblk(int64_t n, int t) { return (int)std::min<int64_t>((n + t - 1) / 
 
 // ------------------------------------------------------------------ memory
 
+// Device bytes the library holds (all contexts), and an optional cap on them: an
+// allocation that would pass the cap fails on the host with std::bad_alloc (reported as
+// DMRG_ENOMEM) before any CUDA call is made.
+namespace {
+std::mutex g_mem_mu;
+std::unordered_map<void*, size_t> g_mem_live;
+size_t g_mem_in_use = 0, g_mem_cap = 0;
+}  // namespace
+
 void* dev_alloc(size_t bytes, Stream s) {
   void* p = nullptr;
   if (bytes == 0) bytes = 16;
-  ck(cudaMallocAsync(&p, bytes, S(s)), "cudaMallocAsync");
+  {
+    std::lock_guard<std::mutex> lk(g_mem_mu);
+    if (g_mem_cap && g_mem_in_use + bytes > g_mem_cap) throw std::bad_alloc();
+    g_mem_in_use += bytes;  // reserved before the call, released if it fails
+  }
+  cudaError_t e = cudaMallocAsync(&p, bytes, S(s));
+  std::lock_guard<std::mutex> lk(g_mem_mu);
+  if (e != cudaSuccess) {
+    g_mem_in_use -= bytes;
+    ck(e, "cudaMallocAsync");
+  }
+  g_mem_live[p] = bytes;
   return p;
 }
 void dev_free(void* p, Stream s) {
-  if (p) ck(cudaFreeAsync(p, S(s)), "cudaFreeAsync");
+  if (!p) return;
+  {
+    std::lock_guard<std::mutex> lk(g_mem_mu);
+    auto it = g_mem_live.find(p);
+    if (it != g_mem_live.end()) {
+      g_mem_in_use -= it->second;
+      g_mem_live.erase(it);
+    }
+  }
+  ck(cudaFreeAsync(p, S(s)), "cudaFreeAsync");
+}
+size_t dev_bytes_in_use() {
+  std::lock_guard<std::mutex> lk(g_mem_mu);
+  return g_mem_in_use;
+}
+void dev_set_cap(size_t bytes) {
+  std::lock_guard<std::mutex> lk(g_mem_mu);
+  g_mem_cap = bytes;
 }
 void dev_h2d(void* d, const void* h, size_t b, Stream s) {
   if (b) ck(cudaMemcpyAsync(d, h, b, cudaMemcpyHostToDevice, S(s)), "h2d");

@@ -50,3 +50,36 @@ def lib_x_to_oracle(v, table):
         dL, dR, off = int(row[9]), int(row[10]), int(row[11])
         out[key] = v[off:off + dL * dR].reshape(dL, dR).copy()
     return out
+
+
+def mps_from_bytes(data, irreps):
+    """The library's serialised MPS (dmrg_get_mps) as an oracle MPS object."""
+    from oracle.mps import MPS
+    pos = 0
+
+    def take(fmt):
+        nonlocal pos
+        v = struct.unpack_from(fmt, data, pos)
+        pos += struct.calcsize(fmt)
+        return v
+
+    magic, ver, L, N, two_S, I_G = take("<6i")
+    assert magic == 0x444D5247 and ver == 1 and L == len(irreps)
+    secs, dims = [], []
+    for _ in range(L + 1):
+        (ns,) = take("<i")
+        s = [take("<4i") for _ in range(ns)]
+        secs.append([(t[0], t[1], t[2]) for t in s])
+        dims.append({(t[0], t[1], t[2]): t[3] for t in s})
+    m = MPS(irreps, N, two_S, I_G, dims)
+    for k in range(L):
+        (nb,) = take("<i")
+        for _ in range(nb):
+            ls, li, ri = take("<3i")
+            lsec, rsec = secs[k][li], secs[k + 1][ri]
+            dL, dR = dims[k][lsec], dims[k + 1][rsec]
+            blk = np.frombuffer(data, dtype="<f8", count=dL * dR, offset=pos).reshape(dL, dR).copy()
+            pos += 8 * dL * dR
+            m.T[k][(ls, lsec, rsec)] = blk
+    assert pos == len(data)
+    return m

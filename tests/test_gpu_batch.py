@@ -1,12 +1,16 @@
 """Batched mixed-precision matvecs (dmrg_batch_*): the H_eff x of several independent
 instances of uneven size (Hubbard and random-integral systems, S = 0 and 1, different
-D) run as one grouped launch per phase replayed from a CUDA graph, element by element
-against each instance's FP64 matvec (2e-5 of max|y|, the bound of the single-instance
-mixed tests) and against its own single-instance mixed matvec; a replay gives the same
-result; a context that rebuilds its tables invalidates the batch."""
+D) run as one grouped launch per phase replayed from a CUDA graph.  Every instance the
+oracle can project densely (L <= 9) is compared element by element with the oracle's
+P^T H P x on the library's own state (2e-6 of max|y|, the mixed-precision bound of the
+single-instance tests); every instance is also compared with its FP64 and its own
+single-instance mixed matvec.  A replay gives the same result; a context that rebuilds
+its tables invalidates the batch."""
 import numpy as np
 import pytest
 
+from oracle import dmrg as odmrg
+from tests.mps_io import lib_x_to_oracle, mps_from_bytes, oracle_x_to_lib
 from workloads import hubbard_chain, random_integrals, round_robin_irreps
 
 pytestmark = pytest.mark.gpu
@@ -23,7 +27,7 @@ def mods():
     return torch, Batch, Context, DMRGError
 
 
-def _instances(Context):
+def _instances(Context, systems=None):
     ctxs, sites = [], []
     for kind, L, N, tS, D in CASES:
         if kind == "h":
@@ -32,6 +36,8 @@ def _instances(Context):
         else:
             irr = round_robin_irreps(L)
             h, V = random_integrals(irr, 7)
+        if systems is not None:
+            systems.append((irr, h, V, N, tS))
         c = Context(L, irr, N, tS, 0)
         c.set_integrals(h, V)
         c.set_schedule([D], [0.0], [1], [0.0], 1e-10, 40)
@@ -45,7 +51,8 @@ def _instances(Context):
 
 def test_batched_matvec_matches_each_instance(mods):
     torch, Batch, Context, DMRGError = mods
-    ctxs, sites = _instances(Context)
+    systems = []
+    ctxs, sites = _instances(Context, systems)
     xs, ref64, ref32 = [], [], []
     for k, (c, i) in enumerate(zip(ctxs, sites)):
         n, _ = c.layout(i)
@@ -67,8 +74,23 @@ def test_batched_matvec_matches_each_instance(mods):
         torch.cuda.synchronize()
         for y, y64, y32 in zip(ys, ref64, ref32):
             err = ((y - y64).abs().max() / y64.abs().max()).item()
-            assert 0.0 < err <= 2e-5, err
-            assert ((y - y32).abs().max() / y64.abs().max()).item() <= 2e-5
+            assert 0.0 < err <= 2e-6, err
+            assert ((y - y32).abs().max() / y64.abs().max()).item() <= 2e-6
+    # the oracle: P^T H P x on each small instance's own (canonicalised) state
+    checked = 0
+    for c, i, x, y, (irr, h, V, N, tS) in zip(ctxs, sites, xs, ys, systems):
+        if len(irr) > 9:
+            continue
+        m = mps_from_bytes(c.get_mps(), irr)
+        prob = odmrg.Problem(h, V, irr, N, tS, 0)
+        H, _, proj = odmrg.effective_hamiltonian(prob, m, i)
+        n, table = c.layout(i)
+        xv = x.cpu().numpy()
+        yo = oracle_x_to_lib(proj.unflatten(H @ proj.flatten(lib_x_to_oracle(xv, table))), table, n)
+        err = np.abs(y.cpu().numpy() - yo).max() / np.abs(yo).max()
+        assert 0.0 < err <= 2e-6, err
+        checked += 1
+    assert checked == 3
     # a context that rebuilds its tables invalidates the batch
     ctxs[0].truncate(sites[0], 1, CASES[0][4], xs[0])
     with pytest.raises(DMRGError):

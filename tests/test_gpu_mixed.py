@@ -3,8 +3,10 @@ split TF32 (a = a_hi + a_lo, three products, FP32 accumulation), Davidson finish
 FP64 iterations.
 
 Tolerances.  One split-TF32 product has a relative error of about 2^-21 (5e-7); the
-FP32 accumulation of K terms adds about sqrt(K) 2^-24 (K <= a few hundred here), and
-the terms of H_eff partly cancel, so the matvec is held to 2e-5 relative to max|y|.
+accumulators are promoted to FP32 registers every two 32-wide K chunks, so the sums add
+little to it (measured 5.5e-7 of max|y| at L=28, D=2500).  The matvec is held to 2e-6
+relative to max|y|: four times the measured level, so that a lost promotion (1e-5
+measured with 48-task runs) or a dropped split term (2^-11) fails.
 Energies are FP64 Rayleigh quotients after the FP64 iterations, held to the 1e-6 Eh
 target of the mixed path (and reported)."""
 import numpy as np
@@ -45,7 +47,7 @@ def test_tensor_core_matvec_and_energy(Context, case):
     y = ctx.matvec(i, v)
     yo = oracle_x_to_lib(proj.unflatten(H @ proj.flatten(lib_x_to_oracle(v, table))), table, n)
     err = np.abs(y - yo).max() / np.abs(yo).max()
-    assert err <= 2e-5, err
+    assert err <= 2e-6, err
     assert err > 0.0  # it really ran in reduced precision
     x = ctx.tt_to_x(i)
     e, it, ok = ctx.davidson(i, x)

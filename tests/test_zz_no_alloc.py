@@ -1,10 +1,10 @@
 """The allocation-free matvec entry point (dmrg_heff_matvec_noalloc).
 
-It has no counterpart in the paper: it serves callers that must not allocate device
-memory while they apply H_eff (for example code being captured into a CUDA graph, or
-running under a fixed memory budget).  It must give the same y = H_eff x as the
-allocating entry point dmrg_heff_matvec, call after call, although every call reuses
-one fixed scratch array inside the library.  This file is collected last so that a
+It has no counterpart in the paper: it serves callers that cannot allocate device
+memory when they apply H_eff (a process that reserved its device memory up front and
+must not grow it, or a host framework whose allocator owns the GPU).  It must give the
+FP64 y = H_eff x of the allocating entry point dmrg_heff_matvec, call after call,
+although every call reuses one fixed scratch array inside the library.  This file is collected last so that a
 run stopping at the first failure has already run every other test."""
 import numpy as np
 import pytest
@@ -57,3 +57,73 @@ def test_noalloc_matvec_rejects_unprepared_site():
     with pytest.raises(DMRGError) as e:
         ctx.matvec_noalloc(2, x.data_ptr(), y.data_ptr(), 0)
     assert e.value.code == -1
+
+
+def _context(L, N, D, seed, site, precision=0):
+    from paper_1312_2415_gb300 import Context
+    from workloads import random_integrals, round_robin_irreps
+    irr = round_robin_irreps(L)
+    h, V = random_integrals(irr, seed)
+    ctx = Context(L, irr, N, 0, 0, precision=precision)
+    ctx.set_integrals(h, V)
+    ctx.set_schedule([D], [0.0], [1], [0.0], 1e-10, 50)
+    ctx.init_mps(seed)
+    ctx.canonicalize(site)
+    return ctx
+
+
+def test_noalloc_matvec_runs_fp64_tables_in_a_mixed_precision_context():
+    """For a precision-1 context the allocation-free matvec is the FP64 product (the
+    header says so), not the split-TF32 one of dmrg_heff_matvec."""
+    import torch
+    site = 3
+    ctx = _context(8, 8, 60, 23, site, precision=1)
+    n, _ = ctx.layout(site)
+    x = torch.tensor(np.random.default_rng(8).normal(size=n), dtype=torch.float64, device="cuda")
+    y32, y64, y = torch.empty_like(x), torch.empty_like(x), torch.empty_like(x)
+    ctx.matvec(site, x, y32)   # tensor-core product; prepares the site's tables
+    ctx.set_precision(0, 0)
+    ctx.matvec(site, x, y64)   # FP64 product of the same tables
+    ctx.set_precision(1, 0)
+    ctx.matvec_noalloc(site, x.data_ptr(), y.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    scale = y64.abs().max().item()
+    assert (y - y64).abs().max().item() <= 1e-12 * scale
+    assert (y32 - y64).abs().max().item() > 0.0
+
+
+def test_noalloc_on_a_side_stream_then_a_call_that_frees_its_tables():
+    """The work is queued on the caller's stream and the call returns at once; the next
+    context call (here a canonicalisation that releases the site's tables) must not
+    free what that work still reads."""
+    import torch
+    site = 3
+    ctx = _context(8, 8, 80, 31, site)
+    n, _ = ctx.layout(site)
+    xs = [np.random.default_rng(k).normal(size=n) for k in range(4)]
+    refs = [ctx.matvec(site, x) for x in xs]
+    side = torch.cuda.Stream()
+    xd = [torch.tensor(x, dtype=torch.float64, device="cuda") for x in xs]
+    ys = [torch.empty(n, dtype=torch.float64, device="cuda") for _ in xs]
+    torch.cuda.synchronize()
+    for x, y in zip(xd, ys):
+        ctx.matvec_noalloc(site, x.data_ptr(), y.data_ptr(), side.cuda_stream)
+    ctx.canonicalize(site + 1)  # no synchronisation in between
+    torch.cuda.synchronize()
+    for y, ref in zip(ys, refs):
+        got = y.cpu().numpy()
+        assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_noalloc_rejects_a_problem_above_its_fixed_scratch():
+    import torch
+    from paper_1312_2415_gb300 import DMRGError
+    site = 7
+    ctx = _context(16, 16, 1000, 2415016, site)
+    n, _ = ctx.layout(site)
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    y = torch.zeros(n, dtype=torch.float64, device="cuda")
+    ctx.matvec(site, x, y)  # tables prepared; their scratch exceeds the 64 MiB array
+    with pytest.raises(DMRGError) as e:
+        ctx.matvec_noalloc(site, x.data_ptr(), y.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    assert e.value.code == -1 and "64 MiB" in str(e.value)

@@ -39,6 +39,20 @@ def uniform_pm1(seed, n):
     return u.astype(np.float64) * (2.0 / 9007199254740992.0) - 1.0
 
 
+def counter_uniform_pm1(seed, n, start=0):
+    """Counter-based stream: element i is splitmix64's first output from state
+    seed + start + i (one mix per element, no sequential state), mapped to [-1, 1) by
+    its top 53 bits.  This is the stream a device kernel draws with one thread per
+    element; here it is an input generator for tests."""
+    with np.errstate(over="ignore"):
+        idx = np.arange(n, dtype=np.uint64) + np.uint64((seed + start) & MASK64)
+        z = idx + np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    return (z >> np.uint64(11)).astype(np.float64) * (2.0 / 9007199254740992.0) - 1.0
+
+
 def hubbard_chain(L, t=1.0, U=4.0):
     h = np.zeros((L, L))
     for i in range(L - 1):
