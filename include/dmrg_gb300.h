@@ -237,11 +237,11 @@ int dmrg_extrapolate(const double* w_disc, const double* energy, int n, double* 
 /* Batched mixed-precision matvecs (no counterpart in the paper, which treats one
  * problem at a time): y_i = H_eff(ctx[i], site[i]) x_i for `count` independent
  * contexts, computed with the split-TF32 tensor-core products of precision 1 (whatever
- * precision the contexts were created with) and run as ONE grouped launch per phase
- * over the symmetry blocks of all instances, replayed from a CUDA graph.
- * dmrg_batch_create prepares each context's tables at its site (as a first
- * dmrg_heff_matvec would), merges them and, if autotune != 0, times the candidate unit
- * sizes (packs of right-operator blocks per phase-1 unit, tasks per phase-2 unit) and
+ * precision the contexts were created with) as ONE launch of the fused matvec kernel
+ * over the output tiles of all instances (after one launch converting every x), replayed
+ * from a CUDA graph.  dmrg_batch_create prepares each context's tables at its site (as
+ * a first dmrg_heff_matvec would) and, if autotune != 0, times the candidate tile shapes
+ * (output rows per tile 128 or 64, x rows per term 64 or 32) on the merged tables and
  * keeps the fastest, then captures the launch sequence in a CUDA graph.  Failures are
  * reported through dmrg_last_error(ctx[0]).  The batch stays valid while no context
  * rebuilds its tables (a matvec at another site, a truncation or a sweep step does):
@@ -258,9 +258,10 @@ int dmrg_batch_io(dmrg_batch* b, int i, double** x, double** y, int64_t* n);
  * Runs that overlap in time, or that overlap a matvec of one of the contexts at the
  * same site, race on those buffers. */
 int dmrg_batch_run(dmrg_batch* b, const double* const* x, double* const* y, uintptr_t stream);
-/* flops of one batched matvec (planner-counted), the chosen unit sizes, the measured
- * time of one launch sequence in the autotuner (0 without it) and the autotuner's time. */
-int dmrg_batch_info(dmrg_batch* b, double* flops, int* packs_per_unit, int* tasks_per_unit,
+/* flops of one batched matvec (planner-counted), the chosen tile shape (output rows per
+ * tile, x rows per term), the measured time of one launch sequence in the autotuner (0
+ * without it) and the autotuner's time. */
+int dmrg_batch_info(dmrg_batch* b, double* flops, int* row_tile, int* x_chunk,
                     double* launch_ms, double* tune_ms);
 const char* dmrg_batch_last_error(dmrg_batch* b);
 void dmrg_batch_destroy(dmrg_batch* b);
@@ -273,6 +274,15 @@ void dmrg_batch_destroy(dmrg_batch* b);
  * used again (with the cap raised or removed, bytes = 0).  Library-wide, not per
  * context. */
 int dmrg_set_device_memory_cap(size_t bytes);
+
+/* Test hook for failure detection (no counterpart in the paper).  While on != 0, each CTA
+ * of the tensor-core matvec kernel starts with a bounded wait on a barrier that nothing
+ * completes (a few thousand polls), so that it takes the path of a timed-out wait: it
+ * records the error, issues nothing, frees its tensor memory and returns.  The calls that
+ * ran it then fail with DMRG_ECUDA ("tensor-core wait timed out"); the error flag is
+ * cleared when it is read, and with the hook off the next call computes normally.  No
+ * fault, trap or endless wait is involved.  Library-wide. */
+int dmrg_test_tc_timeout(int on);
 int dmrg_device_memory_in_use(size_t* bytes);
 
 int dmrg_stats(dmrg_ctx* ctx, dmrg_stats_t* out);

@@ -84,6 +84,7 @@ _SIGS = {
     "dmrg_batch_info": (ctypes.c_int, [_P, _D, _I, _I, _D, _D]),
     "dmrg_batch_last_error": (ctypes.c_char_p, [_P]),
     "dmrg_batch_destroy": (None, [_P]),
+    "dmrg_test_tc_timeout": (ctypes.c_int, [ctypes.c_int]),
     "dmrg_set_device_memory_cap": (ctypes.c_int, [ctypes.c_size_t]),
     "dmrg_device_memory_in_use": (ctypes.c_int, [ctypes.POINTER(ctypes.c_size_t)]),
     "dmrg_stats": (ctypes.c_int, [_P, ctypes.POINTER(Stats)]),
@@ -309,6 +310,13 @@ def set_device_memory_cap(nbytes, path=None):
         raise DMRGError(rc, "dmrg_set_device_memory_cap")
 
 
+def test_tc_timeout(on, path=None):
+    """Failure-detection test hook: the tensor-core kernel's waits give up (see header)."""
+    rc = load(path).dmrg_test_tc_timeout(int(on))
+    if rc != OK:
+        raise DMRGError(rc, "dmrg_test_tc_timeout")
+
+
 def device_memory_in_use(path=None):
     n = ctypes.c_size_t(0)
     rc = load(path).dmrg_device_memory_in_use(ctypes.byref(n))
@@ -370,7 +378,7 @@ class Batch:
         ppu, tpu = ctypes.c_int(), ctypes.c_int()
         self.lib.dmrg_batch_info(self.h, ctypes.byref(f), ctypes.byref(ppu), ctypes.byref(tpu), ctypes.byref(ms),
                                  ctypes.byref(tms))
-        return {"flops": f.value, "packs_per_unit": ppu.value, "tasks_per_unit": tpu.value,
+        return {"flops": f.value, "row_tile": ppu.value, "x_chunk": tpu.value,
                 "launch_ms": ms.value, "tune_ms": tms.value}
 
     def close(self):

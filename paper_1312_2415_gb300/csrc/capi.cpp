@@ -473,6 +473,15 @@ int dmrg_stats(dmrg_ctx* c, dmrg_stats_t* out) {
   });
 }
 
+int dmrg_test_tc_timeout(int on) {
+  try {
+    dmrg::tc_inject_timeout(on);
+  } catch (...) {
+    return DMRG_ECUDA;
+  }
+  return DMRG_OK;
+}
+
 int dmrg_set_device_memory_cap(size_t bytes) {
   dmrg::dev_set_cap(bytes);
   return DMRG_OK;
@@ -543,13 +552,19 @@ int dmrg_batch_create(dmrg_batch** out, dmrg_ctx* const* ctx, const int* site, i
   dmrg_batch* b = new (std::nothrow) dmrg_batch;
   if (!b) return DMRG_ENOMEM;
   const int rc = guard_err(ctx[0]->err, [&] {
-    std::vector<const dmrg::TcHost*> hosts;
+    // the tables of every context at the first candidate tile shape
+    std::vector<dmrg::TcTune> cand;
+    if (autotune) {
+      for (int rt : {128, 64})
+        for (int xc : {64, 32}) cand.push_back({rt, xc});
+    } else {
+      cand.push_back(dmrg::TcTune());
+    }
     for (int i = 0; i < count; ++i) {
       dmrg_ctx* c = ctx[i];
       dmrg::Stream s = dev_stream(c);
-      dmrg::Engine::TcView v = c->eng->prepare_tc(site[i]);
+      dmrg::Engine::TcView v = c->eng->prepare_tc(site[i], cand[0]);
       dmrg::dev_sync(s);
-      hosts.push_back(v.host);
       b->ctx.push_back(c);
       b->site.push_back(site[i]);
       b->serial.push_back(v.serial);
@@ -560,22 +575,19 @@ int dmrg_batch_create(dmrg_batch** out, dmrg_ctx* const* ctx, const int* site, i
     }
     cudaStream_t st;
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) throw std::runtime_error("cuda stream");
-    std::vector<dmrg::TcTune> cand;
-    if (autotune) {
-      for (int ppu : {4, 8, 16})
-        for (int tpu : {16, 32, 48, 96}) cand.push_back({ppu, tpu});
-    } else {
-      cand.push_back(dmrg::TcTune());
-    }
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     const auto t0 = std::chrono::steady_clock::now();
     for (const dmrg::TcTune& t : cand) {
-      dmrg::TcPlan* p = dmrg::tc_plan_build(hosts, t, (dmrg::Stream)st);
+      // every candidate: each context's host tables for this tile shape, merged into one
+      // launch; timed as the mean of three launches after a warm-up
+      std::vector<const dmrg::TcHost*> hosts;
+      for (int i = 0; i < count; ++i) hosts.push_back(ctx[i]->eng->prepare_tc(site[i], t).host);
+      dmrg::TcPlan* p = dmrg::tc_plan_build(hosts, (dmrg::Stream)st);
       float ms = 0.0f;
       if (cand.size() > 1) {
-        dmrg::tc_plan_launch(p, nullptr, (dmrg::Stream)st);  // warm-up
+        dmrg::tc_plan_launch(p, nullptr, (dmrg::Stream)st);
         cudaEventRecord(e0, st);
         for (int r = 0; r < 3; ++r) dmrg::tc_plan_launch(p, nullptr, (dmrg::Stream)st);
         cudaEventRecord(e1, st);
@@ -597,6 +609,9 @@ int dmrg_batch_create(dmrg_batch** out, dmrg_ctx* const* ctx, const int* site, i
     cudaEventDestroy(e1);
     dmrg::dev_sync((dmrg::Stream)st);
     cudaStreamDestroy(st);
+    for (int i = 0; i < count; ++i)
+      if (ctx[i]->eng->tc_serial(site[i]) != b->serial[i])
+        throw std::runtime_error("a context rebuilt its tables while the batch was made");
     if (dmrg::tc_error_flag((dmrg::Stream)cudaStreamLegacy)) throw std::runtime_error("cuda: tensor-core wait timed out");
     b->graph = dmrg::tc_graph_create(b->plan);
     return DMRG_OK;
@@ -637,12 +652,12 @@ int dmrg_batch_run(dmrg_batch* b, const double* const* x, double* const* y, uint
   });
 }
 
-int dmrg_batch_info(dmrg_batch* b, double* flops, int* packs_per_unit, int* tasks_per_unit, double* launch_ms,
+int dmrg_batch_info(dmrg_batch* b, double* flops, int* row_tile, int* x_chunk, double* launch_ms,
                     double* tune_ms) {
   if (!b) return DMRG_EINVAL;
   if (flops) *flops = b->flops;
-  if (packs_per_unit) *packs_per_unit = b->tune.packs_per_unit;
-  if (tasks_per_unit) *tasks_per_unit = b->tune.tasks_per_unit;
+  if (row_tile) *row_tile = b->tune.row_tile;
+  if (x_chunk) *x_chunk = b->tune.x_chunk;
   if (launch_ms) *launch_ms = b->best_ms;
   if (tune_ms) *tune_ms = b->tune_ms;
   return DMRG_OK;

@@ -156,70 +156,66 @@ struct ScatterJob {
 };
 void scatter_batched(const std::vector<ScatterJob>& jobs, Stream s);
 
-// ---- mixed-precision matvec: FP32 data, split-TF32 products on the tensor cores with
-// FP32 accumulation (kernels_tc.cu).  Phase 1 writes Zt = (stack_c D^T)^T column-major for
-// every right-operator block D (several blocks side by side in one MMA tile, the stack
-// tile reused); phase 2 forms W^T = sum coef Zt while staging and accumulates
-// y += C W over a task list (y FP64, added with atomics).  Every FP32 matrix here has a
-// row stride that is a multiple of 4 and a 16-byte aligned first row, with zeros in the
-// padding, so that rows are read as float4. ----
-struct Tc1Entry {   // one right-operator block, or a piece of at most 128 of its rows
-  const float* D;   // first row of the piece: ncols rows of K elements, row stride ldd
-  float* zt;        // first column of its Zt: ncols columns of the stack's rows, stride ldz
-  int ldd, ldz, ncols;
-  int start;        // first column of the piece inside its pack (multiple of 8)
-  float alpha;      // scalar of the operator
+// ---- mixed-precision matvec (kernels_tc.cu): split-TF32 block products on the tcgen05
+// tensor cores with FP32 accumulation, fused per output tile (no intermediate in global
+// memory).  For an output block y_X' and every term (left-operator block C, weighted sum
+// W = sum_s coef_s x_s D_s^T of right-operator products), the kernel forms W^T = sum_s
+// coef_s D_s x_s^T in tensor memory (one accumulator per source, summed with the
+// coefficients in FP32 registers) and adds y^T += W^T C^T (C's scalar folded into the
+// coefficients).  Operands are FP32 "tiled" copies split into a TF32 head (hi) and tail
+// (lo) kept in two arrays of the same layout: a block of R rows and K columns is stored
+// as ceil(K/32) column chunks, each of ceil(R/8) row groups of 8 rows x 32 columns (1 KB)
+// in the K-major core-matrix order of the tensor core's shared-memory operands (zeros in
+// the padding), so that the rows an MMA needs from one chunk are one contiguous run that
+// a single bulk copy moves into shared memory. ----
+struct TfSrc {          // one source of a sub-task: W^T += coef D x^T
+  const float* d;       // hi tiles of the right-operator block: chunk 0, first row group of the output column tile
+  const float* x;       // hi tiles of the x block: chunk 0, first row group of the sub-task's x rows
+  int d_cs, x_cs;       // floats between consecutive K chunks of d and of x
+  int nkc, klast;       // K chunks (ceil(dR / 32)) and valid columns of the last one (1..32)
+  float coef;           // the source's coefficient times the scalars of both operators
 };
-struct Tc1Pack { int e_begin, e_end, n; };  // n = padded columns of the pack (<= 128)
-struct Tc1Unit {
-  const float* A;   // stack rows row0 .. row0 + rows - 1 (rows <= 128), row stride lda
-  int lda, rows, K, row0;
-  int p_begin, p_end;
+struct TfTask {         // one sub-task: y^T += W^T C^T over kdl columns of C
+  const float* c;       // hi tiles of the left-operator block: chunk of its first column, first row group of the tile
+  int c_cs;             // floats between consecutive K chunks of c
+  int kdl;              // x rows of the sub-task (<= 64): N of W^T, K of the second product
+  int s_begin, s_end;   // sources (at least one)
 };
-struct Tc2Src { const float* z; int ldz; float coef; };  // W^T(j, k) += coef z[j ldz + k]
-struct Tc2Task {
-  const float* C;   // left-operator block (m x K, row stride ldc); nullptr = identity
-  int ldc, K;
-  float alpha;
-  int s_begin, s_end;
+struct TfTile {         // one output tile of y, computed by one CTA from all of its terms
+  double* y;            // element (row0, col0) of the output block
+  int ldy, m, nv;       // m <= 128 rows, nv <= 128 columns
+  int t_begin, t_end;   // sub-tasks
+  int64_t dlo, xlo;     // floats from a hi tile to its lo tile (operator pool, x pool)
+  int64_t cost;         // MMA steps (tiles run in decreasing order of cost)
 };
-struct Tc2Unit {
-  double* y;        // output block (row stride ldy); tile rows row0 .., columns col0 ..
-  int ldy, m, n, row0, col0;
-  int t_begin, t_end;
-};
-// one x block (rows x cols, row-major FP64) and its places in the FP32 stack (row-major,
-// stride ld) and in the transposed stack (column-major, stride ldt)
-struct TcXBlock { const double* src; float* dst; float* dstt; int rows, cols, ld, ldt; };
-// one FP64 block converted to FP32 with row stride ld (a multiple of 4)
-struct TcMirror { const double* src; float* dst; int rows, cols, ld; };
-// Host description of one instance's mixed-precision matvec: the tables of both phases
-// and the ranges units are cut from (phase 1: the packs of one 128-row stack tile;
-// phase 2: the tasks of one output tile), reading x from xin and writing y to yout.
+// one FP64 block (rows x cols, row-major) to tiled hi / lo (nrg = ceil(rows / 8) row
+// groups per chunk; lo = hi + lo floats); identity != 0: the rows x rows identity
+struct TfConv { const double* src; float* dst; int rows, cols, nrg, identity; int64_t lo; };
+// Host description of one instance's mixed-precision matvec: its tiles, sub-tasks and
+// sources, the conversion of x (FP64, the ABI's layout) into its tiled pool, and y.
 struct TcHost {
-  std::vector<Tc1Entry> e;
-  std::vector<Tc1Pack> p;
-  std::vector<Tc1Unit> r1;  // p_begin / p_end span every pack of the tile
-  std::vector<Tc2Src> s;
-  std::vector<Tc2Task> t;
-  std::vector<Tc2Unit> r2;  // t_begin / t_end span every task of the tile
-  std::vector<TcXBlock> xb;
+  std::vector<TfSrc> s;
+  std::vector<TfTask> t;
+  std::vector<TfTile> tiles;
+  std::vector<TfConv> xb;
   double* yout = nullptr;
   int64_t n = 0;
 };
-// how ranges are cut into units (one CTA each): packs per phase-1 unit, tasks per
-// phase-2 unit
-struct TcTune { int packs_per_unit = 8, tasks_per_unit = 96; };
+// output tile rows (64 or 128) and x rows per sub-task (32 or 64)
+struct TcTune { int row_tile = 128, x_chunk = 64; };
 struct TcPlan;
-// device tables of one or several instances (one grouped launch per phase for all)
-TcPlan* tc_plan_build(const std::vector<const TcHost*>& inst, TcTune tune, Stream st);
-// clear every y, x -> FP32 stacks, phase 1, phase 2; ev (3 events or nullptr) are
-// recorded before phase 1, between the phases and after.  All pointers are fixed, so
-// the sequence can be captured in a CUDA graph.
+// device tables of one or several instances (one launch of each kernel for all)
+TcPlan* tc_plan_build(const std::vector<const TcHost*>& inst, Stream st);
+// x -> tiled hi / lo, then the fused kernel over every tile; ev (3 events or nullptr)
+// are recorded before the conversion, between the two launches and after.  All pointers
+// are fixed, so the sequence can be captured in a CUDA graph.
 void tc_plan_launch(const TcPlan* p, void* const* ev, Stream s);
 void tc_plan_free(TcPlan* p, Stream s);
-int tc_error_flag(Stream s);  // 1 if a tensor-core kernel timed out on a wait
-void tc_mirror(const std::vector<TcMirror>& m, Stream s);  // blocks -> FP32, padding untouched
+int tc_error_flag(Stream s);  // 1 if a tensor-core kernel gave up on a wait (then cleared)
+// test hook: while set, the fused kernel's first wait is on a barrier that nothing
+// completes, with a short limit, so that it takes the timed-out path
+void tc_inject_timeout(int on);
+void tc_convert(const std::vector<TfConv>& m, Stream s);  // blocks -> tiled hi / lo
 // CUDA graph of tc_plan_launch(p) (captured on a private stream), its replay and release
 void* tc_graph_create(const TcPlan* p);
 void tc_graph_launch(void* g, Stream s);

@@ -826,9 +826,20 @@ struct Engine::MatvecPlan {
   std::vector<std::vector<int>> w_by_x;
   std::vector<int64_t> tall_off, tall_rows;
   std::vector<int> sec_dim;
-  TcHost tch;              // mixed-precision tables (host), kept for batched launches
+  // mixed-precision matvec: the tiled hi / lo operand pools (operators once per plan, x
+  // per matvec), where each block sits in them, the host tables of the current tuning
+  // (kept for batched launches) and their device copy
+  TcHost tch;
+  TcTune tch_tune;
   TcPlan* tc = nullptr;
-  float* tc_zt = nullptr;
+  float* tc_ops = nullptr;
+  float* tc_x = nullptr;
+  int64_t tc_ops_lo = 0, tc_x_lo = 0;
+  std::vector<int64_t> tc_dmir;                  // Z group -> its right-operator block in the pool
+  std::vector<std::vector<int64_t>> tc_cmir;     // (left group, block) -> the block in the pool
+  std::unordered_map<int, int64_t> tc_idmir;     // identity of a dimension -> its place in the pool
+  std::vector<int64_t> tc_xoff;                  // x block -> its place in the x pool
+  double tc_alg_bytes = 0.0;  // operator blocks read once (FP32) + x read and y written (FP64)
   uint64_t serial = 0;      // distinguishes successive plans of an engine
   // excited states: projections v_k of the lower states (nlow x n, row k = v_k) and
   // eta_k v_k, the coefficients c_k = v_k . x and their reduction scratch
@@ -836,8 +847,6 @@ struct Engine::MatvecPlan {
   double* lowv = nullptr;
   double* loww = nullptr;
   double* lowc = nullptr;
-  double tc_bytes1 = 0.0, tc_bytes2 = 0.0;  // compulsory bytes of the two phases
-  float* tc_mem[3] = {nullptr, nullptr, nullptr};  // x32, x32t, operator mirrors
 };
 
 namespace {
@@ -1246,12 +1255,14 @@ namespace dmrg {
 void Engine::release_tc(MatvecPlan* p) {
   tc_plan_free(p->tc, stream_);
   p->tc = nullptr;
-  for (float*& m : p->tc_mem) {
-    if (m) dev_free(m, stream_);
-    m = nullptr;
-  }
-  if (p->tc_zt) dev_free(p->tc_zt, stream_);
-  p->tc_zt = nullptr;
+  if (p->tc_ops) dev_free(p->tc_ops, stream_);
+  if (p->tc_x) dev_free(p->tc_x, stream_);
+  p->tc_ops = p->tc_x = nullptr;
+  p->tc_dmir.clear();
+  p->tc_cmir.clear();
+  p->tc_idmir.clear();
+  p->tc_xoff.clear();
+  p->tch = TcHost();
 }
 
 void Engine::free_plan(MatvecPlan* p) {
@@ -1294,191 +1305,172 @@ void Engine::flush_events() {
   ev_pending_ = false;
 }
 
-// Tables of the mixed-precision matvec (kernels_tc.cu) from the planner's host tables.
-// FP32 layouts: every operator block the matvec reads is mirrored with its row stride
-// rounded up to 4; the stack of right sector c keeps its x blocks at row offsets rounded
-// up to 4 (zero rows between them) with row stride d_c rounded up to 4, and its
-// transpose and every Zt use the padded stack height as stride, so that all rows start
-// on 16 bytes.  Phase 1 runs packs of right-operator blocks per right sector and 128-row
-// stack tile, phase 2 runs task lists per output tile.
+// Operands of the mixed-precision matvec (kernels_tc.cu): every operator block the matvec
+// reads, and the identities that identity operators stand for, tiled and split into TF32
+// hi / lo in one pool (converted once per plan), and a pool for x (converted per
+// matvec); then the tables of the current tuning.
 void Engine::build_tc(MatvecPlan* P) {
   Timer tm;
-  auto r4 = [](int64_t v) { return (v + 3) & ~(int64_t)3; };
-  // padded stacks
-  const int nr = (int)P->sec_dim.size();
-  std::vector<int64_t> rpad(nr, 0), xoff(nr, 0), xtoff(nr, 0);
-  std::vector<int64_t> trow_pad(P->X.size(), 0);
-  for (int x = 0; x < (int)P->X.size(); ++x) {  // blocks of a stack are in row order
-    const XBlock& X = P->X[x];
-    trow_pad[x] = rpad[X.r];
-    rpad[X.r] += r4(X.rows);
-  }
-  int64_t nx = 0, nxt = 0;
-  for (int c = 0; c < nr; ++c) {
-    xoff[c] = nx;
-    xtoff[c] = nxt;
-    nx += rpad[c] * r4(P->sec_dim[c]);
-    nxt += rpad[c] * P->sec_dim[c];
-    nxt = r4(nxt);
-  }
-  float* x32 = (float*)dev_alloc(sizeof(float) * std::max<int64_t>(nx, 4), stream_);
-  P->tc_mem[0] = x32;
-  float* x32t = (float*)dev_alloc(sizeof(float) * std::max<int64_t>(nxt, 4), stream_);
-  P->tc_mem[1] = x32t;
-  dev_zero(x32, sizeof(float) * std::max<int64_t>(nx, 4), stream_);
-  dev_zero(x32t, sizeof(float) * std::max<int64_t>(nxt, 4), stream_);
-  TcHost& H = P->tch;
-  H = TcHost();
-  H.xb.reserve(P->X.size());
-  for (int x = 0; x < (int)P->X.size(); ++x) {
-    const XBlock& X = P->X[x];
-    const int ld = (int)r4(P->sec_dim[X.r]);
-    H.xb.push_back({P->xin + X.off, x32 + xoff[X.r] + trow_pad[x] * ld, x32t + xtoff[X.r] + trow_pad[x], X.rows,
-                    X.cols, ld, (int)rpad[X.r]});
-  }
-  // operator mirrors: every block phase 1 or phase 2 reads
+  auto tsize = [](int rows, int cols) -> int64_t { return (int64_t)((cols + 31) / 32) * ((rows + 7) / 8) * 256; };
   std::unordered_map<const double*, int64_t> moff;
-  moff.reserve(P->zg.size() + P->cl.size() * 4 + 16);
-  std::vector<TcMirror> mir;
-  std::vector<int64_t> mir_off;
-  int64_t nm = 0;
-  double distinct = 0.0;  // unpadded elements of the blocks mirrored so far
+  std::vector<TfConv> conv;
+  std::vector<int64_t> conv_off;
+  int64_t pool = 0;
+  double distinct = 0.0;
   auto want = [&](const double* p, int rows, int cols) -> int64_t {
-    auto ins = moff.emplace(p, nm);
+    auto ins = moff.emplace(p, pool);
     if (ins.second) {
-      mir.push_back({p, nullptr, rows, cols, (int)r4(cols)});
-      mir_off.push_back(nm);
-      nm += (int64_t)rows * r4(cols);
+      conv.push_back({p, nullptr, rows, cols, (rows + 7) / 8, 0, 0});
+      conv_off.push_back(pool);
+      pool += tsize(rows, cols);
       distinct += (double)rows * cols;
     }
     return ins.first->second;
   };
-  std::vector<int64_t> zmir(P->zg.size());
-  for (size_t g = 0; g < P->zg.size(); ++g) zmir[g] = want(P->zg[g].D, P->zg[g].n, P->zg[g].K);
-  const double distinct_d = distinct;
-  std::vector<std::vector<int64_t>> cmir(P->cl.size());  // (gl, cbi) -> mirror offset, -1 = unused
+  auto want_id = [&](int d) -> int64_t {
+    auto it = P->tc_idmir.find(d);
+    if (it != P->tc_idmir.end()) return it->second;
+    conv.push_back({nullptr, nullptr, d, d, (d + 7) / 8, 1, 0});
+    conv_off.push_back(pool);
+    P->tc_idmir[d] = pool;
+    pool += tsize(d, d);
+    return P->tc_idmir[d];
+  };
+  P->tc_dmir.assign(P->zg.size(), -1);
+  for (size_t g = 0; g < P->zg.size(); ++g) P->tc_dmir[g] = want(P->zg[g].D, P->zg[g].n, P->zg[g].K);
+  for (const auto& q : P->wsrc)
+    if (q.zg < 0) want_id(P->X[q.xb].cols);
+  P->tc_cmir.assign(P->cl.size(), {});
   for (const auto& w : P->witems) {
     const CombOp& C = P->cl[w.gl];
-    if (C.identity) continue;
-    auto& cm = cmir[w.gl];
-    if (cm.empty()) cm.assign(C.blocks->size(), -1);
-    if (cm[w.cbi] >= 0) continue;
-    const BlockRef& cb = (*C.blocks)[w.cbi];
-    cm[w.cbi] = want(C.data + cb.off, cb.rows, cb.cols);
-  }
-  float* m32 = (float*)dev_alloc(sizeof(float) * std::max<int64_t>(nm, 4), stream_);
-  P->tc_mem[2] = m32;
-  dev_zero(m32, sizeof(float) * std::max<int64_t>(nm, 4), stream_);
-  for (size_t q = 0; q < mir.size(); ++q) mir[q].dst = m32 + mir_off[q];
-  tc_mirror(mir, stream_);
-  // Zt: one column-major block per phase-1 group, stride = padded stack height
-  std::vector<int64_t> zoff(P->zg.size());
-  int64_t nz = 0;
-  for (size_t g = 0; g < P->zg.size(); ++g) {
-    zoff[g] = nz;
-    nz += r4((int64_t)P->zg[g].n * rpad[P->zg[g].c]);
-  }
-  float* zt = (float*)dev_alloc(sizeof(float) * std::max<int64_t>(nz, 4), stream_);
-  P->tc_zt = zt;
-  // phase 1
-  std::vector<std::vector<int>> byc(nr);
-  for (int g = 0; g < (int)P->zg.size(); ++g) byc[P->zg[g].c].push_back(g);
-  std::vector<Tc1Entry>& ents = H.e;
-  std::vector<Tc1Pack>& packs = H.p;
-  for (int c = 0; c < nr; ++c) {
-    if (byc[c].empty()) continue;
-    const int M = (int)rpad[c], K = P->sec_dim[c], lda = (int)r4(K);
-    const int p0 = (int)packs.size();
-    Tc1Pack cur{(int)ents.size(), (int)ents.size(), 0};
-    for (int g : byc[c]) {
-      const auto& Zg = P->zg[g];
-      const float* D32 = m32 + zmir[g];
-      for (int n0 = 0; n0 < Zg.n; n0 += 128) {
-        const int nc = std::min(128, Zg.n - n0), pad = (nc + 7) & ~7;
-        if (cur.n + pad > 128 || cur.e_end - cur.e_begin == 16) {
-          packs.push_back(cur);
-          cur = {(int)ents.size(), (int)ents.size(), 0};
-        }
-        ents.push_back({D32 + (int64_t)n0 * lda, zt + zoff[g] + (int64_t)n0 * M, lda, M, nc, cur.n, (float)Zg.alpha});
-        cur.n += pad;
-        cur.e_end = (int)ents.size();
-      }
+    if (C.identity) {
+      want_id(w.rows);
+      continue;
     }
-    if (cur.e_end > cur.e_begin) packs.push_back(cur);
-    const int p1 = (int)packs.size();
-    for (int row0 = 0; row0 < M; row0 += 128)
-      H.r1.push_back({x32 + xoff[c] + (int64_t)row0 * lda, lda, std::min(128, M - row0), K, row0, p0, p1});
+    auto& cm = P->tc_cmir[w.gl];
+    if (cm.empty()) cm.assign(C.blocks->size(), -1);
+    if (cm[w.cbi] < 0) {
+      const BlockRef& cb = (*C.blocks)[w.cbi];
+      cm[w.cbi] = want(C.data + cb.off, cb.rows, cb.cols);
+    }
   }
-  // phase 2: the tasks, sources and units of output block x at prefix offsets
-  std::vector<Tc2Src>& srcs = H.s;
-  std::vector<Tc2Task>& tasks = H.t;
+  const int64_t ops = std::max<int64_t>(pool, 256);
+  P->tc_ops = (float*)dev_alloc(sizeof(float) * 2 * ops, stream_);
+  P->tc_ops_lo = ops;
+  dev_zero(P->tc_ops, sizeof(float) * 2 * ops, stream_);
+  for (size_t k = 0; k < conv.size(); ++k) {
+    conv[k].dst = P->tc_ops + conv_off[k];
+    conv[k].lo = ops;
+  }
+  tc_convert(conv, stream_);
+  P->tc_xoff.resize(P->X.size());
+  int64_t xp = 0;
+  for (size_t x = 0; x < P->X.size(); ++x) {
+    P->tc_xoff[x] = xp;
+    xp += tsize(P->X[x].rows, P->X[x].cols);
+  }
+  const int64_t xs = std::max<int64_t>(xp, 256);
+  P->tc_x = (float*)dev_alloc(sizeof(float) * 2 * xs, stream_);
+  P->tc_x_lo = xs;
+  dev_zero(P->tc_x, sizeof(float) * 2 * xs, stream_);  // padding stays zero; x fills the rest
+  P->tc_alg_bytes = 4.0 * distinct + 16.0 * (double)P->n;
+  tc_tables(P, tune_);
+  P->tc = tc_plan_build({&P->tch}, stream_);
+  st_.t_plan_ms += tm.ms();
+}
+
+// Tiles (one CTA each: up to row_tile rows x 128 columns of one output block), their
+// sub-tasks (a term's left-operator block C and its sources, over at most x_chunk x rows)
+// and the sources (right-operator block, x block, coefficient with both scalars).
+void Engine::tc_tables(MatvecPlan* P, TcTune tune) {
+  if (tune.row_tile != 64 && tune.row_tile != 128) throw std::invalid_argument("tc row tile");
+  if (tune.x_chunk != 32 && tune.x_chunk != 64) throw std::invalid_argument("tc x chunk");
+  const int RT = tune.row_tile, XC = tune.x_chunk;
+  TcHost& H = P->tch;
+  H = TcHost();
   const size_t nX = P->X.size();
-  std::vector<int64_t> xt(nX + 1, 0), xs(nX + 1, 0), xu(nX + 1, 0);
+  auto nrg = [](int rows) { return (rows + 7) / 8; };
+  H.xb.reserve(nX);
   for (size_t x = 0; x < nX; ++x) {
-    int64_t ns = 0;
-    for (int wi : P->w_by_x[x]) ns += P->witems[wi].src_end - P->witems[wi].src_begin;
     const XBlock& X = P->X[x];
-    xt[x + 1] = xt[x] + (int64_t)P->w_by_x[x].size();
-    xs[x + 1] = xs[x] + ns;
-    xu[x + 1] = xu[x] + (P->w_by_x[x].empty() ? 0 : (int64_t)((X.rows + 127) / 128) * ((X.cols + 63) / 64));
+    H.xb.push_back({P->xin + X.off, P->tc_x + P->tc_xoff[x], X.rows, X.cols, nrg(X.rows), 0, P->tc_x_lo});
   }
-  if (xs[nX] > std::numeric_limits<int>::max()) throw std::runtime_error("tensor-core tables exceed 2^31 entries");
-  srcs.resize(xs[nX]);
-  tasks.resize(xt[nX]);
-  H.r2.resize(xu[nX]);
-  parallel_chunks(nX, 256, [&](size_t xb, size_t xe) {
+  // sizes per output block, then prefix offsets (the fill runs in parallel)
+  std::vector<int64_t> ntile(nX + 1, 0), ntask(nX + 1, 0), nsrc(nX + 1, 0);
+  for (size_t x = 0; x < nX; ++x) {
+    const XBlock& X = P->X[x];
+    const int64_t tiles = (int64_t)((X.rows + RT - 1) / RT) * ((X.cols + 127) / 128);
+    int64_t tk = 0, sr = 0;
+    for (int wi : P->w_by_x[x]) {
+      const auto& w = P->witems[wi];
+      const int nch = (w.rows + XC - 1) / XC;
+      tk += nch;
+      sr += (int64_t)nch * (w.src_end - w.src_begin);
+    }
+    ntile[x + 1] = ntile[x] + tiles;
+    ntask[x + 1] = ntask[x] + tiles * tk;
+    nsrc[x + 1] = nsrc[x] + tiles * sr;
+  }
+  if (nsrc[nX] > std::numeric_limits<int>::max() || ntask[nX] > std::numeric_limits<int>::max())
+    throw std::runtime_error("tensor-core tables exceed 2^31 entries");
+  H.tiles.resize(ntile[nX]);
+  H.t.resize(ntask[nX]);
+  H.s.resize(nsrc[nX]);
+  parallel_chunks(nX, 64, [&](size_t xb, size_t xe) {
     for (size_t x = xb; x < xe; ++x) {
-      if (P->w_by_x[x].empty()) continue;
       const XBlock& X = P->X[x];
-      int64_t t = xt[x], q = xs[x];
-      for (int wi : P->w_by_x[x]) {
-        const auto& w = P->witems[wi];
-        const CombOp& C = P->cl[w.gl];
-        const BlockRef& cb = (*C.blocks)[w.cbi];
-        Tc2Task tk{C.identity ? nullptr : m32 + cmir[w.gl][w.cbi], (int)r4(cb.cols), w.rows, (float)C.scalar,
-                   (int)q, 0};
-        for (int k = w.src_begin; k < w.src_end; ++k) {
-          const auto& src = P->wsrc[k];
-          const int c = P->X[src.xb].r;
-          if (src.zg >= 0) srcs[q++] = {zt + zoff[src.zg] + trow_pad[src.xb], (int)rpad[c], (float)src.coef};
-          else srcs[q++] = {x32t + xtoff[c] + trow_pad[src.xb], (int)rpad[c], (float)src.coef};
+      int64_t ti = ntile[x], tk = ntask[x], sr = nsrc[x];
+      for (int row0 = 0; row0 < X.rows; row0 += RT)
+        for (int col0 = 0; col0 < X.cols; col0 += 128) {
+          TfTile T{P->yout + X.off + (int64_t)row0 * X.cols + col0, X.cols, std::min(RT, X.rows - row0),
+                   std::min(128, X.cols - col0), (int)tk, 0, P->tc_ops_lo, P->tc_x_lo, 0};
+          for (int wi : P->w_by_x[x]) {
+            const auto& w = P->witems[wi];
+            const CombOp& C = P->cl[w.gl];
+            const int64_t chi = C.identity ? P->tc_idmir.at(w.rows) : P->tc_cmir[w.gl][w.cbi];
+            const int cg = nrg(X.rows);  // C has the output block's rows
+            for (int kc = 0; kc < w.rows; kc += XC) {
+              TfTask q{P->tc_ops + chi + ((int64_t)(kc / 32) * cg + row0 / 8) * 256, cg * 256,
+                       std::min(XC, w.rows - kc), (int)sr, 0};
+              for (int k = w.src_begin; k < w.src_end; ++k) {
+                const auto& src = P->wsrc[k];
+                const XBlock& Xs = P->X[src.xb];
+                const int drows = src.zg >= 0 ? P->zg[src.zg].n : Xs.cols;
+                const int64_t dhi = src.zg >= 0 ? P->tc_dmir[src.zg] : P->tc_idmir.at(Xs.cols);
+                const int nkc = (Xs.cols + 31) / 32;
+                H.s[sr++] = {P->tc_ops + dhi + (int64_t)(col0 / 8) * 256,
+                             P->tc_x + P->tc_xoff[src.xb] + (int64_t)(kc / 8) * 256, nrg(drows) * 256,
+                             nrg(Xs.rows) * 256, nkc, Xs.cols - 32 * (nkc - 1),
+                             (float)(src.craw * P->cr[src.gr].scalar * C.scalar)};
+                T.cost += nkc;
+              }
+              q.s_end = (int)sr;
+              H.t[tk++] = q;
+              T.cost += 2;
+            }
+          }
+          T.t_end = (int)tk;
+          H.tiles[ti++] = T;
         }
-        tk.s_end = (int)q;
-        tasks[t++] = tk;
-      }
-      int64_t u = xu[x];
-      for (int row0 = 0; row0 < X.rows; row0 += 128)
-        for (int col0 = 0; col0 < X.cols; col0 += 64)
-          H.r2[u++] = {P->yout + X.off, X.cols, X.rows, X.cols, row0, col0, (int)xt[x], (int)xt[x + 1]};
     }
   });
   H.yout = P->yout;
   H.n = P->n;
-  // compulsory traffic (unpadded FP32 elements): phase 1 reads x and each right-operator
-  // block once and writes every Z; phase 2 reads each task's Z sub-blocks and each
-  // left-operator block once and writes y (FP64)
-  {
-    double b1 = (double)P->n + distinct_d, b2 = distinct - distinct_d;
-    for (const auto& Zg : P->zg) b1 += (double)Zg.n * P->tall_rows[Zg.c];
-    for (const auto& w : P->witems) b2 += (double)(w.src_end - w.src_begin) * w.rows * w.cols;
-    P->tc_bytes1 = 4.0 * b1;
-    P->tc_bytes2 = 4.0 * b2 + 8.0 * P->n;
-  }
-  P->tc = tc_plan_build({&H}, tune_, stream_);
-  // the host tables are not needed any more
-  std::vector<MatvecPlan::ZGroup>().swap(P->zg);
-  std::vector<MatvecPlan::WSrc>().swap(P->wsrc);
-  std::vector<MatvecPlan::WItem>().swap(P->witems);
-  std::vector<std::vector<int>>().swap(P->w_by_x);
-  st_.t_plan_ms += tm.ms();
+  P->tch_tune = tune;
 }
 
-Engine::TcView Engine::prepare_tc(int i) {
+Engine::TcView Engine::prepare_tc(int i, TcTune tune) {
   check_ready();
   if (!low_.empty()) throw std::invalid_argument("batched matvecs do not carry excited-state projectors");
   if (i < 0 || i > L_ - 2) throw std::out_of_range("site out of range");
   MatvecPlan* p = plan_for(i);
-  if (!p->tc) build_tc(p);
+  try {
+    if (!p->tc) build_tc(p);
+    if (p->tch_tune.row_tile != tune.row_tile || p->tch_tune.x_chunk != tune.x_chunk) tc_tables(p, tune);
+  } catch (...) {
+    release_tc(p);
+    throw;
+  }
   return {&p->tch, p->serial, p->xin, p->yout, p->n, p->flops};
 }
 
@@ -1506,10 +1498,9 @@ void Engine::run_matvec(MatvecPlan* p, const double* x, double* y, bool tc) {
     if (y != p->yout) dev_d2d(y, p->yout, sizeof(double) * p->n, stream_);
     st_.tc_matvecs += 1;
     st_.tc_flops += p->flops;
-    st_.tc_phase1_flops += p->flops1;
-    st_.tc_phase2_flops += p->flops2;
-    st_.tc_phase1_bytes += p->tc_bytes1;
-    st_.tc_phase2_bytes += p->tc_bytes2;
+    st_.tc_phase2_flops += p->flops;
+    st_.tc_phase1_bytes += 16.0 * (double)p->n;
+    st_.tc_phase2_bytes += p->tc_alg_bytes;
     st_.matvecs += 1;
     st_.matvec_flops += p->flops;
     st_.last_matvec_flops = p->flops;

@@ -177,7 +177,7 @@ class Engine {
   // serial (changes whenever the tables are rebuilt), its input / output buffers and
   // flops.  The tables stay valid until the MPS or the site of the engine changes.
   struct TcView { const TcHost* host; uint64_t serial; double* x; double* y; int64_t n; double flops; };
-  TcView prepare_tc(int i);
+  TcView prepare_tc(int i, TcTune tune);
   uint64_t tc_serial(int i) const;
   void set_tune(TcTune t) { tune_ = t; }
   const std::vector<int>& hist_D() const { return hist_D_; }
@@ -200,6 +200,7 @@ class Engine {
   void group_left(int i, std::vector<CombOp>& out, double** scratch, int64_t* scratch_n);
   void group_right(int i, std::vector<CombOp>& out, double** scratch, int64_t* scratch_n);
   void build_tc(MatvecPlan* p);
+  void tc_tables(MatvecPlan* p, TcTune tune);
   MatvecPlan* plan_matvec(int i);
   void free_plan(MatvecPlan* p);
   void release_tc(MatvecPlan* p);  // frees the tensor-core tables of a plan
@@ -262,7 +263,7 @@ class Engine {
   bool ev_tc_ = false;
   int precision_ = 0;
   int refine_iters_ = 0;  // FP64 finishing iterations in mixed mode (0: up to the cap)
-  TcTune tune_;           // unit sizes of the tensor-core matvec
+  TcTune tune_;           // tile shape of the tensor-core matvec
   // per schedule instruction of the last solve: D, lowest energy and largest discarded
   // weight of its last macro-iteration (the data of the extrapolation, Sec. 4.3)
   std::vector<int> hist_D_;

@@ -1,34 +1,36 @@
 // Mixed-precision H_eff matvec on the 5th-generation tensor cores (tcgen05, sm_103a).
 //
-// Data are FP32 (operators mirrored once per two-site problem, x converted per matvec);
-// every block product runs on the tensor cores in TF32 with each operand split into a
-// TF32 head and tail (v = hi + lo) and the three leading products hi*hi + hi*lo + lo*hi
-// accumulated in FP32 in tensor memory (about 2^-21 relative per product, the accuracy
-// of FP32 data).  Operands are staged by the threads into shared memory in the canonical
-// K-major layout without swizzle: core matrices of 8 rows x 16 bytes, 128 bytes apart
-// along K (LBO) and 1024 bytes apart along M/N (SBO) for a 32-column K chunk.  A thread
-// moves one core-matrix row at a time: a float4 from global memory (every FP32 matrix
-// has 16-byte aligned rows padded with zeros), split into two float4 stores.  The
-// blocks are small and irregular (reduced symmetry blocks of a few to a few hundred
-// rows) and are gathered and split while staging, so tensor maps do not apply.
+// The effective Hamiltonian of Eq. 9, written with the renormalised and complementary
+// operators of Sec. 2.5, acts on an output block y_X' as a sum of terms
+//   y_X' += C W,   W = sum_s coef_s x_s D_s^T,
+// C a left-operator block, x_s blocks of the two-site vector and D_s right-operator
+// blocks (the combined operators of the left / right environments).  One CTA owns one
+// output tile (up to 128 rows x 128 columns of one block, so nothing is added with
+// atomics and the summation order is fixed) and runs all of its terms:
+//   product 1: W^T = D_s x_s^T per source, into its own tensor-memory accumulator
+//              (M = 128 output columns, N = x rows of the term, K = the right sector);
+//   the converter warps add coef_s times each accumulator into FP32 registers, split the
+//              sum into TF32 head and tail and store it as the A operand of
+//   product 2: y^T += W^T C^T (M = 128 output columns, N = output rows, K = x rows),
+//              restarted per term and drained into FP32 registers (the tensor core's own
+//              FP32 accumulation loses accuracy over long runs of products).
+// Every product uses split TF32: v = hi + lo with hi = rna_tf32(v), lo = rna_tf32(v - hi),
+// and the three leading products hi*hi + hi*lo + lo*hi (about 2^-21 relative).
 //
-// Phase 1 (k_tc_phase1): for a right sector c the x blocks with that sector form a stack
-// (rows = sum of their left dimensions, columns = d_c).  Every right-operator block D
-// with column sector c gives Z = stack D^T, written transposed (Zt, column-major) so
-// that phase 2 reads it K-contiguously.  A CTA keeps a 128-row tile of the stack in
-// shared memory and runs through packs of operator blocks placed side by side in the
-// MMA's N dimension (up to 128 columns); two accumulators in tensor memory alternate so
-// that the epilogue of one pack overlaps the products of the next.
+// Operands live in global memory already split and tiled in the K-major core-matrix
+// order the MMA reads (see device.hpp), so a warp-specialised pipeline moves them with
+// cp.async.bulk into a shared-memory ring (one producer thread, completion counted in
+// bytes on mbarriers) and a single thread issues the MMAs; only W^T passes through
+// registers.  The shared-memory operand descriptors are K-major without swizzle: core
+// matrices of 8 rows x 16 bytes, 128 bytes apart along K (LBO) and 1024 bytes apart
+// along M/N (SBO), for 32-column chunks.
 //
-// Phase 2 (k_tc_phase2): for an output block of y and a run of its tasks, each task
-// stages a left-operator block C (or the identity) as A and W^T = sum coef Zt (the
-// complementary-operator sums) as B, and accumulates C W in tensor memory; the tile is
-// added to y (FP64) with atomics, since a block's tasks may be split over several CTAs.
-//
-// Every wait on an MMA-completion barrier is bounded; on timeout the CTA records an
-// error, stops issuing work, frees its tensor memory and returns.
+// Every wait is bounded: a CTA that gives up records an error, stops issuing work, waits
+// (bounded) for its own copies and products in flight, frees its tensor memory and
+// returns; the host reads and clears the error flag.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <stdexcept>
 #include <string>
@@ -40,11 +42,24 @@ namespace dmrg {
 
 namespace {
 
-constexpr int kThreads = 256;               // 8 warps: all stage, warps w and w+4 share TMEM lanes
-constexpr long long kSpinLimit = 1ll << 22; // polls of an mbarrier before giving up (seconds)
-constexpr int kTileF = 128 * 32;            // floats of a 128-row x 32-column operand tile
+constexpr long long kSpinLimit = 1ll << 22;  // polls of an mbarrier before giving up (seconds)
+constexpr int kTF = 128 * 32;                // floats of a 128-row x 32-column tile (16 KB)
+constexpr int kS1 = 2;                       // slots of the product-1 operand ring
+constexpr int kWBuf = 4;                     // W^T accumulators (64 tensor-memory columns each)
+constexpr int kYCol = kWBuf * 64;            // first tensor-memory column of the y^T accumulator
+constexpr int kTmemCols = 512;
+// shared memory (floats): product-1 slot = D tile hi, lo (128 rows) and x tile hi, lo
+// (64 rows); product 2: C tiles (128 rows x 2 chunks, hi, lo) and W^T tiles (same)
+constexpr int kS1F = 2 * kTF + kTF;
+constexpr int kB2F = 4 * kTF;
+constexpr int kA2F = 4 * kTF;
+constexpr int kSmemF = kS1 * kS1F + kB2F + kA2F;
+constexpr int kProducerWarp = 0, kMmaWarp = 1, kConvWarps = 8;
+constexpr int kMvThreads = (2 + kConvWarps) * 32;
+constexpr int kConvThreads = kConvWarps * 32;
 
 __device__ int g_tc_error = 0;
+__device__ int g_tc_inject = 0;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -56,7 +71,7 @@ __device__ __forceinline__ float tf32_round(float x) {
   return __uint_as_float(r);
 }
 
-// float index of element (row, k) in a K-major no-swizzle tile with 32 columns
+// float index of element (row, k) of a K-major no-swizzle tile with 32 columns
 __device__ __forceinline__ int kmo(int row, int k) {
   return (row >> 3) * 256 + (k >> 2) * 32 + (row & 7) * 4 + (k & 3);
 }
@@ -80,14 +95,14 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, 
       "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
-// the three split products of one 32-column K chunk (kpad / 8 steps of K = 8)
-__device__ __forceinline__ void mma_chunk(uint32_t tmem, const float* Ah, const float* Al,
-                                          const float* Bh, const float* Bl, int kpad, uint32_t idesc,
-                                          bool first) {
+// the three split products of one 32-column K chunk (kpad / 8 steps of K = 8); the
+// first product restarts the accumulator when `fresh`
+__device__ __forceinline__ void mma_chunk(uint32_t tmem, const float* Ah, const float* Al, const float* Bh,
+                                          const float* Bl, int kpad, uint32_t idesc, bool fresh) {
   const uint32_t ah = smem_u32(Ah), al = smem_u32(Al), bh = smem_u32(Bh), bl = smem_u32(Bl);
   for (int st = 0; st < kpad / 8; ++st) {
     const uint32_t ko = st * 256;  // 8 columns = two core matrices along K
-    mma_tf32(tmem, smem_desc(ah + ko), smem_desc(bh + ko), idesc, (first && st == 0) ? 0u : 1u);
+    mma_tf32(tmem, smem_desc(ah + ko), smem_desc(bh + ko), idesc, (fresh && st == 0) ? 0u : 1u);
     mma_tf32(tmem, smem_desc(ah + ko), smem_desc(bl + ko), idesc, 1u);
     mma_tf32(tmem, smem_desc(al + ko), smem_desc(bh + ko), idesc, 1u);
   }
@@ -99,23 +114,56 @@ __device__ __forceinline__ void mma_commit(uint64_t* mbar) {
                : "memory");
 }
 
-__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
-  const uint32_t a = smem_u32(mbar);
-  for (long long it = 0; it < kSpinLimit; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.b32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(done)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (done) return true;
+__device__ __forceinline__ void mbar_init_n(uint64_t* mbar, int n) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(n));
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(mbar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t* mbar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.b32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(done)
+      : "r"(smem_u32(mbar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// bounded wait that also gives up once another thread has flagged an abort; on its own
+// timeout it records the error and flags the abort
+__device__ __forceinline__ bool wait_or_abort(uint64_t* mbar, uint32_t parity, volatile int* abort_flag,
+                                              long long limit = kSpinLimit) {
+  for (long long it = 0; it < limit; ++it) {
+    if (mbar_test(mbar, parity)) return true;
+    if ((it & 1023) == 1023 && *abort_flag) return false;
   }
+  atomicExch(&g_tc_error, 1);
+  *abort_flag = 1;
   return false;
 }
 
-__device__ __forceinline__ void mbar_init(uint64_t* mbar) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
+// bounded wait that ignores the abort flag (draining work in flight before exit)
+__device__ __forceinline__ void wait_drain(uint64_t* mbar, uint32_t parity) {
+  for (long long it = 0; it < kSpinLimit; ++it)
+    if (mbar_test(mbar, parity)) return;
+  atomicExch(&g_tc_error, 1);
+}
+
+// global -> shared bulk copy counted on mbar (16-byte aligned, size a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(mbar))
+               : "memory");
 }
 
 __device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t cols) {
@@ -141,585 +189,272 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-__device__ __forceinline__ float4 ldg4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+struct Bars {
+  uint64_t s1_full[kS1], s1_empty[kS1];
+  uint64_t b2_full, b2_empty;
+  uint64_t w_full[kWBuf], w_empty[kWBuf];
+  uint64_t a2_full, mma2_done;
+  uint64_t drain, never;
+};
 
-__device__ __forceinline__ void put_split4(float* hi, float* lo, int off, float4 v) {
-  float4 h, l;
-  h.x = tf32_round(v.x);
-  h.y = tf32_round(v.y);
-  h.z = tf32_round(v.z);
-  h.w = tf32_round(v.w);
-  l.x = tf32_round(v.x - h.x);
-  l.y = tf32_round(v.y - h.y);
-  l.z = tf32_round(v.z - h.z);
-  l.w = tf32_round(v.w - h.w);
-  *reinterpret_cast<float4*>(hi + off) = h;
-  *reinterpret_cast<float4*>(lo + off) = l;
-}
-
-__device__ __forceinline__ float4 fma4(float a, float4 x, float4 y) {
-  return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
-}
-
-// Work item e of a tile with nrows rows: 64 items per 8-row group, item = (row group,
-// 4-column group kb, row r7); 32 consecutive items fill 512 consecutive bytes of the tile.
-struct Item { int r, kb; };
-__device__ __forceinline__ Item item(int e) { return {(e >> 6) * 8 + (e & 7), (e >> 3) & 7}; }
-
-// Stage rows [0, nrows) of a 32-column chunk into hi / lo tiles from row-major FP32 data:
-// tile(row_base + r, k) = a X[r ld + k0 + k] for the first kval4 groups of 4 columns,
-// zero for the following groups up to nkg (kpad / 4).  Columns past K inside the last
-// group read the zero padding of X.  Threads t0, t0 + nthr, ... of the caller; each
-// thread issues the loads of up to four items before it uses any of them.
-__device__ __forceinline__ void stage4(float* hi, float* lo, int row_base, int nrows, int nkg, int kval4,
-                                       const float* __restrict__ X, int ld, int k0, float a, int t0,
-                                       int nthr) {
-  const int ne = ((nrows + 7) >> 3) * 64;
-  if (ne <= nthr) {  // one item per thread at most
-    if (t0 >= ne) return;
-    const Item it = item(t0);
-    if (it.r >= nrows || it.kb >= nkg) return;
-    float4 v = it.kb < kval4 ? ldg4(X + (size_t)it.r * ld + k0 + it.kb * 4) : make_float4(0.f, 0.f, 0.f, 0.f);
-    v.x *= a;
-    v.y *= a;
-    v.z *= a;
-    v.w *= a;
-    put_split4(hi, lo, kmo(row_base + it.r, it.kb * 4), v);
-    return;
-  }
-  for (int e0 = 0; e0 < ne; e0 += 4 * nthr) {
-    float4 v[4];
-    Item it[4];
-    bool st[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int e = e0 + t0 + i * nthr;
-      it[i] = item(e);
-      st[i] = e < ne && it[i].r < nrows && it[i].kb < nkg;
-      v[i] = (st[i] && it[i].kb < kval4) ? ldg4(X + (size_t)it[i].r * ld + k0 + it[i].kb * 4)
-                                         : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-      if (st[i]) {
-        v[i].x *= a;
-        v[i].y *= a;
-        v[i].z *= a;
-        v[i].w *= a;
-        put_split4(hi, lo, kmo(row_base + it[i].r, it[i].kb * 4), v[i]);
-      }
-  }
-}
-
-// A = alpha * identity rows row0 .. row0 + nrows - 1 of a K x K identity, columns k0 ..
-__device__ __forceinline__ void stage4_identity(float* hi, float* lo, int nrows, int nkg, int kvalid, int row0,
-                                                int k0, float alpha, int t0, int nthr) {
-  const int ne = ((nrows + 7) >> 3) * 64;
-  for (int e = t0; e < ne; e += nthr) {
-    const Item it = item(e);
-    if (it.r >= nrows || it.kb >= nkg) continue;
-    const int d = row0 + it.r - k0 - it.kb * 4;  // column of the diagonal inside the group
-    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (d >= 0 && d < 4 && k0 + it.kb * 4 + d < k0 + kvalid) (&v.x)[d] = alpha;
-    put_split4(hi, lo, kmo(it.r, it.kb * 4), v);
-  }
-}
-
-// B = W^T rows col0 .. col0 + nrows - 1: sum over sources of coef * z[(col0 + j) ldz + k0 + k].
-// Up to four items per thread; the loads of two sources are issued before their sums.
-__device__ __forceinline__ void stage4_wsum(float* hi, float* lo, int nrows, int nkg, int kval4,
-                                            const Tc2Src* __restrict__ srcs, int s_begin, int s_end, int col0,
-                                            int k0, int t0, int nthr) {
-  const int ne = ((nrows + 7) >> 3) * 64;
-  for (int e0 = 0; e0 < ne; e0 += 4 * nthr) {
-    float4 acc[4];
-    Item it[4];
-    bool ld[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int e = e0 + t0 + i * nthr;
-      it[i] = item(e);
-      if (e >= ne) it[i].r = 1 << 20;
-      ld[i] = it[i].r < nrows && it[i].kb < kval4;
-      acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    for (int si = s_begin; si < s_end; si += 2) {
-      const bool two = si + 1 < s_end;
-      const Tc2Src S0 = srcs[si];
-      const Tc2Src S1 = two ? srcs[si + 1] : S0;
-      const float* z0 = S0.z + (size_t)col0 * S0.ldz + k0;
-      const float* z1 = S1.z + (size_t)col0 * S1.ldz + k0;
-      float4 v0[4], v1[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        v0[i] = ld[i] ? ldg4(z0 + (size_t)it[i].r * S0.ldz + it[i].kb * 4) : make_float4(0.f, 0.f, 0.f, 0.f);
-        v1[i] = (ld[i] && two) ? ldg4(z1 + (size_t)it[i].r * S1.ldz + it[i].kb * 4) : make_float4(0.f, 0.f, 0.f, 0.f);
-      }
-#pragma unroll
-      for (int i = 0; i < 4; ++i) acc[i] = fma4(S1.coef, v1[i], fma4(S0.coef, v0[i], acc[i]));
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-      if (it[i].r < nrows && it[i].kb < nkg) put_split4(hi, lo, kmo(it[i].r, it[i].kb * 4), acc[i]);
-  }
-}
-
-// ------------------------------------------------------------------ phase 1
-
-constexpr int kMaxPackEntries = 16;  // pack columns are padded per entry to multiples of 8
-
-// shared-memory floats: one-chunk units keep the stack tile (hi, lo) and two B buffers;
-// multi-chunk units double-buffer A and B together
-template <bool kOne>
-constexpr int p1_smem_floats() { return kOne ? 6 * kTileF : 8 * kTileF; }
-
-template <bool kOne>
-__global__ void __launch_bounds__(kThreads, 1)
-    k_tc_phase1(const Tc1Unit* __restrict__ units, const Tc1Pack* __restrict__ packs,
-                const Tc1Entry* __restrict__ ents) {
+__global__ void __launch_bounds__(kMvThreads, 1)
+    k_tc_matvec(const TfTile* __restrict__ tiles, const TfTask* __restrict__ tasks, const TfSrc* __restrict__ srcs) {
   extern __shared__ unsigned char smem_dyn[];
-  float* sm = (float*)(((uintptr_t)smem_dyn + 127) & ~(uintptr_t)127);
-  __shared__ __align__(8) uint64_t mbar_buf[2];
-  __shared__ __align__(8) uint64_t mbar_acc[2];
-  __shared__ uint32_t tmem_slot;
-  __shared__ int abort_flag;
-  __shared__ Tc1Entry pent[2][kMaxPackEntries];
-  __shared__ signed char pgrp[2][16];  // entry of each 8-column group, -1 = none
-  __shared__ int pn[2];
-
-  const Tc1Unit u = units[blockIdx.x];
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  if (warp == 0) tmem_alloc(&tmem_slot, 256);
-  if (tid == 0) {
-    mbar_init(&mbar_buf[0]);
-    mbar_init(&mbar_buf[1]);
-    mbar_init(&mbar_acc[0]);
-    mbar_init(&mbar_acc[1]);
-    asm volatile("fence.mbarrier_init.release.cluster;");
-    abort_flag = 0;
-  }
-  const int nch = (u.K + 31) >> 5;
-  if (kOne) {
-    const int kpad = (u.K + 7) & ~7;
-    stage4(sm, sm + kTileF, 0, u.rows, kpad >> 2, (u.K + 3) >> 2, u.A, u.lda, 0, 1.0f, tid, kThreads);
-  }
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;");
-  const uint32_t tmem = tmem_slot;
-  uint32_t ph_buf[2] = {0, 0}, ph_acc[2] = {0, 0};
-
-  // epilogue of pack slot a: accumulator columns -> Zt (column-major, coalesced along rows)
-  auto epilogue = [&](int a) {
-    if (tid == 0 && !mbar_wait(&mbar_acc[a], ph_acc[a])) {
-      atomicExch(&g_tc_error, 1);
-      abort_flag = 1;
-    }
-    ph_acc[a] ^= 1;
-    __syncthreads();
-    if (abort_flag) return;
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    const int q = warp & 3, h = warp >> 2;
-    const int r = q * 32 + lane;
-    const int n16 = (pn[a] + 15) & ~15;
-    for (int c0 = h * 16; c0 < n16; c0 += 32) {
-      float v[16];
-      tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * 128 + c0), v);
-#pragma unroll
-      for (int g8 = 0; g8 < 2; ++g8) {
-        const int e = pgrp[a][(c0 >> 3) + g8];
-        if (e < 0 || r >= u.rows) continue;
-        const Tc1Entry& E = pent[a][e];
-        const int j0 = c0 + 8 * g8 - E.start, nc = E.ncols, ldz = E.ldz;
-        float* zp = E.zt + (size_t)j0 * ldz + u.row0 + r;
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-          if (j0 + j < nc) zp[(size_t)j * ldz] = v[8 * g8 + j];
-      }
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-  };
-
-  int s = 0;
-  const int npk = u.p_end - u.p_begin;
-  for (int pi = 0; pi < npk && !abort_flag; ++pi) {
-    const Tc1Pack P = packs[u.p_begin + pi];
-    const int slot = pi & 1;
-    const int nent = P.e_end - P.e_begin;
-    if (tid < nent) pent[slot][tid] = ents[P.e_begin + tid];
-    if (tid == 0) pn[slot] = P.n;
-    for (int ch = 0; ch < nch; ++ch, ++s) {
-      const int b = s & 1;
-      if (s >= 2) {
-        if (tid == 0 && !mbar_wait(&mbar_buf[b], ph_buf[b])) {
-          atomicExch(&g_tc_error, 1);
-          abort_flag = 1;
-        }
-        ph_buf[b] ^= 1;
-      }
-      __syncthreads();
-      if (abort_flag) break;
-      if (ch == 0 && tid < 16) {
-        int g = -1;
-        for (int e = 0; e < nent; ++e) {
-          const int st = pent[slot][e].start, en = st + ((pent[slot][e].ncols + 7) & ~7);
-          if (tid * 8 >= st && tid * 8 < en) g = e;
-        }
-        pgrp[slot][tid] = (signed char)g;
-      }
-      const int k0 = ch * 32, kvalid = min(32, u.K - k0), kpad = (kvalid + 7) & ~7;
-      const int nkg = kpad >> 2, kval4 = (kvalid + 3) >> 2;
-      float* Ah = kOne ? sm : sm + b * 4 * kTileF;
-      float* Al = Ah + kTileF;
-      float* Bh = kOne ? sm + (2 + 2 * b) * kTileF : Ah + 2 * kTileF;
-      float* Bl = Bh + kTileF;
-      if (!kOne) stage4(Ah, Al, 0, u.rows, nkg, kval4, u.A, u.lda, k0, 1.0f, tid, kThreads);
-      for (int e = 0; e < nent; ++e) {
-        const Tc1Entry& E = pent[slot][e];
-        stage4(Bh, Bl, E.start, E.ncols, nkg, kval4, E.D, E.ldd, k0, E.alpha, tid, kThreads);
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncthreads();
-      if (tid == 0) {
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        mma_chunk(tmem + (uint32_t)(slot * 128), Ah, Al, Bh, Bl, kpad, idesc_tf32((P.n + 15) & ~15), ch == 0);
-        mma_commit(&mbar_buf[b]);
-        if (ch == nch - 1) mma_commit(&mbar_acc[slot]);
-      }
-    }
-    if (abort_flag) break;
-    if (pi >= 1) epilogue((pi - 1) & 1);
-  }
-  if (!abort_flag && npk > 0) epilogue((npk - 1) & 1);
-  asm volatile("tcgen05.fence::before_thread_sync;");
-  __syncthreads();
-  if (warp == 0) tmem_free(tmem, 256);
-}
-
-// ------------------------------------------------------------------ phase 2
-
-// The tensor core's FP32 accumulation loses accuracy over long runs of products (the
-// error of a 48-task run measured ~10x that of a 2-task run), so phase 2 adds its
-// accumulator into FP32 registers every kSegSteps steps and restarts it.
-constexpr int kSegSteps = 2;
-
-// Output tiles of more than 32 rows: all 8 warps stage each step, double-buffered, and
-// drain the accumulator at segment ends.
-constexpr int kP2BufF = 3 * kTileF;  // A hi, A lo (128 rows), B hi, B lo (64 rows)
-
-__global__ void __launch_bounds__(kThreads, 1)
-    k_tc_phase2(const Tc2Unit* __restrict__ units, const Tc2Task* __restrict__ tasks,
-                const Tc2Src* __restrict__ srcs) {
-  extern __shared__ unsigned char smem_dyn[];
-  float* sm = (float*)(((uintptr_t)smem_dyn + 127) & ~(uintptr_t)127);
-  __shared__ __align__(8) uint64_t mbar_buf[2];
-  __shared__ __align__(8) uint64_t mbar_seg;
-  __shared__ uint32_t tmem_slot;
-  __shared__ int abort_flag;
-
-  const Tc2Unit u = units[blockIdx.x];
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int mv = min(128, u.m - u.row0), nv = min(64, u.n - u.col0);
-  const int n16 = (nv + 15) & ~15;
-  const int q = warp & 3, h = warp >> 2;
-  if (warp == 0) tmem_alloc(&tmem_slot, 64);
-  if (tid == 0) {
-    mbar_init(&mbar_buf[0]);
-    mbar_init(&mbar_buf[1]);
-    mbar_init(&mbar_seg);
-    asm volatile("fence.mbarrier_init.release.cluster;");
-    abort_flag = 0;
-  }
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;");
-  const uint32_t tmem = tmem_slot;
-  const uint32_t idesc = idesc_tf32(n16);
-  uint32_t ph_buf[2] = {0, 0}, ph_seg = 0;
-  float acc[2][16];  // this thread's row, columns h*16 + 32*i + j, summed over segments
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 16; ++j) acc[i][j] = 0.0f;
-  int nsteps = 0;
-  for (int t = u.t_begin; t < u.t_end; ++t) nsteps += (tasks[t].K + 31) >> 5;
-  int s = 0, seg_first = 0;
-  for (int t = u.t_begin; t < u.t_end && !abort_flag; ++t) {
-    const Tc2Task T = tasks[t];
-    const int nch = (T.K + 31) >> 5;
-    for (int ch = 0; ch < nch; ++ch, ++s) {
-      const int b = s & 1;
-      if (s >= 2) {  // the MMA of step s - 2 must be done with this buffer
-        if (tid == 0 && !mbar_wait(&mbar_buf[b], ph_buf[b])) {
-          atomicExch(&g_tc_error, 1);
-          abort_flag = 1;
-        }
-        ph_buf[b] ^= 1;
-      }
-      __syncthreads();
-      if (abort_flag) break;
-      const int k0 = ch * 32, kvalid = min(32, T.K - k0), kpad = (kvalid + 7) & ~7;
-      const int nkg = kpad >> 2, kval4 = (kvalid + 3) >> 2;
-      float* Ah = sm + b * kP2BufF;
-      float* Al = Ah + kTileF;
-      float* Bh = Al + kTileF;
-      float* Bl = Bh + kTileF / 2;
-      if (T.C) stage4(Ah, Al, 0, mv, nkg, kval4, T.C + (size_t)u.row0 * T.ldc, T.ldc, k0, T.alpha, tid, kThreads);
-      else stage4_identity(Ah, Al, mv, nkg, kvalid, u.row0, k0, T.alpha, tid, kThreads);
-      stage4_wsum(Bh, Bl, nv, nkg, kval4, srcs, T.s_begin, T.s_end, u.col0, k0, tid, kThreads);
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncthreads();
-      const bool seg_end = (s + 1 - seg_first == kSegSteps) || (s + 1 == nsteps);
-      if (tid == 0) {
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        mma_chunk(tmem, Ah, Al, Bh, Bl, kpad, idesc, s == seg_first);
-        mma_commit(&mbar_buf[b]);
-        if (seg_end) mma_commit(&mbar_seg);
-      }
-      if (seg_end) {
-        // promote the segment's FP32 accumulator to the register sums, then restart it
-        if (tid == 0 && !mbar_wait(&mbar_seg, ph_seg)) {
-          atomicExch(&g_tc_error, 1);
-          abort_flag = 1;
-        }
-        ph_seg ^= 1;
-        __syncthreads();
-        if (abort_flag) break;
-        asm volatile("tcgen05.fence::after_thread_sync;");
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-          const int c0 = h * 16 + 32 * i;
-          if (c0 < n16) {
-            float v[16];
-            tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
-#pragma unroll
-            for (int j = 0; j < 16; ++j) acc[i][j] += v[j];
-          }
-        }
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        seg_first = s + 1;
-      }
-    }
-  }
-  __syncthreads();
-  const int r = q * 32 + lane;
-  if (s > 0 && !abort_flag && r < mv) {
-    double* yr = u.y + (size_t)(u.row0 + r) * u.ldy + u.col0;
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int c = h * 16 + 32 * i + j;
-        if (c < nv) atomicAdd(yr + c, (double)acc[i][j]);
-      }
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;");
-  __syncthreads();
-  if (warp == 0) tmem_free(tmem, 64);
-}
-
-// Phase 2 for output tiles of at most 32 rows (the common case of small symmetry
-// blocks), as a warp-specialised pipeline: four producer groups of two warps each own
-// one shared-memory stage and fill it for every fourth step (a step is one 32-column K
-// chunk of one task); one thread issues the MMAs of the steps in order and releases
-// each stage with tcgen05.commit.  A stage holds A = 32 rows of C (hi, lo) and B = 64
-// rows of W^T (hi, lo); the MMA still reads 128 rows of A, and rows 32..127 fall on the
-// rest of the same stage: they only produce accumulator rows that are never read.
-constexpr int kGroups = 4, kGroupThreads = 64;
-constexpr int kAcc = 4;  // TMEM accumulators (64 columns each) of the MMA warp's segments
-constexpr int kUnitTasks = 128, kUnitSrcs = 384;  // descriptors held in shared memory
-constexpr int kP2sThreads = kGroups * kGroupThreads + 32;
-constexpr int kSA = 32 * 32, kSB = 64 * 32;   // floats of an A (32-row) / B (64-row) tile
-constexpr int kP2sStageF = 2 * kSA + 2 * kSB;  // 24 KB: the 16 KB A footprint stays inside
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(mbar)) : "memory");
-}
-
-__device__ __forceinline__ void mbar_init_n(uint64_t* mbar, int n) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(n));
-}
-
-// bounded wait that also gives up once another thread has flagged an abort
-__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* mbar, uint32_t parity, volatile int* abort_flag) {
-  const uint32_t a = smem_u32(mbar);
-  for (long long it = 0; it < kSpinLimit; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.b32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(done)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (done) return true;
-    if ((it & 1023) == 1023 && *abort_flag) return false;
-  }
-  atomicExch(&g_tc_error, 1);
-  *abort_flag = 1;
-  return false;
-}
-
-__global__ void __launch_bounds__(kP2sThreads, 2)
-    k_tc_phase2s(const Tc2Unit* __restrict__ units, const Tc2Task* __restrict__ tasks,
-                 const Tc2Src* __restrict__ srcs) {
-  extern __shared__ unsigned char smem_dyn[];
-  float* sm = (float*)(((uintptr_t)smem_dyn + 127) & ~(uintptr_t)127);
-  __shared__ __align__(8) uint64_t full[kGroups];
-  __shared__ __align__(8) uint64_t empty[kGroups];
-  __shared__ __align__(8) uint64_t accf[kAcc];
+  float* sm = (float*)(((uintptr_t)smem_dyn + 1023) & ~(uintptr_t)1023);
+  float* s1 = sm;                      // kS1 slots: D hi, D lo (kTF each), x hi, x lo (kTF / 2 each)
+  float* b2 = sm + kS1 * kS1F;         // C: chunk 0 hi, lo, chunk 1 hi, lo
+  float* a2 = b2 + kB2F;               // W^T: chunk 0 hi, lo, chunk 1 hi, lo
+  __shared__ __align__(8) Bars bar;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
-  // the unit's task and source descriptors, loaded once (the loops would otherwise put
-  // a dependent global load in front of every step)
-  __shared__ Tc2Task stask[kUnitTasks];
-  __shared__ Tc2Src ssrc[kUnitSrcs];
 
-  const Tc2Unit u = units[blockIdx.x];
+  const TfTile tile = tiles[blockIdx.x];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int mv = u.m - u.row0, nv = min(64, u.n - u.col0);  // mv <= 32 by construction
-  const int n16 = (nv + 15) & ~15;
-  const int ntask = u.t_end - u.t_begin;  // <= kUnitTasks by construction
-  const int s0 = tasks[u.t_begin].s_begin, nsrc = tasks[u.t_end - 1].s_end - s0;
-  const Tc2Src* S = nsrc <= kUnitSrcs ? ssrc : srcs + s0;  // sources relative to s0
-  for (int k = tid; k < ntask; k += kP2sThreads) stask[k] = tasks[u.t_begin + k];
-  if (nsrc <= kUnitSrcs)
-    for (int k = tid; k < nsrc; k += kP2sThreads) ssrc[k] = srcs[s0 + k];
-  if (warp == kGroups * 2) tmem_alloc(&tmem_slot, 64 * kAcc);
+  const int T = tile.t_end - tile.t_begin;
+  if (warp == kMmaWarp) tmem_alloc(&tmem_slot, kTmemCols);
   if (tid == 0) {
-    for (int g = 0; g < kGroups; ++g) {
-      mbar_init_n(&full[g], kGroupThreads);
-      mbar_init_n(&empty[g], 1);
+    for (int s = 0; s < kS1; ++s) {
+      mbar_init_n(&bar.s1_full[s], 1);
+      mbar_init_n(&bar.s1_empty[s], 1);
     }
-    for (int a = 0; a < kAcc; ++a) mbar_init_n(&accf[a], 1);
+    mbar_init_n(&bar.b2_full, 1);
+    mbar_init_n(&bar.b2_empty, 1);
+    for (int q = 0; q < kWBuf; ++q) {
+      mbar_init_n(&bar.w_full[q], 1);
+      mbar_init_n(&bar.w_empty[q], kConvThreads);
+    }
+    mbar_init_n(&bar.a2_full, kConvThreads);
+    mbar_init_n(&bar.mma2_done, 1);
+    mbar_init_n(&bar.drain, 1);
+    mbar_init_n(&bar.never, 1);
     asm volatile("fence.mbarrier_init.release.cluster;");
     abort_flag = 0;
   }
+  // stale shared memory past the rows a copy fills must be finite: it meets zeros in
+  // padded products
+  for (int e = tid * 4; e < kSmemF; e += kMvThreads * 4)
+    *reinterpret_cast<float4*>(sm + e) = make_float4(0.f, 0.f, 0.f, 0.f);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_slot;
+  if (tid == kMmaWarp * 32 && g_tc_inject) {
+    // test hook: a wait on a barrier that nothing completes, with a short limit
+    wait_or_abort(&bar.never, 0, &abort_flag, 4096);
+  }
+  __syncthreads();
 
-  if (warp < kGroups * 2) {
-    // ---- producers: group g fills stage g for steps s = g, g + 4, ...
-    const int g = warp >> 1, gt = tid & (kGroupThreads - 1);
-    float* Ah = sm + g * kP2sStageF;
-    float* Al = Ah + kSA;
-    float* Bh = Al + kSA;
-    float* Bl = Bh + kSB;
-    int s = 0;
-    for (int t = 0; t < ntask && !abort_flag; ++t) {
-      const Tc2Task& T = stask[t];
-      const int nch = (T.K + 31) >> 5;
-      for (int ch = 0; ch < nch; ++ch, ++s) {
-        if ((s & (kGroups - 1)) != g) continue;
-        const int k = s / kGroups;  // fill number of this stage
-        if (k > 0 && !mbar_wait_or_abort(&empty[g], (k - 1) & 1, &abort_flag)) break;
-        const int k0 = ch * 32, kvalid = min(32, T.K - k0), kpad = (kvalid + 7) & ~7;
-        const int nkg = kpad >> 2, kval4 = (kvalid + 3) >> 2;
-        if (T.C) stage4(Ah, Al, 0, mv, nkg, kval4, T.C + (size_t)u.row0 * T.ldc, T.ldc, k0, T.alpha, gt, kGroupThreads);
-        else stage4_identity(Ah, Al, mv, nkg, kvalid, u.row0, k0, T.alpha, gt, kGroupThreads);
-        stage4_wsum(Bh, Bl, nv, nkg, kval4, S, T.s_begin - s0, T.s_end - s0, u.col0, k0, gt, kGroupThreads);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_arrive(&full[g]);
+  const int nvg = (tile.nv + 7) >> 3, mg = (tile.m + 7) >> 3;
+  if (warp == kProducerWarp) {
+    // ---- producer: bulk copies in the order the MMA thread consumes them
+    if (lane == 0 && !abort_flag) {
+      int step = 0, b2_loads = 0;
+      auto load_b2 = [&](int u) -> bool {
+        if (u >= 1 && !wait_or_abort(&bar.b2_empty, (u - 1) & 1, &abort_flag)) return false;
+        const TfTask tk = tasks[tile.t_begin + u];
+        const int nch = (tk.kdl + 31) >> 5;
+        const uint32_t bytes = 2u * nch * mg * 1024u;
+        mbar_expect_tx(&bar.b2_full, bytes);
+        for (int c = 0; c < nch; ++c) {
+          const float* src = tk.c + (int64_t)c * tk.c_cs;
+          bulk_g2s(b2 + (2 * c) * kTF, src, mg * 1024u, &bar.b2_full);
+          bulk_g2s(b2 + (2 * c + 1) * kTF, src + tile.dlo, mg * 1024u, &bar.b2_full);
+        }
+        ++b2_loads;
+        return true;
+      };
+      bool ok = true;
+      for (int t = 0; t < T && ok; ++t) {
+        const TfTask tk = tasks[tile.t_begin + t];
+        const int kdg = (tk.kdl + 7) >> 3;
+        const uint32_t bytes = 2u * (nvg + kdg) * 1024u;
+        for (int si = tk.s_begin; si < tk.s_end && ok; ++si) {
+          const TfSrc S = srcs[si];
+          for (int kk = 0; kk < S.nkc; ++kk, ++step) {
+            const int slot = step % kS1, use = step / kS1;
+            if (use >= 1 && !wait_or_abort(&bar.s1_empty[slot], (use - 1) & 1, &abort_flag)) { ok = false; break; }
+            float* dst = s1 + slot * kS1F;
+            const float* d = S.d + (int64_t)kk * S.d_cs;
+            const float* x = S.x + (int64_t)kk * S.x_cs;
+            mbar_expect_tx(&bar.s1_full[slot], bytes);
+            bulk_g2s(dst, d, nvg * 1024u, &bar.s1_full[slot]);
+            bulk_g2s(dst + kTF, d + tile.dlo, nvg * 1024u, &bar.s1_full[slot]);
+            bulk_g2s(dst + 2 * kTF, x, kdg * 1024u, &bar.s1_full[slot]);
+            bulk_g2s(dst + 2 * kTF + kTF / 2, x + tile.xlo, kdg * 1024u, &bar.s1_full[slot]);
+          }
+        }
+        if (ok && t >= 1) ok = load_b2(t - 1);
       }
+      if (ok && T >= 1) load_b2(T - 1);
+      // copies still in flight land before the CTA can exit: wait for the last fill of
+      // every slot (a completed phase keeps testing complete while no newer one starts)
+      for (int s = 0; s < kS1; ++s) {
+        const int fills = step / kS1 + (s < step % kS1 ? 1 : 0);
+        if (fills > 0) wait_drain(&bar.s1_full[s], (fills - 1) & 1);
+      }
+      if (b2_loads > 0) wait_drain(&bar.b2_full, (b2_loads - 1) & 1);
+    }
+  } else if (warp == kMmaWarp) {
+    // ---- one thread issues the products; product 2 of term t-1 follows product 1 of t
+    if (lane == 0 && !abort_flag) {
+      int step = 0, src_ctr = 0;
+      const uint32_t idesc2 = idesc_tf32((tile.m + 15) & ~15);
+      bool ok = true;
+      for (int t = 0; t <= T && ok; ++t) {
+        if (t < T) {
+          const TfTask tk = tasks[tile.t_begin + t];
+          const uint32_t idesc1 = idesc_tf32((tk.kdl + 15) & ~15);
+          for (int si = tk.s_begin; si < tk.s_end && ok; ++si, ++src_ctr) {
+            const TfSrc S = srcs[si];
+            const int q = src_ctr % kWBuf, use = src_ctr / kWBuf;
+            if (use >= 1 && !wait_or_abort(&bar.w_empty[q], (use - 1) & 1, &abort_flag)) { ok = false; break; }
+            for (int kk = 0; kk < S.nkc; ++kk, ++step) {
+              const int slot = step % kS1;
+              if (!wait_or_abort(&bar.s1_full[slot], (step / kS1) & 1, &abort_flag)) { ok = false; break; }
+              asm volatile("tcgen05.fence::after_thread_sync;");
+              const int kv = kk == S.nkc - 1 ? S.klast : 32;
+              const float* base = s1 + slot * kS1F;
+              mma_chunk(tmem + (uint32_t)(q * 64), base, base + kTF, base + 2 * kTF, base + 2 * kTF + kTF / 2,
+                        (kv + 7) & ~7, idesc1, kk == 0);
+              mma_commit(&bar.s1_empty[slot]);
+            }
+            if (!ok) break;
+            mma_commit(&bar.w_full[q]);
+          }
+        }
+        if (ok && t >= 1) {
+          const TfTask tp = tasks[tile.t_begin + t - 1];
+          if (!wait_or_abort(&bar.a2_full, (t - 1) & 1, &abort_flag) ||
+              !wait_or_abort(&bar.b2_full, (t - 1) & 1, &abort_flag)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          for (int c = 0; c < 2; ++c) {
+            const int kv = min(32, tp.kdl - 32 * c);
+            if (kv <= 0) break;
+            mma_chunk(tmem + (uint32_t)kYCol, a2 + (2 * c) * kTF, a2 + (2 * c + 1) * kTF, b2 + (2 * c) * kTF,
+                      b2 + (2 * c + 1) * kTF, (kv + 7) & ~7, idesc2, c == 0);
+          }
+          mma_commit(&bar.b2_empty);
+          mma_commit(&bar.mma2_done);
+        }
+      }
+      // every product issued has finished before tensor memory is released
+      mma_commit(&bar.drain);
+      wait_drain(&bar.drain, 0);
     }
   } else {
-    // ---- warp 8: lane 0 issues the MMAs of segment j into accumulator j % kAcc; the
-    // warp adds finished segments (accumulator rows 0..31 = TMEM lanes 0..31) to its
-    // registers kAcc - 1 segments behind, so the tensor core always has work queued
-    const uint32_t idesc = idesc_tf32(n16);
-    float acc[64];
+    // ---- converters: warp w reads tensor-memory lanes 32 (w % 4) .. (its output
+    // columns); half 0 / 1 holds x rows 0..31 / 32..63 of W^T and output rows 0..63 /
+    // 64..127 of y
+    const int quarter = warp & 3, half = (warp - 2) >> 2;
+    const int n = quarter * 32 + lane;
+    const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
+    float yacc[64];
 #pragma unroll
-    for (int i = 0; i < 64; ++i) acc[i] = 0.0f;
-    uint32_t ph_acc[kAcc];
-#pragma unroll
-    for (int a = 0; a < kAcc; ++a) ph_acc[a] = 0;
-    auto drain = [&](int a) {
-      int ok = 1;
-      if (lane == 0) ok = mbar_wait_or_abort(&accf[a], ph_acc[a], &abort_flag);
-      ok = __shfl_sync(0xffffffffu, ok, 0);
-      if (!ok) return;
-      ph_acc[a] ^= 1;
+    for (int j = 0; j < 64; ++j) yacc[j] = 0.0f;
+    auto drain_y = [&]() {
       asm volatile("tcgen05.fence::after_thread_sync;");
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        if (16 * i < n16) {
+        if (64 * half + 16 * i < tile.m) {
           float v[16];
-          tmem_ld16(tmem + (uint32_t)(a * 64 + 16 * i), v);
+          tmem_ld16(lane_base + (uint32_t)(kYCol + 64 * half + 16 * i), v);
 #pragma unroll
-          for (int j = 0; j < 16; ++j) acc[16 * i + j] += v[j];
+          for (int j = 0; j < 16; ++j) yacc[16 * i + j] += v[j];
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;");
-      __syncwarp();
     };
-    int s = 0, seg = 0, in_seg = 0, drained = 0;
-    bool stop = false;
-    for (int t = 0; t < ntask && !stop; ++t) {
-      const int K = stask[t].K;
-      const int nch = (K + 31) >> 5;
-      for (int ch = 0; ch < nch; ++ch, ++s) {
-        const int g = s & (kGroups - 1);
-        if (lane == 0) {
-          if (mbar_wait_or_abort(&full[g], (s / kGroups) & 1, &abort_flag)) {
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            const int kvalid = min(32, K - ch * 32), kpad = (kvalid + 7) & ~7;
-            float* Ah = sm + g * kP2sStageF;
-            mma_chunk(tmem + (uint32_t)((seg % kAcc) * 64), Ah, Ah + kSA, Ah + 2 * kSA, Ah + 2 * kSA + kSB, kpad,
-                      idesc, in_seg == 0);
-            mma_commit(&empty[g]);
-          }
-        }
-        if (__shfl_sync(0xffffffffu, (int)abort_flag, 0)) { stop = true; break; }
-        if (++in_seg == kSegSteps) {
-          if (lane == 0) mma_commit(&accf[seg % kAcc]);
-          __syncwarp();
-          ++seg;
-          in_seg = 0;
-          // the accumulator of segment `seg` is reused next: keep at most kAcc - 1 pending
-          while (seg - drained > kAcc - 1) drain(drained++ % kAcc);
-        }
-      }
-    }
-    if (!stop && !__shfl_sync(0xffffffffu, (int)abort_flag, 0)) {
-      if (in_seg > 0) {
-        if (lane == 0) mma_commit(&accf[seg % kAcc]);
-        __syncwarp();
-        ++seg;
-      }
-      while (drained < seg) drain(drained++ % kAcc);
-      if (!__shfl_sync(0xffffffffu, (int)abort_flag, 0) && lane < mv) {
-        double* yr = u.y + (size_t)(u.row0 + lane) * u.ldy + u.col0;
+    int src_ctr = 0;
+    bool ok = !abort_flag;
+    for (int t = 0; t < T && ok; ++t) {
+      const TfTask tk = tasks[tile.t_begin + t];
+      float wsum[32];
 #pragma unroll
-        for (int j = 0; j < 64; ++j)
-          if (j < nv) atomicAdd(yr + j, (double)acc[j]);
+      for (int j = 0; j < 32; ++j) wsum[j] = 0.0f;
+      for (int si = tk.s_begin; si < tk.s_end; ++si, ++src_ctr) {
+        const int q = src_ctr % kWBuf, use = src_ctr / kWBuf;
+        if (!wait_or_abort(&bar.w_full[q], use & 1, &abort_flag)) { ok = false; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (32 * half < tk.kdl) {
+          const float coef = srcs[si].coef;
+          float v[16];
+          tmem_ld16(lane_base + (uint32_t)(q * 64 + 32 * half), v);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) wsum[j] = fmaf(coef, v[j], wsum[j]);
+          tmem_ld16(lane_base + (uint32_t)(q * 64 + 32 * half + 16), v);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) wsum[16 + j] = fmaf(coef, v[j], wsum[16 + j]);
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        mbar_arrive(&bar.w_empty[q]);
+      }
+      if (!ok) break;
+      // product 2 of the previous term has finished: its result is added to the
+      // registers and the W^T tiles may be overwritten
+      if (t >= 1) {
+        if (!wait_or_abort(&bar.mma2_done, (t - 1) & 1, &abort_flag)) { ok = false; break; }
+        drain_y();
+      }
+      float* ah = a2 + (2 * half) * kTF;
+      float* al = ah + kTF;
+#pragma unroll
+      for (int g = 0; g < 8; ++g) {
+        float4 h, l;
+        float* hv = &h.x;
+        float* lv = &l.x;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float v = (32 * half + 4 * g + e < tk.kdl) ? wsum[4 * g + e] : 0.0f;
+          hv[e] = tf32_round(v);
+          lv[e] = tf32_round(v - hv[e]);
+        }
+        *reinterpret_cast<float4*>(ah + kmo(n, 4 * g)) = h;
+        *reinterpret_cast<float4*>(al + kmo(n, 4 * g)) = l;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(&bar.a2_full);
+    }
+    if (ok && T >= 1) {
+      if (wait_or_abort(&bar.mma2_done, (T - 1) & 1, &abort_flag)) drain_y();
+    }
+    if (!abort_flag && n < tile.nv) {
+#pragma unroll
+      for (int j = 0; j < 64; ++j) {
+        const int r = 64 * half + j;
+        if (r < tile.m) tile.y[(int64_t)r * tile.ldy + n] = (double)yacc[j];
       }
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  if (warp == kGroups * 2) tmem_free(tmem, 64 * kAcc);
+  if (warp == kMmaWarp) tmem_free(tmem, kTmemCols);
 }
 
 // ------------------------------------------------------------------ conversions
 
-// x (FP64) -> the FP32 stacks (row-major) and their transposes, one CTA per x block
-__global__ void k_x_prep(const TcXBlock* __restrict__ xb) {
-  const TcXBlock B = xb[blockIdx.x];
-  const int n = B.rows * B.cols;
+// FP64 blocks -> tiled hi / lo (one CTA per block); identity blocks write their diagonal
+__global__ void k_tiled_convert(const TfConv* __restrict__ m) {
+  const TfConv M = m[blockIdx.x];
+  const int n = M.identity ? M.rows : M.rows * M.cols;
   for (int e = threadIdx.x; e < n; e += blockDim.x) {
-    const int r = e / B.cols, c = e - r * B.cols;
-    const float v = (float)B.src[e];
-    B.dst[(int64_t)r * B.ld + c] = v;
-    B.dstt[(int64_t)c * B.ldt + r] = v;
-  }
-}
-
-// FP64 blocks (row-major, stride cols) -> FP32 with row stride ld, one CTA per block
-__global__ void k_mirror(const TcMirror* __restrict__ m) {
-  const TcMirror M = m[blockIdx.x];
-  const int n = M.rows * M.cols;
-  for (int e = threadIdx.x; e < n; e += blockDim.x) {
-    const int r = e / M.cols, c = e - r * M.cols;
-    M.dst[(int64_t)r * M.ld + c] = (float)M.src[e];
+    int r, c;
+    double v;
+    if (M.identity) {
+      r = c = e;
+      v = 1.0;
+    } else {
+      r = e / M.cols;
+      c = e - r * M.cols;
+      v = M.src[e];
+    }
+    const int64_t off = ((int64_t)(c >> 5) * M.nrg + (r >> 3)) * 256 + ((c & 31) >> 2) * 32 + (r & 7) * 4 + (c & 3);
+    const float f = (float)v;
+    const float hi = tf32_round(f);
+    M.dst[off] = hi;
+    M.dst[off + M.lo] = tf32_round(f - hi);
   }
 }
 
@@ -735,102 +470,70 @@ T* upload(const std::vector<T>& v, Stream s) {
   return p;
 }
 
-size_t smem_bytes(int floats) { return sizeof(float) * (size_t)floats + 128; }
+size_t smem_bytes() { return sizeof(float) * (size_t)kSmemF + 1024; }
 
 }  // namespace
 
 struct TcPlan {
-  Tc1Entry* ents = nullptr;
-  Tc1Pack* packs = nullptr;
-  Tc1Unit* u1 = nullptr;      // one-chunk units first, then multi-chunk units
-  int n1_one = 0, n1_multi = 0;
-  Tc2Src* srcs = nullptr;
-  Tc2Task* tasks = nullptr;
-  Tc2Unit* u2 = nullptr;      // tiles of at most 32 rows first, then the others
-  int n2_small = 0, n2 = 0;
-  TcXBlock* xb = nullptr;
-  int nxb = 0;
-  std::vector<std::pair<double*, int64_t>> clear;  // outputs zeroed before the products
-  int launches = 0;           // kernels of one launch sequence
+  TfTile* tiles = nullptr;
+  TfTask* tasks = nullptr;
+  TfSrc* srcs = nullptr;
+  TfConv* xb = nullptr;
+  int ntiles = 0, nxb = 0;
+  int launches = 0;  // kernels of one launch sequence
 };
 
-TcPlan* tc_plan_build(const std::vector<const TcHost*>& inst, TcTune tune, Stream st) {
-  if (tune.packs_per_unit < 1 || tune.tasks_per_unit < 1 || tune.tasks_per_unit > kUnitTasks)
-    throw std::invalid_argument("tc tuning");
-  std::vector<Tc1Entry> e;
-  std::vector<Tc1Pack> p;
-  std::vector<Tc1Unit> u1, u1m;
-  std::vector<Tc2Src> sr;
-  std::vector<Tc2Task> t;
-  std::vector<Tc2Unit> u2, u2g;
-  std::vector<TcXBlock> xb;
+TcPlan* tc_plan_build(const std::vector<const TcHost*>& inst, Stream st) {
   TcPlan* P = new TcPlan;
-  // one instance: its tables are uploaded as they are (indices need no offsets)
-  const bool single = inst.size() == 1;
-  for (const TcHost* H : inst) {
-    const int e0 = (int)e.size(), p0 = (int)p.size(), s0 = (int)sr.size(), t0 = (int)t.size();
-    for (const Tc1Pack& q : H->p)
-      if (q.e_end - q.e_begin > kMaxPackEntries || q.n > 128) throw std::logic_error("tc pack too large");
-    if (!single) {
-      e.insert(e.end(), H->e.begin(), H->e.end());
-      for (Tc1Pack q : H->p) {
-        q.e_begin += e0;
-        q.e_end += e0;
-        p.push_back(q);
-      }
-    }
-    for (const Tc1Unit& r : H->r1)
-      for (int pb = r.p_begin; pb < r.p_end; pb += tune.packs_per_unit) {
-        Tc1Unit u = r;
-        u.p_begin = p0 + pb;
-        u.p_end = p0 + std::min(r.p_end, pb + tune.packs_per_unit);
-        (r.K <= 32 ? u1 : u1m).push_back(u);
-      }
-    if (!single) {
-      sr.insert(sr.end(), H->s.begin(), H->s.end());
-      for (Tc2Task q : H->t) {
+  try {
+    std::vector<TfSrc> s;
+    std::vector<TfTask> t;
+    std::vector<TfTile> tl;
+    std::vector<TfConv> xb;
+    const bool single = inst.size() == 1;
+    for (const TcHost* H : inst) {
+      if (single) break;  // one instance: its tables are uploaded as they are
+      const int s0 = (int)s.size(), t0 = (int)t.size();
+      s.insert(s.end(), H->s.begin(), H->s.end());
+      for (TfTask q : H->t) {
         q.s_begin += s0;
         q.s_end += s0;
         t.push_back(q);
       }
-    }
-    for (const Tc2Unit& r : H->r2)
-      for (int tb = r.t_begin; tb < r.t_end; tb += tune.tasks_per_unit) {
-        Tc2Unit u = r;
-        u.t_begin = t0 + tb;
-        u.t_end = t0 + std::min(r.t_end, tb + tune.tasks_per_unit);
-        (r.m - r.row0 <= 32 ? u2 : u2g).push_back(u);
+      for (TfTile q : H->tiles) {
+        q.t_begin += t0;
+        q.t_end += t0;
+        tl.push_back(q);
       }
-    if (!single) xb.insert(xb.end(), H->xb.begin(), H->xb.end());
-    if (H->yout && H->n > 0) P->clear.push_back({H->yout, H->n});
+      xb.insert(xb.end(), H->xb.begin(), H->xb.end());
+    }
+    const std::vector<TfTile>& tiles0 = single ? inst[0]->tiles : tl;
+    // tiles in decreasing order of work (the hardware starts CTAs in launch order, so
+    // the longest tiles do not finish last)
+    std::vector<int> order(tiles0.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return tiles0[a].cost > tiles0[b].cost; });
+    std::vector<TfTile> sorted(tiles0.size());
+    for (size_t i = 0; i < order.size(); ++i) sorted[i] = tiles0[order[i]];
+    P->tiles = upload(sorted, st);
+    P->tasks = upload(single ? inst[0]->t : t, st);
+    P->srcs = upload(single ? inst[0]->s : s, st);
+    P->xb = upload(single ? inst[0]->xb : xb, st);
+    P->ntiles = (int)sorted.size();
+    P->nxb = (int)(single ? inst[0]->xb.size() : xb.size());
+    P->launches = (P->nxb > 0) + (P->ntiles > 0);
+  } catch (...) {
+    tc_plan_free(P, st);
+    throw;
   }
-  P->n1_one = (int)u1.size();
-  P->n1_multi = (int)u1m.size();
-  u1.insert(u1.end(), u1m.begin(), u1m.end());
-  P->n2_small = (int)u2.size();
-  u2.insert(u2.end(), u2g.begin(), u2g.end());
-  P->n2 = (int)u2.size();
-  const TcHost* H0 = single ? inst[0] : nullptr;
-  P->ents = upload(single ? H0->e : e, st);
-  P->packs = upload(single ? H0->p : p, st);
-  P->u1 = upload(u1, st);
-  P->srcs = upload(single ? H0->s : sr, st);
-  P->tasks = upload(single ? H0->t : t, st);
-  P->u2 = upload(u2, st);
-  P->xb = upload(single ? H0->xb : xb, st);
-  P->nxb = (int)(single ? H0->xb.size() : xb.size());
-  P->launches = (P->nxb > 0) + (P->n1_one > 0) + (P->n1_multi > 0) + (P->n2_small > 0) + (P->n2 > P->n2_small);
   return P;
 }
 
 void tc_plan_free(TcPlan* p, Stream s) {
   if (!p) return;
-  dev_free(p->ents, s);
-  dev_free(p->packs, s);
-  dev_free(p->u1, s);
-  dev_free(p->srcs, s);
+  dev_free(p->tiles, s);
   dev_free(p->tasks, s);
-  dev_free(p->u2, s);
+  dev_free(p->srcs, s);
   dev_free(p->xb, s);
   delete p;
 }
@@ -840,32 +543,16 @@ namespace {
 void tc_set_attributes() {
   static bool attr = false;
   if (attr) return;
-  ck(cudaFuncSetAttribute(k_tc_phase1<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                          (int)smem_bytes(p1_smem_floats<true>())), "tc phase 1 smem");
-  ck(cudaFuncSetAttribute(k_tc_phase1<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                          (int)smem_bytes(p1_smem_floats<false>())), "tc phase 1 smem");
-  ck(cudaFuncSetAttribute(k_tc_phase2, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                          (int)smem_bytes(2 * kP2BufF)), "tc phase 2 smem");
-  ck(cudaFuncSetAttribute(k_tc_phase2s, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                          (int)smem_bytes(kGroups * kP2sStageF)), "tc phase 2 smem");
+  ck(cudaFuncSetAttribute(k_tc_matvec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes()),
+     "tc matvec smem");
   attr = true;
 }
 
 void tc_enqueue(const TcPlan* p, void* const* ev, cudaStream_t cs) {
   if (ev) event_record(ev[0], cs);
-  for (const auto& c : p->clear) ck(cudaMemsetAsync(c.first, 0, sizeof(double) * (size_t)c.second, cs), "tc zero y");
-  if (p->nxb > 0) k_x_prep<<<p->nxb, 256, 0, cs>>>(p->xb);
-  if (p->n1_one > 0)
-    k_tc_phase1<true><<<p->n1_one, kThreads, smem_bytes(p1_smem_floats<true>()), cs>>>(p->u1, p->packs, p->ents);
-  if (p->n1_multi > 0)
-    k_tc_phase1<false><<<p->n1_multi, kThreads, smem_bytes(p1_smem_floats<false>()), cs>>>(
-        p->u1 + p->n1_one, p->packs, p->ents);
+  if (p->nxb > 0) k_tiled_convert<<<p->nxb, 256, 0, cs>>>(p->xb);
   if (ev) event_record(ev[1], cs);
-  if (p->n2_small > 0)
-    k_tc_phase2s<<<p->n2_small, kP2sThreads, smem_bytes(kGroups * kP2sStageF), cs>>>(p->u2, p->tasks, p->srcs);
-  if (p->n2 > p->n2_small)
-    k_tc_phase2<<<p->n2 - p->n2_small, kThreads, smem_bytes(2 * kP2BufF), cs>>>(p->u2 + p->n2_small, p->tasks,
-                                                                                 p->srcs);
+  if (p->ntiles > 0) k_tc_matvec<<<p->ntiles, kMvThreads, smem_bytes(), cs>>>(p->tiles, p->tasks, p->srcs);
   if (ev) event_record(ev[2], cs);
   ck(cudaGetLastError(), "tc matvec launch");
 }
@@ -919,12 +606,12 @@ void tc_graph_free(void* g) {
   delete G;
 }
 
-void tc_mirror(const std::vector<TcMirror>& m, Stream s) {
+void tc_convert(const std::vector<TfConv>& m, Stream s) {
   if (m.empty()) return;
-  TcMirror* d = upload(m, s);
-  k_mirror<<<(int)m.size(), 256, 0, (cudaStream_t)s>>>(d);
+  TfConv* d = upload(m, s);
+  k_tiled_convert<<<(int)m.size(), 256, 0, (cudaStream_t)s>>>(d);
   note_launches(1);
-  ck(cudaGetLastError(), "tc mirror launch");
+  ck(cudaGetLastError(), "tc convert launch");
   dev_free(d, s);
 }
 
@@ -933,7 +620,18 @@ int tc_error_flag(Stream s) {
   ck(cudaMemcpyFromSymbolAsync(&h, g_tc_error, sizeof(int), 0, cudaMemcpyDeviceToHost, (cudaStream_t)s),
      "tc error flag");
   ck(cudaStreamSynchronize((cudaStream_t)s), "tc error flag");
+  if (h) {
+    const int zero = 0;
+    ck(cudaMemcpyToSymbolAsync(g_tc_error, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, (cudaStream_t)s),
+       "tc error flag");
+    ck(cudaStreamSynchronize((cudaStream_t)s), "tc error flag");
+  }
   return h;
+}
+
+void tc_inject_timeout(int on) {
+  const int v = on ? 1 : 0;
+  ck(cudaMemcpyToSymbol(g_tc_inject, &v, sizeof(int)), "tc inject");
 }
 
 }  // namespace dmrg

@@ -67,7 +67,7 @@ def test_batched_matvec_matches_each_instance(mods):
         xs.append(x)
     b = Batch(ctxs, sites, autotune=True)
     info = b.info()
-    assert info["packs_per_unit"] > 0 and info["tasks_per_unit"] > 0
+    assert info["row_tile"] in (64, 128) and info["x_chunk"] in (32, 64)
     ys = [torch.empty_like(x) for x in xs]
     for rep in range(2):  # a graph replay gives the same products
         b.run(xs, ys)

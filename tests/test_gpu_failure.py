@@ -91,3 +91,38 @@ def test_device_memory_cap_gives_enomem_without_leaking(lib):
     assert pkg.device_memory_in_use() > before
     err = ((y - y64).abs().max() / y64.abs().max()).item()
     assert err < 2e-6, err
+
+
+def test_tensor_core_wait_timeout_is_reported_and_recovered(lib):
+    """The fused kernel's bounded waits: with the test hook on, every CTA gives up on a
+    barrier that nothing completes (a few thousand polls), frees its tensor memory and
+    returns; the call reports DMRG_ECUDA.  With the hook off the next matvec gives the
+    right product (tensor memory and the context are usable)."""
+    torch, pkg = lib
+    L, N, i = 8, 8, 3
+    irr = round_robin_irreps(L)
+    h, V = random_integrals(irr, 5)
+    ctx = pkg.Context(L, irr, N, 0, 0, precision=1)
+    ctx.set_integrals(h, V)
+    ctx.set_schedule([60], [0.0], [1], [0.0], 1e-10, 20)
+    ctx.init_mps(7)
+    ctx.canonicalize(i)
+    n, _ = ctx.layout(i)
+    x = torch.tensor(np.random.default_rng(3).normal(size=n), device="cuda")
+    y, y64 = torch.empty_like(x), torch.empty_like(x)
+    ctx.set_precision(0, 0)
+    ctx.matvec(i, x, y64)
+    ctx.set_precision(1, 0)
+    ctx.matvec(i, x, y)  # tables built, kernel run once normally
+    try:
+        pkg.test_tc_timeout(1)
+        with pytest.raises(pkg.DMRGError) as err:
+            ctx.matvec(i, x, y)
+        assert err.value.code == -5 and "timed out" in str(err.value)
+    finally:
+        pkg.test_tc_timeout(0)
+    for _ in range(2):
+        y.fill_(0.0)
+        ctx.matvec(i, x, y)
+        torch.cuda.synchronize()
+        assert ((y - y64).abs().max() / y64.abs().max()).item() < 2e-6
