@@ -1442,7 +1442,7 @@ void Engine::tc_tables(MatvecPlan* P, TcTune tune) {
                              P->tc_x + P->tc_xoff[src.xb] + (int64_t)(kc / 8) * 256, nrg(drows) * 256,
                              nrg(Xs.rows) * 256, nkc, Xs.cols - 32 * (nkc - 1),
                              (float)(src.craw * P->cr[src.gr].scalar * C.scalar)};
-                T.cost += nkc;
+                T.cost += nkc + (nkc + 1) / 2;
               }
               q.s_end = (int)sr;
               H.t[tk++] = q;

@@ -7,13 +7,15 @@
 // blocks (the combined operators of the left / right environments).  One CTA owns one
 // output tile (up to 128 rows x 128 columns of one block, so nothing is added with
 // atomics and the summation order is fixed) and runs all of its terms:
-//   product 1: W^T = D_s x_s^T per source, into its own tensor-memory accumulator
-//              (M = 128 output columns, N = x rows of the term, K = the right sector);
+//   product 1: W^T = D_s x_s^T per source, into tensor-memory accumulators of at most
+//              two 32-column K chunks each (M = 128 output columns, N = x rows of the
+//              term, K = the right sector);
 //   the converter warps add coef_s times each accumulator into FP32 registers, split the
 //              sum into TF32 head and tail and store it as the A operand of
 //   product 2: y^T += W^T C^T (M = 128 output columns, N = output rows, K = x rows),
-//              restarted per term and drained into FP32 registers (the tensor core's own
-//              FP32 accumulation loses accuracy over long runs of products).
+//              restarted per term and drained into FP32 registers, which are added to y
+//              (FP64) every few terms.  The tensor core's own FP32 accumulation loses
+//              accuracy over long runs of products, hence the short accumulators.
 // Every product uses split TF32: v = hi + lo with hi = rna_tf32(v), lo = rna_tf32(v - hi),
 // and the three leading products hi*hi + hi*lo + lo*hi (about 2^-21 relative).
 //
@@ -54,6 +56,8 @@ constexpr int kS1F = 2 * kTF + kTF;
 constexpr int kB2F = 4 * kTF;
 constexpr int kA2F = 4 * kTF;
 constexpr int kSmemF = kS1 * kS1F + kB2F + kA2F;
+constexpr int kSegChunks = 2;   // K chunks per product-1 accumulator (then added in registers)
+constexpr int kFlushTerms = 16; // terms summed in FP32 registers before they are added to y (FP64)
 constexpr int kProducerWarp = 0, kMmaWarp = 1, kConvWarps = 8;
 constexpr int kMvThreads = (2 + kConvWarps) * 32;
 constexpr int kConvThreads = kConvWarps * 32;
@@ -304,22 +308,24 @@ __global__ void __launch_bounds__(kMvThreads, 1)
         if (t < T) {
           const TfTask tk = tasks[tile.t_begin + t];
           const uint32_t idesc1 = idesc_tf32((tk.kdl + 15) & ~15);
-          for (int si = tk.s_begin; si < tk.s_end && ok; ++si, ++src_ctr) {
+          for (int si = tk.s_begin; si < tk.s_end && ok; ++si) {
             const TfSrc S = srcs[si];
-            const int q = src_ctr % kWBuf, use = src_ctr / kWBuf;
-            if (use >= 1 && !wait_or_abort(&bar.w_empty[q], (use - 1) & 1, &abort_flag)) { ok = false; break; }
-            for (int kk = 0; kk < S.nkc; ++kk, ++step) {
-              const int slot = step % kS1;
-              if (!wait_or_abort(&bar.s1_full[slot], (step / kS1) & 1, &abort_flag)) { ok = false; break; }
-              asm volatile("tcgen05.fence::after_thread_sync;");
-              const int kv = kk == S.nkc - 1 ? S.klast : 32;
-              const float* base = s1 + slot * kS1F;
-              mma_chunk(tmem + (uint32_t)(q * 64), base, base + kTF, base + 2 * kTF, base + 2 * kTF + kTF / 2,
-                        (kv + 7) & ~7, idesc1, kk == 0);
-              mma_commit(&bar.s1_empty[slot]);
+            for (int k0 = 0; k0 < S.nkc && ok; k0 += kSegChunks, ++src_ctr) {
+              const int q = src_ctr % kWBuf, use = src_ctr / kWBuf;
+              if (use >= 1 && !wait_or_abort(&bar.w_empty[q], (use - 1) & 1, &abort_flag)) { ok = false; break; }
+              for (int kk = k0; kk < min(S.nkc, k0 + kSegChunks); ++kk, ++step) {
+                const int slot = step % kS1;
+                if (!wait_or_abort(&bar.s1_full[slot], (step / kS1) & 1, &abort_flag)) { ok = false; break; }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const int kv = kk == S.nkc - 1 ? S.klast : 32;
+                const float* base = s1 + slot * kS1F;
+                mma_chunk(tmem + (uint32_t)(q * 64), base, base + kTF, base + 2 * kTF, base + 2 * kTF + kTF / 2,
+                          (kv + 7) & ~7, idesc1, kk == k0);
+                mma_commit(&bar.s1_empty[slot]);
+              }
+              if (!ok) break;
+              mma_commit(&bar.w_full[q]);
             }
-            if (!ok) break;
-            mma_commit(&bar.w_full[q]);
           }
         }
         if (ok && t >= 1) {
@@ -367,6 +373,22 @@ __global__ void __launch_bounds__(kMvThreads, 1)
       }
       asm volatile("tcgen05.fence::before_thread_sync;");
     };
+    // the FP32 sums of the last terms are added to y (the tile's owner writes it first,
+    // then accumulates into it)
+    bool stored = false;
+    auto flush_y = [&]() {
+      if (abort_flag || n >= tile.nv) return;
+#pragma unroll
+      for (int j = 0; j < 64; ++j) {
+        const int r = 64 * half + j;
+        if (r < tile.m) {
+          double* yp = tile.y + (int64_t)r * tile.ldy + n;
+          *yp = stored ? *yp + (double)yacc[j] : (double)yacc[j];
+        }
+        yacc[j] = 0.0f;
+      }
+      stored = true;
+    };
     int src_ctr = 0;
     bool ok = !abort_flag;
     for (int t = 0; t < T && ok; ++t) {
@@ -374,22 +396,25 @@ __global__ void __launch_bounds__(kMvThreads, 1)
       float wsum[32];
 #pragma unroll
       for (int j = 0; j < 32; ++j) wsum[j] = 0.0f;
-      for (int si = tk.s_begin; si < tk.s_end; ++si, ++src_ctr) {
-        const int q = src_ctr % kWBuf, use = src_ctr / kWBuf;
-        if (!wait_or_abort(&bar.w_full[q], use & 1, &abort_flag)) { ok = false; break; }
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        if (32 * half < tk.kdl) {
-          const float coef = srcs[si].coef;
-          float v[16];
-          tmem_ld16(lane_base + (uint32_t)(q * 64 + 32 * half), v);
+      for (int si = tk.s_begin; si < tk.s_end && ok; ++si) {
+        const float coef = srcs[si].coef;
+        const int nseg = (srcs[si].nkc + kSegChunks - 1) / kSegChunks;
+        for (int g = 0; g < nseg; ++g, ++src_ctr) {
+          const int q = src_ctr % kWBuf, use = src_ctr / kWBuf;
+          if (!wait_or_abort(&bar.w_full[q], use & 1, &abort_flag)) { ok = false; break; }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          if (32 * half < tk.kdl) {
+            float v[16];
+            tmem_ld16(lane_base + (uint32_t)(q * 64 + 32 * half), v);
 #pragma unroll
-          for (int j = 0; j < 16; ++j) wsum[j] = fmaf(coef, v[j], wsum[j]);
-          tmem_ld16(lane_base + (uint32_t)(q * 64 + 32 * half + 16), v);
+            for (int j = 0; j < 16; ++j) wsum[j] = fmaf(coef, v[j], wsum[j]);
+            tmem_ld16(lane_base + (uint32_t)(q * 64 + 32 * half + 16), v);
 #pragma unroll
-          for (int j = 0; j < 16; ++j) wsum[16 + j] = fmaf(coef, v[j], wsum[16 + j]);
+            for (int j = 0; j < 16; ++j) wsum[16 + j] = fmaf(coef, v[j], wsum[16 + j]);
+          }
+          asm volatile("tcgen05.fence::before_thread_sync;");
+          mbar_arrive(&bar.w_empty[q]);
         }
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        mbar_arrive(&bar.w_empty[q]);
       }
       if (!ok) break;
       // product 2 of the previous term has finished: its result is added to the
@@ -397,6 +422,7 @@ __global__ void __launch_bounds__(kMvThreads, 1)
       if (t >= 1) {
         if (!wait_or_abort(&bar.mma2_done, (t - 1) & 1, &abort_flag)) { ok = false; break; }
         drain_y();
+        if (t % kFlushTerms == 0) flush_y();
       }
       float* ah = a2 + (2 * half) * kTF;
       float* al = ah + kTF;
@@ -420,13 +446,7 @@ __global__ void __launch_bounds__(kMvThreads, 1)
     if (ok && T >= 1) {
       if (wait_or_abort(&bar.mma2_done, (T - 1) & 1, &abort_flag)) drain_y();
     }
-    if (!abort_flag && n < tile.nv) {
-#pragma unroll
-      for (int j = 0; j < 64; ++j) {
-        const int r = 64 * half + j;
-        if (r < tile.m) tile.y[(int64_t)r * tile.ldy + n] = (double)yacc[j];
-      }
-    }
+    flush_y();
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
