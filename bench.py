@@ -269,6 +269,18 @@ def timed_steps(ctx, center, D, steps, warmup, first_dir, clk=None, world=1):
     return ms, delta, energies, clocks, d
 
 
+def step_breakdown(delta, steps):
+    """Where a step's time goes: host wall clock of table planning (including the
+    tensor-core tables), truncation (Eqs. 26-28) and operator update, and the device time
+    (CUDA events) of the matvec kernels of both precisions; per step, in ms."""
+    k = max(steps, 1)
+    return {"host_plan": delta["t_plan_ms"] / k, "truncation": delta["t_trunc_ms"] / k,
+            "operator_update": delta["t_update_ms"] / k,
+            "mixed_matvecs_device": (delta["tc_phase1_ms"] + delta["tc_phase2_ms"]) / k,
+            "fp64_matvecs_device": (delta["k_phase1_ms"] + delta["k_phase2_ms"]) / k,
+            "mixed_matvecs": delta["tc_matvecs"] / k, "fp64_matvecs": delta["k_launches"] / k}
+
+
 def matvec_kernel_rates(delta):
     """Device-time GFLOP/s of the matvec kernels by precision (CUDA events around them)."""
     out = {}
@@ -626,7 +638,7 @@ def run_gb300(args):
         k64 = max(1, min(args.steps, args.fp64_steps))
         ms64, d64, e64, _, _ = timed_steps(ctx, center, D, k64, 1, 1)
         r64 = matvec_kernel_rates(d64)
-        fp64 = {"steps": k64, "ms_per_step": ms64 / k64,
+        fp64 = {"steps": k64, "ms_per_step": ms64 / k64, "step_breakdown_ms": step_breakdown(d64, k64),
                 "value": d64["matvec_flops"] / (ms64 * 1e-3) / 1e9, "unit": "GFLOP/s",
                 "matvec": r64.get("fp64"), "roofline": roofline_fp64(d64, peak64)}
         ctx.set_precision(args.precision, args.fp64_iters)
@@ -669,6 +681,7 @@ def run_gb300(args):
                    "block_histogram": hist},
         "matvec": rates, "fp64": fp64, "energy_agreement": acc, "sweep": sweeps,
         "micro_iteration_s": t_max / args.steps / 1e3,
+        "step_breakdown_ms": step_breakdown(delta, args.steps),
         "energy_last": energies[-1] if energies else None,
         "clocks": clocks, "gpu_launches": launches, "roofline": roof,
         "peaks_measured_here": {"fp64_gflops": peak64, "tf32_gflops": peak_tf32,
