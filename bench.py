@@ -235,14 +235,38 @@ def fixed_iters(ctx, D, iters):
     ctx.set_schedule([D], [0.0], [1], [0.0], 1e-14, iters)
 
 
-def timed_steps(ctx, center, D, steps, warmup, first_dir, clk=None, world=1):
-    """warmup + steps micro-iterations at (center, center+1), alternating direction; the
-    timed region is bracketed by barriers, synchronisation and CUDA events."""
+class Walker:
+    """Sites and directions of a sweep that bounces between sites lo and hi (right to hi,
+    then left to lo, ...): each step's site is the neighbour of the last one, or the same
+    site where the sweep turns, as in a macro-iteration (Sec. 4.2)."""
+
+    def __init__(self, lo, hi):
+        self.lo, self.hi, self.site, self.dir = lo, hi, lo, 1
+
+    def peek(self):
+        if self.dir > 0:
+            return (self.site + 1, 1) if self.site < self.hi else (self.site, -1)
+        return (self.site - 1, -1) if self.site > self.lo else (self.site, 1)
+
+    def step(self, ctx, D):
+        nxt = self.peek()
+        ctx.set_next_site(nxt[0])
+        out = ctx.sweep_step(self.site, self.dir, D)
+        self.site, self.dir = nxt
+        return out
+
+
+def window(center):
+    return center - 5, center + 4
+
+
+def timed_steps(ctx, walker, D, steps, warmup, clk=None, world=1):
+    """warmup + steps micro-iterations of a sweep between two sites around the middle
+    (Walker); the timed region is bracketed by barriers, synchronisation and CUDA
+    events."""
     import torch
-    d = first_dir
     for _ in range(warmup):
-        ctx.sweep_step(center, d, D)
-        d = -d
+        walker.step(ctx, D)
     torch.cuda.synchronize()
     st0 = ctx.stats()
     barrier(world)
@@ -254,9 +278,8 @@ def timed_steps(ctx, center, D, steps, warmup, first_dir, clk=None, world=1):
     ev0.record()
     energies = []
     for _ in range(steps):
-        e, wd, it, ok = ctx.sweep_step(center, d, D)
+        e, wd, it, ok = walker.step(ctx, D)
         energies.append(e)
-        d = -d
     ev1.record()
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
@@ -266,7 +289,7 @@ def timed_steps(ctx, center, D, steps, warmup, first_dir, clk=None, world=1):
     ms = ev0.elapsed_time(ev1)
     st1 = ctx.stats()
     delta = {k: st1[k] - st0[k] for k in st1}
-    return ms, delta, energies, clocks, d
+    return ms, delta, energies, clocks
 
 
 def step_breakdown(delta, steps):
@@ -394,6 +417,8 @@ def sweep_time(ctx, L, D, precision, fp64_iters, iters):
     for sites, d in ((range(0, L - 1), 1), (range(L - 2, -1, -1), -1)):
         t0 = time.perf_counter()
         for i in sites:
+            last = (d > 0 and i == L - 2) or (d < 0 and i == 0)
+            ctx.set_next_site(i if last else i + d)
             e, wd, it, ok = ctx.sweep_step(i, d, D)
             es.append(e)
         torch.cuda.synchronize()
@@ -620,12 +645,14 @@ def run_gb300(args):
     ctx.set_precision(args.precision, args.fp64_iters)
     fixed_iters(ctx, D, args.davidson_iters)
     ctx.canonicalize(center)
-    swept_state = ctx.get_mps()
     n_x, table = ctx.layout(center)
     hist = block_histogram(table)
+    lo, hi = window(center)
+    ctx.canonicalize(lo)
+    swept_state = ctx.get_mps()
     # 3: headline steps on that state
     clk = ClockSampler(torch.cuda.current_device())
-    ms, delta, energies, clocks, d = timed_steps(ctx, center, D, args.steps, args.warmup, 1, clk, world)
+    ms, delta, energies, clocks = timed_steps(ctx, Walker(lo, hi), D, args.steps, args.warmup, clk, world)
     value, t_max = aggregate(delta["matvec_flops"], ms, world)
     launches = int(delta["kernels_launched"])
     rates = matvec_kernel_rates(delta)
@@ -634,9 +661,8 @@ def run_gb300(args):
     if not args.no_fp64 and mixed:
         ctx.set_mps(swept_state)
         ctx.set_precision(0, 0)
-        ctx.canonicalize(center)
         k64 = max(1, min(args.steps, args.fp64_steps))
-        ms64, d64, e64, _, _ = timed_steps(ctx, center, D, k64, 1, 1)
+        ms64, d64, e64, _ = timed_steps(ctx, Walker(lo, hi), D, k64, 1)
         r64 = matvec_kernel_rates(d64)
         fp64 = {"steps": k64, "ms_per_step": ms64 / k64, "step_breakdown_ms": step_breakdown(d64, k64),
                 "value": d64["matvec_flops"] / (ms64 * 1e-3) / 1e9, "unit": "GFLOP/s",
@@ -660,8 +686,7 @@ def run_gb300(args):
     e2e = None
     if not args.no_e2e:
         ctx.set_mps(swept_state)
-        ctx.canonicalize(center)
-        e2e = run_e2e(ctx, center, D, args, n_x)
+        e2e = run_e2e(ctx, Walker(lo, hi), D, args)
     out = {
         "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
@@ -669,9 +694,10 @@ def run_gb300(args):
         "dtype": "tf32x3-f32acc+f64" if mixed else "f64",
         "data": "synthetic",
         "config": {"workload": f"{args.workload}: random integrals L={L} N={cfg['N']} S=0 Ag "
-                               f"D2h 8/3/3/2/6/2/2/2, D_SU(2)={D}, middle sites ({center},{center + 1}) of "
-                               + state,
-                   "L": L, "N": cfg["N"], "D": D, "site": center, "two_site_elements": n_x,
+                               f"D2h 8/3/3/2/6/2/2/2, D_SU(2)={D}, micro-iterations of a sweep between sites "
+                               f"{lo} and {hi} (both directions) of " + state,
+                   "L": L, "N": cfg["N"], "D": D, "sites": [lo, hi], "middle_site": center,
+                   "two_site_elements_middle": n_x,
                    "davidson_iters_per_step": args.davidson_iters,
                    "precision": ("split-TF32 tensor-core block products (FP32 data and accumulation) in "
                                  f"Davidson, then {args.fp64_iters} FP64 Davidson iteration(s)") if mixed
@@ -700,35 +726,42 @@ def run_gb300(args):
         dist.destroy_process_group()
 
 
-def run_e2e(ctx, center, D, args, n_x):
-    """The headline step through the host-buffer C ABI (stream 0): dmrg_tt_to_x into
+def run_e2e(ctx, walker, D, args):
+    """The headline steps through the host-buffer C ABI (stream 0): dmrg_tt_to_x into
     pinned host memory, dmrg_davidson from and to it, dmrg_truncate from it and
     dmrg_update_operators: the work of dmrg_sweep_step (Eq. 25, Davidson, Eqs. 26-28, the
     operator update), with the two-site vector crossing host <-> device every step; the
-    energy is read back on the host."""
+    energy is read back on the host.  Same sweep window as the headline steps."""
     import torch
-    x = torch.empty(n_x, dtype=torch.float64).pin_memory().numpy()
     steps = max(1, min(args.steps, args.e2e_steps))
-    d = 1
-    for _ in range(1):  # warm-up step (tables, environments)
-        ctx.tt_to_x(center, x); ctx.davidson(center, x); ctx.truncate(center, d, D, x)
-        ctx.update_operators(center, d)
-        d = -d
+    buf = [torch.empty(0, dtype=torch.float64).pin_memory()]
+
+    def one():
+        i, d = walker.site, walker.dir
+        n, _ = ctx.layout(i)
+        if buf[0].numel() < n:  # one pinned buffer, grown when a site needs more
+            buf[0] = torch.empty(2 * n, dtype=torch.float64).pin_memory()
+        x = buf[0][:n].numpy()
+        ctx.tt_to_x(i, x)
+        e, it, ok = ctx.davidson(i, x)
+        ctx.truncate(i, d, D, x)
+        ctx.update_operators(i, d)
+        walker.site, walker.dir = walker.peek()
+        return n
+
+    one()  # warm-up step (tables, environments)
     st0 = ctx.stats()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    nbytes = 0
     for _ in range(steps):
-        ctx.tt_to_x(center, x)
-        e, it, ok = ctx.davidson(center, x)
-        ctx.truncate(center, d, D, x)
-        ctx.update_operators(center, d)
-        d = -d
+        nbytes += one()
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     st1 = ctx.stats()
     flops = st1["matvec_flops"] - st0["matvec_flops"]
     return {"value": flops / dt / 1e9, "unit": "GFLOP/s", "steps": steps, "s_per_step": dt / steps,
-            "h2d_bytes_per_step": 2 * 8 * n_x, "d2h_bytes_per_step": 2 * 8 * n_x + 8,
+            "h2d_bytes_per_step": 2 * 8 * nbytes // steps, "d2h_bytes_per_step": 2 * 8 * nbytes // steps + 8,
             "path": "dmrg_tt_to_x / dmrg_davidson / dmrg_truncate / dmrg_update_operators with host "
                     "buffers (the work of dmrg_sweep_step)"}
 

@@ -213,6 +213,14 @@ int dmrg_truncate(dmrg_ctx* ctx, int site, int dir, int D, double noise, const d
  * the two-site vector passing through the caller's buffers. */
 int dmrg_update_operators(dmrg_ctx* ctx, int site, int dir);
 
+/* Hint for the next dmrg_sweep_step: the site it will run at (-1 = unknown; used once).
+ * A step at site s changes only the middle bond s+1, so the next step at the same site
+ * keeps every table of this one; a step at another site has its tables built on the
+ * host while this step's FP64 energy (precision 1) is evaluated on the device.  Results
+ * do not depend on the hint.  dmrg_solve sets it for every step of its sweeps.
+ * DMRG_EINVAL unless -1 <= site <= L-2. */
+int dmrg_set_next_site(dmrg_ctx* ctx, int site);
+
 /* One micro-iteration of a sweep (Secs. 2.3-2.5, 3.3): Eq. 25 from T[site], T[site+1],
  * Davidson with the scheme's tolerance and cap, noise gamma * 0.5 * w_disc(previous
  * half sweep), Eqs. 26-28 to D, and the renormalised / complementary operator update

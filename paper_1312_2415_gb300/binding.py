@@ -70,6 +70,7 @@ _SIGS = {
     "dmrg_davidson": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, _D, _I]),
     "dmrg_truncate": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                      ctypes.c_void_p, ctypes.c_size_t, _D]),
+    "dmrg_set_next_site": (ctypes.c_int, [_P, ctypes.c_int]),
     "dmrg_update_operators": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
     "dmrg_sweep_step": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                        _D, _D, _I]),
@@ -284,6 +285,10 @@ class Context:
         self._check(self.lib.dmrg_truncate(self.h, site, int(direction), int(D), float(noise), p, s,
                                            ctypes.byref(w)))
         return w.value
+
+    def set_next_site(self, site):
+        """Hint: the site of the next sweep_step (-1 = unknown); see the header."""
+        self._check(self.lib.dmrg_set_next_site(self.h, int(site)))
 
     def update_operators(self, site, direction):
         """The operator update of a sweep step (after truncate in the same direction)."""

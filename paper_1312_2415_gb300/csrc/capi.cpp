@@ -408,6 +408,14 @@ int dmrg_truncate(dmrg_ctx* c, int site, int dir, int D, double noise, const dou
   });
 }
 
+int dmrg_set_next_site(dmrg_ctx* c, int site) {
+  return guard(c, [&] {
+    if (site < -1 || site > c->L - 2) return DMRG_EINVAL;
+    c->eng->set_next_site(site);
+    return DMRG_OK;
+  });
+}
+
 int dmrg_update_operators(dmrg_ctx* c, int site, int dir) {
   return guard(c, [&] {
     if (dir != 1 && dir != -1) return DMRG_EINVAL;

@@ -187,6 +187,8 @@ struct TfTile {         // one output tile of y, computed by one CTA from all of
   int t_begin, t_end;   // sub-tasks
   int64_t dlo, xlo;     // floats from a hi tile to its lo tile (operator pool, x pool)
   int64_t cost;         // MMA steps (tiles run in decreasing order of cost)
+  int kdg;              // x row groups of the tile's largest term (sizes its product-1 slots)
+  int pad;
 };
 // one FP64 block (rows x cols, row-major) to tiled hi / lo (nrg = ceil(rows / 8) row
 // groups per chunk; lo = hi + lo floats); identity != 0: the rows x rows identity

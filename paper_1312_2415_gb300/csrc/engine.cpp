@@ -1423,7 +1423,7 @@ void Engine::tc_tables(MatvecPlan* P, TcTune tune) {
       for (int row0 = 0; row0 < X.rows; row0 += RT)
         for (int col0 = 0; col0 < X.cols; col0 += 128) {
           TfTile T{P->yout + X.off + (int64_t)row0 * X.cols + col0, X.cols, std::min(RT, X.rows - row0),
-                   std::min(128, X.cols - col0), (int)tk, 0, P->tc_ops_lo, P->tc_x_lo, 0};
+                   std::min(128, X.cols - col0), (int)tk, 0, P->tc_ops_lo, P->tc_x_lo, 0, 1, 0};
           for (int wi : P->w_by_x[x]) {
             const auto& w = P->witems[wi];
             const CombOp& C = P->cl[w.gl];
@@ -1447,6 +1447,7 @@ void Engine::tc_tables(MatvecPlan* P, TcTune tune) {
               q.s_end = (int)sr;
               H.t[tk++] = q;
               T.cost += 2;
+              T.kdg = std::max(T.kdg, (q.kdl + 7) / 8);
             }
           }
           T.t_end = (int)tk;
@@ -2791,6 +2792,9 @@ double Engine::solve(double* e_last_out) {
           double w = 0.0;
           int iters = 0;
           bool conv = false;
+          // the next step is the neighbour in this direction, or the same site where the
+          // sweep turns (a half sweep ends where the next one starts)
+          next_hint_ = step < L_ - 2 ? i + dir : i;
           double e = sweep_step(i, dir, D, gamma, &w, &iters, &conv);
           all_conv = all_conv && conv;
           e_min = std::min(e_min, e);
@@ -2843,6 +2847,8 @@ void Engine::update(int i, int dir) {
 double Engine::sweep_step(int i, int dir, int D, double gamma, double* w_disc, int* iters, bool* conv) {
   check_ready();
   if (i < 0 || i > L_ - 2) throw std::out_of_range("site out of range");
+  const int next = next_hint_;
+  next_hint_ = -1;
   // a change of direction starts a half sweep: the noise of its steps is bounded by the
   // largest discarded weight of the previous one (Sec. 4.2)
   if (dir != half_dir_) {
@@ -2862,18 +2868,45 @@ double Engine::sweep_step(int i, int dir, int D, double gamma, double* w_disc, i
   cached_ = nullptr;  // keep P's combined operators for the update below
   cached_site_ = -1;
   double w;
+  bool keep = false;
   try {
     w = truncate(i, dir, D, x, 0.0);
     half_wmax_ = std::max(half_wmax_, w);
     launch_rq();  // after the decomposition, whose kernels would otherwise queue behind it
     if (dir > 0) update_left_from(i, P->cl);
     else update_right_from(i + 1, P->cr);
+    // The step changed only the middle bond i+1: the environments at bonds i and i+2 and
+    // the x layout of site i, everything P is made of, are unchanged, so a next step at
+    // the same site reuses P.  A next step at another site has its tables built here,
+    // on the host, while the FP64 Rayleigh quotient runs on the side stream.
+    if (next == i) {
+      keep = true;
+    } else if (next >= 0 && next <= L_ - 2) {
+      cached_ = plan_matvec(next);
+      cached_->serial = ++plan_serial_;
+      cached_site_ = next;
+      if (precision_ == 1) {
+        try {
+          build_tc(cached_);
+        } catch (...) {
+          release_tc(cached_);
+          throw;
+        }
+      }
+    }
   } catch (...) {
     if (rq_pending_) { try { finish_rq(); } catch (...) {} }
+    free_plan(P);
+    dev_free(x, stream_);
     throw;
   }
   if (rq_pending_) e = finish_rq() + econst_;
-  free_plan(P);
+  if (keep) {
+    cached_ = P;
+    cached_site_ = i;
+  } else {
+    free_plan(P);
+  }
   dev_free(x, stream_);
   st_.micro_iters += 1;
   *w_disc = w;

@@ -151,6 +151,9 @@ class Engine {
   double sweep_step(int i, int dir, int D, double gamma, double* w_disc, int* iters, bool* conv);
   // the operator update of a sweep step in direction dir, after truncate(i, dir, ...)
   void update(int i, int dir);
+  // the site of the next sweep_step (-1: unknown), used once by the next sweep_step to
+  // build that site's tables while its FP64 energy is being evaluated
+  void set_next_site(int s) { next_hint_ = s; }
   void canonicalize(int center);
   // Spin-summed 1- and 2-RDMs of the current MPS (device outputs, L^2 and L^4 doubles,
   // row-major): Gamma_ijkl = sum_st <a+_is a+_jt a_lt a_ks> projected onto the eight
@@ -257,6 +260,7 @@ class Engine {
   int half_dir_ = 0;
   double half_wmax_ = 0.0;
   uint64_t noise_counter_ = 0;
+  int next_hint_ = -1;
   void* ev_[3] = {nullptr, nullptr, nullptr};
   void flush_events();
   bool ev_pending_ = false;

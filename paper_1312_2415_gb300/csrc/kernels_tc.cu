@@ -46,16 +46,16 @@ namespace {
 
 constexpr long long kSpinLimit = 1ll << 22;  // polls of an mbarrier before giving up (seconds)
 constexpr int kTF = 128 * 32;                // floats of a 128-row x 32-column tile (16 KB)
-constexpr int kS1 = 2;                       // slots of the product-1 operand ring
+constexpr int kMaxS1 = 8;                    // slots of the product-1 operand ring, at most
+constexpr int kS1KB = 96;                    // shared memory of the product-1 ring (KB)
 constexpr int kWBuf = 4;                     // W^T accumulators (64 tensor-memory columns each)
 constexpr int kYCol = kWBuf * 64;            // first tensor-memory column of the y^T accumulator
 constexpr int kTmemCols = 512;
 // shared memory (floats): product-1 slot = D tile hi, lo (128 rows) and x tile hi, lo
 // (64 rows); product 2: C tiles (128 rows x 2 chunks, hi, lo) and W^T tiles (same)
-constexpr int kS1F = 2 * kTF + kTF;
 constexpr int kB2F = 4 * kTF;
 constexpr int kA2F = 4 * kTF;
-constexpr int kSmemF = kS1 * kS1F + kB2F + kA2F;
+constexpr int kSmemF = kS1KB * 256 + kB2F + kA2F;
 constexpr int kSegChunks = 2;   // K chunks per product-1 accumulator (then added in registers)
 constexpr int kFlushTerms = 16; // terms summed in FP32 registers before they are added to y (FP64)
 constexpr int kProducerWarp = 0, kMmaWarp = 1, kConvWarps = 8;
@@ -194,7 +194,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 }
 
 struct Bars {
-  uint64_t s1_full[kS1], s1_empty[kS1];
+  uint64_t s1_full[kMaxS1], s1_empty[kMaxS1];
   uint64_t b2_full, b2_empty;
   uint64_t w_full[kWBuf], w_empty[kWBuf];
   uint64_t a2_full, mma2_done;
@@ -205,8 +205,9 @@ __global__ void __launch_bounds__(kMvThreads, 1)
     k_tc_matvec(const TfTile* __restrict__ tiles, const TfTask* __restrict__ tasks, const TfSrc* __restrict__ srcs) {
   extern __shared__ unsigned char smem_dyn[];
   float* sm = (float*)(((uintptr_t)smem_dyn + 1023) & ~(uintptr_t)1023);
-  float* s1 = sm;                      // kS1 slots: D hi, D lo (kTF each), x hi, x lo (kTF / 2 each)
-  float* b2 = sm + kS1 * kS1F;         // C: chunk 0 hi, lo, chunk 1 hi, lo
+  float* s1 = sm;                      // product-1 slots: D hi, D lo (nvg KB each), x hi, x lo (kdg KB each)
+  float* b2 = sm + kS1KB * 256;        // C: chunk 0 hi, lo, chunk 1 hi, lo (follows the slots, which
+                                       // the MMA's reads of a whole 128-row D tile may run past)
   float* a2 = b2 + kB2F;               // W^T: chunk 0 hi, lo, chunk 1 hi, lo
   __shared__ __align__(8) Bars bar;
   __shared__ uint32_t tmem_slot;
@@ -217,7 +218,7 @@ __global__ void __launch_bounds__(kMvThreads, 1)
   const int T = tile.t_end - tile.t_begin;
   if (warp == kMmaWarp) tmem_alloc(&tmem_slot, kTmemCols);
   if (tid == 0) {
-    for (int s = 0; s < kS1; ++s) {
+    for (int s = 0; s < kMaxS1; ++s) {
       mbar_init_n(&bar.s1_full[s], 1);
       mbar_init_n(&bar.s1_empty[s], 1);
     }
@@ -249,6 +250,10 @@ __global__ void __launch_bounds__(kMvThreads, 1)
   __syncthreads();
 
   const int nvg = (tile.nv + 7) >> 3, mg = (tile.m + 7) >> 3;
+  // product-1 slots sized for this tile (its output columns and its largest term), as
+  // many as fit: small blocks keep more copies in flight
+  const int slot_f = 2 * (nvg + tile.kdg) * 256;
+  const int nslots = min(kMaxS1, (kS1KB * 256) / slot_f);
   if (warp == kProducerWarp) {
     // ---- producer: bulk copies in the order the MMA thread consumes them
     if (lane == 0 && !abort_flag) {
@@ -275,16 +280,16 @@ __global__ void __launch_bounds__(kMvThreads, 1)
         for (int si = tk.s_begin; si < tk.s_end && ok; ++si) {
           const TfSrc S = srcs[si];
           for (int kk = 0; kk < S.nkc; ++kk, ++step) {
-            const int slot = step % kS1, use = step / kS1;
+            const int slot = step % nslots, use = step / nslots;
             if (use >= 1 && !wait_or_abort(&bar.s1_empty[slot], (use - 1) & 1, &abort_flag)) { ok = false; break; }
-            float* dst = s1 + slot * kS1F;
+            float* dst = s1 + slot * slot_f;
             const float* d = S.d + (int64_t)kk * S.d_cs;
             const float* x = S.x + (int64_t)kk * S.x_cs;
             mbar_expect_tx(&bar.s1_full[slot], bytes);
             bulk_g2s(dst, d, nvg * 1024u, &bar.s1_full[slot]);
-            bulk_g2s(dst + kTF, d + tile.dlo, nvg * 1024u, &bar.s1_full[slot]);
-            bulk_g2s(dst + 2 * kTF, x, kdg * 1024u, &bar.s1_full[slot]);
-            bulk_g2s(dst + 2 * kTF + kTF / 2, x + tile.xlo, kdg * 1024u, &bar.s1_full[slot]);
+            bulk_g2s(dst + nvg * 256, d + tile.dlo, nvg * 1024u, &bar.s1_full[slot]);
+            bulk_g2s(dst + 2 * nvg * 256, x, kdg * 1024u, &bar.s1_full[slot]);
+            bulk_g2s(dst + (2 * nvg + tile.kdg) * 256, x + tile.xlo, kdg * 1024u, &bar.s1_full[slot]);
           }
         }
         if (ok && t >= 1) ok = load_b2(t - 1);
@@ -292,8 +297,8 @@ __global__ void __launch_bounds__(kMvThreads, 1)
       if (ok && T >= 1) load_b2(T - 1);
       // copies still in flight land before the CTA can exit: wait for the last fill of
       // every slot (a completed phase keeps testing complete while no newer one starts)
-      for (int s = 0; s < kS1; ++s) {
-        const int fills = step / kS1 + (s < step % kS1 ? 1 : 0);
+      for (int s = 0; s < nslots; ++s) {
+        const int fills = step / nslots + (s < step % nslots ? 1 : 0);
         if (fills > 0) wait_drain(&bar.s1_full[s], (fills - 1) & 1);
       }
       if (b2_loads > 0) wait_drain(&bar.b2_full, (b2_loads - 1) & 1);
@@ -314,13 +319,13 @@ __global__ void __launch_bounds__(kMvThreads, 1)
               const int q = src_ctr % kWBuf, use = src_ctr / kWBuf;
               if (use >= 1 && !wait_or_abort(&bar.w_empty[q], (use - 1) & 1, &abort_flag)) { ok = false; break; }
               for (int kk = k0; kk < min(S.nkc, k0 + kSegChunks); ++kk, ++step) {
-                const int slot = step % kS1;
-                if (!wait_or_abort(&bar.s1_full[slot], (step / kS1) & 1, &abort_flag)) { ok = false; break; }
+                const int slot = step % nslots;
+                if (!wait_or_abort(&bar.s1_full[slot], (step / nslots) & 1, &abort_flag)) { ok = false; break; }
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 const int kv = kk == S.nkc - 1 ? S.klast : 32;
-                const float* base = s1 + slot * kS1F;
-                mma_chunk(tmem + (uint32_t)(q * 64), base, base + kTF, base + 2 * kTF, base + 2 * kTF + kTF / 2,
-                          (kv + 7) & ~7, idesc1, kk == k0);
+                const float* base = s1 + slot * slot_f;
+                mma_chunk(tmem + (uint32_t)(q * 64), base, base + nvg * 256, base + 2 * nvg * 256,
+                          base + (2 * nvg + tile.kdg) * 256, (kv + 7) & ~7, idesc1, kk == k0);
                 mma_commit(&bar.s1_empty[slot]);
               }
               if (!ok) break;

@@ -83,3 +83,32 @@ def mps_from_bytes(data, irreps):
             m.T[k][(ls, lsec, rsec)] = blk
     assert pos == len(data)
     return m
+
+
+def truncation_bound(groups, D):
+    """Element-wise tolerance of the library's truncated two-site tensor against the
+    oracle's for a cut keeping D reduced values: the library decomposes through Gram
+    matrices (M M^T or M^T M) formed with an error ~ eps |M|^2, so the kept subspace moves
+    by ~ eps lambda_max^2 / gap with gap = lambda_D^2 - lambda_{D+1}^2 (Davis-Kahan), and
+    it treats values below 3e-8 lambda_max as zero (their weight bounds the rest)."""
+    import numpy as np
+    vals = sorted(((float(v), g[0][0] + 1) for g in groups for v in g[6]), reverse=True)
+    lam = np.array([v for v, _ in vals])
+    kept = min(D, int(np.sum(lam > 3e-8 * lam[0])))
+    gap = lam[kept - 1] ** 2 - lam[kept] ** 2 if kept < lam.size else lam[0] ** 2
+    # values the oracle keeps (among the first D) but the library treats as zero
+    tiny = np.sqrt(sum(w * v * v for v, w in vals[:D] if v <= 3e-8 * lam[0]))
+    return 1e-12 + 64 * 2.2e-16 * lam[0] ** 2 / max(gap, 1e-300) + 2.0 * tiny
+
+
+def widest_cut(groups, D, window):
+    """The cut within D +- window with the largest gap lambda_D^2 - lambda_{D+1}^2 of the
+    reduced spectrum (so that the truncation is well defined)."""
+    import numpy as np
+    lam = np.sort(np.concatenate([g[6] for g in groups]))[::-1]
+    best, best_gap = D, -1.0
+    for d in range(max(1, D - window), min(lam.size - 1, D + window) + 1):
+        g = lam[d - 1] ** 2 - lam[d] ** 2
+        if g > best_gap:
+            best, best_gap = d, g
+    return best, best_gap / lam[0] ** 2

@@ -140,3 +140,28 @@ def test_decomposed_step_equals_sweep_step(Context):
         eo, wo = odmrg.micro_iteration(prob, mo, i, D, "right")
         assert oka and okb
         assert abs(ea - eo) < 1e-9 and abs(eb - eo) < 1e-9 and abs(wa - wb) < 1e-12 and abs(wa - wo) < 1e-10
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_next_site_hint_does_not_change_results(Context, precision):
+    """dmrg_set_next_site only changes when tables are built (a step at the same site
+    keeps them; another site's are built while the step finishes): a sweep with hints
+    gives the energies and discarded weights of the same sweep without them."""
+    L, N, D = 8, 8, 20
+    irr, h, V = system("random", L, 4)
+    m0 = om.right_canonicalize(om.random_mps(irr, N, 0, 0, D, uniform_pm1(12, 10 ** 6)))
+    out = []
+    for hint in (False, True):
+        c = Context(L, irr, N, 0, 0, precision=precision)
+        c.set_integrals(h, V)
+        c.set_schedule([D], [0.0], [1], [0.0], 1e-12, 400)
+        c.set_mps(mps_to_bytes(m0))
+        seq = [(i, 1) for i in range(L - 1)] + [(i, -1) for i in range(L - 2, -1, -1)] + [(0, 1), (1, 1)]
+        res = []
+        for k, (i, d) in enumerate(seq):
+            if hint and k + 1 < len(seq):
+                c.set_next_site(seq[k + 1][0])
+            e, w, it, ok = c.sweep_step(i, d, D)
+            res.append((e, w))
+        out.append(np.array(res))
+    assert np.abs(out[0] - out[1]).max() < 1e-10

@@ -13,7 +13,7 @@ import pytest
 from oracle import dmrg as odmrg
 from oracle import mps as om
 from oracle.fci import fci_ground_state
-from tests.mps_io import lib_x_to_oracle, mps_to_bytes, oracle_x_to_lib
+from tests.mps_io import lib_x_to_oracle, mps_to_bytes, oracle_x_to_lib, truncation_bound, widest_cut
 from workloads import (hubbard_chain, make_problem, random_integrals, round_robin_irreps,
                        uniform_pm1)
 
@@ -86,7 +86,11 @@ def test_matvec_diag_and_eq25_match_oracle(Context, case):
 @pytest.mark.parametrize("direction", [1, -1])
 def test_truncation_matches_oracle(Context, case, direction):
     """Eqs. 26-28: the discarded weight and the truncated two-site tensor (gauge
-    invariant) agree with the oracle; D below the rank forces a real truncation."""
+    invariant) agree with the oracle.  A cut of the ground state at the widest gap of its
+    reduced spectrum between D = 2 and 6 forces a real truncation; a random unit vector (full rank,
+    no values near the library's zero threshold) is decomposed without a cut.  The
+    tolerance is the Davis-Kahan bound of the library's Gram route (tests/mps_io), asserted
+    to be small itself."""
     kind, L, N, tS, IG, D = case
     i = L // 2 - 1
     irr, h, V, m, prob = setup(kind, L, N, tS, IG, D, 7, i)
@@ -98,26 +102,26 @@ def test_truncation_matches_oracle(Context, case, direction):
     ctx.set_mps(mps_to_bytes(m))
     n, table = ctx.layout(i)
     x = oracle_x_to_lib(vec, table, n)
-    for Dt in (3, 10 ** 6):
+    # the cut between D = 2 and 6 with the widest gap of the reduced spectrum (stated
+    # minimum: 1e-4 of lambda_max^2)
+    _, _, full = om.svd_truncate(m.copy(), i, {k: v.copy() for k, v in vec.items()}, 10 ** 9, "right")
+    cut, rel_gap = widest_cut(full, 4, 2)
+    assert rel_gap > 1e-4, rel_gap
+    rnd = np.random.default_rng(direction + 31).normal(size=n)
+    rnd /= np.linalg.norm(rnd)
+    for Dt, xv in ((cut, x), (10 ** 6, rnd)):
         m2 = m.copy()
-        wd_o, kept, groups = om.svd_truncate(m2, i, {k: v.copy() for k, v in vec.items()}, Dt,
+        wd_o, kept, groups = om.svd_truncate(m2, i, lib_x_to_oracle(xv, table), Dt,
                                              "right" if direction > 0 else "left")
         ctx.set_mps(mps_to_bytes(m))
-        wd = ctx.truncate(i, direction, Dt, x)
+        wd = ctx.truncate(i, direction, Dt, xv)
         assert abs(wd - wd_o) < 1e-12
         xl = ctx.tt_to_x(i)
         xo = oracle_x_to_lib(om.tt_to_x(m2, i), table, n)
-        # The library decomposes through the Gram matrix M M^T (or M^T M), formed with
-        # an error ~ eps |M|^2; the kept subspace then moves by ~ eps lambda_max^2 / gap
-        # with gap = lambda_D^2 - lambda_{D+1}^2 at the cut (Davis-Kahan).
-        # Values below 3e-8 lambda_max are zero for the library (the resolution of the
-        # Gram route) while the oracle keeps them down to 1e-13: their weight bounds the
-        # remaining difference.
-        lam = np.sort(np.concatenate([g[6] for g in groups]))[::-1]
-        kept_n = min(Dt, int(np.sum(lam > 3e-8 * lam[0])))
-        gap = lam[kept_n - 1] ** 2 - lam[kept_n] ** 2 if kept_n < lam.size else lam[0] ** 2
-        tiny = np.sqrt(sum((g[0][0] + 1) * np.sum(g[6][g[6] <= 3e-8 * lam[0]] ** 2) for g in groups))
-        tol = 1e-12 + 64 * 2.2e-16 * lam[0] ** 2 / max(gap, 1e-300) + 2.0 * tiny
+        # Davis-Kahan bound of the library's Gram route plus the weight of values it
+        # treats as zero (tests/mps_io.truncation_bound), asserted small itself
+        tol = truncation_bound(groups, Dt)
+        assert tol < 1e-9, (Dt, tol)
         assert np.abs(xl - xo).max() < tol
 
 
