@@ -189,6 +189,7 @@ struct TfTile {         // one output tile of y, computed by one CTA from all of
   int64_t cost;         // MMA steps (tiles run in decreasing order of cost)
   int kdg;              // x row groups of the tile's largest term (sizes its product-1 slots)
   int pad;
+  int64_t group;        // right sector of the output block (tiles of a group share operator blocks)
 };
 // one FP64 block (rows x cols, row-major) to tiled hi / lo (nrg = ceil(rows / 8) row
 // groups per chunk; lo = hi + lo floats); identity != 0: the rows x rows identity

@@ -1423,7 +1423,7 @@ void Engine::tc_tables(MatvecPlan* P, TcTune tune) {
       for (int row0 = 0; row0 < X.rows; row0 += RT)
         for (int col0 = 0; col0 < X.cols; col0 += 128) {
           TfTile T{P->yout + X.off + (int64_t)row0 * X.cols + col0, X.cols, std::min(RT, X.rows - row0),
-                   std::min(128, X.cols - col0), (int)tk, 0, P->tc_ops_lo, P->tc_x_lo, 0, 1, 0};
+                   std::min(128, X.cols - col0), (int)tk, 0, P->tc_ops_lo, P->tc_x_lo, 0, 1, 0, X.r};
           for (int wi : P->w_by_x[x]) {
             const auto& w = P->witems[wi];
             const CombOp& C = P->cl[w.gl];

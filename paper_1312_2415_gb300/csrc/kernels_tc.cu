@@ -34,6 +34,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <unordered_map>
 #include <stdexcept>
 #include <string>
 
@@ -516,6 +517,7 @@ TcPlan* tc_plan_build(const std::vector<const TcHost*>& inst, Stream st) {
     std::vector<TfTile> tl;
     std::vector<TfConv> xb;
     const bool single = inst.size() == 1;
+    int64_t inst_id = 0;
     for (const TcHost* H : inst) {
       if (single) break;  // one instance: its tables are uploaded as they are
       const int s0 = (int)s.size(), t0 = (int)t.size();
@@ -528,16 +530,31 @@ TcPlan* tc_plan_build(const std::vector<const TcHost*>& inst, Stream st) {
       for (TfTile q : H->tiles) {
         q.t_begin += t0;
         q.t_end += t0;
+        q.group += inst_id << 32;  // groups never span instances
         tl.push_back(q);
       }
+      ++inst_id;
       xb.insert(xb.end(), H->xb.begin(), H->xb.end());
     }
     const std::vector<TfTile>& tiles0 = single ? inst[0]->tiles : tl;
-    // tiles in decreasing order of work (the hardware starts CTAs in launch order, so
-    // the longest tiles do not finish last)
+    // Tiles of output blocks with the same right sector read the same right-operator
+    // blocks: they run together (so that those blocks stay in L2), groups in decreasing
+    // order of their largest tile and tiles in decreasing order of work within a group
+    // (the hardware starts CTAs in launch order, so the longest work does not finish last)
+    std::unordered_map<int64_t, int64_t> gmax;
+    for (const TfTile& q : tiles0) {
+      int64_t& g = gmax[q.group];
+      g = std::max(g, q.cost);
+    }
     std::vector<int> order(tiles0.size());
     for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return tiles0[a].cost > tiles0[b].cost; });
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+      const TfTile &A = tiles0[a], &B = tiles0[b];
+      const int64_t ga = gmax[A.group], gb = gmax[B.group];
+      if (ga != gb) return ga > gb;
+      if (A.group != B.group) return A.group < B.group;
+      return A.cost > B.cost;
+    });
     std::vector<TfTile> sorted(tiles0.size());
     for (size_t i = 0; i < order.size(); ++i) sorted[i] = tiles0[order[i]];
     P->tiles = upload(sorted, st);
