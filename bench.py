@@ -381,7 +381,10 @@ def roofline_fp64(delta, peak64):
 def energy_agreement(ctx, center, D, args):
     """Both Davidsons from the same two-site vector (no truncation in between), converged
     to 1e-9: the FP64 eigenvalue and the mixed-precision one (FP64 Rayleigh quotient
-    after the FP64 finishing iterations)."""
+    after the FP64 finishing iterations).  Also the Rayleigh quotient of the FP64
+    eigenvector through the tensor-core matvec against the FP64 one: the bias of the
+    tensor cores' FP32 accumulation, which is why energies (and the renormalised
+    operators, which enter H itself) stay FP64."""
     import numpy as np
     import torch
     ctx.set_schedule([D], [0.0], [1], [0.0], 1e-9, 300)
@@ -398,8 +401,54 @@ def energy_agreement(ctx, center, D, args):
         out[name] = {"energy": e, "iterations": it, "converged": bool(ok), "s": time.perf_counter() - t0,
                      "tc_matvecs": int(st1["tc_matvecs"] - st0["tc_matvecs"]),
                      "fp64_matvecs": int(st1["k_launches"] - st0["k_launches"])}
+        if name == "fp64":
+            x64 = x.clone()
     out["abs_diff_eh"] = abs(out["mixed"]["energy"] - out["fp64"]["energy"])
     out["target_eh"] = 1e-6
+    y = torch.empty_like(x64)
+    rq = {}
+    for name, prec in (("fp64", 0), ("tensor_core", 1)):
+        ctx.set_precision(prec, 0)
+        ctx.matvec(center, x64, y)
+        torch.cuda.synchronize()
+        rq[name] = (x64 @ y).item() / (x64 @ x64).item()
+    out["rayleigh_quotient_tensor_core_minus_fp64_eh"] = rq["tensor_core"] - rq["fp64"]
+    ctx.set_precision(args.precision, args.fp64_iters)
+    return out
+
+
+def converged_agreement():
+    """The metric's |dE| <= 1e-6 Eh on converged DMRG: the L=12 random-integral system
+    (N=12, S=0, D2h irreps round-robin, D_SU(2)=500), macro-iterations until the energy
+    changes by less than 1e-10 Eh (at most 4), Davidson tolerance 1e-9, both precisions
+    from the same initial MPS; the mixed path runs the tensor-core Davidson, then FP64
+    Davidson iterations to the tolerance.  With the seconds of each solve."""
+    import torch
+    from paper_1312_2415_gb300 import Context
+    from workloads import make_problem
+    cfg, h, V = make_problem("random12")
+    out = {"workload": f"random12: random integrals L={cfg['L']} N={cfg['N']} S=0 Ag, D2h round-robin, "
+                       f"D_SU(2)={cfg['D']}, solved to convergence (E_conv 1e-10 Eh, at most 4 macro-iterations, "
+                       "Davidson tolerance 1e-9)"}
+    for name, prec in (("fp64", 0), ("mixed", 1)):
+        ctx = Context(cfg["L"], cfg["group_irreps"], cfg["N"], cfg["two_S"], cfg["irrep"], group=7,
+                      precision=prec)
+        ctx.set_integrals(h, V)
+        ctx.set_schedule([cfg["D"]], [1e-10], [4], [0.0], 1e-9, 200)
+        ctx.set_precision(prec, 0)
+        ctx.init_mps(cfg["seed"])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        emin, elast = ctx.solve()
+        torch.cuda.synchronize()
+        s = time.perf_counter() - t0
+        st = ctx.stats()
+        out[name] = {"energy": emin, "energy_last": elast, "s": s, "tc_matvecs": int(st["tc_matvecs"]),
+                     "davidson_iterations": int(st["davidson_iters"])}
+        ctx.close()
+    out["abs_diff_eh"] = abs(out["mixed"]["energy"] - out["fp64"]["energy"])
+    out["target_eh"] = 1e-6
+    out["speedup_mixed_vs_fp64"] = out["fp64"]["s"] / out["mixed"]["s"]
     return out
 
 
@@ -598,10 +647,12 @@ def run_gb300(args):
     1. one mixed-precision macro-iteration from the initial MPS of Sec. 4.3 (the metric's
        mixed sweep time); its end state is the swept state the headline steps use;
     2. one FP64 macro-iteration from the same initial MPS with the same Davidson settings
-       (the FP64 sweep time) and the agreement of the two sweeps' energies;
+       (the FP64 sweep time);
     3. the timed micro-iterations at the middle pair of the swept state (value), the same
-       steps on the FP64 path, the converged-Davidson energy agreement at that pair, the
-       roofline of the matvec kernel, and e2e through the host-buffer C ABI."""
+       steps on the FP64 path, the converged-Davidson energy agreement at that pair (and
+       the tensor-core Rayleigh quotient's bias), the energy agreement of converged DMRG
+       in both precisions on the L=12 system, the roofline of the matvec kernel, and e2e
+       through the host-buffer C ABI."""
     import torch
     if args.workload == "batch32":
         return run_batch(args)
@@ -633,10 +684,12 @@ def run_gb300(args):
         if mixed and not args.no_fp64 and not args.no_fp64_sweep:
             ctx.set_mps(start)
             sweeps["fp64"] = sweep_time(ctx, L, D, 0, 0, args.davidson_iters)
-            sweeps["agreement"] = {
+            # not the agreement criterion: one unconverged macro-iteration from a random
+            # MPS at fixed Davidson iterations amplifies matvec rounding into different
+            # trajectories (converged_agreement and energy_agreement carry the criterion)
+            sweeps["trajectory_difference"] = {
                 "abs_diff_last_eh": abs(sweeps["mixed"]["energy_last"] - sweeps["fp64"]["energy_last"]),
-                "abs_diff_min_eh": abs(sweeps["mixed"]["energy_min"] - sweeps["fp64"]["energy_min"]),
-                "target_eh": 1e-6}
+                "abs_diff_min_eh": abs(sweeps["mixed"]["energy_min"] - sweeps["fp64"]["energy_min"])}
             sweeps["speedup_mixed_vs_fp64"] = sweeps["fp64"]["macro_s"] / sweeps["mixed"]["macro_s"]
         ctx.set_mps(swept)
         state = "the state one mixed macro-iteration at D leaves (swept state)"
@@ -671,6 +724,7 @@ def run_gb300(args):
     ctx.set_mps(swept_state)
     ctx.canonicalize(center)
     acc = energy_agreement(ctx, center, D, args) if not args.no_fp64 else None
+    conv = converged_agreement() if not args.no_fp64 and not args.no_sweep else None
     # one marked matvec in each precision after the timed region (NVTX range for profilers)
     xprof = torch.tensor(ctx.tt_to_x(center), dtype=torch.float64, device="cuda")
     yprof = torch.empty_like(xprof)
@@ -705,7 +759,7 @@ def run_gb300(args):
                    "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (renormalised operators of both environments, several GB)",
                    "block_histogram": hist},
-        "matvec": rates, "fp64": fp64, "energy_agreement": acc, "sweep": sweeps,
+        "matvec": rates, "fp64": fp64, "energy_agreement": acc, "converged_agreement": conv, "sweep": sweeps,
         "micro_iteration_s": t_max / args.steps / 1e3,
         "step_breakdown_ms": step_breakdown(delta, args.steps),
         "energy_last": energies[-1] if energies else None,
