@@ -17,15 +17,21 @@
 //              (FP64) every few terms.  The tensor core's own FP32 accumulation loses
 //              accuracy over long runs of products, hence the short accumulators.
 // Every product uses split TF32: v = hi + lo with hi = rna_tf32(v), lo = rna_tf32(v - hi),
-// and the three leading products hi*hi + hi*lo + lo*hi (about 2^-21 relative).
+// and the three leading products hi*hi + hi*lo + lo*hi (about 2^-21 relative).  The
+// second operand's hi and lo tiles sit one above the other in shared memory, so one MMA
+// of twice the N gives A_hi B_hi^T and A_hi B_lo^T side by side in the accumulator and a
+// second one adds A_lo B_hi^T to the first half: two instructions per K step instead of
+// three.  An M = 128 tf32 MMA costs the issuing thread about 40-50 cycles whatever its N
+// up to 64, so fewer, wider instructions are what the small blocks of this method need;
+// products 1 and 2 are issued by two threads.
 //
 // Operands live in global memory already split and tiled in the K-major core-matrix
 // order the MMA reads (see device.hpp), so a warp-specialised pipeline moves them with
-// cp.async.bulk into a shared-memory ring (one producer thread, completion counted in
-// bytes on mbarriers) and a single thread issues the MMAs; only W^T passes through
-// registers.  The shared-memory operand descriptors are K-major without swizzle: core
-// matrices of 8 rows x 16 bytes, 128 bytes apart along K (LBO) and 1024 bytes apart
-// along M/N (SBO), for 32-column chunks.
+// cp.async.bulk into shared memory (completion counted in bytes on mbarriers): a producer
+// thread fills the product-1 ring, the product-2 thread loads the C tiles itself; only
+// W^T passes through registers.  The shared-memory operand descriptors are K-major
+// without swizzle: core matrices of 8 rows x 16 bytes, 128 bytes apart along K (LBO) and
+// 1024 bytes apart along M/N (SBO), for 32-column chunks.
 //
 // Every wait is bounded: a CTA that gives up records an error, stops issuing work, waits
 // (bounded) for its own copies and products in flight, frees its tensor memory and
@@ -49,18 +55,19 @@ constexpr long long kSpinLimit = 1ll << 22;  // polls of an mbarrier before givi
 constexpr int kTF = 128 * 32;                // floats of a 128-row x 32-column tile (16 KB)
 constexpr int kMaxS1 = 8;                    // slots of the product-1 operand ring, at most
 constexpr int kS1KB = 96;                    // shared memory of the product-1 ring (KB)
-constexpr int kWBuf = 4;                     // W^T accumulators (64 tensor-memory columns each)
-constexpr int kYCol = kWBuf * 64;            // first tensor-memory column of the y^T accumulator
+constexpr int kMaxW = 6;                     // W^T accumulators in tensor memory, at most
+constexpr int kMaxB2 = 2;                    // C slots, at most
 constexpr int kTmemCols = 512;
-// shared memory (floats): product-1 slot = D tile hi, lo (128 rows) and x tile hi, lo
-// (64 rows); product 2: C tiles (128 rows x 2 chunks, hi, lo) and W^T tiles (same)
+// shared memory (floats): product-1 slot = D tile hi, lo (up to 128 rows) and x tile hi,
+// lo (kp rows each); product 2: C slots (2 x 128 rows x 2 chunks in all) and W^T tiles
+// (128 rows x 2 chunks, hi, lo)
 constexpr int kB2F = 4 * kTF;
 constexpr int kA2F = 4 * kTF;
 constexpr int kSmemF = kS1KB * 256 + kB2F + kA2F;
 constexpr int kSegChunks = 2;   // K chunks per product-1 accumulator (then added in registers)
 constexpr int kFlushTerms = 16; // terms summed in FP32 registers before they are added to y (FP64)
-constexpr int kProducerWarp = 0, kMmaWarp = 1, kConvWarps = 8;
-constexpr int kMvThreads = (2 + kConvWarps) * 32;
+constexpr int kProducerWarp = 0, kMma1Warp = 1, kMma2Warp = 2, kConvWarp0 = 3, kConvWarps = 8;
+constexpr int kMvThreads = (kConvWarp0 + kConvWarps) * 32;
 constexpr int kConvThreads = kConvWarps * 32;
 
 __device__ int g_tc_error = 0;
@@ -98,19 +105,6 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, 
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
       "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
-
-// the three split products of one 32-column K chunk (kpad / 8 steps of K = 8); the
-// first product restarts the accumulator when `fresh`
-__device__ __forceinline__ void mma_chunk(uint32_t tmem, const float* Ah, const float* Al, const float* Bh,
-                                          const float* Bl, int kpad, uint32_t idesc, bool fresh) {
-  const uint32_t ah = smem_u32(Ah), al = smem_u32(Al), bh = smem_u32(Bh), bl = smem_u32(Bl);
-  for (int st = 0; st < kpad / 8; ++st) {
-    const uint32_t ko = st * 256;  // 8 columns = two core matrices along K
-    mma_tf32(tmem, smem_desc(ah + ko), smem_desc(bh + ko), idesc, (fresh && st == 0) ? 0u : 1u);
-    mma_tf32(tmem, smem_desc(ah + ko), smem_desc(bl + ko), idesc, 1u);
-    mma_tf32(tmem, smem_desc(al + ko), smem_desc(bh + ko), idesc, 1u);
-  }
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t* mbar) {
@@ -181,34 +175,60 @@ __device__ __forceinline__ void tmem_free(uint32_t tmem, uint32_t cols) {
   asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(cols));
 }
 
-// 16 consecutive accumulator columns of this warp's 32 lanes
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
+// 32 consecutive accumulator columns of this warp's 32 lanes
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
 struct Bars {
   uint64_t s1_full[kMaxS1], s1_empty[kMaxS1];
-  uint64_t b2_full, b2_empty;
-  uint64_t w_full[kWBuf], w_empty[kWBuf];
+  uint64_t b2_full[kMaxB2], b2_empty[kMaxB2];
+  uint64_t w_full[kMaxW], w_empty[kMaxW];
   uint64_t a2_full, mma2_done;
-  uint64_t drain, never;
+  uint64_t drain1, drain2, never;
 };
+
+// the two split products of one K step stacked along N: A_hi [B_hi; B_lo]^T (N = 2 kp)
+// into accumulator columns [0, 2 kp) and A_lo B_hi^T (N = kp) into [0, kp); nst steps of
+// K = 8 (8 columns = 256 bytes = 16 in the descriptor's address field), the first
+// product restarting the accumulator when `fresh`
+__device__ __forceinline__ void mma_pair_steps(uint32_t tmem, uint64_t ah, uint64_t al, uint64_t b, uint32_t id2,
+                                               uint32_t id1, int nst, bool fresh) {
+  mma_tf32(tmem, ah, b, id2, fresh ? 0u : 1u);
+  mma_tf32(tmem, al, b, id1, 1u);
+  if (nst > 1) {
+    mma_tf32(tmem, ah + 16, b + 16, id2, 1u);
+    mma_tf32(tmem, al + 16, b + 16, id1, 1u);
+  }
+  if (nst > 2) {
+    mma_tf32(tmem, ah + 32, b + 32, id2, 1u);
+    mma_tf32(tmem, al + 32, b + 32, id1, 1u);
+  }
+  if (nst > 3) {
+    mma_tf32(tmem, ah + 48, b + 48, id2, 1u);
+    mma_tf32(tmem, al + 48, b + 48, id1, 1u);
+  }
+}
 
 __global__ void __launch_bounds__(kMvThreads, 1)
     k_tc_matvec(const TfTile* __restrict__ tiles, const TfTask* __restrict__ tasks, const TfSrc* __restrict__ srcs) {
   extern __shared__ unsigned char smem_dyn[];
   float* sm = (float*)(((uintptr_t)smem_dyn + 1023) & ~(uintptr_t)1023);
-  float* s1 = sm;                      // product-1 slots: D hi, D lo (nvg KB each), x hi, x lo (kdg KB each)
-  float* b2 = sm + kS1KB * 256;        // C: chunk 0 hi, lo, chunk 1 hi, lo (follows the slots, which
-                                       // the MMA's reads of a whole 128-row D tile may run past)
+  float* s1 = sm;                      // product-1 slots: D hi, D lo (nvg KB each), x hi, x lo (kp rows each)
+  float* b2 = sm + kS1KB * 256;        // C slots: per K chunk C hi (mp rows) then C lo (mp rows); they
+                                       // follow the product-1 slots, which the MMA's reads of a whole
+                                       // 128-row D tile may run past
   float* a2 = b2 + kB2F;               // W^T: chunk 0 hi, lo, chunk 1 hi, lo
   __shared__ __align__(8) Bars bar;
   __shared__ uint32_t tmem_slot;
@@ -217,21 +237,24 @@ __global__ void __launch_bounds__(kMvThreads, 1)
   const TfTile tile = tiles[blockIdx.x];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int T = tile.t_end - tile.t_begin;
-  if (warp == kMmaWarp) tmem_alloc(&tmem_slot, kTmemCols);
+  if (warp == kMma1Warp) tmem_alloc(&tmem_slot, kTmemCols);
   if (tid == 0) {
     for (int s = 0; s < kMaxS1; ++s) {
       mbar_init_n(&bar.s1_full[s], 1);
       mbar_init_n(&bar.s1_empty[s], 1);
     }
-    mbar_init_n(&bar.b2_full, 1);
-    mbar_init_n(&bar.b2_empty, 1);
-    for (int q = 0; q < kWBuf; ++q) {
+    for (int s = 0; s < kMaxB2; ++s) {
+      mbar_init_n(&bar.b2_full[s], 1);
+      mbar_init_n(&bar.b2_empty[s], 1);
+    }
+    for (int q = 0; q < kMaxW; ++q) {
       mbar_init_n(&bar.w_full[q], 1);
       mbar_init_n(&bar.w_empty[q], kConvThreads);
     }
     mbar_init_n(&bar.a2_full, kConvThreads);
     mbar_init_n(&bar.mma2_done, 1);
-    mbar_init_n(&bar.drain, 1);
+    mbar_init_n(&bar.drain1, 1);
+    mbar_init_n(&bar.drain2, 1);
     mbar_init_n(&bar.never, 1);
     asm volatile("fence.mbarrier_init.release.cluster;");
     abort_flag = 0;
@@ -244,45 +267,46 @@ __global__ void __launch_bounds__(kMvThreads, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_slot;
-  if (tid == kMmaWarp * 32 && g_tc_inject) {
+  if (tid == kMma1Warp * 32 && g_tc_inject) {
     // test hook: a wait on a barrier that nothing completes, with a short limit
     wait_or_abort(&bar.never, 0, &abort_flag, 4096);
   }
   __syncthreads();
 
+  // Per-tile geometry.  kp: x rows of a term rounded up to 32 (x hi and x lo are stacked
+  // kp rows apart); mp: output rows rounded up to 32 (C hi and C lo stacked mp rows apart).
   const int nvg = (tile.nv + 7) >> 3, mg = (tile.m + 7) >> 3;
-  // product-1 slots sized for this tile (its output columns and its largest term), as
-  // many as fit: small blocks keep more copies in flight
-  const int slot_f = 2 * (nvg + tile.kdg) * 256;
+  const int mp = (tile.m + 31) & ~31;
+  const int kpm = tile.kdg > 4 ? 64 : 32;
+  // product-1 slots sized for this tile (its output columns and its widest term), as many
+  // as fit: small blocks keep more copies in flight
+  const int slot_f = (2 * nvg + kpm / 4) * 256;
   const int nslots = min(kMaxS1, (kS1KB * 256) / slot_f);
+  // tensor memory: W^T accumulators of 2 kpm columns from column 0, y^T (2 mp columns)
+  // at the top
+  const int wcols = 2 * kpm, ycols = 2 * mp;
+  const int nw = min(kMaxW, (kTmemCols - ycols) / wcols);
+  const uint32_t ycol = (uint32_t)(kTmemCols - ycols);
+  // C slots: chunks of 2 mp rows x 32 columns, as many chunks as the widest term needs
+  const int b2_f = 2 * mp * 32 * (kpm / 32);
+  const int nb2 = min(kMaxB2, kB2F / b2_f);
+
   if (warp == kProducerWarp) {
-    // ---- producer: bulk copies in the order the MMA thread consumes them
+    // ---- producer: product-1 operands in the order the MMA thread consumes them
     if (lane == 0 && !abort_flag) {
-      int step = 0, b2_loads = 0;
-      auto load_b2 = [&](int u) -> bool {
-        if (u >= 1 && !wait_or_abort(&bar.b2_empty, (u - 1) & 1, &abort_flag)) return false;
-        const TfTask tk = tasks[tile.t_begin + u];
-        const int nch = (tk.kdl + 31) >> 5;
-        const uint32_t bytes = 2u * nch * mg * 1024u;
-        mbar_expect_tx(&bar.b2_full, bytes);
-        for (int c = 0; c < nch; ++c) {
-          const float* src = tk.c + (int64_t)c * tk.c_cs;
-          bulk_g2s(b2 + (2 * c) * kTF, src, mg * 1024u, &bar.b2_full);
-          bulk_g2s(b2 + (2 * c + 1) * kTF, src + tile.dlo, mg * 1024u, &bar.b2_full);
-        }
-        ++b2_loads;
-        return true;
-      };
+      int slot = 0, round = 0, fills = 0;
       bool ok = true;
       for (int t = 0; t < T && ok; ++t) {
         const TfTask tk = tasks[tile.t_begin + t];
-        const int kdg = (tk.kdl + 7) >> 3;
+        const int kdg = (tk.kdl + 7) >> 3, kp = tk.kdl > 32 ? 64 : 32;
         const uint32_t bytes = 2u * (nvg + kdg) * 1024u;
         for (int si = tk.s_begin; si < tk.s_end && ok; ++si) {
           const TfSrc S = srcs[si];
-          for (int kk = 0; kk < S.nkc; ++kk, ++step) {
-            const int slot = step % nslots, use = step / nslots;
-            if (use >= 1 && !wait_or_abort(&bar.s1_empty[slot], (use - 1) & 1, &abort_flag)) { ok = false; break; }
+          for (int kk = 0; kk < S.nkc; ++kk) {
+            if (round >= 1 && !wait_or_abort(&bar.s1_empty[slot], (round - 1) & 1, &abort_flag)) {
+              ok = false;
+              break;
+            }
             float* dst = s1 + slot * slot_f;
             const float* d = S.d + (int64_t)kk * S.d_cs;
             const float* x = S.x + (int64_t)kk * S.x_cs;
@@ -290,77 +314,123 @@ __global__ void __launch_bounds__(kMvThreads, 1)
             bulk_g2s(dst, d, nvg * 1024u, &bar.s1_full[slot]);
             bulk_g2s(dst + nvg * 256, d + tile.dlo, nvg * 1024u, &bar.s1_full[slot]);
             bulk_g2s(dst + 2 * nvg * 256, x, kdg * 1024u, &bar.s1_full[slot]);
-            bulk_g2s(dst + (2 * nvg + tile.kdg) * 256, x + tile.xlo, kdg * 1024u, &bar.s1_full[slot]);
-          }
-        }
-        if (ok && t >= 1) ok = load_b2(t - 1);
-      }
-      if (ok && T >= 1) load_b2(T - 1);
-      // copies still in flight land before the CTA can exit: wait for the last fill of
-      // every slot (a completed phase keeps testing complete while no newer one starts)
-      for (int s = 0; s < nslots; ++s) {
-        const int fills = step / nslots + (s < step % nslots ? 1 : 0);
-        if (fills > 0) wait_drain(&bar.s1_full[s], (fills - 1) & 1);
-      }
-      if (b2_loads > 0) wait_drain(&bar.b2_full, (b2_loads - 1) & 1);
-    }
-  } else if (warp == kMmaWarp) {
-    // ---- one thread issues the products; product 2 of term t-1 follows product 1 of t
-    if (lane == 0 && !abort_flag) {
-      int step = 0, src_ctr = 0;
-      const uint32_t idesc2 = idesc_tf32((tile.m + 15) & ~15);
-      bool ok = true;
-      for (int t = 0; t <= T && ok; ++t) {
-        if (t < T) {
-          const TfTask tk = tasks[tile.t_begin + t];
-          const uint32_t idesc1 = idesc_tf32((tk.kdl + 15) & ~15);
-          for (int si = tk.s_begin; si < tk.s_end && ok; ++si) {
-            const TfSrc S = srcs[si];
-            for (int k0 = 0; k0 < S.nkc && ok; k0 += kSegChunks, ++src_ctr) {
-              const int q = src_ctr % kWBuf, use = src_ctr / kWBuf;
-              if (use >= 1 && !wait_or_abort(&bar.w_empty[q], (use - 1) & 1, &abort_flag)) { ok = false; break; }
-              for (int kk = k0; kk < min(S.nkc, k0 + kSegChunks); ++kk, ++step) {
-                const int slot = step % nslots;
-                if (!wait_or_abort(&bar.s1_full[slot], (step / nslots) & 1, &abort_flag)) { ok = false; break; }
-                asm volatile("tcgen05.fence::after_thread_sync;");
-                const int kv = kk == S.nkc - 1 ? S.klast : 32;
-                const float* base = s1 + slot * slot_f;
-                mma_chunk(tmem + (uint32_t)(q * 64), base, base + nvg * 256, base + 2 * nvg * 256,
-                          base + (2 * nvg + tile.kdg) * 256, (kv + 7) & ~7, idesc1, kk == k0);
-                mma_commit(&bar.s1_empty[slot]);
-              }
-              if (!ok) break;
-              mma_commit(&bar.w_full[q]);
+            bulk_g2s(dst + 2 * nvg * 256 + kp * 32, x + tile.xlo, kdg * 1024u, &bar.s1_full[slot]);
+            ++fills;
+            if (++slot == nslots) {
+              slot = 0;
+              ++round;
             }
           }
         }
-        if (ok && t >= 1) {
-          const TfTask tp = tasks[tile.t_begin + t - 1];
-          if (!wait_or_abort(&bar.a2_full, (t - 1) & 1, &abort_flag) ||
-              !wait_or_abort(&bar.b2_full, (t - 1) & 1, &abort_flag)) {
-            ok = false;
-            break;
+      }
+      // copies still in flight land before the CTA can exit: wait for the last fill of
+      // every slot (a completed phase keeps testing complete while no newer one starts)
+      for (int s = 0; s < nslots; ++s) {
+        const int f = fills / nslots + (s < fills % nslots ? 1 : 0);
+        if (f > 0) wait_drain(&bar.s1_full[s], (f - 1) & 1);
+      }
+    }
+  } else if (warp == kMma1Warp) {
+    // ---- product 1: W^T = D x^T per source, segments of up to two K chunks per
+    // accumulator
+    if (lane == 0 && !abort_flag) {
+      int slot = 0, round = 0, q = 0, wround = 0;
+      bool ok = true;
+      for (int t = 0; t < T && ok; ++t) {
+        const TfTask tk = tasks[tile.t_begin + t];
+        const int kp = tk.kdl > 32 ? 64 : 32;
+        const uint32_t id2 = idesc_tf32(2 * kp), id1 = idesc_tf32(kp);
+        for (int si = tk.s_begin; si < tk.s_end && ok; ++si) {
+          const TfSrc S = srcs[si];
+          for (int k0 = 0; k0 < S.nkc; k0 += kSegChunks) {
+            if (wround >= 1 && !wait_or_abort(&bar.w_empty[q], (wround - 1) & 1, &abort_flag)) {
+              ok = false;
+              break;
+            }
+            const uint32_t wq = tmem + (uint32_t)(q * wcols);
+            const int k1 = min(S.nkc, k0 + kSegChunks);
+            for (int kk = k0; kk < k1; ++kk) {
+              if (!wait_or_abort(&bar.s1_full[slot], round & 1, &abort_flag)) {
+                ok = false;
+                break;
+              }
+              asm volatile("tcgen05.fence::after_thread_sync;");
+              const int kv = kk == S.nkc - 1 ? S.klast : 32;
+              const float* base = s1 + slot * slot_f;
+              mma_pair_steps(wq, smem_desc(smem_u32(base)), smem_desc(smem_u32(base + nvg * 256)),
+                             smem_desc(smem_u32(base + 2 * nvg * 256)), id2, id1, (kv + 7) >> 3, kk == k0);
+              mma_commit(&bar.s1_empty[slot]);
+              if (++slot == nslots) {
+                slot = 0;
+                ++round;
+              }
+            }
+            if (!ok) break;
+            mma_commit(&bar.w_full[q]);
+            if (++q == nw) {
+              q = 0;
+              ++wround;
+            }
           }
-          asm volatile("tcgen05.fence::after_thread_sync;");
-          for (int c = 0; c < 2; ++c) {
-            const int kv = min(32, tp.kdl - 32 * c);
-            if (kv <= 0) break;
-            mma_chunk(tmem + (uint32_t)kYCol, a2 + (2 * c) * kTF, a2 + (2 * c + 1) * kTF, b2 + (2 * c) * kTF,
-                      b2 + (2 * c + 1) * kTF, (kv + 7) & ~7, idesc2, c == 0);
-          }
-          mma_commit(&bar.b2_empty);
-          mma_commit(&bar.mma2_done);
         }
       }
       // every product issued has finished before tensor memory is released
-      mma_commit(&bar.drain);
-      wait_drain(&bar.drain, 0);
+      mma_commit(&bar.drain1);
+      wait_drain(&bar.drain1, 0);
+    }
+  } else if (warp == kMma2Warp) {
+    // ---- product 2: y^T = W^T C^T per term, fresh accumulator; this thread also loads
+    // the C tiles (slot u % nb2; the next fill of a slot waits for the product that read it)
+    if (lane == 0 && !abort_flag) {
+      int c_fills[kMaxB2] = {0, 0};
+      auto load_c = [&](int u) {
+        const TfTask tk = tasks[tile.t_begin + u];
+        const int nch = (tk.kdl + 31) >> 5, s = u % nb2;
+        float* dst = b2 + s * b2_f;
+        mbar_expect_tx(&bar.b2_full[s], 2u * nch * mg * 1024u);
+        for (int c = 0; c < nch; ++c) {
+          const float* src = tk.c + (int64_t)c * tk.c_cs;
+          bulk_g2s(dst + c * 2 * mp * 32, src, mg * 1024u, &bar.b2_full[s]);
+          bulk_g2s(dst + c * 2 * mp * 32 + mp * 32, src + tile.dlo, mg * 1024u, &bar.b2_full[s]);
+        }
+        ++c_fills[s];
+      };
+      for (int u = 0; u < min(nb2, T); ++u) load_c(u);
+      const uint32_t id2 = idesc_tf32(2 * mp), id1 = idesc_tf32(mp);
+      for (int t = 0; t < T; ++t) {
+        const int s = t % nb2;
+        const TfTask tk = tasks[tile.t_begin + t];
+        if (!wait_or_abort(&bar.a2_full, t & 1, &abort_flag) ||
+            !wait_or_abort(&bar.b2_full[s], (t / nb2) & 1, &abort_flag))
+          break;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const float* cb = b2 + s * b2_f;
+        for (int c = 0; c * 32 < tk.kdl; ++c) {
+          const int kv = min(32, tk.kdl - 32 * c);
+          mma_pair_steps(tmem + ycol, smem_desc(smem_u32(a2 + (2 * c) * kTF)),
+                         smem_desc(smem_u32(a2 + (2 * c + 1) * kTF)), smem_desc(smem_u32(cb + c * 2 * mp * 32)),
+                         id2, id1, (kv + 7) >> 3, c == 0);
+        }
+        mma_commit(&bar.b2_empty[s]);
+        mma_commit(&bar.mma2_done);
+        if (t + nb2 < T) {
+          if (!wait_or_abort(&bar.b2_empty[s], (t / nb2) & 1, &abort_flag)) break;
+          load_c(t + nb2);
+        }
+      }
+      // every product issued has finished before tensor memory is released, and every
+      // C copy has landed
+      mma_commit(&bar.drain2);
+      wait_drain(&bar.drain2, 0);
+      for (int s = 0; s < nb2; ++s)
+        if (c_fills[s] > 0) wait_drain(&bar.b2_full[s], (c_fills[s] - 1) & 1);
     }
   } else {
     // ---- converters: warp w reads tensor-memory lanes 32 (w % 4) .. (its output
     // columns); half 0 / 1 holds x rows 0..31 / 32..63 of W^T and output rows 0..63 /
-    // 64..127 of y
-    const int quarter = warp & 3, half = (warp - 2) >> 2;
+    // 64..127 of y.  Each accumulator holds the hi part in columns [0, kp) and the
+    // stacked lo part in [kp, 2 kp) (y^T: [0, mp) and [mp, 2 mp)); their sum is the product.
+    const int quarter = warp & 3, half = (warp - kConvWarp0) >> 2;
     const int n = quarter * 32 + lane;
     const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
     float yacc[64];
@@ -369,12 +439,15 @@ __global__ void __launch_bounds__(kMvThreads, 1)
     auto drain_y = [&]() {
       asm volatile("tcgen05.fence::after_thread_sync;");
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        if (64 * half + 16 * i < tile.m) {
-          float v[16];
-          tmem_ld16(lane_base + (uint32_t)(kYCol + 64 * half + 16 * i), v);
+      for (int i = 0; i < 2; ++i) {
+        if (64 * half + 32 * i < tile.m) {
+          float v[32];
+          tmem_ld32(lane_base + ycol + (uint32_t)(64 * half + 32 * i), v);
 #pragma unroll
-          for (int j = 0; j < 16; ++j) yacc[16 * i + j] += v[j];
+          for (int j = 0; j < 32; ++j) yacc[32 * i + j] += v[j];
+          tmem_ld32(lane_base + ycol + (uint32_t)(mp + 64 * half + 32 * i), v);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) yacc[32 * i + j] += v[j];
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;");
@@ -395,38 +468,49 @@ __global__ void __launch_bounds__(kMvThreads, 1)
       }
       stored = true;
     };
-    int src_ctr = 0;
+    int q = 0, wround = 0;
     bool ok = !abort_flag;
     for (int t = 0; t < T && ok; ++t) {
       const TfTask tk = tasks[tile.t_begin + t];
+      const int kp = tk.kdl > 32 ? 64 : 32;
       float wsum[32];
 #pragma unroll
       for (int j = 0; j < 32; ++j) wsum[j] = 0.0f;
       for (int si = tk.s_begin; si < tk.s_end && ok; ++si) {
         const float coef = srcs[si].coef;
         const int nseg = (srcs[si].nkc + kSegChunks - 1) / kSegChunks;
-        for (int g = 0; g < nseg; ++g, ++src_ctr) {
-          const int q = src_ctr % kWBuf, use = src_ctr / kWBuf;
-          if (!wait_or_abort(&bar.w_full[q], use & 1, &abort_flag)) { ok = false; break; }
+        for (int g = 0; g < nseg; ++g) {
+          if (!wait_or_abort(&bar.w_full[q], wround & 1, &abort_flag)) {
+            ok = false;
+            break;
+          }
           asm volatile("tcgen05.fence::after_thread_sync;");
           if (32 * half < tk.kdl) {
-            float v[16];
-            tmem_ld16(lane_base + (uint32_t)(q * 64 + 32 * half), v);
+            const uint32_t wa = lane_base + (uint32_t)(q * wcols + 32 * half);
+            float v[32];
+            tmem_ld32(wa, v);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) wsum[j] = fmaf(coef, v[j], wsum[j]);
-            tmem_ld16(lane_base + (uint32_t)(q * 64 + 32 * half + 16), v);
+            for (int j = 0; j < 32; ++j) wsum[j] = fmaf(coef, v[j], wsum[j]);
+            tmem_ld32(wa + (uint32_t)kp, v);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) wsum[16 + j] = fmaf(coef, v[j], wsum[16 + j]);
+            for (int j = 0; j < 32; ++j) wsum[j] = fmaf(coef, v[j], wsum[j]);
           }
           asm volatile("tcgen05.fence::before_thread_sync;");
           mbar_arrive(&bar.w_empty[q]);
+          if (++q == nw) {
+            q = 0;
+            ++wround;
+          }
         }
       }
       if (!ok) break;
       // product 2 of the previous term has finished: its result is added to the
-      // registers and the W^T tiles may be overwritten
+      // registers, and W^T in shared memory and y^T may be overwritten
       if (t >= 1) {
-        if (!wait_or_abort(&bar.mma2_done, (t - 1) & 1, &abort_flag)) { ok = false; break; }
+        if (!wait_or_abort(&bar.mma2_done, (t - 1) & 1, &abort_flag)) {
+          ok = false;
+          break;
+        }
         drain_y();
         if (t % kFlushTerms == 0) flush_y();
       }
@@ -456,7 +540,7 @@ __global__ void __launch_bounds__(kMvThreads, 1)
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  if (warp == kMmaWarp) tmem_free(tmem, kTmemCols);
+  if (warp == kMma1Warp) tmem_free(tmem, kTmemCols);
 }
 
 // ------------------------------------------------------------------ conversions
