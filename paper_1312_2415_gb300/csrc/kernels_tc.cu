@@ -4,9 +4,11 @@
 // operators of Sec. 2.5, acts on an output block y_X' as a sum of terms
 //   y_X' += C W,   W = sum_s coef_s x_s D_s^T,
 // C a left-operator block, x_s blocks of the two-site vector and D_s right-operator
-// blocks (the combined operators of the left / right environments).  One CTA owns one
+// blocks (the combined operators of the left / right environments).  One CTA owns each
 // output tile (up to 128 rows x 128 columns of one block, so nothing is added with
-// atomics and the summation order is fixed) and runs all of its terms:
+// atomics and the summation order is fixed) and runs all of its terms; the launch is
+// persistent (one CTA per SM, each running the list of tiles the host balanced over the
+// CTAs by cost), so the pipeline runs on from one tile into the next:
 //   product 1: W^T = D_s x_s^T per source, into tensor-memory accumulators of at most
 //              two 32-column K chunks each (M = 128 output columns, N = x rows of the
 //              term, K = the right sector);
@@ -55,9 +57,12 @@ constexpr long long kSpinLimit = 1ll << 22;  // polls of an mbarrier before givi
 constexpr int kTF = 128 * 32;                // floats of a 128-row x 32-column tile (16 KB)
 constexpr int kMaxS1 = 8;                    // slots of the product-1 operand ring, at most
 constexpr int kS1KB = 96;                    // shared memory of the product-1 ring (KB)
-constexpr int kMaxW = 6;                     // W^T accumulators in tensor memory, at most
 constexpr int kMaxB2 = 2;                    // C slots, at most
 constexpr int kTmemCols = 512;
+constexpr int kWCols = 128;                  // tensor-memory columns of a W^T accumulator
+constexpr int kNW = 3;                       // W^T accumulators
+constexpr int kYCol = kNW * kWCols;          // first column of the y^T accumulator (128 columns)
+constexpr int kTileQ = 4;                    // tiles taken from the work queue ahead of the slowest role
 // shared memory (floats): product-1 slot = D tile hi, lo (up to 128 rows) and x tile hi,
 // lo (kp rows each); product 2: C slots (2 x 128 rows x 2 chunks in all) and W^T tiles
 // (128 rows x 2 chunks, hi, lo)
@@ -191,12 +196,25 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+// the three split products of one K step, unstacked: A_hi B_hi^T + A_hi B_lo^T +
+// A_lo B_hi^T into the same columns; nst steps of K = 8
+__device__ __forceinline__ void mma_triple_steps(uint32_t tmem, uint64_t ah, uint64_t al, uint64_t bh, uint64_t bl,
+                                                 uint32_t id, int nst, bool fresh) {
+  for (int st = 0; st < nst; ++st) {
+    const uint64_t o = (uint64_t)(16 * st);
+    mma_tf32(tmem, ah + o, bh + o, id, (fresh && st == 0) ? 0u : 1u);
+    mma_tf32(tmem, ah + o, bl + o, id, 1u);
+    mma_tf32(tmem, al + o, bh + o, id, 1u);
+  }
+}
+
 struct Bars {
   uint64_t s1_full[kMaxS1], s1_empty[kMaxS1];
   uint64_t b2_full[kMaxB2], b2_empty[kMaxB2];
-  uint64_t w_full[kMaxW], w_empty[kMaxW];
+  uint64_t w_full[kNW], w_empty[kNW];
   uint64_t a2_full, mma2_done;
   uint64_t drain1, drain2, never;
+  uint64_t tile_full[kTileQ], tile_empty[kTileQ];
 };
 
 // the two split products of one K step stacked along N: A_hi [B_hi; B_lo]^T (N = 2 kp)
@@ -221,8 +239,38 @@ __device__ __forceinline__ void mma_pair_steps(uint32_t tmem, uint64_t ah, uint6
   }
 }
 
+// Geometry of one output tile.  kp: x rows of a term rounded up to 32 (x hi and x lo are
+// stacked kp rows apart); mp: output rows rounded up to 32 (C hi and C lo are stacked mp
+// rows apart).  Product-1 slots are sized for the tile (its output columns and its
+// widest term), as many as fit: small blocks keep more copies in flight.  C slots hold
+// the chunks of the tile's widest term.
+struct TileGeom {
+  int T, nvg, mg, mp, kpm, slot_f, nslots, b2_f, nb2;
+  __device__ explicit TileGeom(const TfTile& t) {
+    T = t.t_end - t.t_begin;
+    nvg = (t.nv + 7) >> 3;
+    mg = (t.m + 7) >> 3;
+    mp = (t.m + 31) & ~31;
+    kpm = t.kdg > 4 ? 64 : 32;
+    slot_f = (2 * nvg + kpm / 4) * 256;
+    nslots = min(kMaxS1, (kS1KB * 256) / slot_f);
+    b2_f = 2 * mp * 32 * (kpm / 32);
+    nb2 = min(kMaxB2, kB2F / b2_f);
+  }
+};
+
+// Persistent: one CTA per SM takes tiles from a work queue (a counter in global memory,
+// zeroed before the launch, handing out the tiles in the planner's order) until it is
+// empty, so the pipeline runs on from one tile into the next.  The producer thread takes
+// each tile and passes its index to the other roles through a small ring in shared
+// memory (tile_full / tile_empty); -1 ends the list.  Ring phases are kept per slot
+// across tiles (bit masks of parities), and a tile whose product-1 slot layout differs
+// from the last one's waits for the last one's slots to be released first.  Tensor
+// memory has a fixed layout: kNW W^T accumulators of 128 columns and the y^T accumulator
+// in the last 128 columns.
 __global__ void __launch_bounds__(kMvThreads, 1)
-    k_tc_matvec(const TfTile* __restrict__ tiles, const TfTask* __restrict__ tasks, const TfSrc* __restrict__ srcs) {
+    k_tc_matvec(const TfTile* __restrict__ tiles, const TfTask* __restrict__ tasks, const TfSrc* __restrict__ srcs,
+                int* __restrict__ queue, int ntiles) {
   extern __shared__ unsigned char smem_dyn[];
   float* sm = (float*)(((uintptr_t)smem_dyn + 1023) & ~(uintptr_t)1023);
   float* s1 = sm;                      // product-1 slots: D hi, D lo (nvg KB each), x hi, x lo (kp rows each)
@@ -233,10 +281,9 @@ __global__ void __launch_bounds__(kMvThreads, 1)
   __shared__ __align__(8) Bars bar;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
+  __shared__ int tile_q[kTileQ];
 
-  const TfTile tile = tiles[blockIdx.x];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int T = tile.t_end - tile.t_begin;
   if (warp == kMma1Warp) tmem_alloc(&tmem_slot, kTmemCols);
   if (tid == 0) {
     for (int s = 0; s < kMaxS1; ++s) {
@@ -247,7 +294,7 @@ __global__ void __launch_bounds__(kMvThreads, 1)
       mbar_init_n(&bar.b2_full[s], 1);
       mbar_init_n(&bar.b2_empty[s], 1);
     }
-    for (int q = 0; q < kMaxW; ++q) {
+    for (int q = 0; q < kNW; ++q) {
       mbar_init_n(&bar.w_full[q], 1);
       mbar_init_n(&bar.w_empty[q], kConvThreads);
     }
@@ -256,6 +303,10 @@ __global__ void __launch_bounds__(kMvThreads, 1)
     mbar_init_n(&bar.drain1, 1);
     mbar_init_n(&bar.drain2, 1);
     mbar_init_n(&bar.never, 1);
+    for (int r = 0; r < kTileQ; ++r) {
+      mbar_init_n(&bar.tile_full[r], 1);
+      mbar_init_n(&bar.tile_empty[r], 2 + kConvThreads);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;");
     abort_flag = 0;
   }
@@ -273,103 +324,125 @@ __global__ void __launch_bounds__(kMvThreads, 1)
   }
   __syncthreads();
 
-  // Per-tile geometry.  kp: x rows of a term rounded up to 32 (x hi and x lo are stacked
-  // kp rows apart); mp: output rows rounded up to 32 (C hi and C lo stacked mp rows apart).
-  const int nvg = (tile.nv + 7) >> 3, mg = (tile.m + 7) >> 3;
-  const int mp = (tile.m + 31) & ~31;
-  const int kpm = tile.kdg > 4 ? 64 : 32;
-  // product-1 slots sized for this tile (its output columns and its widest term), as many
-  // as fit: small blocks keep more copies in flight
-  const int slot_f = (2 * nvg + kpm / 4) * 256;
-  const int nslots = min(kMaxS1, (kS1KB * 256) / slot_f);
-  // tensor memory: W^T accumulators of 2 kpm columns from column 0, y^T (2 mp columns)
-  // at the top
-  const int wcols = 2 * kpm, ycols = 2 * mp;
-  const int nw = min(kMaxW, (kTmemCols - ycols) / wcols);
-  const uint32_t ycol = (uint32_t)(kTmemCols - ycols);
-  // C slots: chunks of 2 mp rows x 32 columns, as many chunks as the widest term needs
-  const int b2_f = 2 * mp * 32 * (kpm / 32);
-  const int nb2 = min(kMaxB2, kB2F / b2_f);
-
+  // the k-th tile of this CTA for the roles other than the producer (-1: none left, or
+  // the CTA gave up)
+  auto next_tile = [&](int k) -> int {
+    const int r = k % kTileQ;
+    if (!wait_or_abort(&bar.tile_full[r], (k / kTileQ) & 1, &abort_flag)) return -1;
+    const int ti = tile_q[r];
+    mbar_arrive(&bar.tile_empty[r]);
+    return ti;
+  };
   if (warp == kProducerWarp) {
-    // ---- producer: product-1 operands in the order the MMA thread consumes them
+    // ---- producer: takes the tiles; product-1 operands in the order the MMA thread
+    // consumes them
     if (lane == 0 && !abort_flag) {
-      int slot = 0, round = 0, fills = 0;
+      uint32_t emp = 0, pend = 0, fpar = 0;  // per slot: release parity, fill not yet released, fill parity
+      int last_slot_f = -1;
       bool ok = true;
-      for (int t = 0; t < T && ok; ++t) {
-        const TfTask tk = tasks[tile.t_begin + t];
-        const int kdg = (tk.kdl + 7) >> 3, kp = tk.kdl > 32 ? 64 : 32;
-        const uint32_t bytes = 2u * (nvg + kdg) * 1024u;
-        for (int si = tk.s_begin; si < tk.s_end && ok; ++si) {
-          const TfSrc S = srcs[si];
-          for (int kk = 0; kk < S.nkc; ++kk) {
-            if (round >= 1 && !wait_or_abort(&bar.s1_empty[slot], (round - 1) & 1, &abort_flag)) {
-              ok = false;
-              break;
+      for (int k = 0; ok; ++k) {
+        // take the next tile and pass it on
+        const int r = k % kTileQ;
+        if (k >= kTileQ && !wait_or_abort(&bar.tile_empty[r], (k / kTileQ - 1) & 1, &abort_flag)) break;
+        int ti = atomicAdd(queue, 1);
+        if (ti >= ntiles) ti = -1;
+        tile_q[r] = ti;
+        mbar_arrive(&bar.tile_full[r]);
+        if (ti < 0) break;
+        const TfTile tile = tiles[ti];
+        const TileGeom g(tile);
+        if (g.slot_f != last_slot_f) {
+          // a new slot layout overlaps the old slots: all of them are released first
+          for (int s = 0; s < kMaxS1 && ok; ++s)
+            if ((pend >> s) & 1u) {
+              ok = wait_or_abort(&bar.s1_empty[s], (emp >> s) & 1u, &abort_flag);
+              emp ^= 1u << s;
+              pend &= ~(1u << s);
             }
-            float* dst = s1 + slot * slot_f;
-            const float* d = S.d + (int64_t)kk * S.d_cs;
-            const float* x = S.x + (int64_t)kk * S.x_cs;
-            mbar_expect_tx(&bar.s1_full[slot], bytes);
-            bulk_g2s(dst, d, nvg * 1024u, &bar.s1_full[slot]);
-            bulk_g2s(dst + nvg * 256, d + tile.dlo, nvg * 1024u, &bar.s1_full[slot]);
-            bulk_g2s(dst + 2 * nvg * 256, x, kdg * 1024u, &bar.s1_full[slot]);
-            bulk_g2s(dst + 2 * nvg * 256 + kp * 32, x + tile.xlo, kdg * 1024u, &bar.s1_full[slot]);
-            ++fills;
-            if (++slot == nslots) {
-              slot = 0;
-              ++round;
+          last_slot_f = g.slot_f;
+        }
+        int slot = 0;
+        for (int t = 0; t < g.T && ok; ++t) {
+          const TfTask tk = tasks[tile.t_begin + t];
+          const int kdg = (tk.kdl + 7) >> 3, kp = tk.kdl > 32 ? 64 : 32;
+          const uint32_t bytes = 2u * (g.nvg + kdg) * 1024u;
+          for (int si = tk.s_begin; si < tk.s_end && ok; ++si) {
+            const TfSrc S = srcs[si];
+            for (int kk = 0; kk < S.nkc; ++kk) {
+              if ((pend >> slot) & 1u) {
+                if (!wait_or_abort(&bar.s1_empty[slot], (emp >> slot) & 1u, &abort_flag)) {
+                  ok = false;
+                  break;
+                }
+                emp ^= 1u << slot;
+              }
+              float* dst = s1 + slot * g.slot_f;
+              const float* d = S.d + (int64_t)kk * S.d_cs;
+              const float* x = S.x + (int64_t)kk * S.x_cs;
+              mbar_expect_tx(&bar.s1_full[slot], bytes);
+              bulk_g2s(dst, d, g.nvg * 1024u, &bar.s1_full[slot]);
+              bulk_g2s(dst + g.nvg * 256, d + tile.dlo, g.nvg * 1024u, &bar.s1_full[slot]);
+              bulk_g2s(dst + 2 * g.nvg * 256, x, kdg * 1024u, &bar.s1_full[slot]);
+              bulk_g2s(dst + 2 * g.nvg * 256 + kp * 32, x + tile.xlo, kdg * 1024u, &bar.s1_full[slot]);
+              pend |= 1u << slot;
+              fpar ^= 1u << slot;
+              if (++slot == g.nslots) slot = 0;
             }
           }
         }
       }
       // copies still in flight land before the CTA can exit: wait for the last fill of
-      // every slot (a completed phase keeps testing complete while no newer one starts)
-      for (int s = 0; s < nslots; ++s) {
-        const int f = fills / nslots + (s < fills % nslots ? 1 : 0);
-        if (f > 0) wait_drain(&bar.s1_full[s], (f - 1) & 1);
-      }
+      // every slot not yet released (a completed phase keeps testing complete while no
+      // newer one starts)
+      for (int s = 0; s < kMaxS1; ++s)
+        if ((pend >> s) & 1u) wait_drain(&bar.s1_full[s], ((fpar >> s) & 1u) ^ 1u);
     }
   } else if (warp == kMma1Warp) {
     // ---- product 1: W^T = D x^T per source, segments of up to two K chunks per
     // accumulator
     if (lane == 0 && !abort_flag) {
-      int slot = 0, round = 0, q = 0, wround = 0;
+      uint32_t ful = 0;  // per slot: parity of the next fill
+      int q = 0, wround = 0;
       bool ok = true;
-      for (int t = 0; t < T && ok; ++t) {
-        const TfTask tk = tasks[tile.t_begin + t];
-        const int kp = tk.kdl > 32 ? 64 : 32;
-        const uint32_t id2 = idesc_tf32(2 * kp), id1 = idesc_tf32(kp);
-        for (int si = tk.s_begin; si < tk.s_end && ok; ++si) {
-          const TfSrc S = srcs[si];
-          for (int k0 = 0; k0 < S.nkc; k0 += kSegChunks) {
-            if (wround >= 1 && !wait_or_abort(&bar.w_empty[q], (wround - 1) & 1, &abort_flag)) {
-              ok = false;
-              break;
-            }
-            const uint32_t wq = tmem + (uint32_t)(q * wcols);
-            const int k1 = min(S.nkc, k0 + kSegChunks);
-            for (int kk = k0; kk < k1; ++kk) {
-              if (!wait_or_abort(&bar.s1_full[slot], round & 1, &abort_flag)) {
+      for (int k = 0; ok; ++k) {
+        const int ti = next_tile(k);
+        if (ti < 0) break;
+        const TfTile tile = tiles[ti];
+        const TileGeom g(tile);
+        int slot = 0;
+        for (int t = 0; t < g.T && ok; ++t) {
+          const TfTask tk = tasks[tile.t_begin + t];
+          const int kp = tk.kdl > 32 ? 64 : 32;
+          const uint32_t id2 = idesc_tf32(2 * kp), id1 = idesc_tf32(kp);
+          for (int si = tk.s_begin; si < tk.s_end && ok; ++si) {
+            const TfSrc S = srcs[si];
+            for (int k0 = 0; k0 < S.nkc; k0 += kSegChunks) {
+              if (wround >= 1 && !wait_or_abort(&bar.w_empty[q], (wround - 1) & 1, &abort_flag)) {
                 ok = false;
                 break;
               }
-              asm volatile("tcgen05.fence::after_thread_sync;");
-              const int kv = kk == S.nkc - 1 ? S.klast : 32;
-              const float* base = s1 + slot * slot_f;
-              mma_pair_steps(wq, smem_desc(smem_u32(base)), smem_desc(smem_u32(base + nvg * 256)),
-                             smem_desc(smem_u32(base + 2 * nvg * 256)), id2, id1, (kv + 7) >> 3, kk == k0);
-              mma_commit(&bar.s1_empty[slot]);
-              if (++slot == nslots) {
-                slot = 0;
-                ++round;
+              const uint32_t wq = tmem + (uint32_t)(q * kWCols);
+              const int k1 = min(S.nkc, k0 + kSegChunks);
+              for (int kk = k0; kk < k1; ++kk) {
+                if (!wait_or_abort(&bar.s1_full[slot], (ful >> slot) & 1u, &abort_flag)) {
+                  ok = false;
+                  break;
+                }
+                ful ^= 1u << slot;
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const int kv = kk == S.nkc - 1 ? S.klast : 32;
+                const float* base = s1 + slot * g.slot_f;
+                mma_pair_steps(wq, smem_desc(smem_u32(base)), smem_desc(smem_u32(base + g.nvg * 256)),
+                               smem_desc(smem_u32(base + 2 * g.nvg * 256)), id2, id1, (kv + 7) >> 3, kk == k0);
+                mma_commit(&bar.s1_empty[slot]);
+                if (++slot == g.nslots) slot = 0;
               }
-            }
-            if (!ok) break;
-            mma_commit(&bar.w_full[q]);
-            if (++q == nw) {
-              q = 0;
-              ++wround;
+              if (!ok) break;
+              mma_commit(&bar.w_full[q]);
+              if (++q == kNW) {
+                q = 0;
+                ++wround;
+              }
             }
           }
         }
@@ -380,163 +453,193 @@ __global__ void __launch_bounds__(kMvThreads, 1)
     }
   } else if (warp == kMma2Warp) {
     // ---- product 2: y^T = W^T C^T per term, fresh accumulator; this thread also loads
-    // the C tiles (slot u % nb2; the next fill of a slot waits for the product that read it)
+    // the C tiles (slot u % nb2 of the tile; the next fill of a slot waits for the
+    // product that read it, and a tile starts once the last one's products have finished)
     if (lane == 0 && !abort_flag) {
-      int c_fills[kMaxB2] = {0, 0};
-      auto load_c = [&](int u) {
-        const TfTask tk = tasks[tile.t_begin + u];
-        const int nch = (tk.kdl + 31) >> 5, s = u % nb2;
-        float* dst = b2 + s * b2_f;
-        mbar_expect_tx(&bar.b2_full[s], 2u * nch * mg * 1024u);
-        for (int c = 0; c < nch; ++c) {
-          const float* src = tk.c + (int64_t)c * tk.c_cs;
-          bulk_g2s(dst + c * 2 * mp * 32, src, mg * 1024u, &bar.b2_full[s]);
-          bulk_g2s(dst + c * 2 * mp * 32 + mp * 32, src + tile.dlo, mg * 1024u, &bar.b2_full[s]);
+      uint32_t bf = 0, bc = 0, lf = 0, filled = 0;  // per C slot: fill parity to wait, commits, last fill, ever filled
+      int gt = 0;                                    // terms of the CTA's earlier tiles
+      int tiles_done = 0;
+      bool ok = true;
+      for (int k = 0; ok; ++k) {
+        const int ti = next_tile(k);
+        if (ti < 0) break;
+        const TfTile tile = tiles[ti];
+        const TileGeom g(tile);
+        auto load_c = [&](int u) {
+          const TfTask tk = tasks[tile.t_begin + u];
+          const int nch = (tk.kdl + 31) >> 5, s = u % g.nb2;
+          float* dst = b2 + s * g.b2_f;
+          mbar_expect_tx(&bar.b2_full[s], 2u * nch * g.mg * 1024u);
+          for (int c = 0; c < nch; ++c) {
+            const float* src = tk.c + (int64_t)c * tk.c_cs;
+            bulk_g2s(dst + c * 2 * g.mp * 32, src, g.mg * 1024u, &bar.b2_full[s]);
+            bulk_g2s(dst + c * 2 * g.mp * 32 + g.mp * 32, src + tile.dlo, g.mg * 1024u, &bar.b2_full[s]);
+          }
+          lf ^= 1u << s;
+          filled |= 1u << s;
+        };
+        for (int u = 0; u < min(g.nb2, g.T); ++u) load_c(u);
+        const uint32_t idm = idesc_tf32((tile.m + 15) & ~15);
+        for (int t = 0; t < g.T; ++t) {
+          const int s = t % g.nb2;
+          const TfTask tk = tasks[tile.t_begin + t];
+          if (!wait_or_abort(&bar.a2_full, (gt + t) & 1, &abort_flag) ||
+              !wait_or_abort(&bar.b2_full[s], (bf >> s) & 1u, &abort_flag)) {
+            ok = false;
+            break;
+          }
+          bf ^= 1u << s;
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const float* cb = b2 + s * g.b2_f;
+          for (int c = 0; c * 32 < tk.kdl; ++c) {
+            const int kv = min(32, tk.kdl - 32 * c);
+            mma_triple_steps(tmem + kYCol, smem_desc(smem_u32(a2 + (2 * c) * kTF)),
+                             smem_desc(smem_u32(a2 + (2 * c + 1) * kTF)), smem_desc(smem_u32(cb + c * 2 * g.mp * 32)),
+                             smem_desc(smem_u32(cb + c * 2 * g.mp * 32 + g.mp * 32)), idm, (kv + 7) >> 3, c == 0);
+          }
+          mma_commit(&bar.b2_empty[s]);
+          bc ^= 1u << s;
+          mma_commit(&bar.mma2_done);
+          if (t + g.nb2 < g.T) {
+            if (!wait_or_abort(&bar.b2_empty[s], ((bc >> s) & 1u) ^ 1u, &abort_flag)) {
+              ok = false;
+              break;
+            }
+            load_c(t + g.nb2);
+          }
         }
-        ++c_fills[s];
-      };
-      for (int u = 0; u < min(nb2, T); ++u) load_c(u);
-      const uint32_t id2 = idesc_tf32(2 * mp), id1 = idesc_tf32(mp);
-      for (int t = 0; t < T; ++t) {
-        const int s = t % nb2;
-        const TfTask tk = tasks[tile.t_begin + t];
-        if (!wait_or_abort(&bar.a2_full, t & 1, &abort_flag) ||
-            !wait_or_abort(&bar.b2_full[s], (t / nb2) & 1, &abort_flag))
-          break;
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        const float* cb = b2 + s * b2_f;
-        for (int c = 0; c * 32 < tk.kdl; ++c) {
-          const int kv = min(32, tk.kdl - 32 * c);
-          mma_pair_steps(tmem + ycol, smem_desc(smem_u32(a2 + (2 * c) * kTF)),
-                         smem_desc(smem_u32(a2 + (2 * c + 1) * kTF)), smem_desc(smem_u32(cb + c * 2 * mp * 32)),
-                         id2, id1, (kv + 7) >> 3, c == 0);
-        }
-        mma_commit(&bar.b2_empty[s]);
-        mma_commit(&bar.mma2_done);
-        if (t + nb2 < T) {
-          if (!wait_or_abort(&bar.b2_empty[s], (t / nb2) & 1, &abort_flag)) break;
-          load_c(t + nb2);
-        }
+        gt += g.T;
+        // the next tile's C layout may overlap this one's slots: its products finish first
+        mma_commit(&bar.drain2);
+        wait_drain(&bar.drain2, tiles_done & 1);
+        ++tiles_done;
       }
-      // every product issued has finished before tensor memory is released, and every
-      // C copy has landed
-      mma_commit(&bar.drain2);
-      wait_drain(&bar.drain2, 0);
-      for (int s = 0; s < nb2; ++s)
-        if (c_fills[s] > 0) wait_drain(&bar.b2_full[s], (c_fills[s] - 1) & 1);
+      // every C copy has landed before the CTA exits (the last fill of every slot)
+      for (int s = 0; s < kMaxB2; ++s)
+        if ((filled >> s) & 1u) wait_drain(&bar.b2_full[s], ((lf >> s) & 1u) ^ 1u);
+      if (tiles_done == 0) {
+        mma_commit(&bar.drain2);
+        wait_drain(&bar.drain2, 0);
+      }
     }
   } else {
     // ---- converters: warp w reads tensor-memory lanes 32 (w % 4) .. (its output
     // columns); half 0 / 1 holds x rows 0..31 / 32..63 of W^T and output rows 0..63 /
-    // 64..127 of y.  Each accumulator holds the hi part in columns [0, kp) and the
-    // stacked lo part in [kp, 2 kp) (y^T: [0, mp) and [mp, 2 mp)); their sum is the product.
+    // 64..127 of y.  A W^T accumulator holds the hi part in columns [0, kp) and the
+    // stacked lo part in [kp, 2 kp); their sum is the product.
     const int quarter = warp & 3, half = (warp - kConvWarp0) >> 2;
     const int n = quarter * 32 + lane;
     const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
-    float yacc[64];
-#pragma unroll
-    for (int j = 0; j < 64; ++j) yacc[j] = 0.0f;
-    auto drain_y = [&]() {
-      asm volatile("tcgen05.fence::after_thread_sync;");
-#pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        if (64 * half + 32 * i < tile.m) {
-          float v[32];
-          tmem_ld32(lane_base + ycol + (uint32_t)(64 * half + 32 * i), v);
-#pragma unroll
-          for (int j = 0; j < 32; ++j) yacc[32 * i + j] += v[j];
-          tmem_ld32(lane_base + ycol + (uint32_t)(mp + 64 * half + 32 * i), v);
-#pragma unroll
-          for (int j = 0; j < 32; ++j) yacc[32 * i + j] += v[j];
-        }
-      }
-      asm volatile("tcgen05.fence::before_thread_sync;");
-    };
-    // the FP32 sums of the last terms are added to y (the tile's owner writes it first,
-    // then accumulates into it)
-    bool stored = false;
-    auto flush_y = [&]() {
-      if (abort_flag || n >= tile.nv) return;
-#pragma unroll
-      for (int j = 0; j < 64; ++j) {
-        const int r = 64 * half + j;
-        if (r < tile.m) {
-          double* yp = tile.y + (int64_t)r * tile.ldy + n;
-          *yp = stored ? *yp + (double)yacc[j] : (double)yacc[j];
-        }
-        yacc[j] = 0.0f;
-      }
-      stored = true;
-    };
-    int q = 0, wround = 0;
+    int q = 0, wround = 0, gt = 0;
     bool ok = !abort_flag;
-    for (int t = 0; t < T && ok; ++t) {
-      const TfTask tk = tasks[tile.t_begin + t];
-      const int kp = tk.kdl > 32 ? 64 : 32;
-      float wsum[32];
+    for (int k = 0; ok; ++k) {
+      const int ti = next_tile(k);
+      if (ti < 0) break;
+      const TfTile tile = tiles[ti];
+      const int T = tile.t_end - tile.t_begin;
+      float yacc[64];
 #pragma unroll
-      for (int j = 0; j < 32; ++j) wsum[j] = 0.0f;
-      for (int si = tk.s_begin; si < tk.s_end && ok; ++si) {
-        const float coef = srcs[si].coef;
-        const int nseg = (srcs[si].nkc + kSegChunks - 1) / kSegChunks;
-        for (int g = 0; g < nseg; ++g) {
-          if (!wait_or_abort(&bar.w_full[q], wround & 1, &abort_flag)) {
+      for (int j = 0; j < 64; ++j) yacc[j] = 0.0f;
+      auto drain_y = [&]() {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+          if (64 * half + 32 * i < tile.m) {
+            float v[32];
+            tmem_ld32(lane_base + (uint32_t)(kYCol + 64 * half + 32 * i), v);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) yacc[32 * i + j] += v[j];
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;");
+      };
+      // the FP32 sums of the last terms are added to y (the tile's owner writes it
+      // first, then accumulates into it)
+      bool stored = false;
+      auto flush_y = [&]() {
+        if (abort_flag || n >= tile.nv) return;
+#pragma unroll
+        for (int j = 0; j < 64; ++j) {
+          const int r = 64 * half + j;
+          if (r < tile.m) {
+            double* yp = tile.y + (int64_t)r * tile.ldy + n;
+            *yp = stored ? *yp + (double)yacc[j] : (double)yacc[j];
+          }
+          yacc[j] = 0.0f;
+        }
+        stored = true;
+      };
+      for (int t = 0; t < T && ok; ++t) {
+        const TfTask tk = tasks[tile.t_begin + t];
+        const int kp = tk.kdl > 32 ? 64 : 32;
+        float wsum[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) wsum[j] = 0.0f;
+        for (int si = tk.s_begin; si < tk.s_end && ok; ++si) {
+          const float coef = srcs[si].coef;
+          const int nseg = (srcs[si].nkc + kSegChunks - 1) / kSegChunks;
+          for (int sg = 0; sg < nseg; ++sg) {
+            if (!wait_or_abort(&bar.w_full[q], wround & 1, &abort_flag)) {
+              ok = false;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            if (32 * half < tk.kdl) {
+              const uint32_t wa = lane_base + (uint32_t)(q * kWCols + 32 * half);
+              float v[32];
+              tmem_ld32(wa, v);
+#pragma unroll
+              for (int j = 0; j < 32; ++j) wsum[j] = fmaf(coef, v[j], wsum[j]);
+              tmem_ld32(wa + (uint32_t)kp, v);
+#pragma unroll
+              for (int j = 0; j < 32; ++j) wsum[j] = fmaf(coef, v[j], wsum[j]);
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            mbar_arrive(&bar.w_empty[q]);
+            if (++q == kNW) {
+              q = 0;
+              ++wround;
+            }
+          }
+        }
+        if (!ok) break;
+        // product 2 of the previous term has finished: its result is added to the
+        // registers, and W^T in shared memory and y^T may be overwritten (the first term
+        // of a tile follows the drain of the CTA's previous tile)
+        if (t >= 1) {
+          if (!wait_or_abort(&bar.mma2_done, (gt + t - 1) & 1, &abort_flag)) {
             ok = false;
             break;
           }
-          asm volatile("tcgen05.fence::after_thread_sync;");
-          if (32 * half < tk.kdl) {
-            const uint32_t wa = lane_base + (uint32_t)(q * wcols + 32 * half);
-            float v[32];
-            tmem_ld32(wa, v);
+          drain_y();
+          if (t % kFlushTerms == 0) flush_y();
+        }
+        float* ah = a2 + (2 * half) * kTF;
+        float* al = ah + kTF;
 #pragma unroll
-            for (int j = 0; j < 32; ++j) wsum[j] = fmaf(coef, v[j], wsum[j]);
-            tmem_ld32(wa + (uint32_t)kp, v);
+        for (int gg = 0; gg < 8; ++gg) {
+          float4 h, l;
+          float* hv = &h.x;
+          float* lv = &l.x;
 #pragma unroll
-            for (int j = 0; j < 32; ++j) wsum[j] = fmaf(coef, v[j], wsum[j]);
+          for (int e = 0; e < 4; ++e) {
+            const float v = (32 * half + 4 * gg + e < tk.kdl) ? wsum[4 * gg + e] : 0.0f;
+            hv[e] = tf32_round(v);
+            lv[e] = tf32_round(v - hv[e]);
           }
-          asm volatile("tcgen05.fence::before_thread_sync;");
-          mbar_arrive(&bar.w_empty[q]);
-          if (++q == nw) {
-            q = 0;
-            ++wround;
-          }
+          *reinterpret_cast<float4*>(ah + kmo(n, 4 * gg)) = h;
+          *reinterpret_cast<float4*>(al + kmo(n, 4 * gg)) = l;
         }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(&bar.a2_full);
       }
-      if (!ok) break;
-      // product 2 of the previous term has finished: its result is added to the
-      // registers, and W^T in shared memory and y^T may be overwritten
-      if (t >= 1) {
-        if (!wait_or_abort(&bar.mma2_done, (t - 1) & 1, &abort_flag)) {
-          ok = false;
-          break;
-        }
-        drain_y();
-        if (t % kFlushTerms == 0) flush_y();
+      if (ok && T >= 1) {
+        if (wait_or_abort(&bar.mma2_done, (gt + T - 1) & 1, &abort_flag)) drain_y();
+        else ok = false;
       }
-      float* ah = a2 + (2 * half) * kTF;
-      float* al = ah + kTF;
-#pragma unroll
-      for (int g = 0; g < 8; ++g) {
-        float4 h, l;
-        float* hv = &h.x;
-        float* lv = &l.x;
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const float v = (32 * half + 4 * g + e < tk.kdl) ? wsum[4 * g + e] : 0.0f;
-          hv[e] = tf32_round(v);
-          lv[e] = tf32_round(v - hv[e]);
-        }
-        *reinterpret_cast<float4*>(ah + kmo(n, 4 * g)) = h;
-        *reinterpret_cast<float4*>(al + kmo(n, 4 * g)) = l;
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_arrive(&bar.a2_full);
+      flush_y();
+      gt += T;
     }
-    if (ok && T >= 1) {
-      if (wait_or_abort(&bar.mma2_done, (T - 1) & 1, &abort_flag)) drain_y();
-    }
-    flush_y();
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
@@ -589,9 +692,21 @@ struct TcPlan {
   TfTask* tasks = nullptr;
   TfSrc* srcs = nullptr;
   TfConv* xb = nullptr;
-  int ntiles = 0, nxb = 0;
+  int* queue = nullptr;        // the persistent kernel's tile counter
+  int ntiles = 0, nxb = 0, grid = 0;
   int launches = 0;  // kernels of one launch sequence
 };
+
+namespace {
+
+int sm_count() {
+  int dev = 0, n = 0;
+  ck(cudaGetDevice(&dev), "device");
+  ck(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev), "SM count");
+  return std::max(n, 1);
+}
+
+}  // namespace
 
 TcPlan* tc_plan_build(const std::vector<const TcHost*>& inst, Stream st) {
   TcPlan* P = new TcPlan;
@@ -641,6 +756,8 @@ TcPlan* tc_plan_build(const std::vector<const TcHost*>& inst, Stream st) {
     });
     std::vector<TfTile> sorted(tiles0.size());
     for (size_t i = 0; i < order.size(); ++i) sorted[i] = tiles0[order[i]];
+    P->grid = (int)std::min<size_t>(sorted.size(), (size_t)sm_count());
+    P->queue = (int*)dev_alloc(sizeof(int), st);
     P->tiles = upload(sorted, st);
     P->tasks = upload(single ? inst[0]->t : t, st);
     P->srcs = upload(single ? inst[0]->s : s, st);
@@ -661,6 +778,7 @@ void tc_plan_free(TcPlan* p, Stream s) {
   dev_free(p->tasks, s);
   dev_free(p->srcs, s);
   dev_free(p->xb, s);
+  dev_free(p->queue, s);
   delete p;
 }
 
@@ -678,7 +796,10 @@ void tc_enqueue(const TcPlan* p, void* const* ev, cudaStream_t cs) {
   if (ev) event_record(ev[0], cs);
   if (p->nxb > 0) k_tiled_convert<<<p->nxb, 256, 0, cs>>>(p->xb);
   if (ev) event_record(ev[1], cs);
-  if (p->ntiles > 0) k_tc_matvec<<<p->ntiles, kMvThreads, smem_bytes(), cs>>>(p->tiles, p->tasks, p->srcs);
+  if (p->ntiles > 0) {
+    ck(cudaMemsetAsync(p->queue, 0, sizeof(int), cs), "tile queue reset");
+    k_tc_matvec<<<p->grid, kMvThreads, smem_bytes(), cs>>>(p->tiles, p->tasks, p->srcs, p->queue, p->ntiles);
+  }
   if (ev) event_record(ev[2], cs);
   ck(cudaGetLastError(), "tc matvec launch");
 }
