@@ -266,6 +266,24 @@ int dmrg_batch_io(dmrg_batch* b, int i, double** x, double** y, int64_t* n);
  * Runs that overlap in time, or that overlap a matvec of one of the contexts at the
  * same site, race on those buffers. */
 int dmrg_batch_run(dmrg_batch* b, const double* const* x, double* const* y, uintptr_t stream);
+/* Davidson's algorithm (Sec. 2.3; the steps of dmrg_davidson) for every instance of the
+ * batch in lockstep: each iteration applies H_eff to all instances with the batched
+ * tensor-core matvec (one graph launch), and each vector operation of the iteration
+ * (dot products, subspace combinations, residual, preconditioner, Gram-Schmidt,
+ * normalisation, the small Rayleigh-Ritz eigenproblems) is one launch over all
+ * instances; an instance that has converged (||r||_2 <= tol) is left as it is while the
+ * others continue.  x: count DEVICE pointers to n_i doubles in the layout of
+ * dmrg_two_site_layout (in: start vectors; out: Ritz vectors of unit norm, sign fixed by
+ * a non-negative overlap with the start).  energy, iters, converged: host arrays of
+ * count entries, or NULL.  energy is the lowest Ritz value of the split-TF32 operator,
+ * or, with fp64_energy != 0, the FP64 Rayleigh quotient of the Ritz vector through each
+ * context's FP64 tables.  The products carry about 5e-7 of max|y| (split TF32), so
+ * tolerances much below ~1e-5 may not be reached: DMRG_ENOTCONV when some instance hits
+ * max_iter (its best pair is still returned).  Runs on `stream` (0 = the default
+ * stream) and returns after the last result is on the host; the batch's buffers are in
+ * use meanwhile.  DMRG_EINVAL as dmrg_batch_run. */
+int dmrg_batch_davidson(dmrg_batch* b, double* const* x, double tol, int max_iter, int fp64_energy,
+                        double* energy, int* iters, int* converged, uintptr_t stream);
 /* flops of one batched matvec (planner-counted), the chosen tile shape (output rows per
  * tile, x rows per term), the measured time of one launch sequence in the autotuner (0
  * without it) and the autotuner's time. */

@@ -83,6 +83,8 @@ _SIGS = {
     "dmrg_batch_run": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
                                       ctypes.c_size_t]),
     "dmrg_batch_info": (ctypes.c_int, [_P, _D, _I, _I, _D, _D]),
+    "dmrg_batch_davidson": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_void_p), ctypes.c_double, ctypes.c_int,
+                                           ctypes.c_int, _D, _I, _I, ctypes.c_size_t]),
     "dmrg_batch_last_error": (ctypes.c_char_p, [_P]),
     "dmrg_batch_destroy": (None, [_P]),
     "dmrg_test_tc_timeout": (ctypes.c_int, [ctypes.c_int]),
@@ -377,6 +379,23 @@ class Batch:
         rc = self.lib.dmrg_batch_run(self.h, xp, yp, s)
         if rc != OK:
             raise DMRGError(rc, self.lib.dmrg_batch_last_error(self.h).decode())
+
+    def davidson(self, xs, tol=1e-5, max_iter=100, fp64_energy=True):
+        """Davidson for every instance in lockstep (dmrg_batch_davidson) on the current torch
+        stream; xs: list of float64 CUDA tensors (start vectors, overwritten by the Ritz
+        vectors).  Returns (energies, iterations, converged) as numpy arrays."""
+        import torch  # device memory / streams only
+        n = len(self.contexts)
+        xp = (ctypes.c_void_p * n)(*[t.data_ptr() for t in xs])
+        e = np.zeros(n)
+        it = np.zeros(n, dtype=np.int32)
+        cv = np.zeros(n, dtype=np.int32)
+        s = torch.cuda.current_stream().cuda_stream or _default_stream_handle(None)
+        rc = self.lib.dmrg_batch_davidson(self.h, xp, float(tol), int(max_iter), int(bool(fp64_energy)),
+                                          _dptr(e), it.ctypes.data_as(_I), cv.ctypes.data_as(_I), s)
+        if rc not in (OK, ENOTCONV):
+            raise DMRGError(rc, self.lib.dmrg_batch_last_error(self.h).decode())
+        return e, it, cv.astype(bool)
 
     def info(self):
         f, ms, tms = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "../../include/dmrg_gb300.h"
+#include "batch.hpp"
 #include "engine.hpp"
 
 struct dmrg_ctx {
@@ -29,6 +30,7 @@ struct dmrg_batch {
   std::vector<int> site;
   std::vector<uint64_t> serial;
   std::vector<double*> x, y;
+  std::vector<const double*> diag;
   std::vector<int64_t> n;
   dmrg::TcPlan* plan = nullptr;
   void* graph = nullptr;
@@ -578,6 +580,7 @@ int dmrg_batch_create(dmrg_batch** out, dmrg_ctx* const* ctx, const int* site, i
       b->serial.push_back(v.serial);
       b->x.push_back(v.x);
       b->y.push_back(v.y);
+      b->diag.push_back(v.diag);
       b->n.push_back(v.n);
       b->flops += v.flops;
     }
@@ -656,6 +659,54 @@ int dmrg_batch_run(dmrg_batch* b, const double* const* x, double* const* y, uint
       if (y[i] && y[i] != b->y[i])
         if (cudaMemcpyAsync(y[i], b->y[i], sizeof(double) * b->n[i], cudaMemcpyDeviceToDevice, s) != cudaSuccess)
           throw std::runtime_error("cuda batch output copy");
+    return DMRG_OK;
+  });
+}
+
+int dmrg_batch_davidson(dmrg_batch* b, double* const* x, double tol, int max_iter, int fp64_energy,
+                        double* energy, int* iters, int* converged, uintptr_t stream) {
+  if (!b || !b->graph || !x) return DMRG_EINVAL;
+  return guard_err(b->err, [&] {
+    const int K = (int)b->ctx.size();
+    for (int i = 0; i < K; ++i) {
+      if (!x[i]) throw std::invalid_argument("null vector");
+      if (b->ctx[i]->eng->tc_serial(b->site[i]) != b->serial[i])
+        throw std::invalid_argument("a context of the batch changed its tables since the batch was made");
+    }
+    cudaStream_t s = stream ? (cudaStream_t)stream : cudaStreamLegacy;
+    std::vector<dmrg::BdInst> inst(K);
+    for (int i = 0; i < K; ++i) inst[i] = {x[i], b->diag[i], b->x[i], b->y[i], b->n[i]};
+    std::vector<dmrg::BdResult> res;
+    int* flags = dmrg::tc_plan_active(b->plan);
+    const std::vector<int> ones(K, 1);
+    try {
+      dmrg::batch_davidson(inst, tol, max_iter, [&] { dmrg::tc_graph_launch(b->graph, (dmrg::Stream)s); }, flags,
+                           (dmrg::Stream)s, res);
+    } catch (...) {
+      dmrg::dev_h2d(flags, ones.data(), sizeof(int) * K, (dmrg::Stream)s);
+      dmrg::dev_sync((dmrg::Stream)s);
+      throw;
+    }
+    // later batched matvecs compute every instance again
+    dmrg::dev_h2d(flags, ones.data(), sizeof(int) * K, (dmrg::Stream)s);
+    dmrg::dev_sync((dmrg::Stream)s);
+    if (dmrg::tc_error_flag((dmrg::Stream)s)) throw std::runtime_error("cuda: tensor-core wait timed out");
+    bool all = true;
+    for (int i = 0; i < K; ++i) {
+      double e = res[i].theta;
+      if (fp64_energy) {
+        // the FP64 Rayleigh quotient of the Ritz vector through the context's own tables
+        e = b->ctx[i]->eng->rayleigh_fp64(b->site[i], x[i]);
+      }
+      if (energy) energy[i] = e;
+      if (iters) iters[i] = res[i].iters;
+      if (converged) converged[i] = res[i].converged;
+      all = all && res[i].converged;
+    }
+    if (!all) {
+      b->err = "Davidson reached its iteration cap for some instance";
+      return DMRG_ENOTCONV;
+    }
     return DMRG_OK;
   });
 }

@@ -121,6 +121,44 @@ void vec_normalize(double* y, const double* nrm2_dev, int64_t n, Stream s);
 // t = r / (theta - diag), |denominator| floored
 void vec_precondition(const double* r, const double* diag, const double* theta_dev, double* t,
                       int64_t n, Stream s);
+// ---- grouped Davidson (all instances of a batch, one launch per operation) ----
+// Workspace of one instance: subspace V and H V (n x (mmax + 1) each, column j at
+// V + j n), the Rayleigh matrix G and its eigenvectors C (mmax x mmax), Ritz values th,
+// dot products (dots, mmax + 2), partial sums (part, mmax x kBdChunks), residual r,
+// correction t, scratch tmp (n x 2 nkeep), the Ritz vector x (the caller's buffer), the
+// start vector x0, the H_eff diagonal, and the batch's matvec input / output bx, by.
+struct BdSlot {
+  double *V, *AV, *G, *C, *th, *dots, *part, *r, *t, *tmp, *x, *x0;
+  const double* diag;
+  double *bx, *by;
+  int64_t n;
+};
+constexpr int kBdChunks = 64;
+enum BdWhich { BD_V = 0, BD_AV, BD_R, BD_T, BD_X, BD_X0, BD_TMP, BD_BX, BD_BY };
+// Every operation skips the instances with act[i] == 0; sl and act are device arrays of
+// count entries, nmax the largest n.
+// <A col (a_col + j), B col b_col> for j < m into G + row * mmax (to_g) or dots
+void bd_dots(const BdSlot* sl, const int* act, int count, int64_t nmax, int aw, int a_col, int m, int bw, int b_col,
+             int to_g, int row, int mmax, Stream s);
+// y = beta y + sum_j c[j] V col j, c = C + cv * m (from_c) or dots
+void bd_combine(const BdSlot* sl, const int* act, int count, int64_t nmax, int vw, int m, int from_c, int cv,
+                double beta, int yw, int y_col, Stream s);
+// y = a x + b y (a = -th[0] when a_theta)
+void bd_axpby(const BdSlot* sl, const int* act, int count, int64_t nmax, int a_theta, double a, int xw, int x_col,
+              double b, int yw, int y_col, Stream s);
+// y /= sqrt(dots[0])
+void bd_normalize(const BdSlot* sl, const int* act, int count, int64_t nmax, int yw, int y_col, Stream s);
+// t = r / (th[0] - diag), denominator floored
+void bd_precondition(const BdSlot* sl, const int* act, int count, int64_t nmax, Stream s);
+// lowest k eigenpairs of the m x m Rayleigh matrices (lower triangles, ld mmax) into th, C
+void bd_small_eig(const BdSlot* sl, const int* act, int count, int mmax, int m, int k, Stream s);
+// G = diag(th[0..k))
+void bd_restart_g(const BdSlot* sl, const int* act, int count, int mmax, int k, Stream s);
+// x = -x where dots[0] < 0
+void bd_sign(const BdSlot* sl, const int* act, int count, int64_t nmax, Stream s);
+// out[2 i] = th[0], out[2 i + 1] = dots[0] of every instance
+void bd_gather(const BdSlot* sl, int count, double* out, Stream s);
+
 // lowest eigenpairs of the m x m (m <= 48) symmetric matrix whose lower triangle is in G
 // (ld gld) -> theta[0..k) ascending, C[v*m + i] = component i of vector v
 void small_eig(const double* G, int gld, int m, int k, double* theta, double* C, Stream s);
@@ -188,7 +226,7 @@ struct TfTile {         // one output tile of y, computed by one CTA from all of
   int64_t dlo, xlo;     // floats from a hi tile to its lo tile (operator pool, x pool)
   int64_t cost;         // MMA steps (tiles run in decreasing order of cost)
   int kdg;              // x row groups of the tile's largest term (sizes its product-1 slots)
-  int pad;
+  int inst;             // instance of a batch (0 for a single matvec)
   int64_t group;        // right sector of the output block (tiles of a group share operator blocks)
 };
 // one FP64 block (rows x cols, row-major) to tiled hi / lo (nrg = ceil(rows / 8) row
@@ -214,6 +252,9 @@ TcPlan* tc_plan_build(const std::vector<const TcHost*>& inst, Stream st);
 // are fixed, so the sequence can be captured in a CUDA graph.
 void tc_plan_launch(const TcPlan* p, void* const* ev, Stream s);
 void tc_plan_free(TcPlan* p, Stream s);
+// per-instance flags (device, one int per instance, 1 after the build): the tiles of an
+// instance whose flag is 0 are skipped (its y is left as it is)
+int* tc_plan_active(TcPlan* p);
 int tc_error_flag(Stream s);  // 1 if a tensor-core kernel gave up on a wait (then cleared)
 // test hook: while set, the fused kernel's first wait is on a barrier that nothing
 // completes, with a short limit, so that it takes the timed-out path

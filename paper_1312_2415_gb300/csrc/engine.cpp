@@ -1472,7 +1472,28 @@ Engine::TcView Engine::prepare_tc(int i, TcTune tune) {
     release_tc(p);
     throw;
   }
-  return {&p->tch, p->serial, p->xin, p->yout, p->n, p->flops};
+  return {&p->tch, p->serial, p->xin, p->yout, p->n, p->flops, p->diag};
+}
+
+double Engine::rayleigh_fp64(int i, const double* x) {
+  check_ready();
+  if (i < 0 || i > L_ - 2) throw std::out_of_range("site out of range");
+  MatvecPlan* P = plan_for(i);
+  run_matvec(P, x, P->yout, false);
+  double* d = (double*)dev_alloc(sizeof(double) * (2 + 1024), stream_);
+  double h[2];
+  try {
+    vec_multidot(P->xin, P->n, 1, P->yout, P->n, d, d + 2, stream_);
+    vec_multidot(P->xin, P->n, 1, P->xin, P->n, d + 1, d + 2, stream_);
+    dev_d2h(h, d, sizeof(h), stream_);
+    dev_sync(stream_);
+  } catch (...) {
+    dev_free(d, stream_);
+    throw;
+  }
+  dev_free(d, stream_);
+  if (!(h[1] > 0.0)) throw std::invalid_argument("zero vector");
+  return h[0] / h[1];
 }
 
 uint64_t Engine::tc_serial(int i) const {
@@ -1700,6 +1721,7 @@ double Engine::davidson_core(MatvecPlan* P, double* x, double tol, int maxit, bo
   double theta = 0.0;
   bool conv = false;
   int it = 0;
+  std::vector<double> rhist;  // residual norms (tensor-core stage)
   auto cleanup = [&]() {
     dev_free(V, stream_); dev_free(AV, stream_); dev_free(G, stream_); dev_free(C, stream_);
     dev_free(th, stream_); dev_free(sc, stream_); dev_free(dots, stream_); dev_free(r, stream_);
@@ -1741,8 +1763,18 @@ double Engine::davidson_core(MatvecPlan* P, double* x, double tol, int maxit, bo
     dev_d2h(hs + 1, dots, sizeof(double), stream_);
     dev_sync(stream_);
     st_.davidson_iters += 1;
-    if (std::sqrt(std::max(hs[1], 0.0)) <= tol) { conv = true; break; }
+    const double rn = std::sqrt(std::max(hs[1], 0.0));
+    if (rn <= tol) { conv = true; break; }
     if (m >= n) { conv = true; break; }
+    if (tc) {
+      // The split-TF32 products bound how far the residual can fall (their bias is about
+      // 1e-7 of |theta| and grows with the problem): once it is within 1e-4 |theta| and
+      // has fallen by less than 20 % over eight iterations, the tensor-core stage stops
+      // and the FP64 iterations take over.
+      rhist.push_back(rn);
+      const size_t k = rhist.size();
+      if (k > 8 && rn <= 1e-4 * std::fabs(theta) && rn > 0.8 * rhist[k - 9]) break;
+    }
     if (it + 1 >= maxit) break;  // no use expanding the subspace on the last iteration
     vec_precondition(r, P->diag, th, t, n, stream_);
     for (int pass = 0; pass < 2; ++pass) {
@@ -2303,31 +2335,49 @@ void Engine::rdm(double* gamma, double* Gamma) {
   canonicalize(0);
   const int64_t L4 = (int64_t)L_ * L_ * L_ * L_;
   double* dg = (double*)dev_alloc(sizeof(double) * L4, stream_);
+  // |x|^2 of every pair, then the scratch of the dot product
+  double* nrm = (double*)dev_alloc(sizeof(double) * (L_ + 1024), stream_);
   dev_zero(dg, sizeof(double) * L4, stream_);
   try {
     for (int i = 0; i <= L_ - 2; ++i) {
       MatvecPlan* P = plan_matvec(i);
       try {
         tt_to_x(i, P->xin);
+        // x is scaled to unit norm on the device (a zero norm is reported after the
+        // pass), so nothing here waits for the device
+        vec_multidot(P->xin, P->n, 1, P->xin, P->n, nrm + i, nrm + L_, stream_);
+        vec_normalize(P->xin, nrm + i, P->n, stream_);
+        // The centre moves on before this pair's products are queued: they read only the
+        // copy of x, P's operators and the environment at bond i, none of which the
+        // normalisation changes.  Its host synchronisation then waits for the previous
+        // pair's products only, and the next pair's tables are built on the host while
+        // the device runs this pair's.
+        if (i < L_ - 2) {
+          left_normalize_site(i);
+          left_normalize_site(i);
+        }
         rdm_site(P, i, dg, i == L_ - 2);
       } catch (...) {
         free_plan(P);
         throw;
       }
       free_plan(P);
-      if (i < L_ - 2) {
-        left_normalize_site(i);
-        left_normalize_site(i);
-      }
     }
     rdm_finish(dg, L_, N_, gamma, Gamma, stream_);
+    std::vector<double> n2(L_ - 1);
+    dev_d2h(n2.data(), nrm, sizeof(double) * n2.size(), stream_);
+    dev_sync(stream_);
+    for (double v : n2)
+      if (!(v > 0.0)) throw std::runtime_error("two-site object has zero norm");
   } catch (...) {
     dev_free(dg, stream_);
+    dev_free(nrm, stream_);
     for (auto& e : lenv_) free_env(e);
     for (auto& e : renv_) free_env(e);
     throw;
   }
   dev_free(dg, stream_);
+  dev_free(nrm, stream_);
   // the environments were built from the full recursion: same values, other tables
   for (auto& e : lenv_) free_env(e);
   for (auto& e : renv_) free_env(e);
@@ -2336,24 +2386,9 @@ void Engine::rdm(double* gamma, double* Gamma) {
   st_.rdm_ms += tm.ms();
 }
 
+// x (P->xin) has unit norm.
 void Engine::rdm_site(MatvecPlan* P, int i, double* dg, bool last) {
-  const int64_t n = P->n;
-  // |x|^2 (tasks of at most 2^30 elements)
-  double* nrm = (double*)dev_alloc(sizeof(double), stream_);
-  dev_zero(nrm, sizeof(double), stream_);
-  {
-    std::vector<DotTask> t;
-    for (int64_t o = 0; o < n; o += (int64_t)1 << 30) {
-      const int c = (int)std::min<int64_t>((int64_t)1 << 30, n - o);
-      t.push_back({P->xin + o, P->xin + o, c, c, 1, c, 1.0});
-    }
-    dot_grouped(t, {{nrm, 0, (int)t.size()}}, stream_);
-  }
-  double n2 = 0.0;
-  dev_d2h(&n2, nrm, sizeof(double), stream_);
-  dev_sync(stream_);
-  dev_free(nrm, stream_);
-  if (!(n2 > 0.0)) throw std::runtime_error("two-site object has zero norm");
+  const double n2 = 1.0;
   // W = sum coef Z (phases 1 and the combine of the FP64 matvec)
   if (P->zsize) dev_zero(P->Z, sizeof(double) * P->zsize, stream_);
   gemm_plan_run(P->p1, stream_);

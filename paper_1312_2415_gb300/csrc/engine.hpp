@@ -179,7 +179,9 @@ class Engine {
   // Batched matvecs: the mixed-precision tables of site i (built if needed), the plan's
   // serial (changes whenever the tables are rebuilt), its input / output buffers and
   // flops.  The tables stay valid until the MPS or the site of the engine changes.
-  struct TcView { const TcHost* host; uint64_t serial; double* x; double* y; int64_t n; double flops; };
+  struct TcView { const TcHost* host; uint64_t serial; double* x; double* y; int64_t n; double flops; const double* diag; };
+  // x^T H x / x^T x with the FP64 matvec of site i's tables (x on the device)
+  double rayleigh_fp64(int i, const double* x);
   TcView prepare_tc(int i, TcTune tune);
   uint64_t tc_serial(int i) const;
   void set_tune(TcTune t) { tune_ = t; }

@@ -505,8 +505,8 @@ __device__ inline void sym_schur2(double app, double aqq, double apq, double& c,
 }
 
 // one CTA: Jacobi on an m x m symmetric matrix in shared memory (m <= 48)
-__global__ void k_small_eig(const double* __restrict__ G, int gld, int m, int k,
-                            double* __restrict__ theta, double* __restrict__ C) {
+__device__ void small_eig_block(const double* __restrict__ G, int gld, int m, int k,
+                                double* __restrict__ theta, double* __restrict__ C) {
   __shared__ double A[48][49];
   __shared__ double Q[48][49];
   __shared__ double cs[32], sn[32];
@@ -584,6 +584,157 @@ __global__ void k_small_eig(const double* __restrict__ G, int gld, int m, int k,
   if (tid < k) theta[tid] = A[order[tid]][order[tid]];
 }
 
+__global__ void k_small_eig(const double* __restrict__ G, int gld, int m, int k,
+                            double* __restrict__ theta, double* __restrict__ C) {
+  small_eig_block(G, gld, m, k, theta, C);
+}
+
+// ---- grouped Davidson kernels: one launch per operation over all instances of a batch
+// (blockIdx.y or blockIdx.x = instance); instances with act[i] == 0 are skipped.
+
+__device__ __forceinline__ double* bd_pick(const BdSlot& s, int which, int col) {
+  switch (which) {
+    case BD_V: return s.V + (int64_t)col * s.n;
+    case BD_AV: return s.AV + (int64_t)col * s.n;
+    case BD_R: return s.r;
+    case BD_T: return s.t;
+    case BD_X: return s.x;
+    case BD_X0: return s.x0;
+    case BD_TMP: return s.tmp + (int64_t)col * s.n;
+    case BD_BX: return s.bx;
+    default: return s.by;
+  }
+}
+
+// part[(j nch + c)] = partial sums of <A col (a_col + j), B>, j < m (grid: nch x m x count)
+__global__ void k_bd_dots_partial(const BdSlot* __restrict__ sl, const int* __restrict__ act, int aw, int a_col,
+                                  int bw, int b_col, int nch) {
+  __shared__ double sh[256];
+  const int i = blockIdx.z, j = blockIdx.y, c = blockIdx.x;
+  if (!act[i]) return;
+  const BdSlot s = sl[i];
+  const double* a = bd_pick(s, aw, a_col + j);
+  const double* b = bd_pick(s, bw, b_col);
+  double v = 0.0;
+  for (int64_t e = (int64_t)c * 256 + threadIdx.x; e < s.n; e += (int64_t)nch * 256) v += a[e] * b[e];
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) s.part[(size_t)j * nch + c] = sh[0];
+}
+
+// out[j] = sum of the partials; out = G + row * mmax (to_g) or dots (grid: m x count)
+__global__ void k_bd_dots_final(const BdSlot* __restrict__ sl, const int* __restrict__ act, int nch, int to_g,
+                                int row, int mmax) {
+  __shared__ double sh[256];
+  const int i = blockIdx.y, j = blockIdx.x;
+  if (!act[i]) return;
+  const BdSlot s = sl[i];
+  double v = 0.0;
+  for (int c = threadIdx.x; c < nch; c += 256) v += s.part[(size_t)j * nch + c];
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) (to_g ? s.G + (size_t)row * mmax : s.dots)[j] = sh[0];
+}
+
+// y = beta y + sum_j c[j] V col j, c = C + cv * m (from_c) or dots
+__global__ void k_bd_combine(const BdSlot* __restrict__ sl, const int* __restrict__ act, int vw, int m, int from_c,
+                             int cv, double beta, int yw, int y_col) {
+  __shared__ double cs[64];
+  const int i = blockIdx.y;
+  if (!act[i]) return;
+  const BdSlot s = sl[i];
+  const double* c = from_c ? s.C + (size_t)cv * m : s.dots;
+  for (int j = threadIdx.x; j < m; j += blockDim.x) cs[j] = c[j];
+  __syncthreads();
+  const double* V = bd_pick(s, vw, 0);
+  double* y = bd_pick(s, yw, y_col);
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < s.n; e += (int64_t)gridDim.x * blockDim.x) {
+    double v = beta == 0.0 ? 0.0 : beta * y[e];
+    for (int j = 0; j < m; ++j) v += cs[j] * V[(size_t)j * s.n + e];
+    y[e] = v;
+  }
+}
+
+// y = a x + b y; a = -theta[0] when a_theta
+__global__ void k_bd_axpby(const BdSlot* __restrict__ sl, const int* __restrict__ act, int a_theta, double a, int xw,
+                           int x_col, double b, int yw, int y_col) {
+  const int i = blockIdx.y;
+  if (!act[i]) return;
+  const BdSlot s = sl[i];
+  const double av = a_theta ? -s.th[0] : a;
+  const double* x = bd_pick(s, xw, x_col);
+  double* y = bd_pick(s, yw, y_col);
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < s.n; e += (int64_t)gridDim.x * blockDim.x)
+    y[e] = av * x[e] + (b == 0.0 ? 0.0 : b * y[e]);
+}
+
+// y /= sqrt(dots[0])
+__global__ void k_bd_normalize(const BdSlot* __restrict__ sl, const int* __restrict__ act, int yw, int y_col) {
+  const int i = blockIdx.y;
+  if (!act[i]) return;
+  const BdSlot s = sl[i];
+  const double sc = s.dots[0] > 0.0 ? 1.0 / sqrt(s.dots[0]) : 0.0;
+  double* y = bd_pick(s, yw, y_col);
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < s.n; e += (int64_t)gridDim.x * blockDim.x)
+    y[e] *= sc;
+}
+
+// t = r / (theta[0] - diag), |denominator| floored as in the single-instance kernel
+__global__ void k_bd_precondition(const BdSlot* __restrict__ sl, const int* __restrict__ act) {
+  const int i = blockIdx.y;
+  if (!act[i]) return;
+  const BdSlot s = sl[i];
+  const double th = s.th[0];
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < s.n; e += (int64_t)gridDim.x * blockDim.x) {
+    double den = th - s.diag[e];
+    if (fabs(den) < 1e-12) den = den < 0 ? -1e-12 : 1e-12;
+    s.t[e] = s.r[e] / den;
+  }
+}
+
+__global__ void k_bd_small_eig(const BdSlot* __restrict__ sl, const int* __restrict__ act, int mmax, int m, int k) {
+  const int i = blockIdx.x;
+  if (!act[i]) return;
+  const BdSlot s = sl[i];
+  small_eig_block(s.G, mmax, m, k, s.th, s.C);
+}
+
+// restart: G = diag(theta[0..k)) (zero elsewhere)
+__global__ void k_bd_restart_g(const BdSlot* __restrict__ sl, const int* __restrict__ act, int mmax, int k) {
+  const int i = blockIdx.x;
+  if (!act[i]) return;
+  const BdSlot s = sl[i];
+  for (int e = threadIdx.x; e < mmax * mmax; e += blockDim.x) {
+    const int r = e / mmax, c = e % mmax;
+    s.G[e] = (r == c && r < k) ? s.th[r] : 0.0;
+  }
+}
+
+__global__ void k_bd_gather(const BdSlot* __restrict__ sl, int count, double* __restrict__ out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+    out[2 * i] = sl[i].th[0];
+    out[2 * i + 1] = sl[i].dots[0];
+  }
+}
+
+// x = -x where <x, x0> (dots[0]) < 0
+__global__ void k_bd_sign(const BdSlot* __restrict__ sl, const int* __restrict__ act) {
+  const int i = blockIdx.y;
+  if (!act[i]) return;
+  const BdSlot s = sl[i];
+  if (!(s.dots[0] < 0.0)) return;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < s.n; e += (int64_t)gridDim.x * blockDim.x)
+    s.x[e] = -s.x[e];
+}
+
 __device__ inline uint64_t splitmix(uint64_t x) {
   x += 0x9E3779B97F4A7C15ull;
   x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -637,6 +788,83 @@ void vec_precondition(const double* r, const double* d, const double* th, double
   k_precondition<<<nblk(n, 256), 256, 0, S(s)>>>(r, d, th, t, n);
   ++g_launches;
   ck(cudaGetLastError(), "precondition");
+}
+
+namespace {
+inline int bd_blocks(int64_t nmax, int count) {
+  // enough CTAs per instance to fill the GPU a few times over, no more than the data needs
+  const int per = (int)std::max<int64_t>(1, std::min<int64_t>((nmax + 255) / 256, std::max(1, 2048 / std::max(count, 1))));
+  return per;
+}
+}  // namespace
+
+void bd_dots(const BdSlot* sl, const int* act, int count, int64_t nmax, int aw, int a_col, int m, int bw, int b_col,
+             int to_g, int row, int mmax, Stream s) {
+  if (m <= 0 || count <= 0) return;
+  const int nch = (int)std::min<int64_t>(kBdChunks, std::max<int64_t>(1, (nmax + 256 * 8 - 1) / (256 * 8)));
+  k_bd_dots_partial<<<dim3(nch, m, count), 256, 0, S(s)>>>(sl, act, aw, a_col, bw, b_col, nch);
+  ++g_launches;
+  k_bd_dots_final<<<dim3(m, count), 256, 0, S(s)>>>(sl, act, nch, to_g, row, mmax);
+  ++g_launches;
+  ck(cudaGetLastError(), "grouped dots");
+}
+
+void bd_combine(const BdSlot* sl, const int* act, int count, int64_t nmax, int vw, int m, int from_c, int cv,
+                double beta, int yw, int y_col, Stream s) {
+  if (count <= 0) return;
+  k_bd_combine<<<dim3(bd_blocks(nmax, count), count), 256, 0, S(s)>>>(sl, act, vw, m, from_c, cv, beta, yw, y_col);
+  ++g_launches;
+  ck(cudaGetLastError(), "grouped combine");
+}
+
+void bd_axpby(const BdSlot* sl, const int* act, int count, int64_t nmax, int a_theta, double a, int xw, int x_col,
+              double b, int yw, int y_col, Stream s) {
+  if (count <= 0) return;
+  k_bd_axpby<<<dim3(bd_blocks(nmax, count), count), 256, 0, S(s)>>>(sl, act, a_theta, a, xw, x_col, b, yw, y_col);
+  ++g_launches;
+  ck(cudaGetLastError(), "grouped axpby");
+}
+
+void bd_normalize(const BdSlot* sl, const int* act, int count, int64_t nmax, int yw, int y_col, Stream s) {
+  if (count <= 0) return;
+  k_bd_normalize<<<dim3(bd_blocks(nmax, count), count), 256, 0, S(s)>>>(sl, act, yw, y_col);
+  ++g_launches;
+  ck(cudaGetLastError(), "grouped normalize");
+}
+
+void bd_precondition(const BdSlot* sl, const int* act, int count, int64_t nmax, Stream s) {
+  if (count <= 0) return;
+  k_bd_precondition<<<dim3(bd_blocks(nmax, count), count), 256, 0, S(s)>>>(sl, act);
+  ++g_launches;
+  ck(cudaGetLastError(), "grouped precondition");
+}
+
+void bd_small_eig(const BdSlot* sl, const int* act, int count, int mmax, int m, int k, Stream s) {
+  if (count <= 0) return;
+  k_bd_small_eig<<<count, 256, 0, S(s)>>>(sl, act, mmax, m, k);
+  ++g_launches;
+  ck(cudaGetLastError(), "grouped small eig");
+}
+
+void bd_restart_g(const BdSlot* sl, const int* act, int count, int mmax, int k, Stream s) {
+  if (count <= 0) return;
+  k_bd_restart_g<<<count, 256, 0, S(s)>>>(sl, act, mmax, k);
+  ++g_launches;
+  ck(cudaGetLastError(), "grouped restart");
+}
+
+void bd_gather(const BdSlot* sl, int count, double* out, Stream s) {
+  if (count <= 0) return;
+  k_bd_gather<<<(count + 127) / 128, 128, 0, S(s)>>>(sl, count, out);
+  ++g_launches;
+  ck(cudaGetLastError(), "grouped gather");
+}
+
+void bd_sign(const BdSlot* sl, const int* act, int count, int64_t nmax, Stream s) {
+  if (count <= 0) return;
+  k_bd_sign<<<dim3(bd_blocks(nmax, count), count), 256, 0, S(s)>>>(sl, act);
+  ++g_launches;
+  ck(cudaGetLastError(), "grouped sign");
 }
 
 void small_eig(const double* G, int gld, int m, int k, double* theta, double* C, Stream s) {

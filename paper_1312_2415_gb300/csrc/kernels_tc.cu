@@ -270,7 +270,7 @@ struct TileGeom {
 // in the last 128 columns.
 __global__ void __launch_bounds__(kMvThreads, 1)
     k_tc_matvec(const TfTile* __restrict__ tiles, const TfTask* __restrict__ tasks, const TfSrc* __restrict__ srcs,
-                int* __restrict__ queue, int ntiles) {
+                int* __restrict__ queue, const int* __restrict__ active, int ntiles) {
   extern __shared__ unsigned char smem_dyn[];
   float* sm = (float*)(((uintptr_t)smem_dyn + 1023) & ~(uintptr_t)1023);
   float* s1 = sm;                      // product-1 slots: D hi, D lo (nvg KB each), x hi, x lo (kp rows each)
@@ -350,6 +350,7 @@ __global__ void __launch_bounds__(kMvThreads, 1)
         mbar_arrive(&bar.tile_full[r]);
         if (ti < 0) break;
         const TfTile tile = tiles[ti];
+        if (!active[tile.inst]) continue;
         const TileGeom g(tile);
         if (g.slot_f != last_slot_f) {
           // a new slot layout overlaps the old slots: all of them are released first
@@ -408,6 +409,7 @@ __global__ void __launch_bounds__(kMvThreads, 1)
         const int ti = next_tile(k);
         if (ti < 0) break;
         const TfTile tile = tiles[ti];
+        if (!active[tile.inst]) continue;
         const TileGeom g(tile);
         int slot = 0;
         for (int t = 0; t < g.T && ok; ++t) {
@@ -464,6 +466,7 @@ __global__ void __launch_bounds__(kMvThreads, 1)
         const int ti = next_tile(k);
         if (ti < 0) break;
         const TfTile tile = tiles[ti];
+        if (!active[tile.inst]) continue;
         const TileGeom g(tile);
         auto load_c = [&](int u) {
           const TfTask tk = tasks[tile.t_begin + u];
@@ -536,6 +539,7 @@ __global__ void __launch_bounds__(kMvThreads, 1)
       const int ti = next_tile(k);
       if (ti < 0) break;
       const TfTile tile = tiles[ti];
+      if (!active[tile.inst]) continue;
       const int T = tile.t_end - tile.t_begin;
       float yacc[64];
 #pragma unroll
@@ -693,6 +697,8 @@ struct TcPlan {
   TfSrc* srcs = nullptr;
   TfConv* xb = nullptr;
   int* queue = nullptr;        // the persistent kernel's tile counter
+  int* active = nullptr;       // per instance: 0 = skip its tiles
+  int ninst = 0;
   int ntiles = 0, nxb = 0, grid = 0;
   int launches = 0;  // kernels of one launch sequence
 };
@@ -730,6 +736,7 @@ TcPlan* tc_plan_build(const std::vector<const TcHost*>& inst, Stream st) {
         q.t_begin += t0;
         q.t_end += t0;
         q.group += inst_id << 32;  // groups never span instances
+        q.inst = (int)inst_id;
         tl.push_back(q);
       }
       ++inst_id;
@@ -758,6 +765,8 @@ TcPlan* tc_plan_build(const std::vector<const TcHost*>& inst, Stream st) {
     for (size_t i = 0; i < order.size(); ++i) sorted[i] = tiles0[order[i]];
     P->grid = (int)std::min<size_t>(sorted.size(), (size_t)sm_count());
     P->queue = (int*)dev_alloc(sizeof(int), st);
+    P->ninst = (int)inst.size();
+    P->active = upload(std::vector<int>(inst.size(), 1), st);
     P->tiles = upload(sorted, st);
     P->tasks = upload(single ? inst[0]->t : t, st);
     P->srcs = upload(single ? inst[0]->s : s, st);
@@ -772,6 +781,8 @@ TcPlan* tc_plan_build(const std::vector<const TcHost*>& inst, Stream st) {
   return P;
 }
 
+int* tc_plan_active(TcPlan* p) { return p ? p->active : nullptr; }
+
 void tc_plan_free(TcPlan* p, Stream s) {
   if (!p) return;
   dev_free(p->tiles, s);
@@ -779,6 +790,7 @@ void tc_plan_free(TcPlan* p, Stream s) {
   dev_free(p->srcs, s);
   dev_free(p->xb, s);
   dev_free(p->queue, s);
+  dev_free(p->active, s);
   delete p;
 }
 
@@ -798,7 +810,8 @@ void tc_enqueue(const TcPlan* p, void* const* ev, cudaStream_t cs) {
   if (ev) event_record(ev[1], cs);
   if (p->ntiles > 0) {
     ck(cudaMemsetAsync(p->queue, 0, sizeof(int), cs), "tile queue reset");
-    k_tc_matvec<<<p->grid, kMvThreads, smem_bytes(), cs>>>(p->tiles, p->tasks, p->srcs, p->queue, p->ntiles);
+    k_tc_matvec<<<p->grid, kMvThreads, smem_bytes(), cs>>>(p->tiles, p->tasks, p->srcs, p->queue, p->active,
+                                                           p->ntiles);
   }
   if (ev) event_record(ev[2], cs);
   ck(cudaGetLastError(), "tc matvec launch");

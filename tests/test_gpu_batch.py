@@ -96,3 +96,54 @@ def test_batched_matvec_matches_each_instance(mods):
     with pytest.raises(DMRGError):
         b.run(xs, ys)
     b.close()
+
+
+def test_batched_davidson_matches_each_instance(mods):
+    """dmrg_batch_davidson: the instances' Davidsons in lockstep (one batched matvec and
+    one launch per vector operation per iteration).  Its FP64-finished energies equal the
+    lowest eigenvalue of the oracle's P^T H P on every instance the oracle projects
+    (L <= 9) and each context's own FP64 Davidson on all, within 1e-6 Eh (the mixed
+    path's target); the Ritz vectors have unit norm and a non-negative overlap with their
+    start vectors; the tensor-core Ritz values sit within the split-TF32 bias (1e-5 of
+    |E|) of them."""
+    torch, Batch, Context, DMRGError = mods
+    systems = []
+    ctxs, sites = _instances(Context, systems)
+    starts, ref = [], []
+    for c, i, (irr, h, V, N, tS), (_, _, _, _, D) in zip(ctxs, sites, systems, CASES):
+        x0 = c.tt_to_x(i)
+        starts.append(torch.tensor(x0, device="cuda"))
+        c.set_precision(0, 0)
+        c.set_schedule([D], [0.0], [1], [0.0], 1e-9, 300)
+        x = x0.copy()
+        e, it, ok = c.davidson(i, x)
+        assert ok
+        ref.append(e)
+        if len(irr) <= 9:
+            m = mps_from_bytes(c.get_mps(), irr)
+            H, _, _ = odmrg.effective_hamiltonian(odmrg.Problem(h, V, irr, N, tS, 0), m, i)
+            assert abs(np.linalg.eigvalsh(H)[0] - e) < 1e-9
+    b = Batch(ctxs, sites, autotune=False)
+    xs = [s.clone() for s in starts]
+    e64, iters, conv = b.davidson(xs, tol=1e-4, max_iter=200, fp64_energy=True)
+    assert conv.all() and (iters >= 1).all()
+    for e, r, x, s in zip(e64, ref, xs, starts):
+        assert abs(e - r) < 1e-6, (e, r)
+        assert abs(torch.linalg.norm(x).item() - 1.0) < 1e-12
+        assert (x @ s).item() >= 0.0
+    xs = [s.clone() for s in starts]
+    etc, _, conv = b.davidson(xs, tol=1e-4, max_iter=200, fp64_energy=False)
+    assert conv.all()
+    for e, r in zip(etc, ref):
+        assert abs(e - r) < 1e-5 * abs(r) + 1e-8, (e, r)
+    # the batched matvec computes every instance again afterwards (the Davidson's
+    # per-instance skip flags are restored)
+    ys = [torch.empty_like(x) for x in xs]
+    b.run(xs, ys)
+    torch.cuda.synchronize()
+    for c, i, x, y in zip(ctxs, sites, xs, ys):
+        c.set_precision(0, 0)
+        y64 = torch.empty_like(x)
+        c.matvec(i, x, y64)
+        assert ((y - y64).abs().max() / y64.abs().max()).item() <= 2e-6
+    b.close()
