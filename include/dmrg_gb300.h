@@ -165,6 +165,14 @@ int dmrg_tt_to_x(dmrg_ctx* ctx, int site, double* x, uintptr_t stream);
 /* y = H_eff x (Eq. 9) with the renormalised and complementary operators of Sec. 2.5. */
 int dmrg_heff_matvec(dmrg_ctx* ctx, int site, const double* x, double* y, uintptr_t stream);
 
+/* *energy = x^T H_eff x / x^T x (the Rayleigh quotient that gives a micro-iteration's
+ * energy, Secs. 2.3 and 4.3; without E_const), always in FP64.  H_eff is symmetric, so it
+ * is evaluated from the block pairs with input block >= output block (the others' share
+ * counted twice): about half of a matvec's second phase.  x: n doubles in the layout of
+ * dmrg_two_site_layout, device pointer when stream != 0, host pointer when stream == 0.
+ * DMRG_EINVAL for a NULL pointer or a zero vector. */
+int dmrg_energy(dmrg_ctx* ctx, int site, const double* x, double* energy, uintptr_t stream);
+
 /* Allocation-free variant of dmrg_heff_matvec (no counterpart in the paper).  It is for
  * callers that cannot allocate device memory at the moment they apply H_eff: a process
  * that reserved its device memory up front and must not grow it (a serving process

@@ -83,6 +83,7 @@ _SIGS = {
     "dmrg_batch_run": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
                                       ctypes.c_size_t]),
     "dmrg_batch_info": (ctypes.c_int, [_P, _D, _I, _I, _D, _D]),
+    "dmrg_energy": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_void_p, _D, ctypes.c_size_t]),
     "dmrg_batch_davidson": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_void_p), ctypes.c_double, ctypes.c_int,
                                            ctypes.c_int, _D, _I, _I, ctypes.c_size_t]),
     "dmrg_batch_last_error": (ctypes.c_char_p, [_P]),
@@ -237,6 +238,13 @@ class Context:
         py, _ = _ptr_and_stream(y)
         self._check(self.lib.dmrg_heff_matvec(self.h, site, px, py, s))
         return y
+
+    def energy(self, site, x):
+        """x^T H_eff x / x^T x in FP64 (dmrg_energy); x: numpy array or CUDA tensor."""
+        p, s = _ptr_and_stream(x)
+        e = ctypes.c_double()
+        self._check(self.lib.dmrg_energy(self.h, site, p, ctypes.byref(e), s))
+        return e.value
 
     def matvec_noalloc(self, site, x, y, stream=0):
         """y = H_eff x without any allocation (x, y: device addresses; see the header)."""

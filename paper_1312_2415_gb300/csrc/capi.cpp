@@ -282,6 +282,23 @@ int dmrg_heff_matvec(dmrg_ctx* c, int site, const double* x, double* y, uintptr_
   });
 }
 
+int dmrg_energy(dmrg_ctx* c, int site, const double* x, double* energy, uintptr_t stream) {
+  return guard(c, [&] {
+    if (!x || !energy) return DMRG_EINVAL;
+    wait_user(stream);
+    const int64_t n = xsize(c, site);
+    dmrg::Stream s = dev_stream(c);
+    if (stream) {
+      *energy = c->eng->rayleigh_fp64(site, x);
+    } else {
+      DevBuf dx(n, s);
+      dmrg::dev_h2d(dx.p, x, sizeof(double) * n, s);
+      *energy = c->eng->rayleigh_fp64(site, dx.p);
+    }
+    return DMRG_OK;
+  });
+}
+
 int dmrg_heff_matvec_noalloc(dmrg_ctx* c, int site, const double* x, double* y, uintptr_t stream) {
   return guard(c, [&] {
     if (!x || !y || !c->stream) return DMRG_EINVAL;

@@ -812,6 +812,12 @@ struct Engine::MatvecPlan {
   GemmPlan* p1 = nullptr;
   GemmPlan* p2 = nullptr;
   double flops = 0.0, flops1 = 0.0, flops2 = 0.0;
+  // the quadratic form x^T H x with the block pairs of input block >= output block
+  // (build_rq; phase 1 restricted to the x rows those pairs read)
+  GemmPlan* rq1 = nullptr;
+  GemmPlan* rq2 = nullptr;
+  CombPlan* rqc = nullptr;
+  double rq_flops1 = 0.0, rq_flops2 = 0.0;
   int64_t ntasks = 0;
   int64_t zsize = 0;
   // host tables kept for the mixed-precision plan (built on first use, then released)
@@ -1271,6 +1277,9 @@ void Engine::free_plan(MatvecPlan* p) {
   gemm_plan_free(p->p1, stream_);
   gemm_plan_free(p->p2, stream_);
   comb_plan_free(p->pc, stream_);
+  gemm_plan_free(p->rq1, stream_);
+  gemm_plan_free(p->rq2, stream_);
+  comb_plan_free(p->rqc, stream_);
   dev_free(p->Z, stream_);
   dev_free(p->W, stream_);
   dev_free(p->xin, stream_);
@@ -1479,7 +1488,8 @@ double Engine::rayleigh_fp64(int i, const double* x) {
   check_ready();
   if (i < 0 || i > L_ - 2) throw std::out_of_range("site out of range");
   MatvecPlan* P = plan_for(i);
-  run_matvec(P, x, P->yout, false);
+  if (x != P->xin) dev_d2d(P->xin, x, sizeof(double) * P->n, stream_);
+  run_rq(P);
   double* d = (double*)dev_alloc(sizeof(double) * (2 + 1024), stream_);
   double h[2];
   try {
@@ -1551,6 +1561,120 @@ void Engine::run_matvec(MatvecPlan* p, const double* x, double* y, bool tc) {
   st_.matvec_flops += p->flops;
   st_.last_matvec_flops = p->flops;
   st_.last_matvec_tasks = p->ntasks;
+}
+
+// The energy x^T H x / x^T x needs only half of the matvec: H_eff is symmetric, so with
+// y_X' = sum_X H_X'X x_X blockwise, x^T H x = sum_X' [x_X'^T H_X'X' x_X' +
+// 2 sum_{X > X'} x_X'^T H_X'X x_X].  The plan below keeps the sources whose input block
+// X is >= the output block X' (those of X > X' with twice the coefficient), drops the W
+// items left without sources, and restricts each phase-1 product to the rows of the x
+// stack that a kept source reads; x^T y' then equals x^T H x up to rounding (y' itself is
+// not H x).
+void Engine::build_rq(MatvecPlan* P) {
+  if (P->rqc) return;
+  const size_t nw = P->witems.size();
+  std::vector<int> wxp(nw, -1);
+  for (int x = 0; x < (int)P->w_by_x.size(); ++x)
+    for (int k : P->w_by_x[x]) wxp[k] = x;
+  std::vector<int64_t> woff(nw + 1, 0);
+  for (size_t k = 0; k < nw; ++k) woff[k + 1] = woff[k] + (int64_t)P->witems[k].rows * P->witems[k].cols;
+  const size_t nz = P->zg.size();
+  std::vector<int64_t> lo(nz, std::numeric_limits<int64_t>::max()), hi(nz, -1);
+  std::vector<CombSrc> cs;
+  std::vector<CombDst> cd;
+  std::vector<char> keep_w(nw, 0);
+  for (size_t k = 0; k < nw; ++k) {
+    const auto& w = P->witems[k];
+    const int xp = wxp[k];
+    const int b0 = (int)cs.size();
+    for (int q = w.src_begin; q < w.src_end; ++q) {
+      const auto& src = P->wsrc[q];
+      if (src.xb < xp) continue;
+      const XBlock& X = P->X[src.xb];
+      const double c = src.xb > xp ? 2.0 * src.coef : src.coef;
+      if (src.zg >= 0) {
+        const auto& z = P->zg[src.zg];
+        cs.push_back({P->Z + z.off + (int64_t)X.trow * z.n, z.n, c});
+        lo[src.zg] = std::min<int64_t>(lo[src.zg], X.trow);
+        hi[src.zg] = std::max<int64_t>(hi[src.zg], X.trow + X.rows);
+      } else {
+        const int sec = -1 - src.zg;  // identity right operator: x rows of the sector
+        cs.push_back({P->xin + P->tall_off[sec] + (int64_t)X.trow * P->sec_dim[sec], P->sec_dim[sec], c});
+      }
+    }
+    if ((int)cs.size() == b0) continue;
+    keep_w[k] = 1;
+    cd.push_back({P->W + woff[k], w.cols, w.rows, w.cols, b0, (int)cs.size(), 0});
+  }
+  std::vector<GemmTask> t1;
+  std::vector<GemmGroup> g1;
+  double f1 = 0.0, f2 = 0.0;
+  for (size_t z = 0; z < nz; ++z) {
+    if (hi[z] < 0) continue;
+    const auto& Zg = P->zg[z];
+    const int64_t r0 = lo[z], rows = hi[z] - lo[z];
+    t1.push_back({P->xin + P->tall_off[Zg.c] + r0 * Zg.K, Zg.D, Zg.K, Zg.K, Zg.K, 0, 1, Zg.alpha});
+    g1.push_back({P->Z + Zg.off + r0 * Zg.n, Zg.n, (int)rows, Zg.n, (int)t1.size() - 1, (int)t1.size(), 0});
+    f1 += 2.0 * rows * Zg.K * Zg.n;
+  }
+  std::vector<GemmTask> t2;
+  std::vector<GemmGroup> g2;
+  for (int x = 0; x < (int)P->w_by_x.size(); ++x) {
+    const int b0 = (int)t2.size();
+    for (int k : P->w_by_x[x]) {
+      if (!keep_w[k]) continue;
+      const auto& w = P->witems[k];
+      const CombOp& C = P->cl[w.gl];
+      const BlockRef& cb = (*C.blocks)[w.cbi];
+      if (C.identity) {
+        t2.push_back({nullptr, P->W + woff[k], 0, w.cols, w.rows, 0, 0, C.scalar});
+      } else {
+        t2.push_back({C.data + cb.off, P->W + woff[k], cb.cols, w.cols, cb.cols, 0, 0, C.scalar});
+        f2 += 2.0 * cb.rows * cb.cols * w.cols;
+      }
+    }
+    if ((int)t2.size() > b0) {
+      const XBlock& X = P->X[x];
+      g2.push_back({P->yout + X.off, X.cols, X.rows, X.cols, b0, (int)t2.size(), 0});
+    }
+  }
+  try {
+    P->rq1 = gemm_plan_upload(t1, g1, stream_);
+    P->rqc = comb_plan_upload(cs, cd, stream_);
+    P->rq2 = gemm_plan_upload(t2, g2, stream_);
+  } catch (...) {
+    gemm_plan_free(P->rq1, stream_);
+    comb_plan_free(P->rqc, stream_);
+    gemm_plan_free(P->rq2, stream_);
+    P->rq1 = P->rq2 = nullptr;
+    P->rqc = nullptr;
+    throw;
+  }
+  P->rq_flops1 = f1;
+  P->rq_flops2 = f2;
+}
+
+// y' of build_rq for the plan's input x (P->xin), into P->yout, on the engine's current
+// stream, with the excited-state projectors added as in a matvec
+void Engine::run_rq(MatvecPlan* P) {
+  build_rq(P);
+  if (P->zsize) dev_zero(P->Z, sizeof(double) * P->zsize, stream_);
+  dev_zero(P->yout, sizeof(double) * std::max<int64_t>(P->n, 1), stream_);
+  flush_events();
+  if (!ev_[0]) for (auto& e : ev_) e = event_create();
+  event_record(ev_[0], stream_);
+  gemm_plan_run(P->rq1, stream_);
+  comb_plan_run(P->rqc, stream_);
+  event_record(ev_[1], stream_);
+  gemm_plan_run(P->rq2, stream_);
+  event_record(ev_[2], stream_);
+  ev_pending_ = true;
+  ev_tc_ = false;
+  add_projectors(P);
+  st_.k_launches += 1;
+  st_.k_phase1_flops += P->rq_flops1;
+  st_.k_phase2_flops += P->rq_flops2;
+  st_.matvec_flops += P->rq_flops1 + P->rq_flops2;
 }
 
 void Engine::matvec(int i, const double* x, double* y) {
@@ -1687,7 +1811,7 @@ void Engine::launch_rq() {
   Stream keep = stream_;
   stream_ = side_;
   try {
-    run_matvec(P, P->xin, P->yout, false);
+    run_rq(P);
     vec_multidot(P->xin, P->n, 1, P->yout, P->n, rq_dev_, rq_dev_ + 2, side_);
     vec_multidot(P->xin, P->n, 1, P->xin, P->n, rq_dev_ + 1, rq_dev_ + 2 + 512, side_);
     event_record(ev_side_[1], side_);
@@ -2927,6 +3051,7 @@ double Engine::sweep_step(int i, int dir, int D, double gamma, double* w_disc, i
           release_tc(cached_);
           throw;
         }
+        build_rq(cached_);
       }
     }
   } catch (...) {

@@ -180,7 +180,8 @@ class Engine {
   // serial (changes whenever the tables are rebuilt), its input / output buffers and
   // flops.  The tables stay valid until the MPS or the site of the engine changes.
   struct TcView { const TcHost* host; uint64_t serial; double* x; double* y; int64_t n; double flops; const double* diag; };
-  // x^T H x / x^T x with the FP64 matvec of site i's tables (x on the device)
+  // x^T H x / x^T x in FP64 with site i's tables (the symmetric form of build_rq; x on
+  // the device)
   double rayleigh_fp64(int i, const double* x);
   TcView prepare_tc(int i, TcTune tune);
   uint64_t tc_serial(int i) const;
@@ -209,6 +210,8 @@ class Engine {
   MatvecPlan* plan_matvec(int i);
   void free_plan(MatvecPlan* p);
   void release_tc(MatvecPlan* p);  // frees the tensor-core tables of a plan
+  void build_rq(MatvecPlan* p);    // tables of the symmetric quadratic form (energy)
+  void run_rq(MatvecPlan* p);
   MatvecPlan* plan_for(int i);
   void run_matvec(MatvecPlan* p, const double* x, double* y, bool tc = false);
   double davidson_core(MatvecPlan* P, double* x, double tol, int maxit, bool tc, int* iters,

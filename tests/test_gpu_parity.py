@@ -169,3 +169,30 @@ def test_full_d_equals_fci_and_u0_closed_form(Context):
         ctx.init_mps(99)
         emin, elast = ctx.solve()
         assert abs(emin - want) < 1e-8
+
+
+@pytest.mark.parametrize("case", CASES[:4], ids=lambda c: f"{c[0]}L{c[1]}N{c[2]}S{c[3]}I{c[4]}")
+def test_energy_symmetric_form_matches_oracle(Context, case):
+    """dmrg_energy: the sweep's FP64 energy from the block pairs of input block >= output
+    block (H_eff symmetric, the others' share counted twice) equals the oracle's
+    x . (P^T H P x) / x . x and the library's own x . (H x) (FP64 matvec) for a random
+    vector, in both precision modes (the energy is FP64 in both).  Tolerance: 1e-12 of
+    |H x| / |x|, the matvec's own bound carried through the dot product."""
+    kind, L, N, tS, IG, D = case
+    for i in sorted({0, L // 2 - 1, L - 2}):
+        irr, h, V, m, prob = setup(kind, L, N, tS, IG, D, 3, i)
+        H, _, proj = odmrg.effective_hamiltonian(prob, m, i)
+        for prec in (0, 1):
+            ctx = Context(L, irr, N, tS, IG, precision=prec)
+            ctx.set_integrals(h, V)
+            ctx.set_mps(mps_to_bytes(m))
+            n, table = ctx.layout(i)
+            v = np.random.default_rng(i + 17).normal(size=n)
+            yo = oracle_x_to_lib(proj.unflatten(H @ proj.flatten(lib_x_to_oracle(v, table))), table, n)
+            eo = (v @ yo) / (v @ v)
+            bound = 1e-12 * np.linalg.norm(yo) / np.linalg.norm(v)
+            e = ctx.energy(i, v)
+            assert abs(e - eo) <= bound, (e, eo, bound)
+            ctx.set_precision(0, 0)
+            y = ctx.matvec(i, v)
+            assert abs(e - (v @ y) / (v @ v)) <= bound
