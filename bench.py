@@ -54,6 +54,7 @@ def parse():
     p.add_argument("--fp64-steps", type=int, default=3, help="timed FP64 steps on the swept state")
     p.add_argument("--e2e-steps", type=int, default=5, help="steps of the host-buffer e2e run")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-batch", action="store_true", help="skip the batch32 summary of the default line")
     return p.parse_args()
 
 
@@ -493,16 +494,12 @@ def batch_instances():
     return out
 
 
-def run_batch(args):
-    """batch32: the mixed-precision matvecs of 32 instances, one at a time (one grouped
-    launch sequence per instance) against one batched, graph-replayed launch sequence
-    over all of them; value = their summed flops over the batched time."""
+def batch_contexts(args):
+    """The 32 instances at their middle pairs, tables prepared, start vectors (Eq. 25)."""
     import torch
-    from paper_1312_2415_gb300 import Batch, Context
+    from paper_1312_2415_gb300 import Context
     from workloads import hubbard_chain, random_integrals, round_robin_irreps
-    torch.cuda.set_device(0)
     ctxs, sites, xs, ys = [], [], [], []
-    t_setup = time.perf_counter()
     for kind, L, tS, D, seed in batch_instances():
         if kind == "hubbard":
             irr, (h, V), group = [0] * L, hubbard_chain(L, 1.0, 4.0), 0
@@ -521,6 +518,54 @@ def run_batch(args):
         c.matvec(i, x, y)  # prepares the instance's tables
         ctxs.append(c); sites.append(i); xs.append(x); ys.append(y)
     torch.cuda.synchronize()
+    return ctxs, sites, xs, ys
+
+
+def batch_summary(args):
+    """The batch32 matvecs for the default line: one batched persistent launch (fixed
+    tile shape, no autotuner) against the instances one at a time, 3 timed runs each."""
+    import torch
+    from paper_1312_2415_gb300 import Batch
+    t0 = time.perf_counter()
+    ctxs, sites, xs, ys = batch_contexts(args)
+
+    def timed(fn, k=3):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(k):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    def sequential():
+        for c, i, x, y in zip(ctxs, sites, xs, ys):
+            c.matvec(i, x, y)
+    seq_ms = timed(sequential)
+    b = Batch(ctxs, sites, autotune=False)
+    bat_ms = timed(lambda: b.run(xs, ys))
+    flops = b.info()["flops"]
+    b.close()
+    for c in ctxs:
+        c.close()
+    return {"workload": "batch32 (32 instances, Hubbard L=8..24 and random-integral L=10..20, N=L, S in {0,1}, "
+                        "D in {64..1024}, middle sites; the initial MPS of Sec. 4.3)",
+            "batched_ms": bat_ms, "sequential_ms": seq_ms, "speedup_vs_sequential": seq_ms / bat_ms,
+            "batched_gflops": flops / (bat_ms * 1e-3) / 1e9, "flops_per_matvec_set": flops,
+            "s": time.perf_counter() - t0, "details": "python bench.py --workload batch32 (autotuner, batched Davidson)"}
+
+
+def run_batch(args):
+    """batch32: the mixed-precision matvecs of 32 instances, one at a time (one grouped
+    launch sequence per instance) against one batched, graph-replayed launch sequence
+    over all of them; value = their summed flops over the batched time."""
+    import torch
+    from paper_1312_2415_gb300 import Batch
+    torch.cuda.set_device(0)
+    t_setup = time.perf_counter()
+    ctxs, sites, xs, ys = batch_contexts(args)
     t_setup = time.perf_counter() - t_setup
 
     def timed(fn):
@@ -765,6 +810,7 @@ def run_gb300(args):
     ctx.canonicalize(center)
     acc = energy_agreement(ctx, center, D, args) if not args.no_fp64 else None
     conv = converged_agreement() if not args.no_fp64 and not args.no_sweep else None
+    batch = batch_summary(args) if not args.no_batch and world == 1 else None
     # one marked matvec in each precision after the timed region (NVTX range for profilers)
     xprof = torch.tensor(ctx.tt_to_x(center), dtype=torch.float64, device="cuda")
     yprof = torch.empty_like(xprof)
@@ -799,7 +845,7 @@ def run_gb300(args):
                    "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (renormalised operators of both environments, several GB)",
                    "block_histogram": hist},
-        "matvec": rates, "fp64": fp64, "energy_agreement": acc, "converged_agreement": conv, "sweep": sweeps,
+        "matvec": rates, "fp64": fp64, "energy_agreement": acc, "converged_agreement": conv, "sweep": sweeps, "batch32": batch,
         "micro_iteration_s": t_max / args.steps / 1e3,
         "step_breakdown_ms": step_breakdown(delta, args.steps),
         "energy_last": energies[-1] if energies else None,
