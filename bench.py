@@ -328,7 +328,16 @@ def matvec_kernel_rates(delta):
 # matvec's main kernel from one ncu capture (a smaller case scaled to a full launch by the
 # units processed, as the profile summary states), keyed by the workload and the SHA-256
 # prefix of the kernel source it was taken with: a changed kernel reports traffic null.
-NCU_TRAFFIC = {}
+# DRAM bytes per launch of k_tc_matvec (dram__bytes_read.sum + dram__bytes_write.sum, one
+# ncu pass, every launch of the timed steps of the default run), keyed by workload and
+# the kernel source it was measured on (a changed kernel reports null):
+#   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none --nvtx
+#       --nvtx-include "steps/" -k regex:k_tc_matvec -c 48 --csv
+#       python bench.py --no-fp64 --no-e2e --no-cpu-baseline --no-batch
+NCU_TRAFFIC = {
+    (("random28", 2500), "fa2e75becb409745"): {
+        "bytes": 4.03e10, "how": "mean over the 48 launches of the timed steps (3.40e10 .. 4.48e10), ncu one pass"},
+}
 
 
 def kernel_source_hash():
@@ -355,7 +364,8 @@ def roofline_mixed(delta, peaks, peak_tf32, workload=None):
     t_hbm, t_tc = byts / (hbm * 1e9), fl / (peak_tf32 * 1e9)
     gbs = byts / (ms * 1e-3) / 1e9
     tfs = fl / (ms * 1e-3) / 1e12
-    traffic = NCU_TRAFFIC.get((workload, kernel_source_hash())) if workload else None
+    tr = NCU_TRAFFIC.get((workload, kernel_source_hash())) if workload else None
+    traffic = tr["bytes"] if tr else None
     hbm_roof = {"achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "peak_source": hsrc}
     tc_roof = {"achieved": tfs, "peak": peak_tf32 / 1e3, "unit": "TFLOP/s", "frac": tfs / (peak_tf32 / 1e3),
                "peak_source": "cuBLAS FP32 GEMM with TF32, 8192^3, measured by bench.py in this run (of measured)"}
@@ -363,7 +373,8 @@ def roofline_mixed(delta, peaks, peak_tf32, workload=None):
     return {"bound": "tensor" if t_tc >= t_hbm else "hbm", "kernel": "k_tc_matvec (fused split-TF32 block "
             "products: x D^T in tensor memory, then C W, per output tile)",
             "achieved": main["achieved"], "peak": main["peak"], "unit": main["unit"], "frac": main["frac"],
-            "traffic": traffic, "peak_source": main["peak_source"], "launch_ms": ms,
+            "traffic": traffic, "traffic_source": tr["how"] if tr else None,
+            "peak_source": main["peak_source"], "launch_ms": ms,
             "algorithmic_bytes": byts, "method_flops": fl,
             "other_roof": {"bound": "hbm" if main is tc_roof else "tensor", **other}}
 
