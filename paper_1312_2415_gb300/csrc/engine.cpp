@@ -75,83 +75,6 @@ void parallel_chunks(size_t n, size_t chunk, F f) {
   if (err) std::rethrow_exception(err);
 }
 
-// parallel_chunks with a private state per thread, made once by mk() (for instance a copy
-// of the coupling coefficients' memo tables): f(state, begin, end)
-template <class MK, class F>
-void parallel_chunks_state(size_t n, size_t chunk, MK mk, F f) {
-  std::atomic<size_t> next{0};
-  std::mutex mu;
-  std::exception_ptr err;
-  auto run = [&]() {
-    try {
-      auto st = mk();
-      for (;;) {
-        const size_t b = next.fetch_add(chunk);
-        if (b >= n) break;
-        f(st, b, std::min(n, b + chunk));
-      }
-    } catch (...) {
-      std::lock_guard<std::mutex> lk(mu);
-      if (!err) err = std::current_exception();
-      next.store(n);
-    }
-  };
-  const unsigned hc = std::thread::hardware_concurrency();
-  const size_t nth = std::min<size_t>(std::max(1u, std::min(16u, hc ? hc : 1u)), (n + chunk - 1) / chunk);
-  std::vector<std::thread> th;
-  for (size_t t = 1; t < nth; ++t) th.emplace_back(run);
-  run();
-  for (auto& t : th) t.join();
-  if (err) std::rethrow_exception(err);
-}
-
-// Tables of an operator update, built per combined operator in parallel and joined in
-// operator order (the same tables as a serial build): phase-1 products Z = (operator
-// block) x (site block) with their ids, and the phase-2 tasks tagged with their output
-// block, whose B holds a Z id until group_by_output resolves it.
-struct UpdZ { int64_t off; int rows, cols; };
-struct UpdPart {
-  std::vector<GemmTask> t1;
-  std::vector<GemmGroup> g1;
-  std::vector<UpdZ> zs;
-  int64_t zsize = 0;
-  std::vector<TaggedTask> out2;
-};
-void join_update_parts(std::vector<UpdPart>& parts, std::vector<GemmTask>& t1, std::vector<GemmGroup>& g1,
-                       std::vector<UpdZ>& zs, int64_t& zsize, std::vector<TaggedTask>& out2) {
-  size_t n1 = 0, nz = 0, n2 = 0;
-  for (const UpdPart& p : parts) {
-    n1 += p.t1.size();
-    nz += p.zs.size();
-    n2 += p.out2.size();
-  }
-  t1.reserve(n1);
-  g1.reserve(nz);
-  zs.reserve(nz);
-  out2.reserve(n2);
-  for (UpdPart& p : parts) {
-    const int tb = (int)t1.size();
-    const intptr_t zb = (intptr_t)zs.size();
-    for (GemmGroup g : p.g1) {
-      g.task_begin += tb;
-      g.task_end += tb;
-      g1.push_back(g);
-    }
-    t1.insert(t1.end(), p.t1.begin(), p.t1.end());
-    for (UpdZ z : p.zs) {
-      z.off += zsize;
-      zs.push_back(z);
-    }
-    zsize += p.zsize;
-    for (TaggedTask q : p.out2) {
-      q.t.B = (const double*)((intptr_t)q.t.B + zb);
-      out2.push_back(q);
-    }
-    UpdPart().t1.swap(p.t1);
-    std::vector<TaggedTask>().swap(p.out2);
-  }
-}
-
 uint64_t splitmix64_next(uint64_t& state) {
   state += 0x9E3779B97F4A7C15ull;
   uint64_t z = state;
@@ -713,40 +636,35 @@ void Engine::update_left_from(int i, std::vector<CombOp>& comb) {
   for (size_t o = 0; o < E.blocks.size(); ++o) bbase[o + 1] = bbase[o] + (int64_t)E.blocks[o].size();
   std::vector<TaggedTask> out2;
   int64_t zsize = 0;
-  std::vector<UpdZ> zs;
-  std::vector<UpdPart> parts(comb.size());
-  parallel_chunks_state(comb.size(), 4, [&]() { return Coupling(*cp_); }, [&](Coupling& cp, size_t cb0, size_t cb1) {
-    for (size_t ci = cb0; ci < cb1; ++ci) {
-      const CombOp& c = comb[ci];
-      if (c.target == id_op) continue;
-      UpdPart& U = parts[ci];
-      for (const BlockRef& cb : *c.blocks) {
-        for (int t : by_l[cb.c]) {
-          const SiteBlock& tb = T.blocks[t];
-          // Z1 = C_blk (rows x cols) . T_t (dL x dM)
-          int zid = -1;
-          for (int tp : by_l[cb.r]) {
-            const SiteBlock& tpb = T.blocks[tp];
-            double coef = c.scalar * cp.left(c.pattern, bl.sec[tb.l].tj, tb.ls, bm.sec[tb.r].tj,
-                                             bl.sec[tpb.l].tj, tpb.ls, bm.sec[tpb.r].tj);
-            if (coef == 0.0) continue;
-            auto it = E.at[c.target].find(bkey(tpb.r, tb.r));
-            if (it == E.at[c.target].end()) continue;
-            if (zid < 0) {
-              zid = (int)U.zs.size();
-              U.zs.push_back({U.zsize, cb.rows, tb.cols});
-              U.zsize += (int64_t)cb.rows * tb.cols;
-              U.t1.push_back({c.data + cb.off, T.data + tb.off, cb.cols, tb.cols, cb.cols, 0, 0, 1.0});
-              U.g1.push_back({nullptr, tb.cols, cb.rows, tb.cols, (int)U.t1.size() - 1, (int)U.t1.size(), 0});
-            }
-            U.out2.push_back({bbase[c.target] + it->second,
-                              {T.data + tpb.off, (const double*)(intptr_t)zid, tpb.cols, tb.cols, tpb.rows, 1, 0, coef}});
+  struct ZRef { int64_t off; int rows, cols; };
+  std::vector<ZRef> zs;
+  for (auto& c : comb) {
+    if (c.target == id_op) continue;
+    for (const BlockRef& cb : *c.blocks) {
+      for (int t : by_l[cb.c]) {
+        const SiteBlock& tb = T.blocks[t];
+        // Z1 = C_blk (rows x cols) . T_t (dL x dM)
+        int zid = -1;
+        for (int tp : by_l[cb.r]) {
+          const SiteBlock& tpb = T.blocks[tp];
+          double coef = c.scalar * cp_->left(c.pattern, bl.sec[tb.l].tj, tb.ls, bm.sec[tb.r].tj,
+                                              bl.sec[tpb.l].tj, tpb.ls, bm.sec[tpb.r].tj);
+          if (coef == 0.0) continue;
+          auto it = E.at[c.target].find(bkey(tpb.r, tb.r));
+          if (it == E.at[c.target].end()) continue;
+          if (zid < 0) {
+            zid = (int)zs.size();
+            zs.push_back({zsize, cb.rows, tb.cols});
+            zsize += (int64_t)cb.rows * tb.cols;
+            t1.push_back({c.data + cb.off, T.data + tb.off, cb.cols, tb.cols, cb.cols, 0, 0, 1.0});
+            g1.push_back({nullptr, tb.cols, cb.rows, tb.cols, (int)t1.size() - 1, (int)t1.size(), 0});
           }
+          out2.push_back({bbase[c.target] + it->second,
+                          {T.data + tpb.off, (const double*)(intptr_t)zid, tpb.cols, tb.cols, tpb.rows, 1, 0, coef}});
         }
       }
     }
-  });
-  join_update_parts(parts, t1, g1, zs, zsize, out2);
+  }
   double* Z = (double*)dev_alloc(sizeof(double) * std::max<int64_t>(zsize, 1), stream_);
   for (size_t z = 0; z < g1.size(); ++z) g1[z].C = Z + zs[z].off;
   dev_zero(Z, sizeof(double) * std::max<int64_t>(zsize, 1), stream_);
@@ -796,41 +714,36 @@ void Engine::update_right_from(int j, std::vector<CombOp>& comb) {
   for (size_t o = 0; o < E.blocks.size(); ++o) bbase[o + 1] = bbase[o] + (int64_t)E.blocks[o].size();
   std::vector<TaggedTask> out2;
   int64_t zsize = 0;
-  std::vector<UpdZ> zs;
-  std::vector<UpdPart> parts(comb.size());
-  parallel_chunks_state(comb.size(), 4, [&]() { return Coupling(*cp_); }, [&](Coupling& cp, size_t cb0, size_t cb1) {
-    for (size_t ci = cb0; ci < cb1; ++ci) {
-      const CombOp& c = comb[ci];
-      if (c.target == h_op) continue;
-      UpdPart& U = parts[ci];
-      for (const BlockRef& db : *c.blocks) {
-        for (int t : by_r[db.c]) {
-          const SiteBlock& tb = T.blocks[t];
-          int zid = -1;
-          for (int tp : by_r[db.r]) {
-            const SiteBlock& tpb = T.blocks[tp];
-            double coef = c.scalar * f(tb) * f(tpb) *
-                          cp.right(c.pattern, tb.ls, br.sec[tb.r].tj, bm.sec[tb.l].tj, tpb.ls,
+  struct ZRef { int64_t off; int rows, cols; };
+  std::vector<ZRef> zs;
+  for (auto& c : comb) {
+    if (c.target == h_op) continue;
+    for (const BlockRef& db : *c.blocks) {
+      for (int t : by_r[db.c]) {
+        const SiteBlock& tb = T.blocks[t];
+        int zid = -1;
+        for (int tp : by_r[db.r]) {
+          const SiteBlock& tpb = T.blocks[tp];
+          double coef = c.scalar * f(tb) * f(tpb) *
+                        cp_->right(c.pattern, tb.ls, br.sec[tb.r].tj, bm.sec[tb.l].tj, tpb.ls,
                                    br.sec[tpb.r].tj, bm.sec[tpb.l].tj);
-            if (coef == 0.0) continue;
-            auto it = E.at[c.target].find(bkey(tpb.l, tb.l));
-            if (it == E.at[c.target].end()) continue;
-            if (zid < 0) {
-              // Z1 = D_blk (dR' x dR) . T_t^T (dR x dM)
-              zid = (int)U.zs.size();
-              U.zs.push_back({U.zsize, db.rows, tb.rows});
-              U.zsize += (int64_t)db.rows * tb.rows;
-              U.t1.push_back({c.data + db.off, T.data + tb.off, db.cols, tb.cols, db.cols, 0, 1, 1.0});
-              U.g1.push_back({nullptr, tb.rows, db.rows, tb.rows, (int)U.t1.size() - 1, (int)U.t1.size(), 0});
-            }
-            U.out2.push_back({bbase[c.target] + it->second,
-                              {T.data + tpb.off, (const double*)(intptr_t)zid, tpb.cols, tb.rows, tpb.cols, 0, 0, coef}});
+          if (coef == 0.0) continue;
+          auto it = E.at[c.target].find(bkey(tpb.l, tb.l));
+          if (it == E.at[c.target].end()) continue;
+          if (zid < 0) {
+            // Z1 = D_blk (dR' x dR) . T_t^T (dR x dM)
+            zid = (int)zs.size();
+            zs.push_back({zsize, db.rows, tb.rows});
+            zsize += (int64_t)db.rows * tb.rows;
+            t1.push_back({c.data + db.off, T.data + tb.off, db.cols, tb.cols, db.cols, 0, 1, 1.0});
+            g1.push_back({nullptr, tb.rows, db.rows, tb.rows, (int)t1.size() - 1, (int)t1.size(), 0});
           }
+          out2.push_back({bbase[c.target] + it->second,
+                          {T.data + tpb.off, (const double*)(intptr_t)zid, tpb.cols, tb.rows, tpb.cols, 0, 0, coef}});
         }
       }
     }
-  });
-  join_update_parts(parts, t1, g1, zs, zsize, out2);
+  }
   double* Z = (double*)dev_alloc(sizeof(double) * std::max<int64_t>(zsize, 1), stream_);
   for (size_t z = 0; z < g1.size(); ++z) g1[z].C = Z + zs[z].off;
   dev_zero(Z, sizeof(double) * std::max<int64_t>(zsize, 1), stream_);
