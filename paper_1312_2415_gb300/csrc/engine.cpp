@@ -1567,9 +1567,9 @@ void Engine::run_matvec(MatvecPlan* p, const double* x, double* y, bool tc) {
 // y_X' = sum_X H_X'X x_X blockwise, x^T H x = sum_X' [x_X'^T H_X'X' x_X' +
 // 2 sum_{X > X'} x_X'^T H_X'X x_X].  The plan below keeps the sources whose input block
 // X is >= the output block X' (those of X > X' with twice the coefficient), drops the W
-// items left without sources, and restricts each phase-1 product to the rows of the x
-// stack that a kept source reads; x^T y' then equals x^T H x up to rounding (y' itself is
-// not H x).
+// items left without sources, and restricts each phase-1 product to the runs of x blocks
+// of the stack that a kept source reads; x^T y' then equals x^T H x up to rounding (y'
+// itself is not H x).
 void Engine::build_rq(MatvecPlan* P) {
   if (P->rqc) return;
   const size_t nw = P->witems.size();
@@ -1579,7 +1579,9 @@ void Engine::build_rq(MatvecPlan* P) {
   std::vector<int64_t> woff(nw + 1, 0);
   for (size_t k = 0; k < nw; ++k) woff[k + 1] = woff[k] + (int64_t)P->witems[k].rows * P->witems[k].cols;
   const size_t nz = P->zg.size();
-  std::vector<int64_t> lo(nz, std::numeric_limits<int64_t>::max()), hi(nz, -1);
+  // rows of the x stack that each phase-1 product must produce: (first row, rows) of the
+  // x blocks its kept sources read
+  std::vector<std::vector<std::pair<int64_t, int64_t>>> need(nz);
   std::vector<CombSrc> cs;
   std::vector<CombDst> cd;
   std::vector<char> keep_w(nw, 0);
@@ -1595,8 +1597,7 @@ void Engine::build_rq(MatvecPlan* P) {
       if (src.zg >= 0) {
         const auto& z = P->zg[src.zg];
         cs.push_back({P->Z + z.off + (int64_t)X.trow * z.n, z.n, c});
-        lo[src.zg] = std::min<int64_t>(lo[src.zg], X.trow);
-        hi[src.zg] = std::max<int64_t>(hi[src.zg], X.trow + X.rows);
+        need[src.zg].push_back({X.trow, X.rows});
       } else {
         const int sec = -1 - src.zg;  // identity right operator: x rows of the sector
         cs.push_back({P->xin + P->tall_off[sec] + (int64_t)X.trow * P->sec_dim[sec], P->sec_dim[sec], c});
@@ -1610,12 +1611,26 @@ void Engine::build_rq(MatvecPlan* P) {
   std::vector<GemmGroup> g1;
   double f1 = 0.0, f2 = 0.0;
   for (size_t z = 0; z < nz; ++z) {
-    if (hi[z] < 0) continue;
+    auto& v = need[z];
+    if (v.empty()) continue;
+    std::sort(v.begin(), v.end());
+    v.erase(std::unique(v.begin(), v.end()), v.end());
     const auto& Zg = P->zg[z];
-    const int64_t r0 = lo[z], rows = hi[z] - lo[z];
-    t1.push_back({P->xin + P->tall_off[Zg.c] + r0 * Zg.K, Zg.D, Zg.K, Zg.K, Zg.K, 0, 1, Zg.alpha});
-    g1.push_back({P->Z + Zg.off + r0 * Zg.n, Zg.n, (int)rows, Zg.n, (int)t1.size() - 1, (int)t1.size(), 0});
-    f1 += 2.0 * rows * Zg.K * Zg.n;
+    // one product per run of consecutive needed x blocks
+    for (size_t a = 0; a < v.size();) {
+      const int64_t r0 = v[a].first;
+      int64_t r1 = v[a].first + v[a].second;
+      size_t b = a + 1;
+      while (b < v.size() && v[b].first <= r1) {
+        r1 = std::max(r1, v[b].first + v[b].second);
+        ++b;
+      }
+      const int64_t rows = r1 - r0;
+      t1.push_back({P->xin + P->tall_off[Zg.c] + r0 * Zg.K, Zg.D, Zg.K, Zg.K, Zg.K, 0, 1, Zg.alpha});
+      g1.push_back({P->Z + Zg.off + r0 * Zg.n, Zg.n, (int)rows, Zg.n, (int)t1.size() - 1, (int)t1.size(), 0});
+      f1 += 2.0 * rows * Zg.K * Zg.n;
+      a = b;
+    }
   }
   std::vector<GemmTask> t2;
   std::vector<GemmGroup> g2;
