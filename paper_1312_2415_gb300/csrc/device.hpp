@@ -228,6 +228,9 @@ struct TfTile {         // one output tile of y, computed by one CTA from all of
   int kdg;              // x row groups of the tile's largest term (sizes its product-1 slots)
   int inst;             // instance of a batch (0 for a single matvec)
   int64_t group;        // right sector of the output block (tiles of a group share operator blocks)
+  int tiny;             // 1: at most 4 x 4 outputs, terms of at most 4 x rows, sources of one K chunk
+                        // (computed on CUDA cores, one term per lane)
+  int pad;
 };
 // one FP64 block (rows x cols, row-major) to tiled hi / lo (nrg = ceil(rows / 8) row
 // groups per chunk; lo = hi + lo floats); identity != 0: the rows x rows identity

@@ -1432,7 +1432,8 @@ void Engine::tc_tables(MatvecPlan* P, TcTune tune) {
       for (int row0 = 0; row0 < X.rows; row0 += RT)
         for (int col0 = 0; col0 < X.cols; col0 += 128) {
           TfTile T{P->yout + X.off + (int64_t)row0 * X.cols + col0, X.cols, std::min(RT, X.rows - row0),
-                   std::min(128, X.cols - col0), (int)tk, 0, P->tc_ops_lo, P->tc_x_lo, 0, 1, 0, X.r};
+                   std::min(128, X.cols - col0), (int)tk, 0, P->tc_ops_lo, P->tc_x_lo, 0, 1, 0, X.r, 0, 0};
+          int kdl_max = 0, nkc_max = 0;
           for (int wi : P->w_by_x[x]) {
             const auto& w = P->witems[wi];
             const CombOp& C = P->cl[w.gl];
@@ -1452,14 +1453,17 @@ void Engine::tc_tables(MatvecPlan* P, TcTune tune) {
                              nrg(Xs.rows) * 256, nkc, Xs.cols - 32 * (nkc - 1),
                              (float)(src.craw * P->cr[src.gr].scalar * C.scalar)};
                 T.cost += nkc + (nkc + 1) / 2;
+                nkc_max = std::max(nkc_max, nkc);
               }
               q.s_end = (int)sr;
               H.t[tk++] = q;
               T.cost += 2;
               T.kdg = std::max(T.kdg, (q.kdl + 7) / 8);
+              kdl_max = std::max(kdl_max, q.kdl);
             }
           }
           T.t_end = (int)tk;
+          T.tiny = T.m <= 4 && T.nv <= 4 && kdl_max <= 4 && nkc_max <= 1;
           H.tiles[ti++] = T;
         }
     }

@@ -650,6 +650,77 @@ __global__ void __launch_bounds__(kMvThreads, 1)
   if (warp == kMma1Warp) tmem_free(tmem, kTmemCols);
 }
 
+// ------------------------------------------------------------------ tiny tiles
+
+// element (row, col) of a tiled hi / lo operand (chunk 0, col < 32) as hi + lo in FP64
+__device__ __forceinline__ double tiled_val(const float* __restrict__ p, int64_t lo, int row, int col) {
+  const int64_t e = (int64_t)kmo(row, col);
+  return (double)p[e] + (double)p[e + lo];
+}
+
+// Output tiles of at most 4 x 4 elements whose terms have at most 4 x rows and whose
+// sources are one K chunk (tile.tiny): the same sum y += C (sum_s coef_s x_s D_s^T) on
+// CUDA cores in FP64 from the FP32 operand tiles, one warp per tile and one term per lane
+// (tensor-core products would be nearly all padding and the pipeline's per-term handoffs
+// would dominate).  The lanes' partial sums are reduced in a fixed order and written
+// once: deterministic, no atomics.
+__global__ void __launch_bounds__(256) k_tc_tiny(const TfTile* __restrict__ tiles, const TfTask* __restrict__ tasks,
+                                                 const TfSrc* __restrict__ srcs, const int* __restrict__ active,
+                                                 int n) {
+  const int w = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (w >= n) return;
+  const TfTile tile = tiles[w];
+  if (!active[tile.inst]) return;
+  double y[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) y[i][j] = 0.0;
+  for (int t = tile.t_begin + lane; t < tile.t_end; t += 32) {
+    const TfTask tk = tasks[t];
+    double W[4][4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) W[k][j] = 0.0;
+    for (int si = tk.s_begin; si < tk.s_end; ++si) {
+      const TfSrc S = srcs[si];
+      const double coef = (double)S.coef;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (k >= tk.kdl) break;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          if (j >= tile.nv) break;
+          double acc = 0.0;
+          for (int r = 0; r < S.klast; ++r) acc += tiled_val(S.x, tile.xlo, k, r) * tiled_val(S.d, tile.dlo, j, r);
+          W[k][j] += coef * acc;
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (i >= tile.m) break;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (k >= tk.kdl) break;
+        const double c = tiled_val(tk.c, tile.dlo, i, k);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) y[i][j] += c * W[k][j];
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      double v = y[i][j];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0 && i < tile.m && j < tile.nv) tile.y[(int64_t)i * tile.ldy + j] = v;
+    }
+}
+
 // ------------------------------------------------------------------ conversions
 
 // FP64 blocks -> tiled hi / lo (one CTA per block); identity blocks write their diagonal
@@ -696,6 +767,8 @@ struct TcPlan {
   TfTask* tasks = nullptr;
   TfSrc* srcs = nullptr;
   TfConv* xb = nullptr;
+  TfTile* tiny = nullptr;      // tiles for k_tc_tiny
+  int ntiny = 0;
   int* queue = nullptr;        // the persistent kernel's tile counter
   int* active = nullptr;       // per instance: 0 = skip its tiles
   int ninst = 0;
@@ -761,8 +834,11 @@ TcPlan* tc_plan_build(const std::vector<const TcHost*>& inst, Stream st) {
       if (A.group != B.group) return A.group < B.group;
       return A.cost > B.cost;
     });
-    std::vector<TfTile> sorted(tiles0.size());
-    for (size_t i = 0; i < order.size(); ++i) sorted[i] = tiles0[order[i]];
+    std::vector<TfTile> sorted, tiny;
+    sorted.reserve(tiles0.size());
+    for (size_t i = 0; i < order.size(); ++i) (tiles0[order[i]].tiny ? tiny : sorted).push_back(tiles0[order[i]]);
+    P->tiny = upload(tiny, st);
+    P->ntiny = (int)tiny.size();
     P->grid = (int)std::min<size_t>(sorted.size(), (size_t)sm_count());
     P->queue = (int*)dev_alloc(sizeof(int), st);
     P->ninst = (int)inst.size();
@@ -773,7 +849,7 @@ TcPlan* tc_plan_build(const std::vector<const TcHost*>& inst, Stream st) {
     P->xb = upload(single ? inst[0]->xb : xb, st);
     P->ntiles = (int)sorted.size();
     P->nxb = (int)(single ? inst[0]->xb.size() : xb.size());
-    P->launches = (P->nxb > 0) + (P->ntiles > 0);
+    P->launches = (P->nxb > 0) + (P->ntiles > 0) + (P->ntiny > 0);
   } catch (...) {
     tc_plan_free(P, st);
     throw;
@@ -790,6 +866,7 @@ void tc_plan_free(TcPlan* p, Stream s) {
   dev_free(p->srcs, s);
   dev_free(p->xb, s);
   dev_free(p->queue, s);
+  dev_free(p->tiny, s);
   dev_free(p->active, s);
   delete p;
 }
@@ -808,6 +885,8 @@ void tc_enqueue(const TcPlan* p, void* const* ev, cudaStream_t cs) {
   if (ev) event_record(ev[0], cs);
   if (p->nxb > 0) k_tiled_convert<<<p->nxb, 256, 0, cs>>>(p->xb);
   if (ev) event_record(ev[1], cs);
+  if (p->ntiny > 0)
+    k_tc_tiny<<<(p->ntiny + 7) / 8, 256, 0, cs>>>(p->tiny, p->tasks, p->srcs, p->active, p->ntiny);
   if (p->ntiles > 0) {
     ck(cudaMemsetAsync(p->queue, 0, sizeof(int), cs), "tile queue reset");
     k_tc_matvec<<<p->grid, kMvThreads, smem_bytes(), cs>>>(p->tiles, p->tasks, p->srcs, p->queue, p->active,

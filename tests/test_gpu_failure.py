@@ -14,7 +14,7 @@ import pytest
 from oracle import dmrg as odmrg
 from oracle import mps as om
 from tests.mps_io import lib_x_to_oracle, mps_to_bytes
-from workloads import random_integrals, round_robin_irreps, uniform_pm1
+from workloads import hubbard_chain, random_integrals, round_robin_irreps, uniform_pm1
 
 pytestmark = pytest.mark.gpu
 
@@ -99,12 +99,14 @@ def test_tensor_core_wait_timeout_is_reported_and_recovered(lib):
     returns; the call reports DMRG_ECUDA.  With the hook off the next matvec gives the
     right product (tensor memory and the context are usable)."""
     torch, pkg = lib
-    L, N, i = 8, 8, 3
-    irr = round_robin_irreps(L)
-    h, V = random_integrals(irr, 5)
+    # blocks large enough for the fused kernel (output tiles of at most 4 x 4 go to the
+    # CUDA-core path, which has no waits): a Hubbard chain (C1, few and large sectors)
+    L, N, i = 12, 12, 5
+    irr = [0] * L
+    h, V = hubbard_chain(L, 1.0, 4.0)
     ctx = pkg.Context(L, irr, N, 0, 0, precision=1)
     ctx.set_integrals(h, V)
-    ctx.set_schedule([60], [0.0], [1], [0.0], 1e-10, 20)
+    ctx.set_schedule([400], [0.0], [1], [0.0], 1e-10, 20)
     ctx.init_mps(7)
     ctx.canonicalize(i)
     n, _ = ctx.layout(i)
