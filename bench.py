@@ -335,15 +335,20 @@ def matvec_kernel_rates(delta):
 #       --nvtx-include "steps/" -k regex:k_tc_matvec -c 48 --csv
 #       python bench.py --no-fp64 --no-e2e --no-cpu-baseline --no-batch
 NCU_TRAFFIC = {
-    (("random28", 2500), "d33efb9b2744a877"): {
+    (("random28", 2500), "f73a6011045fa39d"): {
         "bytes": 4.06e10, "how": "mean over the 48 launches of the timed steps (3.39e10 .. 4.55e10), ncu one pass"},
 }
 
 
 def kernel_source_hash():
+    """Hash of the fused kernel's code (comments and blank space left out, so that a
+    comment change keeps a measured figure valid)."""
     import hashlib
+    import re
     path = os.path.join(ROOT, "paper_1312_2415_gb300", "csrc", "kernels_tc.cu")
-    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+    code = re.sub(r"//[^\n]*", "", open(path).read())
+    code = re.sub(r"\s+", " ", code)
+    return hashlib.sha256(code.encode()).hexdigest()[:16]
 
 
 def roofline_mixed(delta, peaks, peak_tf32, workload=None):

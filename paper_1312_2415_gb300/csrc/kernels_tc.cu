@@ -7,8 +7,9 @@
 // blocks (the combined operators of the left / right environments).  One CTA owns each
 // output tile (up to 128 rows x 128 columns of one block, so nothing is added with
 // atomics and the summation order is fixed) and runs all of its terms; the launch is
-// persistent (one CTA per SM, each running the list of tiles the host balanced over the
-// CTAs by cost), so the pipeline runs on from one tile into the next:
+// persistent (one CTA per SM taking tiles from a work queue), so the pipeline runs on
+// from one tile into the next (tiles of at most 4 x 4 outputs go to a CUDA-core kernel,
+// k_tc_tiny, instead):
 //   product 1: W^T = D_s x_s^T per source, into tensor-memory accumulators of at most
 //              two 32-column K chunks each (M = 128 output columns, N = x rows of the
 //              term, K = the right sector);
