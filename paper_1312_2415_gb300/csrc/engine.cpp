@@ -638,6 +638,10 @@ void Engine::update_left_from(int i, std::vector<CombOp>& comb) {
   int64_t zsize = 0;
   struct ZRef { int64_t off; int rows, cols; };
   std::vector<ZRef> zs;
+  t1.reserve(upd_hint_z_ + upd_hint_z_ / 4);
+  g1.reserve(upd_hint_z_ + upd_hint_z_ / 4);
+  zs.reserve(upd_hint_z_ + upd_hint_z_ / 4);
+  out2.reserve(upd_hint_out_ + upd_hint_out_ / 4);
   for (auto& c : comb) {
     if (c.target == id_op) continue;
     for (const BlockRef& cb : *c.blocks) {
@@ -665,6 +669,8 @@ void Engine::update_left_from(int i, std::vector<CombOp>& comb) {
       }
     }
   }
+  upd_hint_z_ = t1.size();
+  upd_hint_out_ = out2.size();
   double* Z = (double*)dev_alloc(sizeof(double) * std::max<int64_t>(zsize, 1), stream_);
   for (size_t z = 0; z < g1.size(); ++z) g1[z].C = Z + zs[z].off;
   dev_zero(Z, sizeof(double) * std::max<int64_t>(zsize, 1), stream_);
@@ -716,6 +722,10 @@ void Engine::update_right_from(int j, std::vector<CombOp>& comb) {
   int64_t zsize = 0;
   struct ZRef { int64_t off; int rows, cols; };
   std::vector<ZRef> zs;
+  t1.reserve(upd_hint_z_ + upd_hint_z_ / 4);
+  g1.reserve(upd_hint_z_ + upd_hint_z_ / 4);
+  zs.reserve(upd_hint_z_ + upd_hint_z_ / 4);
+  out2.reserve(upd_hint_out_ + upd_hint_out_ / 4);
   for (auto& c : comb) {
     if (c.target == h_op) continue;
     for (const BlockRef& db : *c.blocks) {
@@ -744,6 +754,8 @@ void Engine::update_right_from(int j, std::vector<CombOp>& comb) {
       }
     }
   }
+  upd_hint_z_ = t1.size();
+  upd_hint_out_ = out2.size();
   double* Z = (double*)dev_alloc(sizeof(double) * std::max<int64_t>(zsize, 1), stream_);
   for (size_t z = 0; z < g1.size(); ++z) g1[z].C = Z + zs[z].off;
   dev_zero(Z, sizeof(double) * std::max<int64_t>(zsize, 1), stream_);
@@ -869,7 +881,7 @@ void allowed(const Pattern& P, bool ok[3][3]) {
 }
 }  // namespace
 
-Engine::MatvecPlan* Engine::plan_matvec(int i) {
+Engine::MatvecPlan* Engine::plan_matvec(int i, bool rdm) {
   Timer tm;
   ensure_left(i);
   ensure_right(i + 2);
@@ -1060,7 +1072,7 @@ Engine::MatvecPlan* Engine::plan_matvec(int i) {
                     bucket[sl].clear();
                   }
                   bucket[sl].push_back({gr, dbi, x, coef});
-                  if (xp == x && cb.r == cb.c && db.r == db.c) o.d.push_back({x, gr, dbi, coef});
+                  if (!rdm && xp == x && cb.r == cb.c && db.r == db.c) o.d.push_back({x, gr, dbi, coef});
                 }
               }
             }
@@ -1114,6 +1126,7 @@ Engine::MatvecPlan* Engine::plan_matvec(int i) {
     it_s[it + 1] = it_s[it] + (int64_t)o.s.size();
     it_off[it + 1] = it_off[it] + wb;
     const CombOp& C = P->cl[items[it].gl];
+    if (rdm) continue;
     for (const DRaw& dr : o.d) {
       const CombOp& D = P->cr[dr.gr];
       const BlockRef& db = (*D.blocks)[dr.dbi];
@@ -1140,7 +1153,9 @@ Engine::MatvecPlan* Engine::plan_matvec(int i) {
   std::vector<CombSrc> cs(it_s[nit]);
   std::vector<CombDst> cd(it_w[nit]);
   ws.resize(it_w[nit]);
-  P->wsrc.resize(it_s[nit]);
+  // the RDM pass reads the sources' table only at the last pair
+  const bool keep_src = !rdm || i == L_ - 2;
+  if (keep_src) P->wsrc.resize(it_s[nit]);
   P->witems.resize(it_w[nit]);
   std::vector<double> it_flops(nit, 0.0);
   {
@@ -1163,7 +1178,7 @@ Engine::MatvecPlan* Engine::plan_matvec(int i) {
               // identity right operator: Z is x itself, its alias scalar goes here
               const double coef = D.identity ? q.coef * D.scalar : q.coef;
               cs[si] = {zoff >= 0 ? P->Z + zoff : P->xin + (-1 - zoff), z.ld, coef};
-              P->wsrc[si] = {z.zg, q.x, coef, q.gr, q.coef};
+              if (keep_src) P->wsrc[si] = {z.zg, q.x, coef, q.gr, q.coef};
             }
             w.src_end = (int)si;
             P->witems[wi] = {I.gl, I.cbi, w.rows, w.cols, w.src_begin, w.src_end};
@@ -1187,14 +1202,15 @@ Engine::MatvecPlan* Engine::plan_matvec(int i) {
     for (int k = 0; k < (int)ws.size(); ++k) w_by_x[ws[k].xp].push_back(k);
   }
   // phase 2 grouped by output block: the tasks of block x at the prefix of |w_by_x|
+  // (none for the RDM pass)
   std::vector<int64_t> xt(P->X.size() + 1, 0), xg(P->X.size() + 1, 0);
-  for (size_t x = 0; x < P->X.size(); ++x) {
+  for (size_t x = 0; x < P->X.size() && !rdm; ++x) {
     xt[x + 1] = xt[x] + (int64_t)w_by_x[x].size();
     xg[x + 1] = xg[x] + (w_by_x[x].empty() ? 0 : 1);
   }
   std::vector<GemmTask> t2(xt[P->X.size()]);
   std::vector<GemmGroup> g2(xg[P->X.size()]);
-  parallel_chunks(P->X.size(), 256, [&](size_t xb, size_t xe) {
+  if (!rdm) parallel_chunks(P->X.size(), 256, [&](size_t xb, size_t xe) {
     for (size_t x = xb; x < xe; ++x) {
       if (w_by_x[x].empty()) continue;
       const XBlock& X = P->X[x];
@@ -1209,17 +1225,19 @@ Engine::MatvecPlan* Engine::plan_matvec(int i) {
       g2[xg[x]] = {P->yout + X.off, X.cols, X.rows, X.cols, (int)xt[x], (int)xt[x + 1], 0};
     }
   });
-  // diagonal
+  // diagonal (not for the RDM pass)
   std::vector<DiagTerm> dt;
   std::vector<DiagOut> dov;
-  P->diag = (double*)dev_alloc(sizeof(double) * std::max<int64_t>(P->n, 1), stream_);
-  dev_zero(P->diag, sizeof(double) * std::max<int64_t>(P->n, 1), stream_);
-  for (int x = 0; x < (int)P->X.size(); ++x) {
-    if (dout[x].empty()) continue;
-    const XBlock& X = P->X[x];
-    int d0 = (int)dt.size();
-    dt.insert(dt.end(), dout[x].begin(), dout[x].end());
-    dov.push_back({P->diag + X.off, X.rows, X.cols, d0, (int)dt.size()});
+  if (!rdm) {
+    P->diag = (double*)dev_alloc(sizeof(double) * std::max<int64_t>(P->n, 1), stream_);
+    dev_zero(P->diag, sizeof(double) * std::max<int64_t>(P->n, 1), stream_);
+    for (int x = 0; x < (int)P->X.size(); ++x) {
+      if (dout[x].empty()) continue;
+      const XBlock& X = P->X[x];
+      int d0 = (int)dt.size();
+      dt.insert(dt.end(), dout[x].begin(), dout[x].end());
+      dov.push_back({P->diag + X.off, X.rows, X.cols, d0, (int)dt.size()});
+    }
   }
   P->w_by_x = std::move(w_by_x);
   P->tall_off = std::move(tall_off);
@@ -1227,11 +1245,13 @@ Engine::MatvecPlan* Engine::plan_matvec(int i) {
   P->sec_dim = br.dim;
   P->p1 = gemm_plan_upload(t1, g1, stream_);
   P->pc = comb_plan_upload(cs, cd, stream_);
-  P->p2 = gemm_plan_upload(t2, g2, stream_);
-  DiagPlan* pd = diag_plan_upload(dt, dov, stream_);
-  diag_plan_run(pd, stream_);
-  diag_plan_free(pd, stream_);
-  if (!low_.empty()) {
+  if (!rdm) {
+    P->p2 = gemm_plan_upload(t2, g2, stream_);
+    DiagPlan* pd = diag_plan_upload(dt, dov, stream_);
+    diag_plan_run(pd, stream_);
+    diag_plan_free(pd, stream_);
+  }
+  if (!low_.empty() && !rdm) {
     // the lower states' projections onto this pair's basis: + eta |v><v| in every matvec
     const int m = (int)low_.size();
     P->nlow = m;
@@ -1748,6 +1768,9 @@ void Engine::tt_to_x_of(const std::vector<Bond>& bonds, const std::vector<Site>&
   std::map<std::tuple<int, int, int>, int> ia, ib;  // (ls, l, r) -> block
   for (int t = 0; t < (int)A.blocks.size(); ++t) ia[{A.blocks[t].ls, A.blocks[t].l, A.blocks[t].r}] = t;
   for (int t = 0; t < (int)B.blocks.size(); ++t) ib[{B.blocks[t].ls, B.blocks[t].l, B.blocks[t].r}] = t;
+  // the blocks of A by (ls, l), middle sectors m in increasing order: (m, block)
+  std::map<std::pair<int, int>, std::vector<std::pair<int, int>>> a_by;
+  for (const auto& kv : ia) a_by[{std::get<0>(kv.first), std::get<1>(kv.first)}].push_back({std::get<2>(kv.first), kv.second});
   std::vector<GemmTask> tasks;
   std::vector<GemmGroup> groups;
   for (auto& xb : X) {
@@ -1755,15 +1778,17 @@ void Engine::tt_to_x_of(const std::vector<Bond>& bonds, const std::vector<Site>&
     const int t1 = local_ts(xb.ls1), t2 = local_ts(xb.ls2);
     const int ph = (((tjL + tjR + t1 + t2) / 2) & 1) ? -1 : 1;
     int b0 = (int)tasks.size();
-    for (int m = 0; m < (int)bm.sec.size(); ++m) {
-      auto a = ia.find({xb.ls1, xb.l, m});
+    auto la = a_by.find({xb.ls1, xb.l});
+    const size_t na = la == a_by.end() ? 0 : la->second.size();
+    for (size_t q = 0; q < na; ++q) {
+      const int m = la->second[q].first;
       auto b = ib.find({xb.ls2, m, xb.r});
-      if (a == ia.end() || b == ib.end()) continue;
+      if (b == ib.end()) continue;
       const int tjM = bm.sec[m].tj;
       double c = std::sqrt((double)(tjR + 1)) * std::sqrt((double)(xb.tj + 1)) * ph *
                  std::sqrt((double)(tjM + 1)) * wigner6j(tjL, tjR, xb.tj, t2, t1, tjM);
       if (c == 0.0) continue;
-      const SiteBlock& sa = A.blocks[a->second];
+      const SiteBlock& sa = A.blocks[la->second[q].second];
       const SiteBlock& sb = B.blocks[b->second];
       tasks.push_back({A.data + sa.off, B.data + sb.off, sa.cols, sb.cols, sa.cols, 0, 0, c});
     }
@@ -2483,7 +2508,7 @@ void Engine::rdm(double* gamma, double* Gamma) {
   dev_zero(dg, sizeof(double) * L4, stream_);
   try {
     for (int i = 0; i <= L_ - 2; ++i) {
-      MatvecPlan* P = plan_matvec(i);
+      MatvecPlan* P = plan_matvec(i, true);
       try {
         tt_to_x(i, P->xin);
         // x is scaled to unit norm on the device (a zero norm is reported after the
@@ -2548,21 +2573,40 @@ void Engine::rdm_site(MatvecPlan* P, int i, double* dg, bool last) {
     for (int x = 0; x < (int)P->w_by_x.size(); ++x)
       for (int k : P->w_by_x[x]) wxp[k] = x;
   }
-  // Gbar(gl, cbi) = sum over its W items of x_out W^T / |x|^2
-  std::map<std::pair<int, int>, std::vector<int>> by_blk;
-  for (size_t k = 0; k < nw; ++k) by_blk[{P->witems[k].gl, P->witems[k].cbi}].push_back((int)k);
+  // Gbar(gl, cbi) = sum over its W items of x_out W^T / |x|^2.  The W items of one
+  // (left group, block) pair come in runs of consecutive items; the runs, stably sorted
+  // by (gl, cbi), give every pair's items in increasing order, pair by pair.
+  struct Run { int gl, cbi, b, e; };
+  std::vector<Run> runs;
+  for (size_t k = 0; k < nw; ++k) {
+    const auto& w = P->witems[k];
+    if (!runs.empty() && runs.back().gl == w.gl && runs.back().cbi == w.cbi) runs.back().e = (int)k + 1;
+    else runs.push_back({w.gl, w.cbi, (int)k, (int)k + 1});
+  }
+  std::stable_sort(runs.begin(), runs.end(),
+                   [](const Run& a, const Run& b) { return a.gl != b.gl ? a.gl < b.gl : a.cbi < b.cbi; });
+  std::vector<std::pair<int, int>> by_blk;  // (gl, cbi) of each pair, in order
+  std::vector<int> blk_run;                 // the pair's first run (prefix, one past the last pair)
+  for (size_t r = 0; r < runs.size(); ++r)
+    if (r == 0 || runs[r].gl != runs[r - 1].gl || runs[r].cbi != runs[r - 1].cbi) {
+      by_blk.push_back({runs[r].gl, runs[r].cbi});
+      blk_run.push_back((int)r);
+    }
+  blk_run.push_back((int)runs.size());
   std::vector<GemmTask> gt;
   std::vector<GemmGroup> gg;
   std::vector<int64_t> goff;
   int64_t gsize = 0;
-  for (auto& kv : by_blk) {
-    const CombOp& C = P->cl[kv.first.first];
-    const BlockRef& cb = (*C.blocks)[kv.first.second];
+  gt.reserve(nw);
+  for (size_t q = 0; q < by_blk.size(); ++q) {
+    const CombOp& C = P->cl[by_blk[q].first];
+    const BlockRef& cb = (*C.blocks)[by_blk[q].second];
     const int b0 = (int)gt.size();
-    for (int k : kv.second) {
-      const XBlock& Xp = P->X[wxp[k]];
-      gt.push_back({P->xin + Xp.off, P->W + woff[k], Xp.cols, Xp.cols, Xp.cols, 0, 1, 1.0 / n2});
-    }
+    for (int r = blk_run[q]; r < blk_run[q + 1]; ++r)
+      for (int k = runs[r].b; k < runs[r].e; ++k) {
+        const XBlock& Xp = P->X[wxp[k]];
+        gt.push_back({P->xin + Xp.off, P->W + woff[k], Xp.cols, Xp.cols, Xp.cols, 0, 1, 1.0 / n2});
+      }
     goff.push_back(gsize);
     gg.push_back({nullptr, cb.cols, cb.rows, cb.cols, b0, (int)gt.size(), 0});
     gsize += (int64_t)cb.rows * cb.cols;
@@ -2582,11 +2626,10 @@ void Engine::rdm_site(MatvecPlan* P, int i, double* dg, bool last) {
   std::map<int64_t, std::vector<DotTask>> dots;
   const OpStore& E = lenv_[i];
   {
-    size_t q = 0;
-    for (auto& kv : by_blk) {
-      const CombOp& C = P->cl[kv.first.first];
-      const BlockRef& cb = (*C.blocks)[kv.first.second];
-      const double* gb = Gb + goff[q++];
+    for (size_t q = 0; q < by_blk.size(); ++q) {
+      const CombOp& C = P->cl[by_blk[q].first];
+      const BlockRef& cb = (*C.blocks)[by_blk[q].second];
+      const double* gb = Gb + goff[q];
       for (size_t s = 0; s < C.sources.size(); ++s) {
         const int64_t gi = C.grad[s].first;
         if (gi < 0) continue;

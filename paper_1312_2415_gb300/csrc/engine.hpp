@@ -207,7 +207,9 @@ class Engine {
   void group_right(int i, std::vector<CombOp>& out, double** scratch, int64_t* scratch_n);
   void build_tc(MatvecPlan* p);
   void tc_tables(MatvecPlan* p, TcTune tune);
-  MatvecPlan* plan_matvec(int i);
+  // rdm: only the tables the RDM pass reads (phase 1, the combine into W and the W items;
+  // the sources' table at the last pair); no phase 2, no diagonal, no lower-state terms
+  MatvecPlan* plan_matvec(int i, bool rdm = false);
   void free_plan(MatvecPlan* p);
   void release_tc(MatvecPlan* p);  // frees the tensor-core tables of a plan
   void build_rq(MatvecPlan* p);    // tables of the symmetric quadratic form (energy)
@@ -249,6 +251,9 @@ class Engine {
   std::vector<Site> sites_;
   std::vector<OpStore> lenv_, renv_;
   uint64_t env_serial_ = 0;
+  // table sizes of the last operator update (block products, and their outputs): the next
+  // update reserves that much, since neighbouring bonds have tables of similar size
+  size_t upd_hint_z_ = 0, upd_hint_out_ = 0;
   std::vector<LowState> low_;
   std::vector<int> sched_D_, sched_nmax_;
   std::vector<double> sched_econv_, sched_noise_;
