@@ -26,31 +26,22 @@ namespace {
 inline int64_t bkey(int r, int c) { return ((int64_t)r << 32) | (uint32_t)c; }
 
 // Tasks tagged with an output index, grouped per output in increasing index order
-// (stable: a group's tasks keep their order).  The tasks come in segments, taken in
-// order; a task's B holds a Z id relative to its segment's zbase, and zoff[id] gives the
-// Z offset of that product.
+// (stable: a group's tasks keep their order); zs[id] gives the Z offset of a task whose
+// B holds a Z id.
 struct TaggedTask { int64_t out; GemmTask t; };
-struct TaggedSeg { const TaggedTask* p; size_t n; intptr_t zbase; };
-void group_by_output(const std::vector<TaggedSeg>& segs, int64_t nout, double* Z, const std::vector<int64_t>& zoff,
+void group_by_output(std::vector<TaggedTask>& tagged, int64_t nout, double* Z, const std::vector<int64_t>& zoff,
                      const std::function<void(int64_t, int, int, std::vector<GemmGroup>&)>& make_group,
                      std::vector<GemmTask>& t2, std::vector<GemmGroup>& g2) {
   std::vector<int> cnt(nout + 1, 0);
-  size_t ntag = 0;
-  for (const TaggedSeg& sg : segs) {
-    for (size_t k = 0; k < sg.n; ++k) ++cnt[sg.p[k].out + 1];
-    ntag += sg.n;
-  }
-  if (ntag > (size_t)std::numeric_limits<int>::max()) throw std::runtime_error("operator update tables exceed 2^31 tasks");
+  for (const auto& q : tagged) ++cnt[q.out + 1];
   for (int64_t o = 0; o < nout; ++o) cnt[o + 1] += cnt[o];
-  t2.resize(ntag);
+  t2.resize(tagged.size());
   std::vector<int> pos(cnt.begin(), cnt.end() - 1);
-  for (const TaggedSeg& sg : segs)
-    for (size_t k = 0; k < sg.n; ++k) {
-      const TaggedTask& q = sg.p[k];
-      GemmTask t = q.t;
-      t.B = Z + zoff[(size_t)((intptr_t)t.B + sg.zbase)];
-      t2[pos[q.out]++] = t;
-    }
+  for (const auto& q : tagged) {
+    GemmTask t = q.t;
+    t.B = Z + zoff[(size_t)(intptr_t)t.B];
+    t2[pos[q.out]++] = t;
+  }
   for (int64_t o = 0; o < nout; ++o)
     if (cnt[o + 1] > cnt[o]) make_group(o, cnt[o], cnt[o + 1], g2);
 }
@@ -82,117 +73,6 @@ void parallel_chunks(size_t n, size_t chunk, F f) {
   run();
   for (auto& t : th) t.join();
   if (err) std::rethrow_exception(err);
-}
-
-// The tables of an operator update in parts: each part holds the block products
-// Z = (operator block) x (site block) it creates, in order (one task each; zs: offset in
-// the part's Z, rows, cols), and the output tasks tagged with their output block, whose
-// B holds the part's Z id.
-struct UpdZ { int64_t off; int rows, cols; };
-struct UpdPart {
-  std::vector<GemmTask> t1;
-  std::vector<UpdZ> zs;
-  int64_t zsize = 0;
-  std::vector<TaggedTask> out2;
-};
-struct UpdTables {
-  std::vector<GemmTask> t1;   // one task per block product
-  std::vector<GemmGroup> g1;  // one group per block product (C set by the caller)
-  std::vector<int64_t> zoff;  // offset of each block product in Z
-  int64_t zsize = 0;
-  std::vector<UpdPart> parts;  // the parts' output tasks (their other tables released)
-  std::vector<TaggedSeg> out2;  // the output tasks, part by part
-};
-
-// Builds an operator update's tables over the combined operators ops (in order) on up to
-// 16 threads (the caller's included).  The operators are cut into contiguous parts of
-// about equal work (wo[k]: the site-block pairs operator ops[k] visits, a bound on its
-// output tasks; wz[k]: its site blocks, a bound on its products); body(cp, op, part)
-// appends one operator's tables to a part, cp being the thread's private copy of the
-// coupling memo.  The parts' products are joined in order and their output tasks kept as
-// segments in order, so that the tables equal those of one serial pass over ops.
-template <class F>
-void build_update_tables(const std::vector<int>& ops, const std::vector<int64_t>& wz, const std::vector<int64_t>& wo,
-                         const Coupling& cp0, F body, UpdTables& out) {
-  const unsigned hc = std::thread::hardware_concurrency();
-  const int nth = (int)std::max(1u, std::min(16u, hc ? hc : 1u));
-  int64_t total = 0;
-  for (int64_t w : wo) total += w;
-  const int nparts = (int)std::max<size_t>(1, std::min<size_t>(ops.size(), (size_t)4 * nth));
-  std::vector<size_t> pb(nparts + 1, ops.size());
-  pb[0] = 0;
-  {
-    int64_t acc = 0;
-    int q = 1;
-    for (size_t k = 0; k < ops.size() && q < nparts; ++k) {
-      acc += wo[k];
-      while (q < nparts && acc * nparts >= total * q) pb[q++] = k + 1;
-    }
-  }
-  std::vector<UpdPart>& parts = out.parts;
-  parts.assign(nparts, UpdPart());
-  std::atomic<int> next{0};
-  std::mutex mu;
-  std::exception_ptr err;
-  auto run = [&]() {
-    try {
-      Coupling cp = cp0;
-      for (;;) {
-        const int q = next.fetch_add(1);
-        if (q >= nparts) break;
-        UpdPart& U = parts[q];
-        int64_t bz = 0, bo = 0;
-        for (size_t k = pb[q]; k < pb[q + 1]; ++k) {
-          bz += wz[k];
-          bo += wo[k];
-        }
-        U.t1.reserve(bz);
-        U.zs.reserve(bz);
-        U.out2.reserve(bo);
-        for (size_t k = pb[q]; k < pb[q + 1]; ++k) body(cp, ops[k], U);
-      }
-    } catch (...) {
-      std::lock_guard<std::mutex> lk(mu);
-      if (!err) err = std::current_exception();
-      next.store(nparts);
-    }
-  };
-  {
-    std::vector<std::thread> th;
-    for (int t = 1; t < std::min(nth, nparts); ++t) th.emplace_back(run);
-    run();
-    for (auto& t : th) t.join();
-  }
-  if (err) std::rethrow_exception(err);
-  // join the products in part order (global product id = zb[part] + the part's id)
-  std::vector<size_t> zb(nparts + 1, 0);
-  std::vector<int64_t> sb(nparts + 1, 0);
-  for (int q = 0; q < nparts; ++q) {
-    zb[q + 1] = zb[q] + parts[q].zs.size();
-    sb[q + 1] = sb[q] + parts[q].zsize;
-  }
-  if (zb[nparts] > (size_t)std::numeric_limits<int>::max() - 1)
-    throw std::runtime_error("operator update tables exceed 2^31 products");
-  out.t1.resize(zb[nparts]);
-  out.g1.resize(zb[nparts]);
-  out.zoff.resize(zb[nparts]);
-  out.zsize = sb[nparts];
-  out.out2.clear();
-  for (int q = 0; q < nparts; ++q) out.out2.push_back({parts[q].out2.data(), parts[q].out2.size(), (intptr_t)zb[q]});
-  parallel_chunks(nparts, 1, [&](size_t b, size_t e) {
-    for (size_t q = b; q < e; ++q) {
-      UpdPart& U = parts[q];
-      for (size_t k = 0; k < U.zs.size(); ++k) {
-        const size_t z = zb[q] + k;
-        const UpdZ& zr = U.zs[k];
-        out.t1[z] = U.t1[k];
-        out.g1[z] = {nullptr, zr.cols, zr.rows, zr.cols, (int)z, (int)z + 1, 0};
-        out.zoff[z] = zr.off + sb[q];
-      }
-      std::vector<GemmTask>().swap(U.t1);
-      std::vector<UpdZ>().swap(U.zs);
-    }
-  });
 }
 
 uint64_t splitmix64_next(uint64_t& state) {
@@ -750,26 +630,20 @@ void Engine::update_left_from(int i, std::vector<CombOp>& comb) {
   std::vector<std::vector<int>> by_l(bl.sec.size());
   for (int t = 0; t < (int)T.blocks.size(); ++t) by_l[T.blocks[t].l].push_back(t);
   const int id_op = opsets_[i + 1].find({OP_I, -1, -1, 0});
-  std::vector<GemmTask> t2;
+  std::vector<GemmTask> t1, t2;
+  std::vector<GemmGroup> g1;
   std::vector<int64_t> bbase(E.blocks.size() + 1, 0);  // first output index of each operator
   for (size_t o = 0; o < E.blocks.size(); ++o) bbase[o + 1] = bbase[o] + (int64_t)E.blocks[o].size();
-  // every combined operator but the identity, with its work bounds
-  std::vector<int> ops;
-  std::vector<int64_t> wz, wo;
-  for (size_t ci = 0; ci < comb.size(); ++ci) {
-    if (comb[ci].target == id_op) continue;
-    int64_t a = 0, b = 0;
-    for (const BlockRef& cb : *comb[ci].blocks) {
-      a += (int64_t)by_l[cb.c].size();
-      b += (int64_t)by_l[cb.c].size() * (int64_t)by_l[cb.r].size();
-    }
-    ops.push_back((int)ci);
-    wz.push_back(a);
-    wo.push_back(b);
-  }
-  UpdTables U;
-  build_update_tables(ops, wz, wo, *cp_, [&](Coupling& cp, int ci, UpdPart& P) {
-    const CombOp& c = comb[ci];
+  std::vector<TaggedTask> out2;
+  int64_t zsize = 0;
+  struct ZRef { int64_t off; int rows, cols; };
+  std::vector<ZRef> zs;
+  t1.reserve(upd_hint_z_ + upd_hint_z_ / 4);
+  g1.reserve(upd_hint_z_ + upd_hint_z_ / 4);
+  zs.reserve(upd_hint_z_ + upd_hint_z_ / 4);
+  out2.reserve(upd_hint_out_ + upd_hint_out_ / 4);
+  for (auto& c : comb) {
+    if (c.target == id_op) continue;
     for (const BlockRef& cb : *c.blocks) {
       for (int t : by_l[cb.c]) {
         const SiteBlock& tb = T.blocks[t];
@@ -777,36 +651,37 @@ void Engine::update_left_from(int i, std::vector<CombOp>& comb) {
         int zid = -1;
         for (int tp : by_l[cb.r]) {
           const SiteBlock& tpb = T.blocks[tp];
-          double coef = c.scalar * cp.left(c.pattern, bl.sec[tb.l].tj, tb.ls, bm.sec[tb.r].tj,
-                                           bl.sec[tpb.l].tj, tpb.ls, bm.sec[tpb.r].tj);
+          double coef = c.scalar * cp_->left(c.pattern, bl.sec[tb.l].tj, tb.ls, bm.sec[tb.r].tj,
+                                              bl.sec[tpb.l].tj, tpb.ls, bm.sec[tpb.r].tj);
           if (coef == 0.0) continue;
           auto it = E.at[c.target].find(bkey(tpb.r, tb.r));
           if (it == E.at[c.target].end()) continue;
           if (zid < 0) {
-            zid = (int)P.zs.size();
-            P.zs.push_back({P.zsize, cb.rows, tb.cols});
-            P.zsize += (int64_t)cb.rows * tb.cols;
-            P.t1.push_back({c.data + cb.off, T.data + tb.off, cb.cols, tb.cols, cb.cols, 0, 0, 1.0});
+            zid = (int)zs.size();
+            zs.push_back({zsize, cb.rows, tb.cols});
+            zsize += (int64_t)cb.rows * tb.cols;
+            t1.push_back({c.data + cb.off, T.data + tb.off, cb.cols, tb.cols, cb.cols, 0, 0, 1.0});
+            g1.push_back({nullptr, tb.cols, cb.rows, tb.cols, (int)t1.size() - 1, (int)t1.size(), 0});
           }
-          P.out2.push_back({bbase[c.target] + it->second,
-                            {T.data + tpb.off, (const double*)(intptr_t)zid, tpb.cols, tb.cols, tpb.rows, 1, 0, coef}});
+          out2.push_back({bbase[c.target] + it->second,
+                          {T.data + tpb.off, (const double*)(intptr_t)zid, tpb.cols, tb.cols, tpb.rows, 1, 0, coef}});
         }
       }
     }
-  }, U);
-  std::vector<GemmTask>& t1 = U.t1;
-  std::vector<GemmGroup>& g1 = U.g1;
-  const int64_t zsize = U.zsize;
+  }
+  upd_hint_z_ = t1.size();
+  upd_hint_out_ = out2.size();
   double* Z = (double*)dev_alloc(sizeof(double) * std::max<int64_t>(zsize, 1), stream_);
-  for (size_t z = 0; z < g1.size(); ++z) g1[z].C = Z + U.zoff[z];
+  for (size_t z = 0; z < g1.size(); ++z) g1[z].C = Z + zs[z].off;
   dev_zero(Z, sizeof(double) * std::max<int64_t>(zsize, 1), stream_);
   std::vector<GemmGroup> g2;
   {
-    const std::vector<int64_t>& zoff = U.zoff;
+    std::vector<int64_t> zoff(zs.size());
+    for (size_t z = 0; z < zs.size(); ++z) zoff[z] = zs[z].off;
     std::vector<std::pair<int, int>> at(bbase.back());  // output index -> (op, block)
     for (size_t o = 0; o + 1 < bbase.size(); ++o)
       for (int64_t b = bbase[o]; b < bbase[o + 1]; ++b) at[b] = {(int)o, (int)(b - bbase[o])};
-    group_by_output(U.out2, bbase.back(), Z, zoff,
+    group_by_output(out2, bbase.back(), Z, zoff,
                     [&](int64_t id, int b0, int b1, std::vector<GemmGroup>& g) {
                       const BlockRef& ob = E.blocks[at[id].first][at[id].second];
                       g.push_back({E.data + ob.off, ob.cols, ob.rows, ob.cols, b0, b1, 0});
@@ -839,26 +714,20 @@ void Engine::update_right_from(int j, std::vector<CombOp>& comb) {
   auto f = [&](const SiteBlock& b) {
     return std::sqrt((double)(br.sec[b.r].tj + 1) / (double)(bm.sec[b.l].tj + 1));
   };
-  std::vector<GemmTask> t2;
+  std::vector<GemmTask> t1, t2;
+  std::vector<GemmGroup> g1;
   std::vector<int64_t> bbase(E.blocks.size() + 1, 0);  // first output index of each operator
   for (size_t o = 0; o < E.blocks.size(); ++o) bbase[o + 1] = bbase[o] + (int64_t)E.blocks[o].size();
-  // every combined operator but the partner of H, with its work bounds
-  std::vector<int> ops;
-  std::vector<int64_t> wz, wo;
-  for (size_t ci = 0; ci < comb.size(); ++ci) {
-    if (comb[ci].target == h_op) continue;
-    int64_t a = 0, b = 0;
-    for (const BlockRef& db : *comb[ci].blocks) {
-      a += (int64_t)by_r[db.c].size();
-      b += (int64_t)by_r[db.c].size() * (int64_t)by_r[db.r].size();
-    }
-    ops.push_back((int)ci);
-    wz.push_back(a);
-    wo.push_back(b);
-  }
-  UpdTables U;
-  build_update_tables(ops, wz, wo, *cp_, [&](Coupling& cp, int ci, UpdPart& P) {
-    const CombOp& c = comb[ci];
+  std::vector<TaggedTask> out2;
+  int64_t zsize = 0;
+  struct ZRef { int64_t off; int rows, cols; };
+  std::vector<ZRef> zs;
+  t1.reserve(upd_hint_z_ + upd_hint_z_ / 4);
+  g1.reserve(upd_hint_z_ + upd_hint_z_ / 4);
+  zs.reserve(upd_hint_z_ + upd_hint_z_ / 4);
+  out2.reserve(upd_hint_out_ + upd_hint_out_ / 4);
+  for (auto& c : comb) {
+    if (c.target == h_op) continue;
     for (const BlockRef& db : *c.blocks) {
       for (int t : by_r[db.c]) {
         const SiteBlock& tb = T.blocks[t];
@@ -866,37 +735,38 @@ void Engine::update_right_from(int j, std::vector<CombOp>& comb) {
         for (int tp : by_r[db.r]) {
           const SiteBlock& tpb = T.blocks[tp];
           double coef = c.scalar * f(tb) * f(tpb) *
-                        cp.right(c.pattern, tb.ls, br.sec[tb.r].tj, bm.sec[tb.l].tj, tpb.ls,
-                                 br.sec[tpb.r].tj, bm.sec[tpb.l].tj);
+                        cp_->right(c.pattern, tb.ls, br.sec[tb.r].tj, bm.sec[tb.l].tj, tpb.ls,
+                                   br.sec[tpb.r].tj, bm.sec[tpb.l].tj);
           if (coef == 0.0) continue;
           auto it = E.at[c.target].find(bkey(tpb.l, tb.l));
           if (it == E.at[c.target].end()) continue;
           if (zid < 0) {
             // Z1 = D_blk (dR' x dR) . T_t^T (dR x dM)
-            zid = (int)P.zs.size();
-            P.zs.push_back({P.zsize, db.rows, tb.rows});
-            P.zsize += (int64_t)db.rows * tb.rows;
-            P.t1.push_back({c.data + db.off, T.data + tb.off, db.cols, tb.cols, db.cols, 0, 1, 1.0});
+            zid = (int)zs.size();
+            zs.push_back({zsize, db.rows, tb.rows});
+            zsize += (int64_t)db.rows * tb.rows;
+            t1.push_back({c.data + db.off, T.data + tb.off, db.cols, tb.cols, db.cols, 0, 1, 1.0});
+            g1.push_back({nullptr, tb.rows, db.rows, tb.rows, (int)t1.size() - 1, (int)t1.size(), 0});
           }
-          P.out2.push_back({bbase[c.target] + it->second,
-                            {T.data + tpb.off, (const double*)(intptr_t)zid, tpb.cols, tb.rows, tpb.cols, 0, 0, coef}});
+          out2.push_back({bbase[c.target] + it->second,
+                          {T.data + tpb.off, (const double*)(intptr_t)zid, tpb.cols, tb.rows, tpb.cols, 0, 0, coef}});
         }
       }
     }
-  }, U);
-  std::vector<GemmTask>& t1 = U.t1;
-  std::vector<GemmGroup>& g1 = U.g1;
-  const int64_t zsize = U.zsize;
+  }
+  upd_hint_z_ = t1.size();
+  upd_hint_out_ = out2.size();
   double* Z = (double*)dev_alloc(sizeof(double) * std::max<int64_t>(zsize, 1), stream_);
-  for (size_t z = 0; z < g1.size(); ++z) g1[z].C = Z + U.zoff[z];
+  for (size_t z = 0; z < g1.size(); ++z) g1[z].C = Z + zs[z].off;
   dev_zero(Z, sizeof(double) * std::max<int64_t>(zsize, 1), stream_);
   std::vector<GemmGroup> g2;
   {
-    const std::vector<int64_t>& zoff = U.zoff;
+    std::vector<int64_t> zoff(zs.size());
+    for (size_t z = 0; z < zs.size(); ++z) zoff[z] = zs[z].off;
     std::vector<std::pair<int, int>> at(bbase.back());  // output index -> (op, block)
     for (size_t o = 0; o + 1 < bbase.size(); ++o)
       for (int64_t b = bbase[o]; b < bbase[o + 1]; ++b) at[b] = {(int)o, (int)(b - bbase[o])};
-    group_by_output(U.out2, bbase.back(), Z, zoff,
+    group_by_output(out2, bbase.back(), Z, zoff,
                     [&](int64_t id, int b0, int b1, std::vector<GemmGroup>& g) {
                       const BlockRef& ob = E.blocks[at[id].first][at[id].second];
                       g.push_back({E.data + ob.off, ob.cols, ob.rows, ob.cols, b0, b1, 0});

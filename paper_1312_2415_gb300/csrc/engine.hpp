@@ -251,6 +251,9 @@ class Engine {
   std::vector<Site> sites_;
   std::vector<OpStore> lenv_, renv_;
   uint64_t env_serial_ = 0;
+  // table sizes of the last operator update (block products, and their outputs): the next
+  // update reserves that much, since neighbouring bonds have tables of similar size
+  size_t upd_hint_z_ = 0, upd_hint_out_ = 0;
   std::vector<LowState> low_;
   std::vector<int> sched_D_, sched_nmax_;
   std::vector<double> sched_econv_, sched_noise_;
